@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark of the fast-electron hybrid-PIC step on one GB300.
+
+Workload: 128^3 cells of 1 um gold, 1e7 macro-electrons injected over
+100 fs at 1e21 W/cm^2 (T_hot = 13.7 MeV), dt = 0.5 fs, reflux on all faces;
+the 200-step injection runs before timing, then K steps are timed with the
+full population resident in HBM.  One step = push/collide/emit/deposit,
+E and B update, heating, (injection), and the cell sort every 20 steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+    python bench.py --impl reference ...   # the FP64 CPU oracle, timed alone
+
+With N > 1 (torchrun), every rank runs an independent replica of the
+workload (the step has no exchange to shard): value = all ranks'
+particle-steps over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fast-electron particle-steps/s at 1e7 e-, FP32 vs FP64, CE(>1MeV) within 1%"
+UNIT = "particle-steps/s"
+WORKLOAD = ("128^3 cells x 1 um Au (Z=79, n_i=5.9e28 m^-3, T0=1 eV), 1e7 e- injected over "
+            "100 fs at 1e21 W/cm^2 in a 5 um disc, 30 deg cone, dt=0.5 fs, reflux on all faces, "
+            "timed after the injection window")
+# algorithmic bytes per particle-step of the push kernel: the SoA state is
+# read once (x,y,z,ux,uy,uz,tau + u32 id) and written once (7 reals)
+ALG_BYTES = {"fp32": 7 * 4 + 4 + 7 * 4, "fp64": 7 * 8 + 4 + 7 * 8}
+SORT_INTERVAL = 20
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "of measured"}
+    return {"hbm_gbs": 6800.0, "source": "of fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("HPIC_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce(world, vals, op="max"):
+    if world == 1:
+        return vals
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vals, dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return t.tolist()
+
+
+def oracle_rate(steps_timed: int, warmup: int, budget_s: float) -> dict:
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    the same 128^3 target and laser, stepped from t = 0 through the start of
+    the injection window (5e4 new electrons per step), every step including
+    the full 128^3 field and heating update.  Serial: one host core."""
+    from oracle import oracle as O
+    from paper_2107_01723_gb300 import workloads as W
+    cfg = W.config2()
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    o.step(max(warmup, 1))
+    ps0 = o.tallies()["particle_steps"]
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps_timed:
+        o.step(1)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    ps = o.tallies()["particle_steps"] - ps0
+    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle steps {max(warmup, 1)}..{max(warmup, 1) + done - 1} of the headline "
+                       f"workload (injection phase, {int(ps / max(done, 1))} live e- per step on "
+                       f"average, full 128^3 field/heat update each step), serial FP64, {dt:.1f} s"),
+            "steps_timed": done, "seconds": dt}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    r = oracle_rate(args.steps, args.warmup, budget_s=150.0)
+    line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * r["seconds"] / max(r["steps_timed"], 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 oracle"},
+            "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2107_01723_gb300 import build as B
+    from paper_2107_01723_gb300 import hpic
+    from paper_2107_01723_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    barrier(world)
+    cfg = W.config2()
+    run = dict(cfg["run"], target_index=rank)
+    prec = hpic.HPIC_FP32_MIXED if args.precision == "fp32" else hpic.HPIC_FP64
+    stream = torch.cuda.Stream()
+    sim = hpic.Sim(cfg["target"], cfg["laser"], run, precision=prec, device=local,
+                   stream=stream.cuda_stream, sort_interval=SORT_INTERVAL)
+    # setup: the injection window (200 steps) builds the 1e7-electron state
+    sim.step(200)
+    sim.step(args.warmup)
+    live = sim.n
+    t0 = sim.tallies()
+    launches0 = hpic.hpic_launch_count(sim.h)
+    hpic.hpic_profile(sim.h, True)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler()
+    clocks.start()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    sim.step(args.steps)
+    end.record(stream)
+    end.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = start.elapsed_time(end)
+    t1 = sim.tallies()
+    k_ms, k_launches, k_ps = hpic.hpic_kernel_time(sim.h)
+    hpic.hpic_profile(sim.h, False)
+    launches = hpic.hpic_launch_count(sim.h) - launches0
+    ps = t1["particle_steps"] - t0["particle_steps"]
+    ms_max, = allreduce(world, [ms], "max")
+    ps_sum, = allreduce(world, [ps], "sum")
+    value = ps_sum / (ms_max / 1e3)
+
+    # end to end through the C-ABI with host buffers: upload the state from
+    # host arrays, K steps, read tallies and the state back
+    host = sim.particles()
+    nbytes_state = len(host["id"]) * (7 * (4 if args.precision == "fp32" else 8) + 4)
+    torch.cuda.synchronize()
+    barrier(world)
+    w0 = time.perf_counter()
+    e_t0 = sim.tallies()
+    sim.set_particles(host)
+    sim.step(args.steps)
+    e_t1 = sim.tallies()
+    back = sim.particles()
+    wall = time.perf_counter() - w0
+    e_ps = e_t1["particle_steps"] - e_t0["particle_steps"]
+    wall_max, = allreduce(world, [wall], "max")
+    e_ps_sum, = allreduce(world, [e_ps], "sum")
+    tally_bytes = 19 * 8
+    e2e = {"value": e_ps_sum / wall_max, "unit": UNIT,
+           "h2d_bytes_per_step": nbytes_state / args.steps,
+           "d2h_bytes_per_step": (len(back["id"]) * (7 * (4 if args.precision == "fp32" else 8) + 4)
+                                  + 2 * tally_bytes) / args.steps,
+           "what": ("hpic_load_particles from host arrays + hpic_step(K) + hpic_read_tallies + "
+                    "hpic_read_particles to host, wall clock")}
+
+    # FP64 reference path on the same workload (shorter run), for "FP32 vs FP64"
+    fp64 = None
+    if args.precision == "fp32" and not args.no_fp64 and world == 1:
+        s64 = hpic.Sim(cfg["target"], cfg["laser"], run, precision=hpic.HPIC_FP64, device=local,
+                       stream=stream.cuda_stream, sort_interval=SORT_INTERVAL)
+        s64.step(200 + args.warmup)
+        k64 = max(args.steps // 4, 10)
+        a0 = s64.tallies()["particle_steps"]
+        hpic.hpic_profile(s64.h, True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64.step(k64)
+        e1.record(stream)
+        e1.synchronize()
+        m64 = e0.elapsed_time(e1)
+        a1 = s64.tallies()["particle_steps"]
+        km, kl, kp = hpic.hpic_kernel_time(s64.h)
+        fp64 = {"value": (a1 - a0) / (m64 / 1e3), "unit": UNIT, "steps": k64,
+                "ms_per_step": m64 / k64,
+                "push_kernel_gbs": ALG_BYTES["fp64"] * kp / (km / 1e3) / 1e9 if km > 0 else None}
+        s64.close()
+
+    if rank != 0:
+        sim.close()
+        return
+    pk = peaks()
+    k_avg_ms = k_ms / max(k_launches, 1)
+    achieved = ALG_BYTES[args.precision] * (k_ps / max(k_launches, 1)) / (k_avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "kernel": "k_push (push/collide/emit/deposit)",
+                "kernel_ms_avg": k_avg_ms, "kernel_share_of_step": k_ms / ms if ms > 0 else None,
+                "bytes_per_particle_step": ALG_BYTES[args.precision], "peak_source": pk["source"]}
+    cpu = None
+    if not args.no_cpu_baseline:
+        r = oracle_rate(12, 2, budget_s=25.0)
+        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD,
+                       "precision": ("fp32-mixed: particles and fields f32; T, eta, tallies f64"
+                                     if args.precision == "fp32" else "fp64 throughout"),
+                       "sort_interval": SORT_INTERVAL, "live_electrons_at_start": live,
+                       "l2": "inputs larger than L2 (particle state >= 320 MB per step)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "fp64": fp64}
+    print(json.dumps(line), flush=True)
+    sim.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        # the oracle runs on rank 0 only; other ranks exit without work
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+        return
+    world, rank, local = dist_setup()
+    run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

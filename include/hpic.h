@@ -1,0 +1,230 @@
+/*
+ * hpic.h -- C-ABI of the GB300 fast-electron hybrid-PIC step.
+ *
+ * Method: Morris, Robinson & Ridgers, "Highly efficient conversion of laser
+ * energy to hard X-rays in high intensity laser-solid simulations",
+ * arXiv 2107.01723.  One step advances the hot electrons of one target
+ * through the resistive fields of the cold solid and updates the solid:
+ *   - relativistic push in E, B (Lorentz force; Sec. III.B, field loss),
+ *   - ionisation drag, Eq. (5) (Sec. III.B),
+ *   - Davies elastic scatter, Eq. (B4) (App. B),
+ *   - optical-depth bremsstrahlung emission with photon tallies (App. B),
+ *   - escape / reflux at the target faces (Sec. II.A, Table I),
+ *   - hot-electron current deposit and the hybrid field solve
+ *     E = eta (curl B / mu0 - j_h), dB/dt = -curl E, Eqs. (A1)-(A3),
+ *   - Ohmic + ionisation heating, Eqs. (A7)-(A8), and the resistivity
+ *     eta(T) of Eqs. (A4)-(A6),
+ *   - injection of new hot electrons, Eq. (B1) and Sec. II.B.
+ *
+ * Conventions for every function:
+ *   - Returns an hpic_status (0 = success).  Nothing aborts or throws across
+ *     this boundary.  On failure hpic_last_error() describes the cause.
+ *   - Host pointers are caller-owned; the library copies what it needs and
+ *     keeps no host pointer after a call returns.  All device memory is
+ *     allocated, owned and freed by the library.
+ *   - All work is enqueued on the context's CUDA stream (the one passed at
+ *     creation, or the legacy default stream if NULL).  hpic_step returns
+ *     once the work is enqueued; every hpic_read_* call synchronises that
+ *     stream before it returns.
+ *   - A context may be used from one host thread at a time.
+ *   - Units are SI at the interface (m, s, J, K, V/m, T, A/m^2, Ohm m),
+ *     except particle momentum, given as u = p / (m_e c).
+ *
+ * Grid layout (Yee staggering, the reading used throughout): the target is
+ * nx*ny*nz cubic cells of side dx.  Each vector component (E, B, j_h) is an
+ * (nx+1)*(ny+1)*(nz+1) array of doubles, index i + (nx+1)*(j + (ny+1)*k),
+ * located at (in cells) Ex (i+1/2, j, k), Ey (i, j+1/2, k), Ez (i, j, k+1/2),
+ * Bx (i, j+1/2, k+1/2), By (i+1/2, j, k+1/2), Bz (i+1/2, j+1/2, k); entries
+ * beyond a staggered extent are padding (zero).  Cell scalars (T, eta, drag
+ * heat) are nx*ny*nz doubles, index i + nx*(j + ny*k).
+ */
+#ifndef HPIC_H
+#define HPIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HPIC_OK = 0,
+  HPIC_EINVAL = -1,    /* an argument is out of range or inconsistent */
+  HPIC_ENOMEM = -2,    /* a device or host allocation failed */
+  HPIC_ECUDA = -3,     /* a CUDA call failed (message in hpic_last_error) */
+  HPIC_ETIMEOUT = -4,  /* a bounded device wait gave up */
+  HPIC_ESTATE = -5,    /* call not allowed in the context's current state */
+  HPIC_ENONFINITE = -6 /* non-finite particle state was found and removed */
+} hpic_status;
+
+typedef enum { HPIC_FP64 = 0, HPIC_FP32_MIXED = 1 } hpic_precision;
+
+/* physics switches for hpic_run_params.physics (bitmask) */
+enum {
+  HPIC_DRAG = 1,     /* ionisation drag, Eq. (5) */
+  HPIC_SCATTER = 2,  /* Davies scatter, Eq. (B4) */
+  HPIC_BREM = 4,     /* bremsstrahlung emission, App. B */
+  HPIC_FIELDS = 8,   /* E from Eq. (A2) every step (else E is held) */
+  HPIC_FARADAY = 16, /* B from Eq. (A3) every step (else B is held: the
+                        paper's B = 0 test, Sec. III.A) */
+  HPIC_HEATING = 32, /* T and eta update, Eqs. (A4)-(A8) */
+  HPIC_ALL = 63
+};
+
+/* grid codes for hpic_read_grid / hpic_write_grid */
+enum {
+  HPIC_GRID_T = 0, HPIC_GRID_ETA = 1,
+  HPIC_GRID_EX = 2, HPIC_GRID_EY = 3, HPIC_GRID_EZ = 4,
+  HPIC_GRID_BX = 5, HPIC_GRID_BY = 6, HPIC_GRID_BZ = 7,
+  HPIC_GRID_JX = 8, HPIC_GRID_JY = 9, HPIC_GRID_JZ = 10,
+  HPIC_GRID_HEAT = 11 /* drag heat (J) deposited per cell in the last step */
+};
+
+/* One target: a uniform single-element solid filling the box (App. A). */
+typedef struct {
+  int32_t nx, ny, nz;   /* cells, each >= 2 */
+  double dx_m;          /* cell side; must exceed c * dt */
+  double Z;             /* atomic number */
+  double n_i_m3;        /* ion number density */
+  double I_ex_J;        /* mean excitation energy (the paper uses 11 eV * Z) */
+  double Zstar;         /* ionisation state in eta, Eq. (A4) */
+  double lnLambda;      /* Coulomb logarithm in Eq. (A5) */
+  double eta_max_ohm_m; /* cap on eta */
+  double lambda1;       /* cold-limit factor of Eq. (A6); 0 drops that limit */
+  double lambda2;       /* multiplier on eta (App. A) */
+  double T0_K;          /* initial background temperature */
+} hpic_target_desc;
+
+/* Laser and injection, Eq. (1), Eq. (B1), Sec. II.B, with flat-top
+ * envelopes: a disc of radius spot_radius_m centred at (0, spot_y, spot_z)
+ * for t < t_inj_s. */
+typedef struct {
+  double I0_Wm2;        /* peak intensity, W m^-2 (1e20 W/cm^2 = 1e24) */
+  double lambda_m;      /* wavelength */
+  double eta_l2e;       /* laser -> hot electron energy efficiency */
+  double spot_radius_m;
+  double spot_y_m, spot_z_m;
+  double t_inj_s;       /* injection window */
+  double cone_half_angle_rad; /* uniform in solid angle within this cone */
+  int64_t n_macro;      /* macro-electrons over the whole window (< 2^32-1) */
+} hpic_laser_desc;
+
+typedef struct {
+  double dt_s;          /* time step */
+  uint64_t seed;        /* Philox4x32-10 key */
+  uint32_t target_index;/* fourth Philox counter word */
+  int32_t precision;    /* hpic_precision */
+  double kappa_esc;     /* escape energy kappa_esc a0 m_e c^2 (Sec. II.A) */
+  double kappa_tnsa;    /* reflux |p| loss kappa_tnsa a0 m_e c (Sec. II.A) */
+  double sigma_dtheta_rad; /* reflux scatter range +-sigma/2 (Sec. II.A) */
+  double brem_boost;    /* cross-section boost B; photon weight w/B (Sec. II.B) */
+  double k_min_J;       /* lowest photon energy modelled */
+  double E_cut_J;       /* tracking cut: electrons below it are absorbed */
+  int32_t n_Ebins, n_thbins; /* photon tally: log energy x polar angle */
+  double tally_Emin_J, tally_Emax_J;
+  double ce_threshold_J;/* X-ray threshold (1 MeV in the paper) */
+  int32_t table_rows, table_cols; /* inverse-CDF photon table */
+  double table_Emax_J;  /* top electron energy of the table */
+  int32_t curlB_term;   /* 1: E = eta(curl B/mu0 - j_h) (Eq. A2); 0: E = -eta j_h */
+  int32_t physics;      /* HPIC_* bitmask */
+  int32_t sort_interval;/* steps between cell sorts (0 = never) */
+  int32_t max_history;  /* length of the per-step X-ray history */
+} hpic_run_params;
+
+/* Energy-budget and event tallies (all FP64).  Budget identity, closed by
+ * construction: E_injected = E_live + W_field + E_drag + E_xray
+ *                            + E_escaped + E_reflux. */
+typedef struct {
+  double E_injected, N_injected; /* injected energy (J) and real electrons */
+  double W_field;       /* energy lost by electrons to E (J; gain < 0) */
+  double E_drag;        /* ionisation heat incl. absorbed electrons (J) */
+  double E_xray;        /* photon energy, all k >= k_min (J) */
+  double E_xray_above;  /* photon energy with k >= ce_threshold (J) */
+  double E_escaped;     /* energy of escaped electrons (J) */
+  double E_reflux;      /* energy lost in reflux events (J) */
+  double E_ohmic_grid;  /* sum eta j_h.j_h dt V over cells and steps (J) */
+  double n_injected, n_escaped, n_refluxed, n_reflux_absorbed;
+  double n_cut, n_emitted, particle_steps;
+  double n_nonfinite;   /* particles removed for non-finite state */
+  double E_live;        /* kinetic energy of live electrons now (J) */
+  double E_B_field;     /* magnetic energy sum B^2/(2 mu0) V now (J) */
+} hpic_tallies;
+
+typedef struct hpic_ctx hpic_ctx;
+
+/* Create a context for one target on `device`, with work on `cuda_stream`
+ * (a cudaStream_t, or NULL).  Builds the photon inverse-CDF table on the
+ * device, sets T = T0 and eta = eta(T0) everywhere, E = B = 0, no electrons.
+ * Errors: HPIC_EINVAL (dx <= c dt, a dimension < 2, bad bins or table),
+ * HPIC_ENOMEM, HPIC_ECUDA.  *out is NULL on failure. */
+int hpic_init_target(hpic_ctx **out, const hpic_target_desc *target,
+                     const hpic_run_params *run, int device, void *cuda_stream);
+
+/* Schedule injection (Eq. (B1), Sec. II.B): step s < t_inj/dt injects
+ * floor((s+1) N/S) - floor(s N/S) electrons at x = 1e-6 dx, with energies
+ * exponential of mean a0 m_e c^2, disc positions and cone directions
+ * uniform; they first move in the next step.  Reserves device room for
+ * n_macro more electrons.  Errors: HPIC_EINVAL, HPIC_ENOMEM, HPIC_ESTATE
+ * (a laser was already scheduled). */
+int hpic_inject_electrons(hpic_ctx *ctx, const hpic_laser_desc *laser);
+
+/* Advance n_steps >= 0 steps (asynchronous).  Errors: HPIC_EINVAL, HPIC_ECUDA. */
+int hpic_step(hpic_ctx *ctx, int64_t n_steps);
+
+/* Counting sort of the electrons by cell; drops absorbed/escaped slots.
+ * Also run every sort_interval steps inside hpic_step.  Asynchronous. */
+int hpic_sort(hpic_ctx *ctx);
+
+/* Tallies accumulated since creation or the last reset (synchronises). */
+int hpic_read_tallies(hpic_ctx *ctx, hpic_tallies *out);
+int hpic_reset_tallies(hpic_ctx *ctx);
+/* Photon histograms, (n_Ebins + 2) rows (underflow, bins, overflow) x
+ * n_thbins, row-major; energy-weighted (J) and number-weighted (photons).
+ * Either pointer may be NULL.  Polar angle is measured from +x. */
+int hpic_read_hist(hpic_ctx *ctx, double *energy_weighted, double *number_weighted);
+/* Per-step X-ray energy above ce_threshold, max_history doubles. */
+int hpic_read_history(hpic_ctx *ctx, double *out);
+
+/* Number of doubles in grid `which` (see the layout above). */
+int hpic_grid_len(const hpic_ctx *ctx, int which, int64_t *len);
+int hpic_read_grid(hpic_ctx *ctx, int which, double *host_out);
+/* Overwrite a grid from host doubles (state restore, tests).  Writing T or
+ * eta does not recompute the other. */
+int hpic_write_grid(hpic_ctx *ctx, int which, const double *host_in);
+
+/* Live electrons (synchronises). */
+int hpic_count_particles(hpic_ctx *ctx, int64_t *n);
+/* Copy live electrons out in storage order: positions (m), u = p/(m_e c),
+ * remaining optical depth tau, id.  Fails with HPIC_EINVAL if cap is less
+ * than the live count; *n receives the count. */
+int hpic_read_particles(hpic_ctx *ctx, double *x, double *y, double *z,
+                        double *ux, double *uy, double *uz, double *tau,
+                        uint32_t *id, int64_t cap, int64_t *n);
+/* Replace the electron population with n host electrons (same units).
+ * Positions must lie in [0, n*dx] on each axis.  Errors: HPIC_EINVAL,
+ * HPIC_ENOMEM. */
+int hpic_load_particles(hpic_ctx *ctx, int64_t n, const double *x, const double *y,
+                        const double *z, const double *ux, const double *uy,
+                        const double *uz, const double *tau, const uint32_t *id);
+/* Step counter (the Philox counter word) and the next injection id. */
+int hpic_get_clock(hpic_ctx *ctx, int64_t *step, int64_t *next_id);
+int hpic_set_clock(hpic_ctx *ctx, int64_t step, int64_t next_id);
+
+/* Kernel timing of the particle push/collide/emit/deposit kernel: when
+ * enabled, CUDA events bracket each of its launches on the context stream.
+ * hpic_kernel_time returns the summed device time (ms), the launch count
+ * and the particle-steps those launches processed, then clears them. */
+int hpic_profile(hpic_ctx *ctx, int enable);
+int hpic_kernel_time(hpic_ctx *ctx, double *ms, int64_t *launches, double *particle_steps);
+
+/* Kernels launched by this context since creation (all kinds). */
+int hpic_launch_count(const hpic_ctx *ctx, int64_t *launches);
+
+int hpic_destroy(hpic_ctx *ctx);
+/* Last error of ctx, or of the last failed creation when ctx is NULL. */
+const char *hpic_last_error(const hpic_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

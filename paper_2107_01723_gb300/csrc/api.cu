@@ -1,0 +1,847 @@
+// Host side of the C-ABI in include/hpic.h: context, device buffers, the
+// folding of the paper's SI coefficients into normalised kernel constants,
+// and the per-step launch sequence.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hpic.h"
+#include "kernels.h"
+
+namespace {
+
+// CODATA 2018 SI values; mu0 taken as 1/(eps0 c^2)
+constexpr double QE = 1.602176634e-19;
+constexpr double ME = 9.1093837015e-31;
+constexpr double CL = 299792458.0;
+constexpr double EPS0 = 8.8541878128e-12;
+constexpr double HPL = 6.62607015e-34;
+constexpr double KB = 1.380649e-23;
+constexpr double PI = 3.14159265358979323846;
+constexpr double HBAR = HPL / (2.0 * PI);
+constexpr double MU0 = 1.0 / (EPS0 * CL * CL);
+constexpr double MC2 = ME * CL * CL;
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct hpic_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  hpic_target_desc tgt{};
+  hpic_run_params run{};
+  hpic_laser_desc laser{};
+  bool have_laser = false;
+  bool fp32 = false;
+  size_t rsz = 8;  // bytes per particle/field real
+  hpic::Consts K{};
+  int sm_count = 1;
+  // particles: two SoA buffers (the sort ping-pongs between them)
+  long long cap = 0;
+  long long stride = 0;  // elements per array inside a buffer
+  void *pbuf[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint32_t *keys = nullptr;
+  uint32_t *counts = nullptr;
+  uint32_t *partials = nullptr;
+  // grid
+  void *fields = nullptr;  // E[3], B[3], J[3] of R, each nvec
+  double *T = nullptr, *eta = nullptr, *H = nullptr;
+  // tallies and tables
+  double *tal = nullptr, *hist = nullptr, *history = nullptr, *scratch = nullptr;
+  double *t64 = nullptr;
+  float *t32 = nullptr;
+  hpic::Counters *cnt = nullptr;
+  long long host_step = 0;
+  long long launches = 0;
+  // profiling of the particle kernel
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  long long prof_launches = 0;
+  double prof_ps0 = 0.0;
+  std::string err;
+};
+
+namespace {
+
+int fail(hpic_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg; else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(hpic_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, HPIC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                        \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);            \
+  } while (0)
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+int n_rows(const hpic_ctx *c) { return c->run.n_Ebins + 2; }
+long long hist_len(const hpic_ctx *c) { return (long long)n_rows(c) * c->run.n_thbins; }
+
+template <typename R>
+hpic::PView<R> pview(const hpic_ctx *c, int which) {
+  char *b = static_cast<char *>(c->pbuf[which]);
+  const size_t s = (size_t)c->stride * sizeof(R);
+  hpic::PView<R> v;
+  v.x = reinterpret_cast<R *>(b);
+  v.y = reinterpret_cast<R *>(b + s);
+  v.z = reinterpret_cast<R *>(b + 2 * s);
+  v.ux = reinterpret_cast<R *>(b + 3 * s);
+  v.uy = reinterpret_cast<R *>(b + 4 * s);
+  v.uz = reinterpret_cast<R *>(b + 5 * s);
+  v.tau = reinterpret_cast<R *>(b + 6 * s);
+  v.id = reinterpret_cast<uint32_t *>(b + 7 * s);
+  return v;
+}
+
+template <typename R>
+hpic::GView<R> gview(const hpic_ctx *c) {
+  hpic::GView<R> g;
+  R *f = static_cast<R *>(c->fields);
+  const long long nv = c->K.nvec;
+  for (int a = 0; a < 3; ++a) {
+    g.E[a] = f + a * nv;
+    g.B[a] = f + (3 + a) * nv;
+    g.J[a] = f + (6 + a) * nv;
+  }
+  g.T = c->T;
+  g.eta = c->eta;
+  g.H = c->H;
+  return g;
+}
+
+hpic::TallyView tview(const hpic_ctx *c) { return hpic::TallyView{c->tal, c->hist, c->history}; }
+
+int grid_blocks(const hpic_ctx *c, long long work) {
+  const long long want = (work + 255) / 256;
+  const long long cap = (long long)c->sm_count * 8;
+  long long g = want < cap ? want : cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+size_t particle_bytes(const hpic_ctx *c, long long stride) {
+  return (size_t)stride * (7 * c->rsz + sizeof(uint32_t));
+}
+
+int read_counters(hpic_ctx *ctx, hpic::Counters *h) {
+  CK(cudaMemcpyAsync(h, ctx->cnt, sizeof(*h), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return HPIC_OK;
+}
+
+int write_counters(hpic_ctx *ctx, const hpic::Counters *h) {
+  CK(cudaMemcpyAsync(ctx->cnt, h, sizeof(*h), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return HPIC_OK;
+}
+
+// grow particle storage to hold `need` slots, keeping the first n
+int reserve(hpic_ctx *ctx, long long need) {
+  if (need <= ctx->cap) return HPIC_OK;
+  hpic::Counters h;
+  int rc = read_counters(ctx, &h);
+  if (rc) return rc;
+  const long long cap = round_up(need < 1024 ? 1024 : need, 64);
+  void *nb[2] = {nullptr, nullptr};
+  uint32_t *nk = nullptr;
+  for (int b = 0; b < 2; ++b) {
+    if (cudaMalloc(&nb[b], particle_bytes(ctx, cap)) != cudaSuccess) {
+      cudaGetLastError();
+      if (nb[0]) cudaFree(nb[0]);
+      return fail(ctx, HPIC_ENOMEM, "particle storage allocation failed");
+    }
+  }
+  if (cudaMalloc(&nk, cap * sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(nb[0]);
+    cudaFree(nb[1]);
+    return fail(ctx, HPIC_ENOMEM, "sort key allocation failed");
+  }
+  if (ctx->pbuf[ctx->cur] && h.n > 0) {
+    const size_t so = (size_t)ctx->stride, sn = (size_t)cap;
+    char *src = static_cast<char *>(ctx->pbuf[ctx->cur]);
+    char *dst = static_cast<char *>(nb[0]);
+    for (int a = 0; a < 7; ++a)
+      CK(cudaMemcpyAsync(dst + a * sn * ctx->rsz, src + a * so * ctx->rsz, h.n * ctx->rsz,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dst + 7 * sn * ctx->rsz, src + 7 * so * ctx->rsz, h.n * sizeof(uint32_t),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  cudaFree(ctx->pbuf[0]);
+  cudaFree(ctx->pbuf[1]);
+  cudaFree(ctx->keys);
+  ctx->pbuf[0] = nb[0];
+  ctx->pbuf[1] = nb[1];
+  ctx->keys = nk;
+  ctx->cur = 0;
+  ctx->cap = cap;
+  ctx->stride = cap;
+  return HPIC_OK;
+}
+
+// fold the paper's SI coefficients into normalised kernel constants
+void fold_constants(hpic_ctx *c) {
+  const hpic_target_desc &t = c->tgt;
+  const hpic_run_params &r = c->run;
+  hpic::Consts &K = c->K;
+  const double dx = t.dx_m, dt = r.dt_s, Z = t.Z, ni = t.n_i_m3;
+  K.nx = t.nx; K.ny = t.ny; K.nz = t.nz;
+  K.nvec = (long long)(t.nx + 1) * (t.ny + 1) * (t.nz + 1);
+  K.ncell = (long long)t.nx * t.ny * t.nz;
+  K.cdt_dx = CL * dt / dx;
+  // Eq. (5): S v dt = Z n_i e^4 dt / (4 pi eps0^2 m_e v) [bracket]
+  K.K_ion = Z * ni * std::pow(QE, 4) * dt / (4.0 * PI * EPS0 * EPS0 * ME * CL) / MC2;
+  K.L_I = std::log(MC2 / t.I_ex_J);
+  // Eq. (B4) with p = m_e c u
+  K.K_sc = Z * Z * std::pow(QE, 4) * ni * dt / (2.0 * PI * EPS0 * EPS0 * ME * ME * std::pow(CL, 3));
+  K.K_lg = 4.0 * EPS0 * HPL * CL / (std::cbrt(Z) * QE * QE);
+  // Eq. (4) per unit gamma; sigma_tot n_i v dt = boost Kb c dt/mc2 * (u/eps) G(u0)
+  const double Lrad = std::log(5.6 * PI * EPS0 * HBAR * CL / (std::cbrt(Z) * QE * QE));
+  const double Kb = std::pow(QE, 6) * ni * Z * Z * Lrad /
+                    (12.0 * PI * PI * PI * std::pow(EPS0, 3) * ME * std::pow(CL, 3) * HBAR);
+  K.K_tau = r.brem_boost * Kb * CL * dt / MC2;
+  K.k_min = r.k_min_J / MC2;
+  K.boost = r.brem_boost;
+  K.inv_boost = 1.0 / r.brem_boost;
+  K.E_cut = r.E_cut_J / MC2;
+  K.sigma_dtheta = r.sigma_dtheta_rad;
+  K.n_E = r.n_Ebins;
+  K.n_th = r.n_thbins;
+  K.tE_min = r.tally_Emin_J / MC2;
+  K.tE_max = r.tally_Emax_J / MC2;
+  K.inv_dlogE = r.n_Ebins / std::log(r.tally_Emax_J / r.tally_Emin_J);
+  K.ce_thr = r.ce_threshold_J / MC2;
+  K.max_history = r.max_history;
+  K.t_rows = r.table_rows;
+  K.t_cols = r.table_cols;
+  K.t_inv_dlog = (r.table_rows - 1) / std::log(r.table_Emax_J / r.k_min_J);
+  // Eqs. (A2)-(A3) in normalised fields
+  K.F_curl = r.curlB_term ? 1.0 / (CL * dx * MU0) : 0.0;
+  K.F_j = QE * QE * dt / (ME * dx * dx * dx);
+  // Eqs. (A4)-(A8)
+  K.F_ohm = std::pow(QE * CL / (dx * dx * dx), 2) * dt;
+  K.F_H = MC2 / (dx * dx * dx);
+  K.dx3 = dx * dx * dx;
+  K.heat_den = Z * ni * KB;
+  K.Tp_fac = (KB / QE) * std::pow(Z, -4.0 / 3.0);
+  K.eta_num = t.lambda2 * ME / (t.Zstar * ni * QE * QE);
+  K.A_hot = 128.0 * PI * EPS0 * EPS0 / (3.0 * std::pow(QE, 4)) * std::sqrt(ME / (2.0 * PI)) /
+            (t.Zstar * t.Zstar * ni * t.lnLambda);
+  K.B_cold = std::cbrt(3.0 / (4.0 * PI * ni)) * t.lambda1 * std::sqrt(ME / 3.0);
+  K.eta_max = t.eta_max_ohm_m;
+  K.lambda1 = t.lambda1;
+  K.key0 = (uint32_t)(r.seed & 0xFFFFFFFFull);
+  K.key1 = (uint32_t)(r.seed >> 32);
+  K.target_index = r.target_index;
+  K.physics = r.physics;
+  // laser-dependent terms; without a laser a0 = 0 and the weight is 1
+  double a0 = 0.0, w = 1.0;
+  if (c->have_laser) {
+    const hpic_laser_desc &l = c->laser;
+    a0 = 8.5e-6 * std::sqrt(l.I0_Wm2 * l.lambda_m * l.lambda_m);  // Eq. (1)
+    if (l.n_macro > 0 && a0 > 0.0) {
+      const double N_real = l.eta_l2e * l.I0_Wm2 * PI * l.spot_radius_m * l.spot_radius_m *
+                            l.t_inj_s / (a0 * MC2);  // Eq. (B1) summed, flat-top
+      w = N_real / (double)l.n_macro;
+    }
+    K.spot_r = l.spot_radius_m / dx;
+    K.spot_y = l.spot_y_m / dx;
+    K.spot_z = l.spot_z_m / dx;
+    K.cos_cone = std::cos(l.cone_half_angle_rad);
+    K.n_macro = l.n_macro;
+    long long S = std::llround(l.t_inj_s / dt);
+    K.n_inj_steps = S < 1 ? 1 : S;
+  } else {
+    K.n_macro = 0;
+    K.n_inj_steps = 1;
+  }
+  K.w = w;
+  K.T_hot = a0;
+  K.eps_esc = r.kappa_esc * a0;
+  K.du_reflux = r.kappa_tnsa * a0;
+}
+
+double eta_host(const hpic_ctx *c, double T) {
+  const hpic::Consts &K = c->K;
+  const double kT = KB * T;
+  double tau = K.A_hot * kT * std::sqrt(kT);
+  if (K.lambda1 > 0.0) {
+    const double tc = K.B_cold / std::sqrt(kT);
+    tau = tc > tau ? tc : tau;
+  }
+  const double e = K.eta_num / tau;
+  return e < K.eta_max ? e : K.eta_max;
+}
+
+void destroy_all(hpic_ctx *c) {
+  cudaFree(c->pbuf[0]);
+  cudaFree(c->pbuf[1]);
+  cudaFree(c->keys);
+  cudaFree(c->counts);
+  cudaFree(c->partials);
+  cudaFree(c->fields);
+  cudaFree(c->T);
+  cudaFree(c->eta);
+  cudaFree(c->H);
+  cudaFree(c->tal);
+  cudaFree(c->hist);
+  cudaFree(c->history);
+  cudaFree(c->scratch);
+  cudaFree(c->t64);
+  cudaFree(c->t32);
+  cudaFree(c->cnt);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+}
+
+double grid_scale(const hpic_ctx *c, int which) {
+  const double dx = c->tgt.dx_m, dt = c->run.dt_s;
+  switch (which) {
+    case HPIC_GRID_EX: case HPIC_GRID_EY: case HPIC_GRID_EZ: return -ME * CL / (QE * dt);
+    case HPIC_GRID_BX: case HPIC_GRID_BY: case HPIC_GRID_BZ: return -ME / (QE * dt);
+    case HPIC_GRID_JX: case HPIC_GRID_JY: case HPIC_GRID_JZ: return -QE * CL / (dx * dx * dx);
+    case HPIC_GRID_HEAT: return MC2;
+    default: return 1.0;
+  }
+}
+
+template <typename R>
+int step_impl(hpic_ctx *ctx, long long nsteps) {
+  auto P = [&](int b) { return pview<R>(ctx, b); };
+  const hpic::GView<R> G = gview<R>(ctx);
+  const hpic::TallyView tv = tview(ctx);
+  const R *tab = ctx->fp32 ? reinterpret_cast<const R *>(ctx->t32)
+                           : reinterpret_cast<const R *>(ctx->t64);
+  const int gp = grid_blocks(ctx, ctx->cap);
+  const int gg = grid_blocks(ctx, ctx->K.nvec);
+  for (long long s = 0; s < nsteps; ++s) {
+    CK(cudaMemsetAsync(G.J[0], 0, 3 * ctx->K.nvec * ctx->rsz, ctx->stream));
+    CK(cudaMemsetAsync(ctx->H, 0, ctx->K.ncell * sizeof(double), ctx->stream));
+    if (ctx->prof) {
+      if (ctx->ev_used + 2 > ctx->ev.size()) {
+        for (int q = 0; q < 64; ++q) {
+          cudaEvent_t e;
+          CK(cudaEventCreate(&e));
+          ctx->ev.push_back(e);
+        }
+      }
+      CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
+    }
+    hpic::launch_push<R>(ctx->K, P(ctx->cur), G, tab, ctx->cnt, tv, gp, ctx->stream);
+    ctx->launches += 1;
+    if (ctx->prof) {
+      CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
+      ctx->ev_used += 2;
+      ctx->prof_launches += 1;
+    }
+    if (ctx->K.physics & hpic::P_FIELDS) {
+      hpic::launch_efield<R>(ctx->K, G, gg, ctx->stream);
+      ctx->launches += 1;
+    }
+    hpic::launch_bheat<R>(ctx->K, G, tv, gg, ctx->stream);
+    ctx->launches += 1;
+    if (ctx->have_laser && ctx->host_step < ctx->K.n_inj_steps && ctx->K.n_macro > 0) {
+      const long long S = ctx->K.n_inj_steps, N = ctx->K.n_macro, st = ctx->host_step;
+      const long long c = (N * (st + 1)) / S - (N * st) / S;
+      hpic::launch_inject<R>(ctx->K, P(ctx->cur), ctx->cnt, ctx->cap, tv,
+                             grid_blocks(ctx, c > 0 ? c : 1), ctx->stream);
+      ctx->launches += 1;
+    }
+    hpic::launch_advance(ctx->cnt, ctx->cap, ctx->stream);
+    ctx->launches += 1;
+    ctx->host_step += 1;
+    if (ctx->run.sort_interval > 0 && ctx->host_step % ctx->run.sort_interval == 0) {
+      ctx->launches += hpic::launch_sort<R>(ctx->K, P(ctx->cur), P(ctx->cur ^ 1), ctx->cnt,
+                                            ctx->keys, ctx->counts, ctx->partials, gp,
+                                            ctx->stream);
+      ctx->cur ^= 1;
+    }
+    CK(cudaGetLastError());
+  }
+  return HPIC_OK;
+}
+
+template <typename R>
+int sort_impl(hpic_ctx *ctx) {
+  ctx->launches += hpic::launch_sort<R>(ctx->K, pview<R>(ctx, ctx->cur), pview<R>(ctx, ctx->cur ^ 1),
+                                        ctx->cnt, ctx->keys, ctx->counts, ctx->partials,
+                                        grid_blocks(ctx, ctx->cap), ctx->stream);
+  ctx->cur ^= 1;
+  CK(cudaGetLastError());
+  return HPIC_OK;
+}
+
+template <typename R>
+int read_particles_impl(hpic_ctx *ctx, double *x, double *y, double *z, double *ux, double *uy,
+                        double *uz, double *tau, uint32_t *id, int64_t cap, int64_t *n_out) {
+  hpic::Counters h;
+  int rc = read_counters(ctx, &h);
+  if (rc) return rc;
+  const long long n = h.n;
+  std::vector<R> a[7];
+  std::vector<uint32_t> ids(n);
+  const hpic::PView<R> P = pview<R>(ctx, ctx->cur);
+  R *src[7] = {P.x, P.y, P.z, P.ux, P.uy, P.uz, P.tau};
+  for (int q = 0; q < 7; ++q) {
+    a[q].resize(n);
+    if (n) CK(cudaMemcpyAsync(a[q].data(), src[q], n * sizeof(R), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (n) CK(cudaMemcpyAsync(ids.data(), P.id, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  long long live = 0;
+  for (long long i = 0; i < n; ++i) live += ids[i] != hpic::kDead;
+  *n_out = live;
+  if (live > cap) return fail(ctx, HPIC_EINVAL, "output capacity below the live particle count");
+  const double dx = ctx->tgt.dx_m;
+  long long m = 0;
+  for (long long i = 0; i < n; ++i) {
+    if (ids[i] == hpic::kDead) continue;
+    if (x) x[m] = (double)a[0][i] * dx;
+    if (y) y[m] = (double)a[1][i] * dx;
+    if (z) z[m] = (double)a[2][i] * dx;
+    if (ux) ux[m] = (double)a[3][i];
+    if (uy) uy[m] = (double)a[4][i];
+    if (uz) uz[m] = (double)a[5][i];
+    if (tau) tau[m] = (double)a[6][i];
+    if (id) id[m] = ids[i];
+    ++m;
+  }
+  return HPIC_OK;
+}
+
+template <typename R>
+int load_particles_impl(hpic_ctx *ctx, int64_t n, const double *x, const double *y,
+                        const double *z, const double *ux, const double *uy, const double *uz,
+                        const double *tau, const uint32_t *id) {
+  const double dx = ctx->tgt.dx_m;
+  const int nn[3] = {ctx->tgt.nx, ctx->tgt.ny, ctx->tgt.nz};
+  const double *pos[3] = {x, y, z};
+  for (int64_t i = 0; i < n; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      const double X = pos[a][i] / dx;
+      if (!(X >= 0.0 && X <= (double)nn[a]))
+        return fail(ctx, HPIC_EINVAL, "particle position outside the target");
+    }
+    if (id[i] == hpic::kDead) return fail(ctx, HPIC_EINVAL, "id 0xFFFFFFFF is reserved");
+  }
+  const long long extra = ctx->have_laser ? ctx->K.n_macro : 0;
+  int rc = reserve(ctx, n + extra);
+  if (rc) return rc;
+  const hpic::PView<R> P = pview<R>(ctx, ctx->cur);
+  R *dst[7] = {P.x, P.y, P.z, P.ux, P.uy, P.uz, P.tau};
+  const double *src[7] = {x, y, z, ux, uy, uz, tau};
+  std::vector<R> buf(n);
+  for (int q = 0; q < 7; ++q) {
+    const double s = q < 3 ? 1.0 / dx : 1.0;
+    for (int64_t i = 0; i < n; ++i) buf[i] = (R)(src[q][i] * s);
+    if (n) CK(cudaMemcpyAsync(dst[q], buf.data(), n * sizeof(R), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (n) CK(cudaMemcpyAsync(P.id, id, n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+  hpic::Counters h;
+  rc = read_counters(ctx, &h);
+  if (rc) return rc;
+  h.n = n;
+  return write_counters(ctx, &h);
+}
+
+bool valid_grid(int which) { return which >= HPIC_GRID_T && which <= HPIC_GRID_HEAT; }
+
+}  // namespace
+
+extern "C" {
+
+int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_params *r,
+                     int device, void *cuda_stream) {
+  if (!out) return fail(nullptr, HPIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!t || !r) return fail(nullptr, HPIC_EINVAL, "target or run params NULL");
+  if (t->nx < 2 || t->ny < 2 || t->nz < 2) return fail(nullptr, HPIC_EINVAL, "each dimension must be >= 2");
+  if ((long long)t->nx * t->ny * t->nz >= 0xFFFFFFFFll)
+    return fail(nullptr, HPIC_EINVAL, "too many cells for 32-bit sort keys");
+  if (!(t->dx_m > 0) || !(r->dt_s > 0) || CL * r->dt_s >= t->dx_m)
+    return fail(nullptr, HPIC_EINVAL, "need dx > c dt > 0");
+  if (!(t->Z > 0) || !(t->n_i_m3 > 0) || !(t->I_ex_J > 0) || !(t->Zstar > 0) ||
+      !(t->lnLambda > 0) || !(t->eta_max_ohm_m > 0) || !(t->lambda2 > 0) || !(t->T0_K > 0) ||
+      t->lambda1 < 0)
+    return fail(nullptr, HPIC_EINVAL, "material parameters must be positive");
+  if (r->precision != HPIC_FP64 && r->precision != HPIC_FP32_MIXED)
+    return fail(nullptr, HPIC_EINVAL, "unknown precision");
+  if (!(r->brem_boost > 0) || !(r->k_min_J > 0) || !(r->E_cut_J > 0) ||
+      !(r->table_Emax_J > r->k_min_J) || r->table_rows < 2 || r->table_cols < 2 ||
+      r->n_Ebins < 1 || r->n_thbins < 1 || !(r->tally_Emax_J > r->tally_Emin_J) ||
+      !(r->tally_Emin_J > 0) || r->max_history < 0 || r->sort_interval < 0 ||
+      r->kappa_esc < 0 || r->kappa_tnsa < 0 || r->sigma_dtheta_rad < 0 ||
+      (r->physics & ~HPIC_ALL) != 0)
+    return fail(nullptr, HPIC_EINVAL, "run parameters out of range");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return fail(nullptr, HPIC_ECUDA, "no such CUDA device");
+  }
+  hpic_ctx *ctx = new hpic_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->tgt = *t;
+  ctx->run = *r;
+  ctx->fp32 = r->precision == HPIC_FP32_MIXED;
+  ctx->rsz = ctx->fp32 ? 4 : 8;
+  auto bail = [&](int code) {
+    const std::string m = ctx->err;
+    destroy_all(ctx);
+    delete ctx;
+    g_create_error = m;
+    return code;
+  };
+  if (cudaSetDevice(device) != cudaSuccess) { cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice"); return bail(HPIC_ECUDA); }
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  fold_constants(ctx);
+  const hpic::Consts &K = ctx->K;
+  const long long m = K.ncell + 1;
+  const long long ntiles = (m + 4095) / 4096;
+  bool ok = cudaMalloc(&ctx->fields, 9 * K.nvec * ctx->rsz) == cudaSuccess &&
+            cudaMalloc(&ctx->T, K.ncell * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&ctx->eta, K.ncell * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&ctx->H, K.ncell * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&ctx->counts, m * sizeof(uint32_t)) == cudaSuccess &&
+            cudaMalloc(&ctx->partials, (ntiles + 1) * sizeof(uint32_t)) == cudaSuccess &&
+            cudaMalloc(&ctx->tal, hpic::T_COUNT * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&ctx->hist, 2 * hist_len(ctx) * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&ctx->history, (r->max_history > 0 ? r->max_history : 1) * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&ctx->scratch, 2 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&ctx->t64, (size_t)r->table_rows * r->table_cols * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&ctx->t32, (size_t)r->table_rows * r->table_cols * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&ctx->cnt, sizeof(hpic::Counters)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    fail(ctx, HPIC_ENOMEM, "device allocation failed");
+    return bail(HPIC_ENOMEM);
+  }
+  int rc = reserve(ctx, 1024);
+  if (rc) return bail(rc);
+  cudaStream_t st = ctx->stream;
+  std::vector<double> T0(K.ncell, t->T0_K), E0(K.ncell, eta_host(ctx, t->T0_K));
+  if (cudaMemsetAsync(ctx->fields, 0, 9 * K.nvec * ctx->rsz, st) != cudaSuccess ||
+      cudaMemsetAsync(ctx->H, 0, K.ncell * sizeof(double), st) != cudaSuccess ||
+      cudaMemsetAsync(ctx->tal, 0, hpic::T_COUNT * sizeof(double), st) != cudaSuccess ||
+      cudaMemsetAsync(ctx->hist, 0, 2 * hist_len(ctx) * sizeof(double), st) != cudaSuccess ||
+      cudaMemsetAsync(ctx->history, 0, (r->max_history > 0 ? r->max_history : 1) * sizeof(double), st) != cudaSuccess ||
+      cudaMemsetAsync(ctx->cnt, 0, sizeof(hpic::Counters), st) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->T, T0.data(), K.ncell * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->eta, E0.data(), K.ncell * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cuda_fail(ctx, cudaGetLastError(), "initialisation");
+    return bail(HPIC_ECUDA);
+  }
+  hpic::launch_table(K, r->k_min_J / MC2, r->table_Emax_J / MC2, ctx->t64, ctx->t32, st);
+  ctx->launches += 1;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cuda_fail(ctx, e, "table build");
+    return bail(HPIC_ECUDA);
+  }
+  *out = ctx;
+  return HPIC_OK;
+}
+
+int hpic_inject_electrons(hpic_ctx *ctx, const hpic_laser_desc *l) {
+  if (!ctx || !l) return fail(ctx, HPIC_EINVAL, "NULL argument");
+  if (ctx->have_laser) return fail(ctx, HPIC_ESTATE, "a laser is already scheduled");
+  if (!(l->I0_Wm2 >= 0) || !(l->lambda_m > 0) || !(l->eta_l2e >= 0) || !(l->spot_radius_m >= 0) ||
+      !(l->t_inj_s >= 0) || l->n_macro < 0 || l->n_macro >= 0xFFFFFFFFll ||
+      !(l->cone_half_angle_rad >= 0) || l->cone_half_angle_rad > PI)
+    return fail(ctx, HPIC_EINVAL, "laser parameters out of range");
+  const double Ly = ctx->tgt.ny * ctx->tgt.dx_m, Lz = ctx->tgt.nz * ctx->tgt.dx_m;
+  if (l->spot_y_m - l->spot_radius_m < 0 || l->spot_y_m + l->spot_radius_m > Ly ||
+      l->spot_z_m - l->spot_radius_m < 0 || l->spot_z_m + l->spot_radius_m > Lz)
+    return fail(ctx, HPIC_EINVAL, "injection disc does not fit on the x = 0 face");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  hpic::Counters h;
+  int rc = read_counters(ctx, &h);
+  if (rc) return rc;
+  if (h.next_id + l->n_macro >= 0xFFFFFFFFll) return fail(ctx, HPIC_EINVAL, "id space exhausted");
+  rc = reserve(ctx, h.n + l->n_macro);
+  if (rc) return rc;
+  ctx->laser = *l;
+  ctx->have_laser = true;
+  fold_constants(ctx);
+  return HPIC_OK;
+}
+
+int hpic_step(hpic_ctx *ctx, int64_t n) {
+  if (!ctx) return HPIC_EINVAL;
+  if (n < 0) return fail(ctx, HPIC_EINVAL, "negative step count");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  return ctx->fp32 ? step_impl<float>(ctx, n) : step_impl<double>(ctx, n);
+}
+
+int hpic_sort(hpic_ctx *ctx) {
+  if (!ctx) return HPIC_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  return ctx->fp32 ? sort_impl<float>(ctx) : sort_impl<double>(ctx);
+}
+
+int hpic_read_tallies(hpic_ctx *ctx, hpic_tallies *out) {
+  if (!ctx || !out) return fail(ctx, HPIC_EINVAL, "NULL argument");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  CK(cudaMemsetAsync(ctx->scratch, 0, 2 * sizeof(double), ctx->stream));
+  const int gp = grid_blocks(ctx, ctx->cap), gg = grid_blocks(ctx, ctx->K.nvec);
+  if (ctx->fp32) {
+    hpic::launch_live_energy<float>(ctx->K, pview<float>(ctx, ctx->cur), ctx->cnt, ctx->scratch, gp, ctx->stream);
+    hpic::launch_field_energy<float>(ctx->K, gview<float>(ctx), ctx->scratch + 1, gg, ctx->stream);
+  } else {
+    hpic::launch_live_energy<double>(ctx->K, pview<double>(ctx, ctx->cur), ctx->cnt, ctx->scratch, gp, ctx->stream);
+    hpic::launch_field_energy<double>(ctx->K, gview<double>(ctx), ctx->scratch + 1, gg, ctx->stream);
+  }
+  ctx->launches += 2;
+  CK(cudaGetLastError());
+  double t[hpic::T_COUNT], sc[2];
+  CK(cudaMemcpyAsync(t, ctx->tal, sizeof(t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(sc, ctx->scratch, sizeof(sc), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  out->E_injected = t[hpic::T_E_INJ] * MC2;
+  out->N_injected = t[hpic::T_N_INJ];
+  out->W_field = t[hpic::T_W_FIELD] * MC2;
+  out->E_drag = t[hpic::T_E_DRAG] * MC2;
+  out->E_xray = t[hpic::T_E_XRAY] * MC2;
+  out->E_xray_above = t[hpic::T_E_XRAY_ABOVE] * MC2;
+  out->E_escaped = t[hpic::T_E_ESC] * MC2;
+  out->E_reflux = t[hpic::T_E_REFLUX] * MC2;
+  out->E_ohmic_grid = t[hpic::T_E_OHMIC];
+  out->n_injected = t[hpic::T_N_INJECTED];
+  out->n_escaped = t[hpic::T_N_ESC];
+  out->n_refluxed = t[hpic::T_N_REFLUX];
+  out->n_reflux_absorbed = t[hpic::T_N_REFLUX_ABS];
+  out->n_cut = t[hpic::T_N_CUT];
+  out->n_emitted = t[hpic::T_N_EMIT];
+  out->particle_steps = t[hpic::T_PSTEPS];
+  out->n_nonfinite = t[hpic::T_N_NONFINITE];
+  out->E_live = sc[0] * MC2;
+  const double bs = ME / (QE * ctx->run.dt_s);
+  out->E_B_field = sc[1] * bs * bs * ctx->K.dx3 / (2.0 * MU0);
+  return t[hpic::T_N_NONFINITE] > 0 ? HPIC_ENONFINITE : HPIC_OK;
+}
+
+int hpic_reset_tallies(hpic_ctx *ctx) {
+  if (!ctx) return HPIC_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  CK(cudaMemsetAsync(ctx->tal, 0, hpic::T_COUNT * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->hist, 0, 2 * hist_len(ctx) * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->history, 0, (ctx->run.max_history > 0 ? ctx->run.max_history : 1) * sizeof(double), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return HPIC_OK;
+}
+
+int hpic_read_hist(hpic_ctx *ctx, double *ew, double *nw) {
+  if (!ctx) return HPIC_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  const long long L = hist_len(ctx);
+  if (ew) CK(cudaMemcpyAsync(ew, ctx->hist, L * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (nw) CK(cudaMemcpyAsync(nw, ctx->hist + L, L * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ew) for (long long i = 0; i < L; ++i) ew[i] *= MC2;
+  return HPIC_OK;
+}
+
+int hpic_read_history(hpic_ctx *ctx, double *out) {
+  if (!ctx || !out) return fail(ctx, HPIC_EINVAL, "NULL argument");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  const int L = ctx->run.max_history;
+  if (L > 0) {
+    CK(cudaMemcpyAsync(out, ctx->history, L * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < L; ++i) out[i] *= MC2;
+  }
+  return HPIC_OK;
+}
+
+int hpic_grid_len(const hpic_ctx *ctx, int which, int64_t *len) {
+  if (!ctx || !len || !valid_grid(which)) return HPIC_EINVAL;
+  *len = (which == HPIC_GRID_T || which == HPIC_GRID_ETA || which == HPIC_GRID_HEAT) ? ctx->K.ncell
+                                                                                   : ctx->K.nvec;
+  return HPIC_OK;
+}
+
+int hpic_read_grid(hpic_ctx *ctx, int which, double *out) {
+  if (!ctx || !out || !valid_grid(which)) return fail(ctx, HPIC_EINVAL, "bad grid request");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  int64_t L;
+  hpic_grid_len(ctx, which, &L);
+  const double s = grid_scale(ctx, which);
+  if (which == HPIC_GRID_T || which == HPIC_GRID_ETA || which == HPIC_GRID_HEAT) {
+    const double *src = which == HPIC_GRID_T ? ctx->T : (which == HPIC_GRID_ETA ? ctx->eta : ctx->H);
+    CK(cudaMemcpyAsync(out, src, L * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int64_t i = 0; i < L; ++i) out[i] *= s;
+    return HPIC_OK;
+  }
+  const int slot = which - HPIC_GRID_EX;  // 0..8: E, B, J
+  const char *src = static_cast<const char *>(ctx->fields) + slot * L * ctx->rsz;
+  if (ctx->fp32) {
+    std::vector<float> b(L);
+    CK(cudaMemcpyAsync(b.data(), src, L * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int64_t i = 0; i < L; ++i) out[i] = (double)b[i] * s;
+  } else {
+    CK(cudaMemcpyAsync(out, src, L * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int64_t i = 0; i < L; ++i) out[i] *= s;
+  }
+  return HPIC_OK;
+}
+
+int hpic_write_grid(hpic_ctx *ctx, int which, const double *in) {
+  if (!ctx || !in || !valid_grid(which)) return fail(ctx, HPIC_EINVAL, "bad grid request");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  int64_t L;
+  hpic_grid_len(ctx, which, &L);
+  const double s = 1.0 / grid_scale(ctx, which);
+  if (which == HPIC_GRID_T || which == HPIC_GRID_ETA || which == HPIC_GRID_HEAT) {
+    double *dst = which == HPIC_GRID_T ? ctx->T : (which == HPIC_GRID_ETA ? ctx->eta : ctx->H);
+    std::vector<double> b(in, in + L);
+    for (auto &v : b) v *= s;
+    CK(cudaMemcpyAsync(dst, b.data(), L * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return HPIC_OK;
+  }
+  const int slot = which - HPIC_GRID_EX;
+  char *dst = static_cast<char *>(ctx->fields) + slot * L * ctx->rsz;
+  if (ctx->fp32) {
+    std::vector<float> b(L);
+    for (int64_t i = 0; i < L; ++i) b[i] = (float)(in[i] * s);
+    CK(cudaMemcpyAsync(dst, b.data(), L * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else {
+    std::vector<double> b(in, in + L);
+    for (auto &v : b) v *= s;
+    CK(cudaMemcpyAsync(dst, b.data(), L * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return HPIC_OK;
+}
+
+int hpic_count_particles(hpic_ctx *ctx, int64_t *n) {
+  if (!ctx || !n) return fail(ctx, HPIC_EINVAL, "NULL argument");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  hpic::Counters h;
+  int rc = read_counters(ctx, &h);
+  if (rc) return rc;
+  std::vector<uint32_t> ids(h.n);
+  const char *b = static_cast<const char *>(ctx->pbuf[ctx->cur]);
+  if (h.n) {
+    CK(cudaMemcpyAsync(ids.data(), b + 7 * (size_t)ctx->stride * ctx->rsz, h.n * sizeof(uint32_t),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  long long live = 0;
+  for (uint32_t v : ids) live += v != hpic::kDead;
+  *n = live;
+  return HPIC_OK;
+}
+
+int hpic_read_particles(hpic_ctx *ctx, double *x, double *y, double *z, double *ux, double *uy,
+                        double *uz, double *tau, uint32_t *id, int64_t cap, int64_t *n) {
+  if (!ctx || !n) return fail(ctx, HPIC_EINVAL, "NULL argument");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  return ctx->fp32 ? read_particles_impl<float>(ctx, x, y, z, ux, uy, uz, tau, id, cap, n)
+                   : read_particles_impl<double>(ctx, x, y, z, ux, uy, uz, tau, id, cap, n);
+}
+
+int hpic_load_particles(hpic_ctx *ctx, int64_t n, const double *x, const double *y,
+                        const double *z, const double *ux, const double *uy, const double *uz,
+                        const double *tau, const uint32_t *id) {
+  if (!ctx || n < 0 || (n > 0 && (!x || !y || !z || !ux || !uy || !uz || !tau || !id)))
+    return fail(ctx, HPIC_EINVAL, "bad particle arguments");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  return ctx->fp32 ? load_particles_impl<float>(ctx, n, x, y, z, ux, uy, uz, tau, id)
+                   : load_particles_impl<double>(ctx, n, x, y, z, ux, uy, uz, tau, id);
+}
+
+int hpic_get_clock(hpic_ctx *ctx, int64_t *step, int64_t *next_id) {
+  if (!ctx) return HPIC_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  hpic::Counters h;
+  int rc = read_counters(ctx, &h);
+  if (rc) return rc;
+  if (step) *step = h.step;
+  if (next_id) *next_id = h.next_id;
+  return HPIC_OK;
+}
+
+int hpic_set_clock(hpic_ctx *ctx, int64_t step, int64_t next_id) {
+  if (!ctx || step < 0 || next_id < 0 || step >= 0xFFFFFFFFll || next_id >= 0xFFFFFFFFll)
+    return fail(ctx, HPIC_EINVAL, "clock out of range");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  hpic::Counters h;
+  int rc = read_counters(ctx, &h);
+  if (rc) return rc;
+  h.step = step;
+  h.next_id = next_id;
+  ctx->host_step = step;
+  return write_counters(ctx, &h);
+}
+
+int hpic_profile(hpic_ctx *ctx, int enable) {
+  if (!ctx) return HPIC_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof = enable != 0;
+  ctx->ev_used = 0;
+  ctx->prof_launches = 0;
+  double ps;
+  CK(cudaMemcpy(&ps, ctx->tal + hpic::T_PSTEPS, sizeof(double), cudaMemcpyDeviceToHost));
+  ctx->prof_ps0 = ps;
+  return HPIC_OK;
+}
+
+int hpic_kernel_time(hpic_ctx *ctx, double *ms, int64_t *launches, double *psteps) {
+  if (!ctx) return HPIC_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  CK(cudaStreamSynchronize(ctx->stream));
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]));
+    total += t;
+  }
+  double ps;
+  CK(cudaMemcpy(&ps, ctx->tal + hpic::T_PSTEPS, sizeof(double), cudaMemcpyDeviceToHost));
+  if (ms) *ms = total;
+  if (launches) *launches = ctx->prof_launches;
+  if (psteps) *psteps = ps - ctx->prof_ps0;
+  ctx->ev_used = 0;
+  ctx->prof_launches = 0;
+  ctx->prof_ps0 = ps;
+  return HPIC_OK;
+}
+
+int hpic_launch_count(const hpic_ctx *ctx, int64_t *launches) {
+  if (!ctx || !launches) return HPIC_EINVAL;
+  *launches = ctx->launches;
+  return HPIC_OK;
+}
+
+int hpic_destroy(hpic_ctx *ctx) {
+  if (!ctx) return HPIC_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  destroy_all(ctx);
+  delete ctx;
+  return HPIC_OK;
+}
+
+const char *hpic_last_error(const hpic_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

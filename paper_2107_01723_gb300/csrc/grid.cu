@@ -1,0 +1,405 @@
+// Grid-side kernels of the hybrid-PIC step (arXiv 2107.01723):
+//   k_efield : E = eta (curl B / mu0 - j_h) on edges, Eq. (A2), tangential E
+//              zero on the walls (conducting boundary)
+//   k_bheat  : B -= dt curl E on faces, Eq. (A3), fused with the background
+//              heating dT = rho/(Z n_i C k_B), Eqs. (A7)-(A8), rho = Ohmic
+//              eta j_h.j_h dt + ionisation heat, and eta(T), Eqs. (A4)-(A6)
+//   sort     : counting sort of electrons by cell (GPU data layout)
+//   k_table  : inverse-CDF bremsstrahlung table from the closed-form CDF
+#include "kernels.h"
+
+namespace hpic {
+
+__device__ __forceinline__ void node_of(long long q, int nx, int ny, int &i, int &j, int &k) {
+  const long long sy = nx + 1, sz = (long long)(nx + 1) * (ny + 1);
+  k = (int)(q / sz);
+  const long long r = q - (long long)k * sz;
+  j = (int)(r / sy);
+  i = (int)(r - (long long)j * sy);
+}
+
+// ---------------------------------------------------------------- E, Eq. (A2)
+template <typename R>
+__global__ void __launch_bounds__(256) k_efield(const Consts K, GView<R> g) {
+  const int nx = K.nx, ny = K.ny, nz = K.nz;
+  const int sy = nx + 1;
+  const long long sz = (long long)(nx + 1) * (ny + 1);
+  const long long cy = nx, cz = (long long)nx * ny;
+  const R Fc = R(K.F_curl), Fj = R(K.F_j);
+  const R *Bx = g.B[0], *By = g.B[1], *Bz = g.B[2];
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < K.nvec;
+       q += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_of(q, nx, ny, i, j, k);
+    R ex = 0, ey = 0, ez = 0;
+    const long long c = i + cy * j + cz * k;  // cell (i, j, k)
+    if (i < nx && j >= 1 && j <= ny - 1 && k >= 1 && k <= nz - 1) {
+      const R curl = (Bz[q] - Bz[q - sy]) - (By[q] - By[q - sz]);
+      const R eta = R(0.25 * (g.eta[c - cy - cz] + g.eta[c - cz] + g.eta[c - cy] + g.eta[c]));
+      ex = eta * (Fc * curl - Fj * g.J[0][q]);
+    }
+    if (j < ny && i >= 1 && i <= nx - 1 && k >= 1 && k <= nz - 1) {
+      const R curl = (Bx[q] - Bx[q - sz]) - (Bz[q] - Bz[q - 1]);
+      const R eta = R(0.25 * (g.eta[c - 1 - cz] + g.eta[c - cz] + g.eta[c - 1] + g.eta[c]));
+      ey = eta * (Fc * curl - Fj * g.J[1][q]);
+    }
+    if (k < nz && i >= 1 && i <= nx - 1 && j >= 1 && j <= ny - 1) {
+      const R curl = (By[q] - By[q - 1]) - (Bx[q] - Bx[q - sy]);
+      const R eta = R(0.25 * (g.eta[c - 1 - cy] + g.eta[c - cy] + g.eta[c - 1] + g.eta[c]));
+      ez = eta * (Fc * curl - Fj * g.J[2][q]);
+    }
+    g.E[0][q] = ex;
+    g.E[1][q] = ey;
+    g.E[2][q] = ez;
+  }
+}
+
+// heat capacity, Eq. (A8): T' = (k_B T/e) Z^(-4/3)
+__device__ __forceinline__ double heat_capacity(double T, double Tp_fac) {
+  const double tp = T * Tp_fac;
+  return 0.3 + 1.2 * tp * (2.2 + tp) / ((1.1 + tp) * (1.1 + tp));
+}
+
+// reduced Lee-More resistivity, Eqs. (A4)-(A6), capped
+__device__ __forceinline__ double resistivity(const Consts &K, double T) {
+  const double kT = 1.380649e-23 * T;
+  double tau = K.A_hot * kT * sqrt(kT);
+  if (K.lambda1 > 0.0) {
+    const double tc = K.B_cold / sqrt(kT);
+    tau = tc > tau ? tc : tau;
+  }
+  const double eta = K.eta_num / tau;
+  return eta < K.eta_max ? eta : K.eta_max;
+}
+
+// ---------------------------------------------------------------- B, Eq. (A3), and heating
+template <typename R>
+__global__ void __launch_bounds__(256) k_bheat(const Consts K, GView<R> g, TallyView tv) {
+  __shared__ double smem[32];
+  const int nx = K.nx, ny = K.ny, nz = K.nz;
+  const int sy = nx + 1;
+  const long long sz = (long long)(nx + 1) * (ny + 1);
+  const R cdt = R(K.cdt_dx);
+  const R *Ex = g.E[0], *Ey = g.E[1], *Ez = g.E[2];
+  double e_ohm = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < K.nvec;
+       q += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_of(q, nx, ny, i, j, k);
+    if (K.physics & P_FARADAY) {
+      if (j < ny && k < nz) g.B[0][q] -= cdt * ((Ez[q + sy] - Ez[q]) - (Ey[q + sz] - Ey[q]));
+      if (i < nx && k < nz) g.B[1][q] -= cdt * ((Ex[q + sz] - Ex[q]) - (Ez[q + 1] - Ez[q]));
+      if (i < nx && j < ny) g.B[2][q] -= cdt * ((Ey[q + 1] - Ey[q]) - (Ex[q + sy] - Ex[q]));
+    }
+    if (i < nx && j < ny && k < nz) {
+      const long long c = i + (long long)nx * (j + (long long)ny * k);
+      double rho = g.H[c] * K.F_H;
+      if (K.physics & P_FIELDS) {
+        const R *Jx = g.J[0], *Jy = g.J[1], *Jz = g.J[2];
+        const double jbx = 0.25 * ((double)Jx[q] + Jx[q + sy] + Jx[q + sz] + Jx[q + sy + sz]);
+        const double jby = 0.25 * ((double)Jy[q] + Jy[q + 1] + Jy[q + sz] + Jy[q + 1 + sz]);
+        const double jbz = 0.25 * ((double)Jz[q] + Jz[q + 1] + Jz[q + sy] + Jz[q + 1 + sy]);
+        const double ro = g.eta[c] * K.F_ohm * (jbx * jbx + jby * jby + jbz * jbz);
+        e_ohm += ro * K.dx3;
+        rho += ro;
+      }
+      if (K.physics & P_HEATING) {
+        const double T = g.T[c];
+        const double Tn = T + rho / (K.heat_den * heat_capacity(T, K.Tp_fac));
+        g.T[c] = Tn;
+        g.eta[c] = resistivity(K, Tn);
+      }
+    }
+  }
+  const double v[1] = {e_ohm};
+  const int slot[1] = {T_E_OHMIC};
+  block_flush<1>(v, slot, tv.tal, smem);
+}
+
+// ---------------------------------------------------------------- counting sort
+// warp-aggregated atomic increment: lanes with equal keys share one atomic
+__device__ __forceinline__ uint32_t agg_inc(uint32_t *ctr, uint32_t key) {
+  const unsigned mask = __activemask();
+  const unsigned peers = __match_any_sync(mask, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(ctr + key, (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + rank;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_sort_keys(const Consts K, PView<R> p, const Counters *cnt, uint32_t *keys, uint32_t *counts) {
+  const long long n = cnt->n;
+  for (long long ip = blockIdx.x * (long long)blockDim.x + threadIdx.x; ip < n;
+       ip += (long long)gridDim.x * blockDim.x) {
+    uint32_t key = (uint32_t)K.ncell;
+    if (p.id[ip] != kDead) {
+      int i = (int)m_floor(p.x[ip]), j = (int)m_floor(p.y[ip]), k = (int)m_floor(p.z[ip]);
+      i = min(max(i, 0), K.nx - 1);
+      j = min(max(j, 0), K.ny - 1);
+      k = min(max(k, 0), K.nz - 1);
+      key = (uint32_t)(i + (long long)K.nx * (j + (long long)K.ny * k));
+    }
+    keys[ip] = key;
+    agg_inc(counts, key);
+  }
+}
+
+constexpr int kScanTile = 4096;  // counts per block in the scan
+
+// per-tile sums of counts[0, m)
+__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *counts, long long m,
+                                                     uint32_t *partials) {
+  __shared__ uint32_t ws[32];
+  const long long base = (long long)blockIdx.x * kScanTile;
+  uint32_t s = 0;
+  for (int t = threadIdx.x; t < kScanTile; t += blockDim.x) {
+    const long long q = base + t;
+    if (q < m) s += counts[q];
+  }
+  s = __reduce_add_sync(0xffffffffu, s);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t v = ws[threadIdx.x];
+    v = __reduce_add_sync(0xffffffffu, v);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  }
+}
+
+// exclusive scan of the tile sums in one block; total to partials[ntiles]
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t *partials, int ntiles) {
+  __shared__ uint32_t ws[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < ntiles; base += blockDim.x) {
+    const int t = base + threadIdx.x;
+    const uint32_t v = t < ntiles ? partials[t] : 0u;
+    // inclusive warp scan
+    uint32_t x = v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t z = ws[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+        if (lane >= o) z += y;
+      }
+      ws[lane] = z;
+    }
+    __syncthreads();
+    const uint32_t incl = x + (warp > 0 ? ws[warp - 1] : 0u) + carry;
+    if (t < ntiles) partials[t] = incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[ntiles] = carry;
+}
+
+// exclusive scan within each tile plus its tile offset, in place
+__global__ void __launch_bounds__(1024) k_scan_apply(uint32_t *counts, long long m,
+                                                     const uint32_t *partials) {
+  __shared__ uint32_t ws[32];
+  __shared__ uint32_t carry;
+  const long long base = (long long)blockIdx.x * kScanTile;
+  if (threadIdx.x == 0) carry = partials[blockIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int off = 0; off < kScanTile; off += blockDim.x) {
+    const long long q = base + off + threadIdx.x;
+    const uint32_t v = q < m ? counts[q] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t z = ws[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+        if (lane >= o) z += y;
+      }
+      ws[lane] = z;
+    }
+    __syncthreads();
+    const uint32_t incl = x + (warp > 0 ? ws[warp - 1] : 0u) + carry;
+    if (q < m) counts[q] = incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = incl;
+    __syncthreads();
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_sort_scatter(const Consts K, PView<R> src, PView<R> dst, const Counters *cnt,
+               const uint32_t *keys, uint32_t *offsets) {
+  const long long n = cnt->n;
+  for (long long ip = blockIdx.x * (long long)blockDim.x + threadIdx.x; ip < n;
+       ip += (long long)gridDim.x * blockDim.x) {
+    const uint32_t key = keys[ip];
+    if (key >= (uint32_t)K.ncell) continue;
+    const uint32_t q = agg_inc(offsets, key);
+    dst.x[q] = src.x[ip];
+    dst.y[q] = src.y[ip];
+    dst.z[q] = src.z[ip];
+    dst.ux[q] = src.ux[ip];
+    dst.uy[q] = src.uy[ip];
+    dst.uz[q] = src.uz[ip];
+    dst.tau[q] = src.tau[ip];
+    dst.id[q] = src.id[ip];
+  }
+}
+
+// live count = exclusive offset of the dead bin (the scatter never touches it)
+__global__ void k_sort_finish(Counters *cnt, const uint32_t *offsets, long long ncell) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cnt->n = offsets[ncell];
+}
+
+// ---------------------------------------------------------------- photon table
+// Row i: eps_i = k_min (E_max/k_min)^(i/(rows-1)); column j: the v with
+// CDF(k_min (eps_i/k_min)^v) = j/(cols-1), where CDF is the normalised
+// integral of s(u)/u, s(u) = (4/3)(1-u) + u^2, from u0 = k_min/eps to u.
+// Solved by Newton's method on y = ln u (dG/dy = s(e^y)) inside a bracket.
+__global__ void k_table(int rows, int cols, double k_min, double E_max, double *t64, float *t32) {
+  const long long nt = (long long)rows * cols;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nt;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q / cols), j = (int)(q - (long long)i * cols);
+    const double r = (double)j / (double)(cols - 1);
+    double v;
+    if (i == 0 || j == 0 || j == cols - 1) {
+      v = (i == 0) ? r : (j == 0 ? 0.0 : 1.0);
+    } else {
+      const double lu0 = ((double)i / (double)(rows - 1)) * -log(E_max / k_min);  // ln u0 < 0
+      const double u0 = exp(lu0);
+      // G(y) = (4/3)(y - lu0 - (e^y - u0)) + (e^{2y} - u0^2)/2, target r G(0)
+      const double G1 = (4.0 / 3.0) * (-lu0 - (1.0 - u0)) + 0.5 * (1.0 - u0 * u0);
+      const double target = r * G1;
+      double lo = lu0, hi = 0.0, y = lu0 + r * (-lu0);
+      for (int it = 0; it < 100; ++it) {
+        const double e = exp(y);
+        const double Gy = (4.0 / 3.0) * (y - lu0 - (e - u0)) + 0.5 * (e * e - u0 * u0) - target;
+        if (Gy < 0.0) lo = y; else hi = y;
+        const double dG = (4.0 / 3.0) * (1.0 - e) + e * e;
+        double yn = y - Gy / dG;
+        if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
+        if (fabs(yn - y) < 1e-16 * fabs(lu0)) { y = yn; break; }
+        y = yn;
+      }
+      v = 1.0 - y / lu0;
+    }
+    t64[q] = v;
+    t32[q] = (float)v;
+  }
+}
+
+// ---------------------------------------------------------------- read-time sums
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_live_energy(const Consts K, PView<R> p, const Counters *cnt, double *dst) {
+  __shared__ double smem[32];
+  const long long n = cnt->n;
+  double e = 0.0;
+  for (long long ip = blockIdx.x * (long long)blockDim.x + threadIdx.x; ip < n;
+       ip += (long long)gridDim.x * blockDim.x) {
+    if (p.id[ip] == kDead) continue;
+    const double ux = p.ux[ip], uy = p.uy[ip], uz = p.uz[ip];
+    const double u2 = ux * ux + uy * uy + uz * uz;
+    e += K.w * u2 / (1.0 + sqrt(1.0 + u2));
+  }
+  const double v[1] = {e};
+  const int slot[1] = {0};
+  block_flush<1>(v, slot, dst, smem);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_field_energy(const Consts K, GView<R> g, double *dst) {
+  __shared__ double smem[32];
+  double e = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < K.nvec;
+       q += (long long)gridDim.x * blockDim.x) {
+    for (int c = 0; c < 3; ++c) {
+      const double b = g.B[c][q];
+      e += b * b;
+    }
+  }
+  const double v[1] = {e};
+  const int slot[1] = {0};
+  block_flush<1>(v, slot, dst, smem);
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename R>
+void launch_efield(const Consts &K, GView<R> g, int grid, cudaStream_t st) {
+  k_efield<R><<<grid, 256, 0, st>>>(K, g);
+}
+
+template <typename R>
+void launch_bheat(const Consts &K, GView<R> g, TallyView tv, int grid, cudaStream_t st) {
+  k_bheat<R><<<grid, 256, 0, st>>>(K, g, tv);
+}
+
+template <typename R>
+int launch_sort(const Consts &K, PView<R> src, PView<R> dst, Counters *cnt, uint32_t *keys,
+                uint32_t *counts, uint32_t *partials, int grid, cudaStream_t st) {
+  const long long m = K.ncell + 1;
+  const int ntiles = (int)((m + kScanTile - 1) / kScanTile);
+  cudaMemsetAsync(counts, 0, m * sizeof(uint32_t), st);
+  k_sort_keys<R><<<grid, 256, 0, st>>>(K, src, cnt, keys, counts);
+  k_scan_tiles<<<ntiles, 1024, 0, st>>>(counts, m, partials);
+  k_scan_top<<<1, 1024, 0, st>>>(partials, ntiles);
+  k_scan_apply<<<ntiles, 1024, 0, st>>>(counts, m, partials);
+  k_sort_scatter<R><<<grid, 256, 0, st>>>(K, src, dst, cnt, keys, counts);
+  k_sort_finish<<<1, 32, 0, st>>>(cnt, counts, K.ncell);
+  return 6;
+}
+
+void launch_table(const Consts &K, double k_min, double E_max, double *t64, float *t32,
+                  cudaStream_t st) {
+  const long long nt = (long long)K.t_rows * K.t_cols;
+  const int grid = (int)((nt + 255) / 256);
+  k_table<<<grid, 256, 0, st>>>(K.t_rows, K.t_cols, k_min, E_max, t64, t32);
+}
+
+template <typename R>
+void launch_live_energy(const Consts &K, PView<R> p, Counters *cnt, double *dst, int grid,
+                        cudaStream_t st) {
+  k_live_energy<R><<<grid, 256, 0, st>>>(K, p, cnt, dst);
+}
+
+template <typename R>
+void launch_field_energy(const Consts &K, GView<R> g, double *dst, int grid, cudaStream_t st) {
+  k_field_energy<R><<<grid, 256, 0, st>>>(K, g, dst);
+}
+
+#define HPIC_INST(R)                                                                          \
+  template void launch_efield<R>(const Consts &, GView<R>, int, cudaStream_t);                \
+  template void launch_bheat<R>(const Consts &, GView<R>, TallyView, int, cudaStream_t);      \
+  template int launch_sort<R>(const Consts &, PView<R>, PView<R>, Counters *, uint32_t *,     \
+                              uint32_t *, uint32_t *, int, cudaStream_t);                     \
+  template void launch_live_energy<R>(const Consts &, PView<R>, Counters *, double *, int,    \
+                                      cudaStream_t);                                          \
+  template void launch_field_energy<R>(const Consts &, GView<R>, double *, int, cudaStream_t);
+HPIC_INST(float)
+HPIC_INST(double)
+#undef HPIC_INST
+
+}  // namespace hpic

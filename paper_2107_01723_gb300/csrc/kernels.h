@@ -1,0 +1,57 @@
+// Internal declarations shared by the kernel translation units and api.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace hpic {
+
+// particle storage: structure of arrays, positions in cells, momenta u = p/(m_e c)
+template <typename R>
+struct PView {
+  R *x, *y, *z, *ux, *uy, *uz, *tau;
+  uint32_t *id;
+};
+
+// grid storage: vector components as (nx+1)(ny+1)(nz+1) arrays (x fastest)
+template <typename R>
+struct GView {
+  R *E[3], *B[3], *J[3];
+  double *T, *eta, *H;  // cell-centred, double
+};
+
+struct TallyView {
+  double *tal;      // T_COUNT scalars
+  double *hist;     // 2 x (n_E+2) x n_th: energy-weighted, then number-weighted
+  double *history;  // max_history
+};
+
+template <typename R>
+void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
+                 TallyView tv, int grid, cudaStream_t st);
+template <typename R>
+void launch_inject(const Consts &K, PView<R> p, Counters *cnt, long long cap, TallyView tv,
+                   int grid, cudaStream_t st);
+void launch_advance(Counters *cnt, long long cap, cudaStream_t st);
+
+template <typename R>
+void launch_efield(const Consts &K, GView<R> g, int grid, cudaStream_t st);
+template <typename R>
+void launch_bheat(const Consts &K, GView<R> g, TallyView tv, int grid, cudaStream_t st);
+
+// counting sort by cell: keys/counts/offsets are scratch; returns launches made
+template <typename R>
+int launch_sort(const Consts &K, PView<R> src, PView<R> dst, Counters *cnt, uint32_t *keys,
+                uint32_t *counts, uint32_t *partials, int grid, cudaStream_t st);
+
+void launch_table(const Consts &K, double k_min, double E_max, double *t64, float *t32,
+                  cudaStream_t st);
+
+template <typename R>
+void launch_live_energy(const Consts &K, PView<R> p, Counters *cnt, double *dst, int grid,
+                        cudaStream_t st);
+template <typename R>
+void launch_field_energy(const Consts &K, GView<R> g, double *dst, int grid, cudaStream_t st);
+
+}  // namespace hpic

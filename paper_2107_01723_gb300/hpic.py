@@ -1,0 +1,330 @@
+"""ctypes binding of the C-ABI in include/hpic.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library; this module converts
+Python dicts and numpy arrays to the ABI's structs and pointers.  The
+library is paper_2107_01723_gb300/_build/libhpic.so; if it is missing the
+first call raises (build it with `python -m paper_2107_01723_gb300.build`).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libhpic.so")
+
+HPIC_OK, HPIC_EINVAL, HPIC_ENOMEM, HPIC_ECUDA, HPIC_ETIMEOUT, HPIC_ESTATE, HPIC_ENONFINITE = \
+    0, -1, -2, -3, -4, -5, -6
+HPIC_FP64, HPIC_FP32_MIXED = 0, 1
+HPIC_DRAG, HPIC_SCATTER, HPIC_BREM, HPIC_FIELDS, HPIC_FARADAY, HPIC_HEATING = 1, 2, 4, 8, 16, 32
+HPIC_ALL = 63
+GRID = {"T": 0, "eta": 1, "Ex": 2, "Ey": 3, "Ez": 4, "Bx": 5, "By": 6, "Bz": 7,
+        "jx": 8, "jy": 9, "jz": 10, "heat": 11}
+
+
+class HpicError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hpic error {code}: {msg}")
+        self.code = code
+
+
+class hpic_target_desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("dx_m", C.c_double),
+                ("Z", C.c_double), ("n_i_m3", C.c_double), ("I_ex_J", C.c_double),
+                ("Zstar", C.c_double), ("lnLambda", C.c_double), ("eta_max_ohm_m", C.c_double),
+                ("lambda1", C.c_double), ("lambda2", C.c_double), ("T0_K", C.c_double)]
+
+
+class hpic_laser_desc(C.Structure):
+    _fields_ = [("I0_Wm2", C.c_double), ("lambda_m", C.c_double), ("eta_l2e", C.c_double),
+                ("spot_radius_m", C.c_double), ("spot_y_m", C.c_double), ("spot_z_m", C.c_double),
+                ("t_inj_s", C.c_double), ("cone_half_angle_rad", C.c_double),
+                ("n_macro", C.c_int64)]
+
+
+class hpic_run_params(C.Structure):
+    _fields_ = [("dt_s", C.c_double), ("seed", C.c_uint64), ("target_index", C.c_uint32),
+                ("precision", C.c_int32), ("kappa_esc", C.c_double), ("kappa_tnsa", C.c_double),
+                ("sigma_dtheta_rad", C.c_double), ("brem_boost", C.c_double),
+                ("k_min_J", C.c_double), ("E_cut_J", C.c_double), ("n_Ebins", C.c_int32),
+                ("n_thbins", C.c_int32), ("tally_Emin_J", C.c_double), ("tally_Emax_J", C.c_double),
+                ("ce_threshold_J", C.c_double), ("table_rows", C.c_int32),
+                ("table_cols", C.c_int32), ("table_Emax_J", C.c_double),
+                ("curlB_term", C.c_int32), ("physics", C.c_int32), ("sort_interval", C.c_int32),
+                ("max_history", C.c_int32)]
+
+
+_TALLY_NAMES = ("E_injected", "N_injected", "W_field", "E_drag", "E_xray", "E_xray_above",
+                "E_escaped", "E_reflux", "E_ohmic_grid", "n_injected", "n_escaped", "n_refluxed",
+                "n_reflux_absorbed", "n_cut", "n_emitted", "particle_steps", "n_nonfinite",
+                "E_live", "E_B_field")
+
+
+class hpic_tallies(C.Structure):
+    _fields_ = [(n, C.c_double) for n in _TALLY_NAMES]
+
+
+_lib = None
+_DP = C.POINTER(C.c_double)
+_UP = C.POINTER(C.c_uint32)
+_I64P = C.POINTER(C.c_int64)
+
+
+def lib() -> C.CDLL:
+    """Load libhpic.so; raise if it has not been built (no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise FileNotFoundError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2107_01723_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        sig = {
+            "hpic_init_target": [C.POINTER(vp), C.POINTER(hpic_target_desc),
+                                 C.POINTER(hpic_run_params), C.c_int, vp],
+            "hpic_inject_electrons": [vp, C.POINTER(hpic_laser_desc)],
+            "hpic_step": [vp, C.c_int64],
+            "hpic_sort": [vp],
+            "hpic_read_tallies": [vp, C.POINTER(hpic_tallies)],
+            "hpic_reset_tallies": [vp],
+            "hpic_read_hist": [vp, _DP, _DP],
+            "hpic_read_history": [vp, _DP],
+            "hpic_grid_len": [vp, C.c_int, _I64P],
+            "hpic_read_grid": [vp, C.c_int, _DP],
+            "hpic_write_grid": [vp, C.c_int, _DP],
+            "hpic_count_particles": [vp, _I64P],
+            "hpic_read_particles": [vp] + [_DP] * 7 + [_UP, C.c_int64, _I64P],
+            "hpic_load_particles": [vp, C.c_int64] + [_DP] * 7 + [_UP],
+            "hpic_get_clock": [vp, _I64P, _I64P],
+            "hpic_set_clock": [vp, C.c_int64, C.c_int64],
+            "hpic_profile": [vp, C.c_int],
+            "hpic_kernel_time": [vp, _DP, _I64P, _DP],
+            "hpic_launch_count": [vp, _I64P],
+            "hpic_destroy": [vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.hpic_last_error.argtypes = [vp]
+        L.hpic_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(code: int, h=None) -> int:
+    if code != HPIC_OK:
+        msg = lib().hpic_last_error(h)
+        raise HpicError(code, msg.decode() if msg else "")
+    return code
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP) if a is not None else None
+
+
+def _up(a):
+    return a.ctypes.data_as(_UP) if a is not None else None
+
+
+# ---- structs from the workload dicts (SI units) ----
+def target_desc(t: dict) -> hpic_target_desc:
+    return hpic_target_desc(t["nx"], t["ny"], t["nz"], t["dx"], t["Z"], t["n_i"], t["I_ex"],
+                            t["Zstar"], t["lnLambda"], t["eta_max"], t["lambda1"], t["lambda2"],
+                            t["T0"])
+
+
+def laser_desc(l: dict) -> hpic_laser_desc:
+    return hpic_laser_desc(l["I0"], l["lambda"], l["eta_l2e"], l["spot_r"], l["spot_y"],
+                           l["spot_z"], l["t_inj"], l["cone_half"], int(l["n_macro"]))
+
+
+def run_params(r: dict, precision: int = HPIC_FP64, sort_interval: int = 0) -> hpic_run_params:
+    return hpic_run_params(r["dt"], int(r["seed"]), int(r.get("target_index", 0)), precision,
+                           r["kappa_esc"], r["kappa_tnsa"], r["sigma_dtheta"], r["brem_boost"],
+                           r["k_min"], r["E_cut"], r["n_E"], r["n_theta"], r["tally_E_min"],
+                           r["tally_E_max"], r["ce_threshold"], r["table_rows"], r["table_cols"],
+                           r["table_E_max"], r["curlB_term"], r["physics"], sort_interval,
+                           r["max_history"])
+
+
+# ---- the ABI's calls, same names ----
+def hpic_init_target(target: dict, run: dict, precision: int = HPIC_FP64, device: int = 0,
+                     stream: int = 0, sort_interval: int = 0) -> C.c_void_p:
+    h = C.c_void_p()
+    t, r = target_desc(target), run_params(run, precision, sort_interval)
+    _check(lib().hpic_init_target(C.byref(h), C.byref(t), C.byref(r), device,
+                                  C.c_void_p(stream) if stream else None))
+    return h
+
+
+def hpic_inject_electrons(h, laser: dict) -> None:
+    l = laser_desc(laser)
+    _check(lib().hpic_inject_electrons(h, C.byref(l)), h)
+
+
+def hpic_step(h, n: int = 1) -> None:
+    _check(lib().hpic_step(h, int(n)), h)
+
+
+def hpic_sort(h) -> None:
+    _check(lib().hpic_sort(h), h)
+
+
+def hpic_read_tallies(h, allow_nonfinite: bool = False) -> dict:
+    t = hpic_tallies()
+    code = lib().hpic_read_tallies(h, C.byref(t))
+    if not (allow_nonfinite and code == HPIC_ENONFINITE):
+        _check(code, h)
+    return {n: getattr(t, n) for n in _TALLY_NAMES}
+
+
+def hpic_reset_tallies(h) -> None:
+    _check(lib().hpic_reset_tallies(h), h)
+
+
+def hpic_read_hist(h, n_E: int, n_th: int):
+    hE = np.empty((n_E + 2) * n_th)
+    hN = np.empty_like(hE)
+    _check(lib().hpic_read_hist(h, _dp(hE), _dp(hN)), h)
+    return hE.reshape(n_E + 2, n_th), hN.reshape(n_E + 2, n_th)
+
+
+def hpic_read_history(h, length: int) -> np.ndarray:
+    out = np.empty(max(length, 1))
+    _check(lib().hpic_read_history(h, _dp(out)), h)
+    return out[:length]
+
+
+def hpic_read_grid(h, which: str) -> np.ndarray:
+    n = C.c_int64()
+    _check(lib().hpic_grid_len(h, GRID[which], C.byref(n)), h)
+    out = np.empty(n.value)
+    _check(lib().hpic_read_grid(h, GRID[which], _dp(out)), h)
+    return out
+
+
+def hpic_write_grid(h, which: str, values) -> None:
+    a = np.ascontiguousarray(values, dtype=np.float64)
+    n = C.c_int64()
+    _check(lib().hpic_grid_len(h, GRID[which], C.byref(n)), h)
+    if a.size != n.value:
+        raise ValueError(f"grid {which} needs {n.value} values, got {a.size}")
+    _check(lib().hpic_write_grid(h, GRID[which], _dp(a)), h)
+
+
+def hpic_count_particles(h) -> int:
+    n = C.c_int64()
+    _check(lib().hpic_count_particles(h, C.byref(n)), h)
+    return n.value
+
+
+def hpic_read_particles(h) -> dict:
+    n = hpic_count_particles(h)
+    out = {k: np.empty(n) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")}
+    out["id"] = np.empty(n, dtype=np.uint32)
+    got = C.c_int64()
+    _check(lib().hpic_read_particles(h, *[_dp(out[k]) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")],
+                                     _up(out["id"]), n, C.byref(got)), h)
+    return out
+
+
+def hpic_load_particles(h, p: dict) -> None:
+    arrs = [np.ascontiguousarray(p[k], dtype=np.float64) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")]
+    ids = np.ascontiguousarray(p["id"], dtype=np.uint32)
+    _check(lib().hpic_load_particles(h, len(ids), *[_dp(a) for a in arrs], _up(ids)), h)
+
+
+def hpic_get_clock(h):
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib().hpic_get_clock(h, C.byref(a), C.byref(b)), h)
+    return a.value, b.value
+
+
+def hpic_set_clock(h, step: int, next_id: int) -> None:
+    _check(lib().hpic_set_clock(h, int(step), int(next_id)), h)
+
+
+def hpic_profile(h, enable: bool) -> None:
+    _check(lib().hpic_profile(h, 1 if enable else 0), h)
+
+
+def hpic_kernel_time(h):
+    ms, n, ps = C.c_double(), C.c_int64(), C.c_double()
+    _check(lib().hpic_kernel_time(h, C.byref(ms), C.byref(n), C.byref(ps)), h)
+    return ms.value, n.value, ps.value
+
+
+def hpic_launch_count(h) -> int:
+    n = C.c_int64()
+    _check(lib().hpic_launch_count(h, C.byref(n)), h)
+    return n.value
+
+
+def hpic_destroy(h) -> None:
+    if h:
+        _check(lib().hpic_destroy(h))
+
+
+class Sim:
+    """One target on the GPU: the C-ABI calls bundled with their workload dicts."""
+
+    def __init__(self, target: dict, laser: dict | None, run: dict, precision: int = HPIC_FP64,
+                 device: int = 0, stream: int = 0, sort_interval: int = 0):
+        self.target, self.run = dict(target), dict(run)
+        self.h = hpic_init_target(target, run, precision, device, stream, sort_interval)
+        if laser is not None:
+            hpic_inject_electrons(self.h, laser)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            hpic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1) -> None:
+        hpic_step(self.h, n)
+
+    def sort(self) -> None:
+        hpic_sort(self.h)
+
+    def tallies(self) -> dict:
+        return hpic_read_tallies(self.h)
+
+    def reset_tallies(self) -> None:
+        hpic_reset_tallies(self.h)
+
+    def hist(self):
+        return hpic_read_hist(self.h, self.run["n_E"], self.run["n_theta"])
+
+    def history(self) -> np.ndarray:
+        return hpic_read_history(self.h, self.run["max_history"])
+
+    def grid(self, which: str) -> np.ndarray:
+        return hpic_read_grid(self.h, which)
+
+    def set_grid(self, which: str, values) -> None:
+        hpic_write_grid(self.h, which, values)
+
+    @property
+    def n(self) -> int:
+        return hpic_count_particles(self.h)
+
+    def particles(self) -> dict:
+        return hpic_read_particles(self.h)
+
+    def set_particles(self, p: dict) -> None:
+        hpic_load_particles(self.h, p)
+
+    def clock(self):
+        return hpic_get_clock(self.h)
+
+    def set_clock(self, step: int, next_id: int) -> None:
+        hpic_set_clock(self.h, step, next_id)

@@ -1,0 +1,62 @@
+"""Helpers for the GPU-vs-oracle parity tests: move a state from the oracle
+into a GPU context through the C-ABI, and compare states element by element."""
+import numpy as np
+
+from oracle import oracle as O
+from paper_2107_01723_gb300 import hpic
+
+PKEYS = ("x", "y", "z", "ux", "uy", "uz", "tau")
+GRIDS_STATE = ("T", "eta", "Ex", "Ey", "Ez", "Bx", "By", "Bz")
+ENERGY_TALLIES = ("E_injected", "W_field", "E_drag", "E_xray", "E_xray_above", "E_escaped",
+                  "E_reflux", "E_ohmic_grid")
+COUNT_TALLIES = ("n_injected", "n_escaped", "n_refluxed", "n_reflux_absorbed", "n_cut",
+                 "n_emitted", "particle_steps")
+
+
+def gpu_from_oracle(osim: O.OracleSim, cfg: dict, precision: int, sort_interval: int = 0):
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=precision,
+                 sort_interval=sort_interval)
+    g.set_particles(osim.particles())
+    for k in GRIDS_STATE:
+        g.set_grid(k, osim.grid(k))
+    step, nid = osim.clock()
+    g.set_clock(step, nid)
+    g.reset_tallies()
+    return g
+
+
+def by_id(p: dict) -> dict:
+    o = np.argsort(p["id"], kind="stable")
+    return {k: np.asarray(v)[o] for k, v in p.items()}
+
+
+def assert_particles_close(gp: dict, op: dict, tol: float, dx: float):
+    gp, op = by_id(gp), by_id(op)
+    assert np.array_equal(gp["id"], op["id"]), (
+        f"surviving ids differ: {len(gp['id'])} vs {len(op['id'])}, "
+        f"only GPU {np.setdiff1d(gp['id'], op['id'])[:10]}, only oracle {np.setdiff1d(op['id'], gp['id'])[:10]}")
+    for k in PKEYS:
+        scale = dx if k in ("x", "y", "z") else 1.0
+        err = np.abs(gp[k] - op[k]) / (np.abs(op[k]) + scale)
+        assert err.size == 0 or err.max() <= tol, (k, float(err.max()), int(np.argmax(err)))
+
+
+def assert_field_close(g: np.ndarray, o: np.ndarray, tol: float, name: str):
+    scale = max(np.abs(o).max(), 1e-300)
+    err = np.abs(g - o).max() / scale
+    assert err <= tol, (name, float(err))
+
+
+def tally_delta(after: dict, before: dict) -> dict:
+    return {k: after[k] - before[k] for k in after}
+
+
+def assert_tallies_close(gt: dict, ot: dict, tol: float, abs_tol: float, exact_counts: bool = True):
+    """Energy tallies within tol relative plus abs_tol (J).  In FP32 a
+    per-electron energy difference carries a few ulp of the electron's own
+    energy, so abs_tol scales with the kinetic energy held by the electrons."""
+    for k in ENERGY_TALLIES:
+        assert abs(gt[k] - ot[k]) <= tol * abs(ot[k]) + abs_tol, (k, gt[k], ot[k])
+    for k in COUNT_TALLIES:
+        if exact_counts:
+            assert gt[k] == ot[k], (k, gt[k], ot[k])

@@ -1,0 +1,97 @@
+"""Host-side checks of the C-ABI (no GPU): the library loads, exports every
+function include/hpic.h declares, its struct layouts match the binding, and
+argument validation fails with the documented codes before any CUDA work."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2107_01723_gb300 import build as B
+from paper_2107_01723_gb300 import hpic
+from paper_2107_01723_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hpic.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return hpic.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hpic_\w+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_layouts_match_header(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "hpic.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\","
+        "sizeof(hpic_target_desc), sizeof(hpic_laser_desc), sizeof(hpic_run_params),"
+        "sizeof(hpic_tallies), offsetof(hpic_run_params, kappa_esc),"
+        "offsetof(hpic_run_params, max_history), offsetof(hpic_laser_desc, n_macro));return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [C.sizeof(hpic.hpic_target_desc), C.sizeof(hpic.hpic_laser_desc),
+            C.sizeof(hpic.hpic_run_params), C.sizeof(hpic.hpic_tallies),
+            hpic.hpic_run_params.kappa_esc.offset, hpic.hpic_run_params.max_history.offset,
+            hpic.hpic_laser_desc.n_macro.offset]
+    assert got == want
+
+
+def _bad(lib, target, run):
+    h = C.c_void_p()
+    t, r = hpic.target_desc(target), hpic.run_params(run)
+    code = lib.hpic_init_target(C.byref(h), C.byref(t), C.byref(r), 0, None)
+    assert not h.value
+    return code, lib.hpic_last_error(None).decode()
+
+
+def test_validation_rejects_bad_arguments(lib):
+    c = W.config_small()
+    t, r = c["target"], c["run"]
+    assert _bad(lib, dict(t, nx=1), r)[0] == hpic.HPIC_EINVAL
+    assert _bad(lib, dict(t, dx=1e-7), r)[0] == hpic.HPIC_EINVAL  # c dt > dx
+    assert _bad(lib, dict(t, Z=0.0), r)[0] == hpic.HPIC_EINVAL
+    assert _bad(lib, t, dict(r, n_E=0))[0] == hpic.HPIC_EINVAL
+    assert _bad(lib, t, dict(r, table_rows=1))[0] == hpic.HPIC_EINVAL
+    assert _bad(lib, t, dict(r, physics=64))[0] == hpic.HPIC_EINVAL
+    code, msg = _bad(lib, dict(t, nx=1), r)
+    assert "dimension" in msg
+    assert lib.hpic_init_target(None, None, None, 0, None) == hpic.HPIC_EINVAL
+    assert lib.hpic_step(None, 1) == hpic.HPIC_EINVAL
+    assert lib.hpic_destroy(None) == hpic.HPIC_EINVAL
+
+
+def test_no_device_is_an_error_not_a_fallback(lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    c = W.config_small()
+    code, msg = _bad(lib, c["target"], c["run"])
+    assert code == hpic.HPIC_ECUDA
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(hpic, "_lib", None)
+    monkeypatch.setattr(hpic, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(FileNotFoundError):
+        hpic.lib()

@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Tolerances (derived in DESIGN.md, "Parity bar"):
+  FP64 path: 1e-12 relative per element after one step (rounding order only).
+  FP32-mixed path: 1e-5 relative per element after one step (particle state
+  relative to |value| + dx or 1; fields relative to their max-norm), energy
+  tallies within 1e-5 relative plus 1e-6 of the electrons' kinetic energy.
+Decisions (survival, emission, reflux) must agree exactly at these sizes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2107_01723_gb300 import hpic
+from paper_2107_01723_gb300 import workloads as W
+
+from parity import (GRIDS_STATE, assert_field_close, assert_particles_close,
+                    assert_tallies_close, by_id, gpu_from_oracle, tally_delta)
+
+pytestmark = pytest.mark.gpu
+
+PREC = {"fp64": (hpic.HPIC_FP64, 1e-12, 1e-12), "fp32": (hpic.HPIC_FP32_MIXED, 1e-5, 1e-6)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2107_01723_gb300 import build
+    build.build()
+
+
+def small_cfg(**kw):
+    base = dict(n=(12, 10, 14), n_macro=6000, I_Wcm2=1e21, steps=40, spot_r=3e-6, t_inj=20e-15)
+    base.update(kw)
+    return W.config_small(**base)
+
+
+def one_step_compare(osim, cfg, prec_name, sort_first=False):
+    prec, tol, abs_frac = PREC[prec_name]
+    g = gpu_from_oracle(osim, cfg, prec)
+    if sort_first:
+        g.sort()
+    ot0 = osim.tallies()
+    hE0, hN0 = osim.hist()
+    osim.step(1)
+    g.step(1)
+    dx = cfg["target"]["dx"]
+    assert_particles_close(g.particles(), osim.particles(), tol, dx)
+    for k in ("jx", "jy", "jz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "heat"):
+        assert_field_close(g.grid(k), osim.grid(k), tol, k)
+    for k in ("T", "eta"):
+        err = np.max(np.abs(g.grid(k) - osim.grid(k)) / np.abs(osim.grid(k)))
+        assert err <= tol, (k, err)
+    gt = g.tallies()
+    ot = tally_delta(osim.tallies(), ot0)
+    assert_tallies_close(gt, ot, tol, abs_frac * ot0["E_live"])
+    ghE, ghN = g.hist()
+    oE, oN = osim.hist()
+    assert_field_close(ghE, oE - hE0, tol, "histE")
+    assert_field_close(ghN, oN - hN0, tol, "histN")
+    assert g.clock() == osim.clock()
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_single_step_parity(prec):
+    cfg = small_cfg()
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    o.step(30)  # fields, heating, reflux and injection are all active at step 30
+    t = o.tallies()
+    assert t["n_refluxed"] > 0 and t["n_emitted"] > 0
+    one_step_compare(o, cfg, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_single_step_parity_after_sort(prec):
+    cfg = small_cfg(seed=3)
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    o.step(25)
+    one_step_compare(o, cfg, prec, sort_first=True)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_injection_from_empty(prec):
+    cfg = small_cfg()
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    one_step_compare(o, cfg, prec)  # step 0: nothing moves, 150 electrons injected
+
+
+def test_edge_cases_fp64():
+    """Walls, the cut, zero optical depth and escape, in one step."""
+    cfg = small_cfg(n=(6, 5, 7), n_macro=0)
+    mc2 = 8.1871057769e-14
+    tgt = cfg["target"]
+    L = np.array([tgt["nx"], tgt["ny"], tgt["nz"]]) * tgt["dx"]
+    ue = lambda e: math.sqrt((e / mc2) * (e / mc2 + 2))
+    rows = [  # x, y, z, ux, uy, uz, tau
+        (L[0], 2e-6, 2e-6, ue(2e-13), 0, 0, 5.0),          # on the far x wall, moving out
+        (0.0, 0.0, 0.0, -ue(1e-13), -ue(1e-13), -1e-3, 5.0),  # corner, reflux on three faces
+        (3e-6, 2e-6, 3e-6, ue(1e-17), 0, 0, 5.0),          # below the 1 keV cut
+        (3e-6, 2e-6, 3e-6, 0, ue(5e-12), 0, 0.0),          # zero optical depth: emits now
+        (L[0] - 1e-8, 1e-6, 1e-6, ue(5e-11), 0, 0, 5.0),   # above the escape energy
+        (1e-6, L[1], L[2], 0.5, 0.5, 0.5, 5.0),            # on two far walls
+    ]
+    a = np.array(rows)
+    p = {k: a[:, i] for i, k in enumerate(("x", "y", "z", "ux", "uy", "uz", "tau"))}
+    p["id"] = np.arange(len(rows), dtype=np.uint32)
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    o.set_particles(p)
+    o.step(0)
+    g = gpu_from_oracle(o, cfg, hpic.HPIC_FP64)
+    o.step(1)
+    g.step(1)
+    assert_particles_close(g.particles(), o.particles(), 1e-12, tgt["dx"])
+    gt, ot = g.tallies(), o.tallies()
+    assert ot["n_cut"] >= 1 and ot["n_escaped"] >= 1 and ot["n_emitted"] >= 1
+    assert_tallies_close(gt, ot, 1e-12, 1e-25)
+    g.close()
+
+
+def test_empty_population_steps():
+    cfg = small_cfg(n_macro=0)
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=hpic.HPIC_FP32_MIXED)
+    g.step(5)
+    t = g.tallies()
+    assert t["particle_steps"] == 0 and t["E_injected"] == 0 and g.n == 0
+    assert g.clock()[0] == 5
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_run_tracks_oracle(prec):
+    """60 steps from an empty target: the FP64 path stays on the oracle's
+    trajectory (only atomic-order rounding differs); FP32 agrees statistically."""
+    cfg = small_cfg(n_macro=4000, seed=5)
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=PREC[prec][0], sort_interval=10)
+    o.step(60)
+    g.step(60)
+    ot, gt = o.tallies(), g.tallies()
+    for k in ("E_injected", "E_xray", "E_drag", "W_field", "E_live"):
+        rtol = 1e-9 if prec == "fp64" else 0.02
+        assert gt[k] == pytest.approx(ot[k], rel=rtol), k
+    for t in (ot, gt):
+        rhs = t["E_live"] + t["W_field"] + t["E_drag"] + t["E_xray"] + t["E_escaped"] + t["E_reflux"]
+        assert abs(t["E_injected"] - rhs) / t["E_injected"] < (1e-11 if t is ot or prec == "fp64" else 1e-4)
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sort_keeps_population(prec):
+    cfg = small_cfg(n_macro=5000, seed=7)
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=PREC[prec][0])
+    g.step(35)
+    before = by_id(g.particles())
+    g.sort()
+    after_raw = g.particles()
+    after = by_id(after_raw)
+    for k in before:
+        assert np.array_equal(before[k], after[k]), k
+    dx = cfg["target"]["dx"]
+    nx, ny = cfg["target"]["nx"], cfg["target"]["ny"]
+    ci = np.minimum(np.floor(after_raw["x"] / dx), nx - 1)
+    cj = np.minimum(np.floor(after_raw["y"] / dx), ny - 1)
+    ck = np.minimum(np.floor(after_raw["z"] / dx), cfg["target"]["nz"] - 1)
+    key = ci + nx * (cj + ny * ck)
+    assert np.all(np.diff(key) >= 0)
+    g.close()
+
+
+def test_load_rejects_outside_positions():
+    cfg = small_cfg(n_macro=0)
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"])
+    p = {k: np.zeros(1) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")}
+    p["x"][0] = -1e-9
+    p["id"] = np.zeros(1, dtype=np.uint32)
+    with pytest.raises(hpic.HpicError) as e:
+        g.set_particles(p)
+    assert e.value.code == hpic.HPIC_EINVAL
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_full_size_headline(prec):
+    """128^3 gold, 1e7 electrons at 1e21 W/cm^2 (the headline workload) in the
+    launch configuration the benchmark times (cell sort every 20 steps).
+
+    (1) The oracle computes the first two steps itself -- 5e4 electrons
+    injected at step 0 and pushed at step 1 through the full 128^3 grid, plus
+    the step-1 injection -- and every electron and grid element is compared.
+    (2) After the 200-step injection, properties that hold at any size:
+    energy closure, total current, div B, heating, tally consistency."""
+    cfg = W.config2()
+    prec_id, tol, abs_frac = PREC[prec]
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec_id, sort_interval=20)
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    g.step(2)
+    o.step(2)
+    dx = cfg["target"]["dx"]
+    assert_particles_close(g.particles(), o.particles(), tol, dx)
+    for k in ("jx", "jy", "jz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "heat"):
+        assert_field_close(g.grid(k), o.grid(k), tol, k)
+    for k in ("T", "eta"):
+        err = np.max(np.abs(g.grid(k) - o.grid(k)) / np.abs(o.grid(k)))
+        assert err <= tol, (k, err)
+    ot = o.tallies()
+    assert_tallies_close(g.tallies(), ot, tol, abs_frac * ot["E_injected"])
+    del o
+    if prec == "fp64":
+        g.close()
+        return
+    g.step(248)
+    t = g.tallies()
+    assert t["n_injected"] == 10_000_000
+    rhs = t["E_live"] + t["W_field"] + t["E_drag"] + t["E_xray"] + t["E_escaped"] + t["E_reflux"]
+    assert abs(t["E_injected"] - rhs) / t["E_injected"] < 1e-4
+    live = t["n_injected"] - t["n_cut"] - t["n_escaped"] - t["n_reflux_absorbed"]
+    assert g.n == live
+    P = g.particles()
+    gam = np.sqrt(1 + P["ux"] ** 2 + P["uy"] ** 2 + P["uz"] ** 2)
+    w = t["N_injected"] / t["n_injected"]
+    V = dx ** 3
+    for comp, uk in (("jx", "ux"), ("jy", "uy"), ("jz", "uz")):
+        want = -1.602176634e-19 * 299792458.0 * w * np.sum(P[uk] / gam) / V
+        assert g.grid(comp).sum() == pytest.approx(want, rel=1e-4, abs=1e-6 * abs(want) + 1.0), comp
+    nx = ny = nz = 128
+    shp = (nz + 1, ny + 1, nx + 1)
+    Bx, By, Bz = (g.grid(k).reshape(shp) for k in ("Bx", "By", "Bz"))
+    div = (Bx[:nz, :ny, 1:] - Bx[:nz, :ny, :nx]) + (By[:nz, 1:, :nx] - By[:nz, :ny, :nx]) \
+        + (Bz[1:, :ny, :nx] - Bz[:nz, :ny, :nx])
+    assert np.abs(div).max() < 1e-5 * max(np.abs(Bx).max(), np.abs(By).max(), np.abs(Bz).max())
+    T = g.grid("T")
+    assert T.min() >= cfg["target"]["T0"] and T.max() > 2 * cfg["target"]["T0"]
+    hE, hN = g.hist()
+    assert hE.sum() == pytest.approx(t["E_xray"], rel=1e-9)
+    assert hN.sum() == pytest.approx(t["n_emitted"] * w / cfg["run"]["brem_boost"], rel=1e-9)
+    assert g.history().sum() == pytest.approx(t["E_xray_above"], rel=1e-9)
+    g.close()

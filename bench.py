@@ -292,8 +292,49 @@ def run_gpu(args, world, rank, local):
     sim.close()
 
 
+def run_full(args):
+    """The whole 10 ps (20000-step) headline run in FP32-mixed and in FP64:
+    X-ray conversion efficiency above 1 MeV, CE = E_xray(k >= 1 MeV) /
+    E_laser with E_laser = E_injected / eta_l2e, and the energy-budget
+    closure, for both precisions."""
+    import torch
+
+    from paper_2107_01723_gb300 import build as B
+    from paper_2107_01723_gb300 import hpic
+    from paper_2107_01723_gb300 import workloads as W
+    B.build()
+    cfg = W.config2()
+    steps = cfg["steps"] if args.full_steps <= 0 else args.full_steps
+    out = {"what": "full headline run, CE(>1 MeV) FP32-mixed vs FP64", "steps": steps}
+    stream = torch.cuda.Stream()
+    for name, prec in (("fp32", hpic.HPIC_FP32_MIXED), ("fp64", hpic.HPIC_FP64)):
+        sim = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec,
+                       stream=stream.cuda_stream, sort_interval=SORT_INTERVAL)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        t = sim.tallies()
+        E_laser = t["E_injected"] / cfg["laser"]["eta_l2e"]
+        rhs = t["E_live"] + t["W_field"] + t["E_drag"] + t["E_xray"] + t["E_escaped"] + t["E_reflux"]
+        out[name] = {"CE_above_1MeV": t["E_xray_above"] / E_laser,
+                     "eta_e2g": t["E_xray_above"] / t["E_injected"],
+                     "closure": (t["E_injected"] - rhs) / t["E_injected"],
+                     "particle_steps": t["particle_steps"], "seconds": e0.elapsed_time(e1) / 1e3,
+                     "particle_steps_per_s": t["particle_steps"] / (e0.elapsed_time(e1) / 1e3),
+                     "live_at_end": sim.n, "tallies": t}
+        sim.close()
+    out["CE_rel_diff"] = out["fp32"]["CE_above_1MeV"] / out["fp64"]["CE_above_1MeV"] - 1.0
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--full-run", action="store_true",
+                    help="run the whole headline workload in FP32 and FP64 and compare CE")
+    ap.add_argument("--full-steps", type=int, default=0)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
@@ -304,6 +345,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.full_run:
+        run_full(args)
+        return
     if args.impl == "reference":
         # the oracle runs on rank 0 only; other ranks exit without work
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))

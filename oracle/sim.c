@@ -427,8 +427,9 @@ static void inject(orc_sim *s) {
     double rr = s->l.spot_r * sqrt(R8[0]);
     double ph = 2.0 * PI * R8[1];
     double eps = -s->T_hot * log(1.0 - R8[2]);
-    double ct = 1.0 - R8[3] * (1.0 - cosc);
-    double st_ = sqrt((1.0 - ct) * (1.0 + ct));
+    double omc = R8[3] * (1.0 - cosc);  /* 1 - cos(theta), uniform in solid angle */
+    double ct = 1.0 - omc;
+    double st_ = sqrt(omc * (2.0 - omc));
     double cph = 2.0 * PI * R9[0];
     double un = u_of_eps(eps);
     int64_t q = s->n + i;

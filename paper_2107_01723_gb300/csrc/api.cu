@@ -48,7 +48,8 @@ struct hpic_ctx {
   uint32_t *counts = nullptr;
   uint32_t *partials = nullptr;
   // grid
-  void *fields = nullptr;  // E[3], B[3], J[3] of R, each nvec
+  void *fields = nullptr;  // E[3], B[3], J[3] of R, each nvec long, vstride apart
+  long long vstride = 0;   // nvec + >= 4 padding, a multiple of 64 (aligned vector access)
   double *T = nullptr, *eta = nullptr, *H = nullptr;
   // tallies and tables
   double *tal = nullptr, *hist = nullptr, *history = nullptr, *scratch = nullptr;
@@ -108,7 +109,7 @@ template <typename R>
 hpic::GView<R> gview(const hpic_ctx *c) {
   hpic::GView<R> g;
   R *f = static_cast<R *>(c->fields);
-  const long long nv = c->K.nvec;
+  const long long nv = c->vstride;
   for (int a = 0; a < 3; ++a) {
     g.E[a] = f + a * nv;
     g.B[a] = f + (3 + a) * nv;
@@ -199,6 +200,10 @@ void fold_constants(hpic_ctx *c) {
   K.nx = t.nx; K.ny = t.ny; K.nz = t.nz;
   K.nvec = (long long)(t.nx + 1) * (t.ny + 1) * (t.nz + 1);
   K.ncell = (long long)t.nx * t.ny * t.nz;
+  K.nti = (t.nx + 3) / 4;
+  K.ntj = (t.ny + 3) / 4;
+  K.ntk = (t.nz + 3) / 4;
+  K.nkeys = (long long)K.nti * K.ntj * K.ntk * 64;
   K.cdt_dx = CL * dt / dx;
   // Eq. (5): S v dt = Z n_i e^4 dt / (4 pi eps0^2 m_e v) [bracket]
   K.K_ion = Z * ni * std::pow(QE, 4) * dt / (4.0 * PI * EPS0 * EPS0 * ME * CL) / MC2;
@@ -258,7 +263,7 @@ void fold_constants(hpic_ctx *c) {
     K.spot_r = l.spot_radius_m / dx;
     K.spot_y = l.spot_y_m / dx;
     K.spot_z = l.spot_z_m / dx;
-    K.cos_cone = std::cos(l.cone_half_angle_rad);
+    K.omc_cone = 2.0 * std::pow(std::sin(0.5 * l.cone_half_angle_rad), 2);
     K.n_macro = l.n_macro;
     long long S = std::llround(l.t_inj_s / dt);
     K.n_inj_steps = S < 1 ? 1 : S;
@@ -325,7 +330,7 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
   const int gp = grid_blocks(ctx, ctx->cap);
   const int gg = grid_blocks(ctx, ctx->K.nvec);
   for (long long s = 0; s < nsteps; ++s) {
-    CK(cudaMemsetAsync(G.J[0], 0, 3 * ctx->K.nvec * ctx->rsz, ctx->stream));
+    CK(cudaMemsetAsync(G.J[0], 0, 3 * ctx->vstride * ctx->rsz, ctx->stream));
     CK(cudaMemsetAsync(ctx->H, 0, ctx->K.ncell * sizeof(double), ctx->stream));
     if (ctx->prof) {
       if (ctx->ev_used + 2 > ctx->ev.size()) {
@@ -467,8 +472,8 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
   *out = nullptr;
   if (!t || !r) return fail(nullptr, HPIC_EINVAL, "target or run params NULL");
   if (t->nx < 2 || t->ny < 2 || t->nz < 2) return fail(nullptr, HPIC_EINVAL, "each dimension must be >= 2");
-  if ((long long)t->nx * t->ny * t->nz >= 0xFFFFFFFFll)
-    return fail(nullptr, HPIC_EINVAL, "too many cells for 32-bit sort keys");
+  if ((long long)(t->nx + 4) * (t->ny + 4) * (t->nz + 4) >= 0x7FFFFFFFll)
+    return fail(nullptr, HPIC_EINVAL, "grid too large for 31-bit node indices");
   if (!(t->dx_m > 0) || !(r->dt_s > 0) || CL * r->dt_s >= t->dx_m)
     return fail(nullptr, HPIC_EINVAL, "need dx > c dt > 0");
   if (!(t->Z > 0) || !(t->n_i_m3 > 0) || !(t->I_ex_J > 0) || !(t->Zstar > 0) ||
@@ -507,9 +512,10 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
   cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
   fold_constants(ctx);
   const hpic::Consts &K = ctx->K;
-  const long long m = K.ncell + 1;
+  ctx->vstride = round_up(K.nvec + 4, 64);
+  const long long m = K.nkeys + 1;
   const long long ntiles = (m + 4095) / 4096;
-  bool ok = cudaMalloc(&ctx->fields, 9 * K.nvec * ctx->rsz) == cudaSuccess &&
+  bool ok = cudaMalloc(&ctx->fields, 9 * ctx->vstride * ctx->rsz) == cudaSuccess &&
             cudaMalloc(&ctx->T, K.ncell * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ctx->eta, K.ncell * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ctx->H, K.ncell * sizeof(double)) == cudaSuccess &&
@@ -531,7 +537,7 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
   if (rc) return bail(rc);
   cudaStream_t st = ctx->stream;
   std::vector<double> T0(K.ncell, t->T0_K), E0(K.ncell, eta_host(ctx, t->T0_K));
-  if (cudaMemsetAsync(ctx->fields, 0, 9 * K.nvec * ctx->rsz, st) != cudaSuccess ||
+  if (cudaMemsetAsync(ctx->fields, 0, 9 * ctx->vstride * ctx->rsz, st) != cudaSuccess ||
       cudaMemsetAsync(ctx->H, 0, K.ncell * sizeof(double), st) != cudaSuccess ||
       cudaMemsetAsync(ctx->tal, 0, hpic::T_COUNT * sizeof(double), st) != cudaSuccess ||
       cudaMemsetAsync(ctx->hist, 0, 2 * hist_len(ctx) * sizeof(double), st) != cudaSuccess ||
@@ -686,7 +692,7 @@ int hpic_read_grid(hpic_ctx *ctx, int which, double *out) {
     return HPIC_OK;
   }
   const int slot = which - HPIC_GRID_EX;  // 0..8: E, B, J
-  const char *src = static_cast<const char *>(ctx->fields) + slot * L * ctx->rsz;
+  const char *src = static_cast<const char *>(ctx->fields) + slot * ctx->vstride * ctx->rsz;
   if (ctx->fp32) {
     std::vector<float> b(L);
     CK(cudaMemcpyAsync(b.data(), src, L * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
@@ -715,7 +721,7 @@ int hpic_write_grid(hpic_ctx *ctx, int which, const double *in) {
     return HPIC_OK;
   }
   const int slot = which - HPIC_GRID_EX;
-  char *dst = static_cast<char *>(ctx->fields) + slot * L * ctx->rsz;
+  char *dst = static_cast<char *>(ctx->fields) + slot * ctx->vstride * ctx->rsz;
   if (ctx->fp32) {
     std::vector<float> b(L);
     for (int64_t i = 0; i < L; ++i) b[i] = (float)(in[i] * s);

@@ -38,6 +38,8 @@ struct Counters {
 struct Consts {
   int nx, ny, nz;
   long long nvec, ncell;
+  int nti, ntj, ntk;       // 4x4x4 cell tiles per axis (sort order)
+  long long nkeys;         // nti*ntj*ntk*64 sort keys (the dead bin is nkeys)
   double cdt_dx;           // c dt / dx: cells per step at v = c
   double w;                // macro-electron weight (real electrons)
   // drag, Eq. (5): d_eps = K_ion/beta * bracket
@@ -62,7 +64,7 @@ struct Consts {
   double F_ohm, F_H, dx3, heat_den, Tp_fac;
   double eta_num, A_hot, B_cold, eta_max, lambda1;
   // injection, Eq. (B1)
-  double T_hot, spot_r, spot_y, spot_z, cos_cone;
+  double T_hot, spot_r, spot_y, spot_z, omc_cone;  // omc_cone = 1 - cos(cone)
   long long n_macro, n_inj_steps;
   // RNG
   uint32_t key0, key1, target_index;
@@ -103,8 +105,8 @@ __device__ __forceinline__ float m_exp(float x) { return expf(x); }
 __device__ __forceinline__ double m_exp(double x) { return exp(x); }
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float m_acos(float x) { return acosf(x); }
-__device__ __forceinline__ double m_acos(double x) { return acos(x); }
+__device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
 __device__ __forceinline__ void m_sincos(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void m_sincos(double x, double *s, double *c) { sincos(x, s, c); }
 // sin/cos of 2 pi u without rounding 2 pi u first
@@ -112,6 +114,13 @@ __device__ __forceinline__ void m_sincos2pi(float u, float *s, float *c) { sinco
 __device__ __forceinline__ void m_sincos2pi(double u, double *s, double *c) { sincospi(2.0 * u, s, c); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
+
+// Sort key of cell (i, j, k): 4x4x4 tiles in x-fastest tile order, cells
+// x-fastest inside a tile, so consecutive electrons share a compact box.
+__host__ __device__ __forceinline__ uint32_t tile_key(int i, int j, int k, int nti, int ntj) {
+  const uint32_t t = (uint32_t)(((k >> 2) * ntj + (j >> 2)) * nti + (i >> 2));
+  return t * 64u + (uint32_t)(((k & 3) << 4) | ((j & 3) << 2) | (i & 3));
+}
 
 template <typename R>
 __device__ __forceinline__ R kinetic(R ux, R uy, R uz) {

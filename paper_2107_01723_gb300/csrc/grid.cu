@@ -136,13 +136,13 @@ k_sort_keys(const Consts K, PView<R> p, const Counters *cnt, uint32_t *keys, uin
   const long long n = cnt->n;
   for (long long ip = blockIdx.x * (long long)blockDim.x + threadIdx.x; ip < n;
        ip += (long long)gridDim.x * blockDim.x) {
-    uint32_t key = (uint32_t)K.ncell;
+    uint32_t key = (uint32_t)K.nkeys;
     if (p.id[ip] != kDead) {
       int i = (int)m_floor(p.x[ip]), j = (int)m_floor(p.y[ip]), k = (int)m_floor(p.z[ip]);
       i = min(max(i, 0), K.nx - 1);
       j = min(max(j, 0), K.ny - 1);
       k = min(max(k, 0), K.nz - 1);
-      key = (uint32_t)(i + (long long)K.nx * (j + (long long)K.ny * k));
+      key = tile_key(i, j, k, K.nti, K.ntj);
     }
     keys[ip] = key;
     agg_inc(counts, key);
@@ -255,7 +255,7 @@ k_sort_scatter(const Consts K, PView<R> src, PView<R> dst, const Counters *cnt,
   for (long long ip = blockIdx.x * (long long)blockDim.x + threadIdx.x; ip < n;
        ip += (long long)gridDim.x * blockDim.x) {
     const uint32_t key = keys[ip];
-    if (key >= (uint32_t)K.ncell) continue;
+    if (key >= (uint32_t)K.nkeys) continue;
     const uint32_t q = agg_inc(offsets, key);
     dst.x[q] = src.x[ip];
     dst.y[q] = src.y[ip];
@@ -360,7 +360,7 @@ void launch_bheat(const Consts &K, GView<R> g, TallyView tv, int grid, cudaStrea
 template <typename R>
 int launch_sort(const Consts &K, PView<R> src, PView<R> dst, Counters *cnt, uint32_t *keys,
                 uint32_t *counts, uint32_t *partials, int grid, cudaStream_t st) {
-  const long long m = K.ncell + 1;
+  const long long m = K.nkeys + 1;
   const int ntiles = (int)((m + kScanTile - 1) / kScanTile);
   cudaMemsetAsync(counts, 0, m * sizeof(uint32_t), st);
   k_sort_keys<R><<<grid, 256, 0, st>>>(K, src, cnt, keys, counts);
@@ -368,7 +368,7 @@ int launch_sort(const Consts &K, PView<R> src, PView<R> dst, Counters *cnt, uint
   k_scan_top<<<1, 1024, 0, st>>>(partials, ntiles);
   k_scan_apply<<<ntiles, 1024, 0, st>>>(counts, m, partials);
   k_sort_scatter<R><<<grid, 256, 0, st>>>(K, src, dst, cnt, keys, counts);
-  k_sort_finish<<<1, 32, 0, st>>>(cnt, counts, K.ncell);
+  k_sort_finish<<<1, 32, 0, st>>>(cnt, counts, K.nkeys);
   return 6;
 }
 

@@ -27,6 +27,14 @@ struct TallyView {
   double *history;  // max_history
 };
 
+// the per-electron constants in the kernel's own precision (folded on the
+// host so that no double->float conversion runs per electron)
+template <typename R>
+struct HotK {
+  R w, cdt, E_cut, K_ion, L_I, K_sc, K_lg, K_tau, k_min, inv_boost;
+  R eps_esc, du_reflux, sigma_dtheta, tE_min, tE_max, inv_dlogE, th_scale, t_inv_dlog;
+};
+
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
                  TallyView tv, int grid, cudaStream_t st);

@@ -12,10 +12,17 @@
 //   current deposit at x^{n+1}                       j_h of Eq. (A2)
 // Random numbers: Philox4x32-10, counter (step, id, block, target), key = seed;
 // block 0 scatter, 1 emission, 2..4 reflux on x/y/z faces, 8-9 injection.
+//
+// Memory traffic: the electron state streams through once (evict-first
+// loads and stores, so the grid stays resident in L2); the grid is read
+// through the read-only path and the current is added by reductions in L2.
+// Electrons are kept sorted by 4x4x4 cell tiles, so a warp's gathers and
+// reductions fall on few L2 lines.
 #include "kernels.h"
 
 namespace hpic {
 
+// ---------------------------------------------------------------- geometry
 template <typename R>
 struct Axis {
   int iN, iS;  // base node of the node-centred / half-staggered lattice
@@ -41,32 +48,57 @@ __device__ __forceinline__ Axis<R> axis_weights(R X, int n) {
   return a;
 }
 
+// the x-neighbour pair (G[q], G[q+1]) through the read-only path.  (Aligned
+// 16-byte pair loads and v4 vector reductions were measured slower here:
+// the per-lane alignment selects and the +0 lanes cost more than they save.)
 template <typename R>
-__device__ __forceinline__ R trilerp(const R *__restrict__ G, long long b, int sy, long long sz,
-                                     R fx, R fy, R fz) {
-  const R gx = R(1) - fx;
-  const R c00 = __ldg(G + b) * gx + __ldg(G + b + 1) * fx;
-  const R c10 = __ldg(G + b + sy) * gx + __ldg(G + b + sy + 1) * fx;
-  const R c01 = __ldg(G + b + sz) * gx + __ldg(G + b + sz + 1) * fx;
-  const R c11 = __ldg(G + b + sz + sy) * gx + __ldg(G + b + sz + sy + 1) * fx;
-  const R c0 = c00 * (R(1) - fy) + c10 * fy;
-  const R c1 = c01 * (R(1) - fy) + c11 * fy;
-  return c0 * (R(1) - fz) + c1 * fz;
+__device__ __forceinline__ void ld_pair(const R *G, int q, R &v0, R &v1) {
+  v0 = __ldg(G + q);
+  v1 = __ldg(G + q + 1);
 }
 
 template <typename R>
-__device__ __forceinline__ void spread(R *G, long long b, int sy, long long sz, R fx, R fy, R fz,
-                                       R v) {
+__device__ __forceinline__ void red_pair(R *G, int q, R v0, R v1) {
+  atomicAdd(G + q, v0);
+  atomicAdd(G + q + 1, v1);
+}
+
+// the grid as the push kernel sees it; node (i, j, k) lives at i + sy*j + sz*k
+template <typename R>
+struct Grid {
+  const R *F[6];  // Ex Ey Ez Bx By Bz
+  R *J[3];
+  double *H;
+  int sy, sz, nx, ny;
+  __device__ __forceinline__ int node(int i, int j, int k) const { return i + sy * j + sz * k; }
+};
+
+template <typename R>
+__device__ __forceinline__ R trilerp(const Grid<R> &g, int c, int b, R fx, R fy, R fz) {
+  const R gx = R(1) - fx;
+  R a0, a1, b0, b1, c0, c1, d0, d1;
+  ld_pair(g.F[c], b, a0, a1);
+  ld_pair(g.F[c], b + g.sy, b0, b1);
+  ld_pair(g.F[c], b + g.sz, c0, c1);
+  ld_pair(g.F[c], b + g.sz + g.sy, d0, d1);
+  const R e00 = a0 * gx + a1 * fx;
+  const R e10 = b0 * gx + b1 * fx;
+  const R e01 = c0 * gx + c1 * fx;
+  const R e11 = d0 * gx + d1 * fx;
+  const R e0 = e00 * (R(1) - fy) + e10 * fy;
+  const R e1 = e01 * (R(1) - fy) + e11 * fy;
+  return e0 * (R(1) - fz) + e1 * fz;
+}
+
+template <typename R>
+__device__ __forceinline__ void spread(const Grid<R> &g, int c, int b, R fx, R fy, R fz, R v) {
   const R gx = R(1) - fx, gy = R(1) - fy, gz = R(1) - fz;
   const R v0 = v * gz, v1 = v * fz;
-  atomicAdd(G + b, v0 * gy * gx);
-  atomicAdd(G + b + 1, v0 * gy * fx);
-  atomicAdd(G + b + sy, v0 * fy * gx);
-  atomicAdd(G + b + sy + 1, v0 * fy * fx);
-  atomicAdd(G + b + sz, v1 * gy * gx);
-  atomicAdd(G + b + sz + 1, v1 * gy * fx);
-  atomicAdd(G + b + sz + sy, v1 * fy * gx);
-  atomicAdd(G + b + sz + sy + 1, v1 * fy * fx);
+  R *G = g.J[c];
+  red_pair(G, b, v0 * gy * gx, v0 * gy * fx);
+  red_pair(G, b + g.sy, v0 * fy * gx, v0 * fy * fx);
+  red_pair(G, b + g.sz, v1 * gy * gx, v1 * gy * fx);
+  red_pair(G, b + g.sz + g.sy, v1 * fy * gx, v1 * fy * fx);
 }
 
 // G(u0) = integral_{u0}^{1} s(u)/u du for s(u) = (4/3)(1-u) + u^2
@@ -77,23 +109,24 @@ __device__ __forceinline__ R shape_G(R u0) {
 
 // photon energy from the inverse-CDF table (rows: ln eps, columns: r)
 template <typename R>
-__device__ __forceinline__ R sample_k(const Consts &K, const R *__restrict__ tab, R eps, R r) {
-  const R lr = m_log(eps / R(K.k_min));
-  R L = lr * R(K.t_inv_dlog);
+__device__ __forceinline__ R sample_k(const HotK<R> &h, int rows, int cols,
+                                      const R *__restrict__ tab, R eps, R r) {
+  const R lr = m_log(eps / h.k_min);
+  R L = lr * h.t_inv_dlog;
   int i = (int)m_floor(L);
-  i = min(max(i, 0), K.t_rows - 2);
+  i = min(max(i, 0), rows - 2);
   R f = L - R(i);
   f = f < R(0) ? R(0) : (f > R(1) ? R(1) : f);
-  const R cpos = r * R(K.t_cols - 1);
+  const R cpos = r * R(cols - 1);
   int j = (int)m_floor(cpos);
-  j = min(max(j, 0), K.t_cols - 2);
+  j = min(max(j, 0), cols - 2);
   const R g = cpos - R(j);
-  const R *t0 = tab + (long long)i * K.t_cols + j;
-  const R *t1 = t0 + K.t_cols;
+  const R *t0 = tab + i * cols + j;
+  const R *t1 = t0 + cols;
   const R va = __ldg(t0) * (R(1) - g) + __ldg(t0 + 1) * g;
   const R vb = __ldg(t1) * (R(1) - g) + __ldg(t1 + 1) * g;
   const R v = va * (R(1) - f) + vb * f;
-  return R(K.k_min) * m_exp(v * lr);
+  return h.k_min * m_exp(v * lr);
 }
 
 // photon polar angle: theta = t/gamma, t ~ t/(1+t^2)^2 truncated at theta = pi
@@ -106,234 +139,265 @@ __device__ __forceinline__ R photon_theta(R gamma, R u) {
   return m_sqrt(F / omF) / gamma;
 }
 
+// per-thread tally accumulators
 template <typename R>
-__global__ void __launch_bounds__(256)
-k_push(const Consts K, PView<R> p, GView<R> g, const R *__restrict__ tab, Counters *cnt,
-       TallyView tv) {
-  __shared__ double smem[13 * 32];
-  const long long n = cnt->n;
-  const long long step_ll = cnt->step;
-  const uint32_t step = (uint32_t)step_ll;
-  const int nx = K.nx, ny = K.ny, nz = K.nz;
-  const int sy = nx + 1;
-  const long long sz = (long long)(nx + 1) * (ny + 1);
-  const R w = R(K.w);
-  const R cdt = R(K.cdt_dx);
-  const R Ecut = R(K.E_cut);
+struct Acc {
+  R W = 0, drag = 0;
+  double esc = 0, ref = 0, x = 0, xa = 0;
+  int n_esc = 0, n_ref = 0, n_refabs = 0, n_cut = 0, n_emit = 0, n_steps = 0, n_nf = 0;
+};
 
-  R a_W = 0, a_drag = 0;
-  double a_esc = 0, a_ref = 0, a_x = 0, a_xa = 0;
-  int c_esc = 0, c_ref = 0, c_refabs = 0, c_cut = 0, c_emit = 0, c_steps = 0, c_nf = 0;
+struct StepCtx {
+  uint32_t step, key0, key1, target;
+  long long step_ll;
+};
+
+// Advance one live electron through the step.  Returns false when the
+// electron is absorbed or escapes (the caller marks its slot dead).  On
+// true, the state holds x^{n+1}, u^{n+1} and tau, and its current is
+// deposited.
+template <typename R>
+__device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const Grid<R> &g,
+                                        const R *__restrict__ tab, const TallyView &tv,
+                                        const StepCtx &sc, uint32_t id, R &X, R &Y, R &Zc,
+                                        R &ux, R &uy, R &uz, R &tau, Acc<R> &acc) {
+  const int nx = K.nx, ny = K.ny, nz = K.nz;
+
+  // ---- gather at x^n
+  const Axis<R> ax = axis_weights(X, nx), ay = axis_weights(Y, ny), az = axis_weights(Zc, nz);
+  const R Ex = trilerp(g, 0, g.node(ax.iS, ay.iN, az.iN), ax.fS, ay.fN, az.fN);
+  const R Ey = trilerp(g, 1, g.node(ax.iN, ay.iS, az.iN), ax.fN, ay.fS, az.fN);
+  const R Ez = trilerp(g, 2, g.node(ax.iN, ay.iN, az.iS), ax.fN, ay.fN, az.fS);
+  const R Bx = trilerp(g, 3, g.node(ax.iN, ay.iS, az.iS), ax.fN, ay.fS, az.fS);
+  const R By = trilerp(g, 4, g.node(ax.iS, ay.iN, az.iS), ax.fS, ay.fN, az.fS);
+  const R Bz = trilerp(g, 5, g.node(ax.iS, ay.iS, az.iN), ax.fS, ay.fS, az.fN);
+
+  // ---- Boris push: half kick, rotation, half kick
+  const R eps0 = kinetic(ux, uy, uz);
+  {
+    const R mx = ux + R(0.5) * Ex, my = uy + R(0.5) * Ey, mz = uz + R(0.5) * Ez;
+    const R gm = m_sqrt(R(1) + mx * mx + my * my + mz * mz);
+    const R hh = R(0.5) / gm;
+    const R tx = Bx * hh, ty = By * hh, tz = Bz * hh;
+    const R s2 = R(2) / (R(1) + tx * tx + ty * ty + tz * tz);
+    const R sx = tx * s2, sy_ = ty * s2, sz_ = tz * s2;
+    const R qx = mx + (my * tz - mz * ty), qy = my + (mz * tx - mx * tz), qz = mz + (mx * ty - my * tx);
+    ux = mx + (qy * sz_ - qz * sy_) + R(0.5) * Ex;
+    uy = my + (qz * sx - qx * sz_) + R(0.5) * Ey;
+    uz = mz + (qx * sy_ - qy * sx) + R(0.5) * Ez;
+  }
+  R eps = kinetic(ux, uy, uz);
+  acc.W += h.w * (eps0 - eps);
+  R heat = 0;
+  bool alive = true;
+
+  // ---- tracking cut and ionisation drag, Eq. (5)
+  if (eps < h.E_cut) {
+    heat += h.w * eps;
+    alive = false;
+  } else if (K.physics & P_DRAG) {
+    const R gam = R(1) + eps;
+    const R beta = u_of_eps(eps) / gam;
+    const R ig = R(1) / gam;
+    R br = m_log(eps) + h.L_I + R(0.5) * m_log(gam + R(1)) + R(0.909) * ig * ig -
+           R(0.818) * ig - R(0.246);
+    br = br < R(0) ? R(0) : br;
+    const R de = h.K_ion / beta * br;
+    const R eps1 = eps - de;
+    if (eps1 < h.E_cut) {
+      heat += h.w * eps;
+      alive = false;
+    } else {
+      const R s = u_of_eps(eps1) / m_sqrt(ux * ux + uy * uy + uz * uz);
+      ux *= s; uy *= s; uz *= s;
+      heat += h.w * de;
+      eps = eps1;
+    }
+  }
+
+  // ---- Davies scatter, Eq. (B4): polar Gamma*sigma, azimuth uniform
+  if (alive && (K.physics & P_SCATTER)) {
+    const U4 r0 = philox10(sc.step, id, 0u, sc.target, sc.key0, sc.key1);
+    const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
+    const R gam = m_sqrt(R(1) + un * un);
+    R lg = m_log(h.K_lg * un);
+    lg = lg < R(0) ? R(0) : lg;
+    const R sig = m_sqrt(h.K_sc * gam / (un * un * un) * lg);
+    R s1, c1, s2, c2, st, ct;
+    m_sincos2pi(unif<R>(r0.b), &s1, &c1);
+    const R gauss = m_sqrt(R(-2) * m_log(unif<R>(r0.a))) * c1;
+    m_sincos(gauss * sig, &st, &ct);
+    m_sincos2pi(unif<R>(r0.c), &s2, &c2);
+    const R inv = R(1) / un;
+    R dx = ux * inv, dy = uy * inv, dz = uz * inv;
+    rotate(dx, dy, dz, ct, st, c2, s2);
+    ux = un * dx; uy = un * dy; uz = un * dz;
+  }
+
+  // ---- bremsstrahlung by optical depth (App. B)
+  if (alive && (K.physics & P_BREM) && eps > h.k_min) {
+    tau -= h.K_tau * u_of_eps(eps) / eps * shape_G(h.k_min / eps);
+    if (tau <= R(0)) {
+      const U4 r1 = philox10(sc.step, id, 1u, sc.target, sc.key0, sc.key1);
+      const R k = sample_k(h, K.t_rows, K.t_cols, tab, eps, unif<R>(r1.a));
+      const R thg = photon_theta(R(1) + eps, unif<R>(r1.b));
+      const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
+      R dx = ux / un, dy = uy / un, dz = uz / un;
+      R st, ct, sp, cp;
+      m_sincos(thg, &st, &ct);
+      m_sincos2pi(unif<R>(r1.c), &sp, &cp);
+      rotate(dx, dy, dz, ct, st, cp, sp);
+      const R th = m_atan2(m_sqrt(dy * dy + dz * dz), dx);  // polar angle from +x
+      // photon tally: energy row (underflow, log bins, overflow) x polar bin
+      int row;
+      if (k < h.tE_min) row = 0;
+      else if (k >= h.tE_max) row = K.n_E + 1;
+      else row = min(max(1 + (int)m_floor(h.inv_dlogE * m_log(k / h.tE_min)), 1), K.n_E);
+      const int col = min(max((int)m_floor(th * h.th_scale), 0), K.n_th - 1);
+      const double wph = K.w * K.inv_boost;
+      const double ek = wph * (double)k;
+      const int hb = row * K.n_th + col;
+      atomicAdd(tv.hist + hb, ek);
+      atomicAdd(tv.hist + (K.n_E + 2) * K.n_th + hb, wph);
+      acc.x += ek;
+      if ((double)k >= K.ce_thr) {
+        acc.xa += ek;
+        if (sc.step_ll < K.max_history) atomicAdd(tv.history + sc.step_ll, ek);
+      }
+      ++acc.n_emit;
+      tau = -m_log(R(1) - unif<R>(r1.d));
+      eps -= k * h.inv_boost;
+      if (eps < h.E_cut) {
+        heat += h.w * eps;
+        alive = false;
+      } else {
+        const R s = u_of_eps(eps) / un;
+        ux *= s; uy *= s; uz *= s;
+      }
+    }
+  }
+
+  acc.drag += heat;
+  if (heat != R(0)) atomicAdd(g.H + (ax.iN + nx * (ay.iN + ny * az.iN)), (double)heat);
+  if (!alive) {
+    ++acc.n_cut;
+    return false;
+  }
+
+  // ---- move, then escape or reflux at each face crossed (x, y, z)
+  R ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+  R pos[3] = {X + ux * ig * h.cdt, Y + uy * ig * h.cdt, Zc + uz * ig * h.cdt};
+  R u[3] = {ux, uy, uz};
+  const int nn[3] = {nx, ny, nz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const R L = R(nn[a]);
+    if (pos[a] >= R(0) && pos[a] <= L) continue;
+    const R e_out = kinetic(u[0], u[1], u[2]);
+    if (e_out >= h.eps_esc) {
+      acc.esc += (double)(h.w * e_out);
+      ++acc.n_esc;
+      return false;
+    }
+    const bool low = pos[a] < R(0);
+    pos[a] = low ? -pos[a] : R(2) * L - pos[a];
+    u[a] = -u[a];
+    const R un = m_sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const R un2 = un - h.du_reflux;
+    if (un2 <= R(0)) {
+      acc.ref += (double)(h.w * e_out);
+      ++acc.n_refabs;
+      return false;
+    }
+    const U4 r2 = philox10(sc.step, id, 2u + a, sc.target, sc.key0, sc.key1);
+    const R xi = h.sigma_dtheta * (unif<R>(r2.a) - R(0.5));
+    R st, ct, sp, cp;
+    m_sincos(xi, &st, &ct);
+    m_sincos2pi(unif<R>(r2.b), &sp, &cp);
+    const R inv = R(1) / un;
+    R d[3] = {u[0] * inv, u[1] * inv, u[2] * inv};
+    rotate(d[0], d[1], d[2], ct, st, cp, sp);
+    if (low && d[a] < R(0)) d[a] = -d[a];
+    if (!low && d[a] > R(0)) d[a] = -d[a];
+    u[0] = un2 * d[0]; u[1] = un2 * d[1]; u[2] = un2 * d[2];
+    acc.ref += (double)(h.w * (e_out - kinetic(u[0], u[1], u[2])));
+    ++acc.n_ref;
+  }
+  X = pos[0]; Y = pos[1]; Zc = pos[2];
+  ux = u[0]; uy = u[1]; uz = u[2];
+
+  // ---- current deposit at x^{n+1}: J += w (u/gamma) S(x)
+  ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+  const Axis<R> bx = axis_weights(X, nx), by = axis_weights(Y, ny), bz = axis_weights(Zc, nz);
+  spread(g, 0, g.node(bx.iS, by.iN, bz.iN), bx.fS, by.fN, bz.fN, h.w * ux * ig);
+  spread(g, 1, g.node(bx.iN, by.iS, bz.iN), bx.fN, by.fS, bz.fN, h.w * uy * ig);
+  spread(g, 2, g.node(bx.iN, by.iN, bz.iS), bx.fN, by.fN, bz.fS, h.w * uz * ig);
+  return true;
+}
+
+// evict-first access to the streaming electron state
+template <typename R>
+__device__ __forceinline__ R ld_stream(const R *p) { return __ldcs(p); }
+template <typename R>
+__device__ __forceinline__ void st_stream(R *p, R v) { __stcs(p, v); }
+
+template <typename R>
+__global__ void __launch_bounds__(256, 2)
+k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__restrict__ tab,
+       Counters *cnt, TallyView tv) {
+  __shared__ double red[13 * 32];
+  const long long n = cnt->n;
+  StepCtx sc;
+  sc.step_ll = cnt->step;
+  sc.step = (uint32_t)sc.step_ll;
+  sc.key0 = K.key0;
+  sc.key1 = K.key1;
+  sc.target = K.target_index;
+
+  Grid<R> g;
+  for (int c = 0; c < 3; ++c) {
+    g.F[c] = gv.E[c];
+    g.F[3 + c] = gv.B[c];
+    g.J[c] = gv.J[c];
+  }
+  g.H = gv.H;
+  g.sy = K.nx + 1;
+  g.sz = (K.nx + 1) * (K.ny + 1);
+  g.nx = K.nx;
+  g.ny = K.ny;
+  Acc<R> acc;
 
   for (long long ip = blockIdx.x * (long long)blockDim.x + threadIdx.x; ip < n;
        ip += (long long)gridDim.x * blockDim.x) {
-    const uint32_t id = p.id[ip];
+    const uint32_t id = ld_stream(p.id + ip);
     if (id == kDead) continue;
-    R X = p.x[ip], Y = p.y[ip], Zc = p.z[ip];
-    R ux = p.ux[ip], uy = p.uy[ip], uz = p.uz[ip];
-    R tau = p.tau[ip];
+    R X = ld_stream(p.x + ip), Y = ld_stream(p.y + ip), Zc = ld_stream(p.z + ip);
+    R ux = ld_stream(p.ux + ip), uy = ld_stream(p.uy + ip), uz = ld_stream(p.uz + ip);
+    R tau = ld_stream(p.tau + ip);
     if (!(isfinite(X) && isfinite(Y) && isfinite(Zc) && isfinite(ux) && isfinite(uy) &&
           isfinite(uz) && isfinite(tau))) {
       p.id[ip] = kDead;
-      ++c_nf;
+      ++acc.n_nf;
       continue;
     }
-    ++c_steps;
-    const U4 r0 = philox10(step, id, 0u, K.target_index, K.key0, K.key1);
-
-    // ---- gather at x^n
-    const Axis<R> ax = axis_weights(X, nx), ay = axis_weights(Y, ny), az = axis_weights(Zc, nz);
-    const R Ex = trilerp(g.E[0], ax.iS + sy * (long long)ay.iN + sz * az.iN, sy, sz, ax.fS, ay.fN, az.fN);
-    const R Ey = trilerp(g.E[1], ax.iN + sy * (long long)ay.iS + sz * az.iN, sy, sz, ax.fN, ay.fS, az.fN);
-    const R Ez = trilerp(g.E[2], ax.iN + sy * (long long)ay.iN + sz * az.iS, sy, sz, ax.fN, ay.fN, az.fS);
-    const R Bx = trilerp(g.B[0], ax.iN + sy * (long long)ay.iS + sz * az.iS, sy, sz, ax.fN, ay.fS, az.fS);
-    const R By = trilerp(g.B[1], ax.iS + sy * (long long)ay.iN + sz * az.iS, sy, sz, ax.fS, ay.fN, az.fS);
-    const R Bz = trilerp(g.B[2], ax.iS + sy * (long long)ay.iS + sz * az.iN, sy, sz, ax.fS, ay.fS, az.fN);
-    const long long cell = ax.iN + (long long)nx * (ay.iN + (long long)ny * az.iN);
-
-    // ---- Boris push: half kick, rotation, half kick
-    const R eps0 = kinetic(ux, uy, uz);
-    {
-      const R mx = ux + R(0.5) * Ex, my = uy + R(0.5) * Ey, mz = uz + R(0.5) * Ez;
-      const R gm = m_sqrt(R(1) + mx * mx + my * my + mz * mz);
-      const R h = R(0.5) / gm;
-      const R tx = Bx * h, ty = By * h, tz = Bz * h;
-      const R s2 = R(2) / (R(1) + tx * tx + ty * ty + tz * tz);
-      const R sx = tx * s2, sy_ = ty * s2, sz_ = tz * s2;
-      const R qx = mx + (my * tz - mz * ty), qy = my + (mz * tx - mx * tz), qz = mz + (mx * ty - my * tx);
-      ux = mx + (qy * sz_ - qz * sy_) + R(0.5) * Ex;
-      uy = my + (qz * sx - qx * sz_) + R(0.5) * Ey;
-      uz = mz + (qx * sy_ - qy * sx) + R(0.5) * Ez;
-    }
-    R eps = kinetic(ux, uy, uz);
-    a_W += w * (eps0 - eps);
-    R heat = 0;
-    bool alive = true;
-
-    // ---- tracking cut and ionisation drag, Eq. (5)
-    if (eps < Ecut) {
-      heat += w * eps;
-      alive = false;
-    } else if (K.physics & P_DRAG) {
-      const R gam = R(1) + eps;
-      const R un = u_of_eps(eps);
-      const R beta = un / gam;
-      const R ig = R(1) / gam;
-      R br = m_log(eps) + R(K.L_I) + R(0.5) * m_log(gam + R(1)) + R(0.909) * ig * ig -
-             R(0.818) * ig - R(0.246);
-      br = br < R(0) ? R(0) : br;
-      const R de = R(K.K_ion) / beta * br;
-      const R eps1 = eps - de;
-      if (eps1 < Ecut) {
-        heat += w * eps;
-        alive = false;
-      } else {
-        const R sc = u_of_eps(eps1) / m_sqrt(ux * ux + uy * uy + uz * uz);
-        ux *= sc; uy *= sc; uz *= sc;
-        heat += w * de;
-        eps = eps1;
-      }
-    }
-
-    // ---- Davies scatter, Eq. (B4): polar Gamma*sigma, azimuth uniform
-    if (alive && (K.physics & P_SCATTER)) {
-      const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
-      const R gam = m_sqrt(R(1) + un * un);
-      R lg = m_log(R(K.K_lg) * un);
-      lg = lg < R(0) ? R(0) : lg;
-      const R sig = m_sqrt(R(K.K_sc) * gam / (un * un * un) * lg);
-      R s1, c1, s2, c2, st, ct;
-      m_sincos2pi(unif<R>(r0.b), &s1, &c1);
-      const R gauss = m_sqrt(R(-2) * m_log(unif<R>(r0.a))) * c1;
-      m_sincos(gauss * sig, &st, &ct);
-      m_sincos2pi(unif<R>(r0.c), &s2, &c2);
-      const R inv = R(1) / un;
-      R dx = ux * inv, dy = uy * inv, dz = uz * inv;
-      rotate(dx, dy, dz, ct, st, c2, s2);
-      ux = un * dx; uy = un * dy; uz = un * dz;
-    }
-
-    // ---- bremsstrahlung by optical depth (App. B)
-    if (alive && (K.physics & P_BREM) && eps > R(K.k_min)) {
-      const R un_e = u_of_eps(eps);
-      tau -= R(K.K_tau) * un_e / eps * shape_G(R(K.k_min) / eps);
-      if (tau <= R(0)) {
-        const U4 r1 = philox10(step, id, 1u, K.target_index, K.key0, K.key1);
-        const R k = sample_k(K, tab, eps, unif<R>(r1.a));
-        const R gam = R(1) + eps;
-        const R thg = photon_theta(gam, unif<R>(r1.b));
-        const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
-        R dx = ux / un, dy = uy / un, dz = uz / un;
-        R st, ct, sp, cp;
-        m_sincos(thg, &st, &ct);
-        m_sincos2pi(unif<R>(r1.c), &sp, &cp);
-        rotate(dx, dy, dz, ct, st, cp, sp);
-        dx = dx > R(1) ? R(1) : (dx < R(-1) ? R(-1) : dx);
-        const R th = m_acos(dx);
-        // photon tally: energy row (underflow, log bins, overflow) x polar bin
-        int row;
-        if (k < R(K.tE_min)) row = 0;
-        else if (k >= R(K.tE_max)) row = K.n_E + 1;
-        else {
-          row = 1 + (int)m_floor(R(K.inv_dlogE) * m_log(k / R(K.tE_min)));
-          row = min(max(row, 1), K.n_E);
-        }
-        int col = (int)m_floor(th * R(K.n_th / 3.14159265358979323846));
-        col = min(max(col, 0), K.n_th - 1);
-        const double wph = K.w * K.inv_boost;
-        const double ek = wph * (double)k;
-        const long long hb = (long long)row * K.n_th + col;
-        atomicAdd(tv.hist + hb, ek);
-        atomicAdd(tv.hist + (long long)(K.n_E + 2) * K.n_th + hb, wph);
-        a_x += ek;
-        if ((double)k >= K.ce_thr) {
-          a_xa += ek;
-          if (step_ll < K.max_history) atomicAdd(tv.history + step_ll, ek);
-        }
-        ++c_emit;
-        tau = -m_log(R(1) - unif<R>(r1.d));
-        eps -= k * R(K.inv_boost);
-        if (eps < Ecut) {
-          heat += w * eps;
-          alive = false;
-        } else {
-          const R sc = u_of_eps(eps) / un;
-          ux *= sc; uy *= sc; uz *= sc;
-        }
-      }
-    }
-
-    if (!alive) {
-      ++c_cut;
-      p.id[ip] = kDead;
+    ++acc.n_steps;
+    if (advance(K, h, g, tab, tv, sc, id, X, Y, Zc, ux, uy, uz, tau, acc)) {
+      st_stream(p.x + ip, X); st_stream(p.y + ip, Y); st_stream(p.z + ip, Zc);
+      st_stream(p.ux + ip, ux); st_stream(p.uy + ip, uy); st_stream(p.uz + ip, uz);
+      st_stream(p.tau + ip, tau);
     } else {
-      // ---- move, then escape or reflux at each face crossed (x, y, z)
-      R ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
-      R pos[3] = {X + ux * ig * cdt, Y + uy * ig * cdt, Zc + uz * ig * cdt};
-      R u[3] = {ux, uy, uz};
-      const int nn[3] = {nx, ny, nz};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const R L = R(nn[a]);
-        if (!alive || (pos[a] >= R(0) && pos[a] <= L)) continue;
-        const R e_out = kinetic(u[0], u[1], u[2]);
-        if (e_out >= R(K.eps_esc)) {
-          a_esc += (double)(w * e_out);
-          ++c_esc;
-          alive = false;
-          continue;
-        }
-        const bool low = pos[a] < R(0);
-        pos[a] = low ? -pos[a] : R(2) * L - pos[a];
-        u[a] = -u[a];
-        const R un = m_sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        const R un2 = un - R(K.du_reflux);
-        if (un2 <= R(0)) {
-          a_ref += (double)(w * e_out);
-          ++c_refabs;
-          alive = false;
-          continue;
-        }
-        const U4 r2 = philox10(step, id, 2u + a, K.target_index, K.key0, K.key1);
-        const R xi = R(K.sigma_dtheta) * (unif<R>(r2.a) - R(0.5));
-        R st, ct, sp, cp;
-        m_sincos(xi, &st, &ct);
-        m_sincos2pi(unif<R>(r2.b), &sp, &cp);
-        const R inv = R(1) / un;
-        R d[3] = {u[0] * inv, u[1] * inv, u[2] * inv};
-        rotate(d[0], d[1], d[2], ct, st, cp, sp);
-        if (low && d[a] < R(0)) d[a] = -d[a];
-        if (!low && d[a] > R(0)) d[a] = -d[a];
-        u[0] = un2 * d[0]; u[1] = un2 * d[1]; u[2] = un2 * d[2];
-        a_ref += (double)(w * (e_out - kinetic(u[0], u[1], u[2])));
-        ++c_ref;
-      }
-      if (!alive) {
-        p.id[ip] = kDead;
-      } else {
-        p.x[ip] = pos[0]; p.y[ip] = pos[1]; p.z[ip] = pos[2];
-        p.ux[ip] = u[0]; p.uy[ip] = u[1]; p.uz[ip] = u[2];
-        p.tau[ip] = tau;
-        // ---- current deposit at x^{n+1}: J += w (u/gamma) S(x)
-        ig = R(1) / m_sqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        const Axis<R> bx = axis_weights(pos[0], nx), by = axis_weights(pos[1], ny),
-                      bz = axis_weights(pos[2], nz);
-        spread(g.J[0], bx.iS + sy * (long long)by.iN + sz * bz.iN, sy, sz, bx.fS, by.fN, bz.fN, w * u[0] * ig);
-        spread(g.J[1], bx.iN + sy * (long long)by.iS + sz * bz.iN, sy, sz, bx.fN, by.fS, bz.fN, w * u[1] * ig);
-        spread(g.J[2], bx.iN + sy * (long long)by.iN + sz * bz.iS, sy, sz, bx.fN, by.fN, bz.fS, w * u[2] * ig);
-      }
+      p.id[ip] = kDead;
     }
-    a_drag += heat;
-    if (heat != R(0)) atomicAdd(g.H + cell, (double)heat);
   }
 
-  const double v[13] = {(double)a_W, (double)a_drag, a_esc, a_ref, a_x, a_xa, (double)c_esc,
-                        (double)c_ref, (double)c_refabs, (double)c_cut, (double)c_emit,
-                        (double)c_steps, (double)c_nf};
+  const double v[13] = {(double)acc.W, (double)acc.drag, acc.esc, acc.ref, acc.x, acc.xa,
+                        (double)acc.n_esc, (double)acc.n_ref, (double)acc.n_refabs,
+                        (double)acc.n_cut, (double)acc.n_emit, (double)acc.n_steps,
+                        (double)acc.n_nf};
   const int slot[13] = {T_W_FIELD, T_E_DRAG, T_E_ESC, T_E_REFLUX, T_E_XRAY, T_E_XRAY_ABOVE,
                         T_N_ESC, T_N_REFLUX, T_N_REFLUX_ABS, T_N_CUT, T_N_EMIT, T_PSTEPS,
                         T_N_NONFINITE};
-  block_flush<13>(v, slot, tv.tal, smem);
+  block_flush<13>(v, slot, tv.tal, red);
 }
 
 // ---------------------------------------------------------------- injection
@@ -365,8 +429,9 @@ k_inject(const Consts K, PView<R> p, Counters *cnt, long long cap, TallyView tv)
     R sp, cp;
     m_sincos2pi(unif<R>(r8.b), &sp, &cp);
     const R eps = -R(K.T_hot) * m_log(R(1) - unif<R>(r8.c));
-    const R ct = R(1) - unif<R>(r8.d) * (R(1) - R(K.cos_cone));
-    const R stt = m_sqrt((R(1) - ct) * (R(1) + ct));
+    const R omc = unif<R>(r8.d) * R(K.omc_cone);  // 1 - cos(theta)
+    const R ct = R(1) - omc;
+    const R stt = m_sqrt(omc * (R(2) - omc));
     R sc, cc;
     m_sincos2pi(unif<R>(r9.a), &sc, &cc);
     const R un = u_of_eps(eps);
@@ -401,9 +466,33 @@ __global__ void k_advance(Counters *cnt, long long cap) {
 
 // ---------------------------------------------------------------- launchers
 template <typename R>
+HotK<R> make_hot(const Consts &K) {
+  HotK<R> h;
+  h.w = R(K.w);
+  h.cdt = R(K.cdt_dx);
+  h.E_cut = R(K.E_cut);
+  h.K_ion = R(K.K_ion);
+  h.L_I = R(K.L_I);
+  h.K_sc = R(K.K_sc);
+  h.K_lg = R(K.K_lg);
+  h.K_tau = R(K.K_tau);
+  h.k_min = R(K.k_min);
+  h.inv_boost = R(K.inv_boost);
+  h.eps_esc = R(K.eps_esc);
+  h.du_reflux = R(K.du_reflux);
+  h.sigma_dtheta = R(K.sigma_dtheta);
+  h.tE_min = R(K.tE_min);
+  h.tE_max = R(K.tE_max);
+  h.inv_dlogE = R(K.inv_dlogE);
+  h.th_scale = R(K.n_th / 3.14159265358979323846);
+  h.t_inv_dlog = R(K.t_inv_dlog);
+  return h;
+}
+
+template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
                  TallyView tv, int grid, cudaStream_t st) {
-  k_push<R><<<grid, 256, 0, st>>>(K, p, g, table, cnt, tv);
+  k_push<R><<<grid, 256, 0, st>>>(K, make_hot<R>(K), p, g, table, cnt, tv);
 }
 
 template <typename R>

@@ -90,7 +90,7 @@ def test_injection_from_empty(prec):
 
 def test_edge_cases_fp64():
     """Walls, the cut, zero optical depth and escape, in one step."""
-    cfg = small_cfg(n=(6, 5, 7), n_macro=0)
+    cfg = small_cfg(n=(6, 5, 7), n_macro=0, spot_r=1e-6)
     mc2 = 8.1871057769e-14
     tgt = cfg["target"]
     L = np.array([tgt["nx"], tgt["ny"], tgt["nz"]]) * tgt["dx"]
@@ -161,10 +161,13 @@ def test_sort_keeps_population(prec):
         assert np.array_equal(before[k], after[k]), k
     dx = cfg["target"]["dx"]
     nx, ny = cfg["target"]["nx"], cfg["target"]["ny"]
-    ci = np.minimum(np.floor(after_raw["x"] / dx), nx - 1)
-    cj = np.minimum(np.floor(after_raw["y"] / dx), ny - 1)
-    ck = np.minimum(np.floor(after_raw["z"] / dx), cfg["target"]["nz"] - 1)
-    key = ci + nx * (cj + ny * ck)
+    ci = np.minimum(np.floor(after_raw["x"] / dx), nx - 1).astype(np.int64)
+    cj = np.minimum(np.floor(after_raw["y"] / dx), ny - 1).astype(np.int64)
+    ck = np.minimum(np.floor(after_raw["z"] / dx), cfg["target"]["nz"] - 1).astype(np.int64)
+    # 4x4x4 cell tiles in x-fastest order, cells x-fastest inside a tile
+    nti, ntj = (nx + 3) // 4, (ny + 3) // 4
+    tile = ((ck >> 2) * ntj + (cj >> 2)) * nti + (ci >> 2)
+    key = tile * 64 + ((ck & 3) << 4) + ((cj & 3) << 2) + (ci & 3)
     assert np.all(np.diff(key) >= 0)
     g.close()
 

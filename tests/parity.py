@@ -41,10 +41,23 @@ def assert_particles_close(gp: dict, op: dict, tol: float, dx: float):
         assert err.size == 0 or err.max() <= tol, (k, float(err.max()), int(np.argmax(err)))
 
 
-def assert_field_close(g: np.ndarray, o: np.ndarray, tol: float, name: str):
-    scale = max(np.abs(o).max(), 1e-300)
-    err = np.abs(g - o).max() / scale
+def assert_field_close(g: np.ndarray, o: np.ndarray, tol: float, name: str, scale=None):
+    """Max-norm error relative to `scale` (default: the field's own max-norm)."""
+    if scale is None:
+        scale = np.abs(o).max()
+    err = np.abs(g - o).max() / max(scale, 1e-300)
     assert err <= tol, (name, float(err))
+
+
+def assert_vector_close(gsim, osim_grid, prefix: str, tol: float):
+    """Components of one vector field (E, B or j_h) against the max-norm of the
+    whole vector: a transverse component that nearly cancels is judged on the
+    field's scale, not on its own small maximum."""
+    comps = [prefix + c for c in "xyz"]
+    o = {c: osim_grid(c) for c in comps}
+    scale = max(np.abs(v).max() for v in o.values())
+    for c in comps:
+        assert_field_close(gsim(c), o[c], tol, c, scale)
 
 
 def tally_delta(after: dict, before: dict) -> dict:

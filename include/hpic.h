@@ -220,6 +220,29 @@ int hpic_kernel_time(hpic_ctx *ctx, double *ms, int64_t *launches, double *parti
 /* Kernels launched by this context since creation (all kinds). */
 int hpic_launch_count(const hpic_ctx *ctx, int64_t *launches);
 
+/* Cell sort for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is a service of this library.  Callers such as code
+ * running inside a CUDA stream capture (allocation cannot be captured),
+ * hosts with a device-memory budget fixed at start-up, or plug-ins whose
+ * framework owns all device allocations cannot call cudaMalloc; this entry
+ * point allocates nothing.  It sorts the caller's n electron slots
+ * (in_soa: x, y, z in cells, i.e. position / dx, then ux, uy, uz, tau, all
+ * float for HPIC_FP32_MIXED or double for HPIC_FP64, then uint32 ids; all
+ * device pointers) into out_soa (same layout, room for n) in the order of
+ * hpic_sort: 4x4x4 cell tiles, x-fastest; slots with id 0xFFFFFFFF are
+ * dropped and the number kept is written to *n_live_dev (device int64).
+ * Scratch comes from one fixed 8 MiB + 64 KiB device array inside the
+ * library, which every GPU that loads the library holds until exit; hence
+ * the limits n <= 1048576 and nti*ntj*ntk*64 <= 1048576 cells (each
+ * dimension rounded up to a multiple of 4), beyond which it returns
+ * HPIC_EINVAL with a message in hpic_last_error(NULL).  The first call on a
+ * device looks up the scratch address on that device; make that call
+ * before any stream capture.  Calls share the scratch: calls that overlap on
+ * the GPU race, so serialise them.  Asynchronous on cuda_stream. */
+int hpic_sort_cells_noalloc(int32_t nx, int32_t ny, int32_t nz, int32_t precision, int64_t n,
+                            const void *const in_soa[8], void *const out_soa[8],
+                            int64_t *n_live_dev, int device, void *cuda_stream);
+
 int hpic_destroy(hpic_ctx *ctx);
 /* Last error of ctx, or of the last failed creation when ctx is NULL. */
 const char *hpic_last_error(const hpic_ctx *ctx);

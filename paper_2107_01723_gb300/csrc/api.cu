@@ -28,6 +28,8 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+void hpic::set_global_error(const char *msg) { g_create_error = msg; }
+
 struct hpic_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;

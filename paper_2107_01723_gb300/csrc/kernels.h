@@ -35,6 +35,9 @@ struct HotK {
   R eps_esc, du_reflux, sigma_dtheta, tE_min, tE_max, inv_dlogE, th_scale, t_inv_dlog;
 };
 
+// message returned by hpic_last_error(NULL) (entry points without a context)
+void set_global_error(const char *msg);
+
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
                  TallyView tv, int grid, cudaStream_t st);

@@ -104,6 +104,9 @@ def lib() -> C.CDLL:
             "hpic_launch_count": [vp, _I64P],
             "hpic_destroy": [vp],
         }
+        sig["hpic_sort_cells_noalloc"] = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
+                                          C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                          C.c_void_p, C.c_int, C.c_void_p]
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -261,6 +264,19 @@ def hpic_launch_count(h) -> int:
     n = C.c_int64()
     _check(lib().hpic_launch_count(h, C.byref(n)), h)
     return n.value
+
+
+def hpic_sort_cells_noalloc(nx: int, ny: int, nz: int, precision: int, n: int, in_ptrs,
+                            out_ptrs, n_live_dev_ptr: int, device: int = 0,
+                            stream: int = 0) -> None:
+    """Cell sort without any allocation, for callers that cannot allocate
+    (see include/hpic.h).  in_ptrs/out_ptrs: 8 device addresses each
+    (x, y, z in cells, ux, uy, uz, tau, id); n_live_dev_ptr: a device int64."""
+    ins = (C.c_void_p * 8)(*[int(p) for p in in_ptrs])
+    outs = (C.c_void_p * 8)(*[int(p) for p in out_ptrs])
+    _check(lib().hpic_sort_cells_noalloc(nx, ny, nz, precision, int(n), ins, outs,
+                                         C.c_void_p(int(n_live_dev_ptr)), device,
+                                         C.c_void_p(stream) if stream else None))
 
 
 def hpic_destroy(h) -> None:

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) k_bheat(const Consts K, GView<R> g, Tally
         e_ohm += ro * K.dx3;
         rho += ro;
       }
-      if (K.physics & P_HEATING) {
+      if ((K.physics & P_HEATING) && rho != 0.0) {  // rho = 0 leaves T and eta(T) as they are
         const double T = g.T[c];
         const double Tn = T + rho / (K.heat_den * heat_capacity(T, K.Tp_fac));
         g.T[c] = Tn;

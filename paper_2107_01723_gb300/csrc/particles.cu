@@ -160,7 +160,8 @@ template <typename R>
 __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const Grid<R> &g,
                                         const R *__restrict__ tab, const TallyView &tv,
                                         const StepCtx &sc, uint32_t id, R &X, R &Y, R &Zc,
-                                        R &ux, R &uy, R &uz, R &tau, Acc<R> &acc) {
+                                        R &ux, R &uy, R &uz, R &tau, Acc<R> &acc, R &heat_out,
+                                        int &heat_cell) {
   const int nx = K.nx, ny = K.ny, nz = K.nz;
 
   // ---- gather at x^n
@@ -278,7 +279,8 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
   }
 
   acc.drag += heat;
-  if (heat != R(0)) atomicAdd(g.H + (ax.iN + nx * (ay.iN + ny * az.iN)), (double)heat);
+  heat_out = heat;  // deposited by the warp in the cell of x^n
+  heat_cell = ax.iN + nx * (ay.iN + ny * az.iN);
   if (!alive) {
     ++acc.n_cut;
     return false;
@@ -326,13 +328,124 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
   X = pos[0]; Y = pos[1]; Zc = pos[2];
   ux = u[0]; uy = u[1]; uz = u[2];
 
-  // ---- current deposit at x^{n+1}: J += w (u/gamma) S(x)
-  ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
-  const Axis<R> bx = axis_weights(X, nx), by = axis_weights(Y, ny), bz = axis_weights(Zc, nz);
-  spread(g, 0, g.node(bx.iS, by.iN, bz.iN), bx.fS, by.fN, bz.fN, h.w * ux * ig);
-  spread(g, 1, g.node(bx.iN, by.iS, bz.iN), bx.fN, by.fS, bz.fN, h.w * uy * ig);
-  spread(g, 2, g.node(bx.iN, by.iN, bz.iS), bx.fN, by.fN, bz.fS, h.w * uz * ig);
-  return true;
+  return true;  // the caller's warp deposits the current at x^{n+1}
+}
+
+// ---------------------------------------------------------------- warp deposits
+// Electrons sorted by cell sit in contiguous runs of lanes with equal keys.
+// A run's contributions are summed by a segmented shuffle reduction and its
+// first lane (the head) adds the sums to L2, so a cell holding many
+// electrons costs one atomic per node instead of one per electron.
+struct Runs {
+  bool head;  // first lane of its run
+  int end;    // last lane of the run
+  int count;  // runs in the warp
+};
+
+__device__ __forceinline__ Runs runs_of(uint32_t key) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+  Runs r;
+  r.head = lane == 0 || prev != key;
+  const unsigned heads = __ballot_sync(0xffffffffu, r.head);
+  const unsigned after = heads & ~((2u << lane) - 1u);  // heads after this lane
+  r.end = after ? __ffs(after) - 2 : 31;
+  r.count = __popc(heads);
+  return r;
+}
+
+// sum of v over [lane, end]; at a head lane, the whole run
+template <typename R>
+__device__ __forceinline__ R seg_sum(R v, int end) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const R y = __shfl_down_sync(0xffffffffu, v, off);
+    if (lane + off <= end) v += y;
+  }
+  return v;
+}
+
+// drag heat into the cell of x^n (heat_cell < 0: nothing to add)
+template <typename R>
+__device__ __forceinline__ void warp_heat(const Grid<R> &g, R heat, int heat_cell) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t key = heat_cell >= 0 ? (uint32_t)heat_cell : 0x80000000u + lane;
+  const Runs r = runs_of(key);
+  const R s = r.count == 32 ? heat : seg_sum(heat, r.end);
+  if (r.head && heat_cell >= 0 && s != R(0)) atomicAdd(g.H + heat_cell, (double)s);
+}
+
+// Per-axis weights of one electron on the 3 nodes iN-1, iN, iN+1: the
+// node-centred lattice uses slots 1, 2; the half-staggered one slots off,
+// off+1 with off = iS - iN + 1.
+template <typename R>
+struct Slots {
+  R n[3], s[3];
+};
+
+template <typename R>
+__device__ __forceinline__ Slots<R> slots_of(const Axis<R> &a) {
+  Slots<R> w;
+  w.n[0] = R(0);
+  w.n[1] = R(1) - a.fN;
+  w.n[2] = a.fN;
+  const int off = a.iS - a.iN + 1;  // 0 or 1
+  w.s[0] = off == 0 ? R(1) - a.fS : R(0);
+  w.s[1] = off == 0 ? a.fS : R(1) - a.fS;
+  w.s[2] = off == 0 ? R(0) : a.fS;
+  return w;
+}
+
+// one current component over its 12-node frame: staggered along axis SA
+template <typename R, int SA>
+__device__ __forceinline__ void frame_component(const Grid<R> &g, int c, const Runs &r, bool dep,
+                                                int i, int j, int k, const Slots<R> &wx,
+                                                const Slots<R> &wy, const Slots<R> &wz, R v) {
+#pragma unroll
+  for (int cz = (SA == 2 ? 0 : 1); cz < 3; ++cz)
+#pragma unroll
+    for (int cy = (SA == 1 ? 0 : 1); cy < 3; ++cy)
+#pragma unroll
+      for (int cx = (SA == 0 ? 0 : 1); cx < 3; ++cx) {
+        const R w = (SA == 0 ? wx.s[cx] : wx.n[cx]) * (SA == 1 ? wy.s[cy] : wy.n[cy]) *
+                    (SA == 2 ? wz.s[cz] : wz.n[cz]);
+        const R s = seg_sum(dep ? v * w : R(0), r.end);
+        if (r.head && dep && s != R(0)) atomicAdd(g.J[c] + g.node(i - 1 + cx, j - 1 + cy, k - 1 + cz), s);
+      }
+}
+
+// current J += w (u/gamma) S(x) at x^{n+1} for the lanes with dep set
+template <typename R>
+__device__ __forceinline__ void warp_current(const Consts &K, const HotK<R> &h, const Grid<R> &g,
+                                             bool dep, R X, R Y, R Zc, R ux, R uy, R uz) {
+  const int lane = threadIdx.x & 31;
+  Axis<R> bx{}, by{}, bz{};
+  R vx = R(0), vy = R(0), vz = R(0);
+  uint32_t key = 0x80000000u + lane;
+  if (dep) {
+    const R ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+    bx = axis_weights(X, K.nx);
+    by = axis_weights(Y, K.ny);
+    bz = axis_weights(Zc, K.nz);
+    vx = h.w * ux * ig;
+    vy = h.w * uy * ig;
+    vz = h.w * uz * ig;
+    key = (uint32_t)(bx.iN + K.nx * (by.iN + K.ny * bz.iN));
+  }
+  const Runs r = runs_of(key);
+  if (r.count > 16) {  // sparse warp: one atomic per node and electron
+    if (dep) {
+      spread(g, 0, g.node(bx.iS, by.iN, bz.iN), bx.fS, by.fN, bz.fN, vx);
+      spread(g, 1, g.node(bx.iN, by.iS, bz.iN), bx.fN, by.fS, bz.fN, vy);
+      spread(g, 2, g.node(bx.iN, by.iN, bz.iS), bx.fN, by.fN, bz.fS, vz);
+    }
+    return;
+  }
+  const Slots<R> wx = slots_of(bx), wy = slots_of(by), wz = slots_of(bz);
+  frame_component<R, 0>(g, 0, r, dep, bx.iN, by.iN, bz.iN, wx, wy, wz, vx);
+  frame_component<R, 1>(g, 1, r, dep, bx.iN, by.iN, bz.iN, wx, wy, wz, vy);
+  frame_component<R, 2>(g, 2, r, dep, bx.iN, by.iN, bz.iN, wx, wy, wz, vz);
 }
 
 // evict-first access to the streaming electron state
@@ -367,27 +480,44 @@ k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__rest
   g.ny = K.ny;
   Acc<R> acc;
 
-  for (long long ip = blockIdx.x * (long long)blockDim.x + threadIdx.x; ip < n;
-       ip += (long long)gridDim.x * blockDim.x) {
-    const uint32_t id = ld_stream(p.id + ip);
-    if (id == kDead) continue;
-    R X = ld_stream(p.x + ip), Y = ld_stream(p.y + ip), Zc = ld_stream(p.z + ip);
-    R ux = ld_stream(p.ux + ip), uy = ld_stream(p.uy + ip), uz = ld_stream(p.uz + ip);
-    R tau = ld_stream(p.tau + ip);
-    if (!(isfinite(X) && isfinite(Y) && isfinite(Zc) && isfinite(ux) && isfinite(uy) &&
-          isfinite(uz) && isfinite(tau))) {
-      p.id[ip] = kDead;
-      ++acc.n_nf;
-      continue;
+  // warp-uniform loop: every lane reaches the warp-cooperative deposits
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); base < n;
+       base += stride) {
+    const long long ip = base + lane;
+    bool live = false, dep = false;
+    uint32_t id = kDead;
+    R X = 0, Y = 0, Zc = 0, ux = 0, uy = 0, uz = 0, tau = 0, heat = 0;
+    int heat_cell = -1;
+    if (ip < n) {
+      id = ld_stream(p.id + ip);
+      if (id != kDead) {
+        X = ld_stream(p.x + ip); Y = ld_stream(p.y + ip); Zc = ld_stream(p.z + ip);
+        ux = ld_stream(p.ux + ip); uy = ld_stream(p.uy + ip); uz = ld_stream(p.uz + ip);
+        tau = ld_stream(p.tau + ip);
+        if (isfinite(X) && isfinite(Y) && isfinite(Zc) && isfinite(ux) && isfinite(uy) &&
+            isfinite(uz) && isfinite(tau)) {
+          live = true;
+        } else {
+          p.id[ip] = kDead;
+          ++acc.n_nf;
+        }
+      }
     }
-    ++acc.n_steps;
-    if (advance(K, h, g, tab, tv, sc, id, X, Y, Zc, ux, uy, uz, tau, acc)) {
-      st_stream(p.x + ip, X); st_stream(p.y + ip, Y); st_stream(p.z + ip, Zc);
-      st_stream(p.ux + ip, ux); st_stream(p.uy + ip, uy); st_stream(p.uz + ip, uz);
-      st_stream(p.tau + ip, tau);
-    } else {
-      p.id[ip] = kDead;
+    if (live) {
+      ++acc.n_steps;
+      dep = advance(K, h, g, tab, tv, sc, id, X, Y, Zc, ux, uy, uz, tau, acc, heat, heat_cell);
+      if (dep) {
+        st_stream(p.x + ip, X); st_stream(p.y + ip, Y); st_stream(p.z + ip, Zc);
+        st_stream(p.ux + ip, ux); st_stream(p.uy + ip, uy); st_stream(p.uz + ip, uz);
+        st_stream(p.tau + ip, tau);
+      } else {
+        p.id[ip] = kDead;
+      }
     }
+    warp_heat(g, heat, heat != R(0) ? heat_cell : -1);
+    warp_current(K, h, g, dep, X, Y, Zc, ux, uy, uz);
   }
 
   const double v[13] = {(double)acc.W, (double)acc.drag, acc.esc, acc.ref, acc.x, acc.xa,

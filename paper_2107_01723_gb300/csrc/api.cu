@@ -474,8 +474,9 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
   *out = nullptr;
   if (!t || !r) return fail(nullptr, HPIC_EINVAL, "target or run params NULL");
   if (t->nx < 2 || t->ny < 2 || t->nz < 2) return fail(nullptr, HPIC_EINVAL, "each dimension must be >= 2");
-  if ((long long)(t->nx + 4) * (t->ny + 4) * (t->nz + 4) >= 0x7FFFFFFFll)
-    return fail(nullptr, HPIC_EINVAL, "grid too large for 31-bit node indices");
+  if ((long long)(t->nx + 4) * (t->ny + 4) * (t->nz + 4) >= 0x7FFFFFFFll ||
+      (long long)t->nx * t->ny * t->nz >= (1ll << 27) - 1)
+    return fail(nullptr, HPIC_EINVAL, "grid too large (at most 2^27 - 2 cells)");
   if (!(t->dx_m > 0) || !(r->dt_s > 0) || CL * r->dt_s >= t->dx_m)
     return fail(nullptr, HPIC_EINVAL, "need dx > c dt > 0");
   if (!(t->Z > 0) || !(t->n_i_m3 > 0) || !(t->I_ex_J > 0) || !(t->Zstar > 0) ||

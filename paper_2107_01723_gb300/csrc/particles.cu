@@ -104,7 +104,7 @@ __device__ __forceinline__ void spread(const Grid<R> &g, int c, int b, R fx, R f
 // G(u0) = integral_{u0}^{1} s(u)/u du for s(u) = (4/3)(1-u) + u^2
 template <typename R>
 __device__ __forceinline__ R shape_G(R u0) {
-  return R(4.0 / 3.0) * (-m_log(u0) - (R(1) - u0)) + R(0.5) * (R(1) - u0 * u0);
+  return R(4.0 / 3.0) * (-m_flog(u0) - (R(1) - u0)) + R(0.5) * (R(1) - u0 * u0);
 }
 
 // photon energy from the inverse-CDF table (rows: ln eps, columns: r)
@@ -200,7 +200,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     const R gam = R(1) + eps;
     const R beta = u_of_eps(eps) / gam;
     const R ig = R(1) / gam;
-    R br = m_log(eps) + h.L_I + R(0.5) * m_log(gam + R(1)) + R(0.909) * ig * ig -
+    R br = m_flog(eps) + h.L_I + R(0.5) * m_flog(gam + R(1)) + R(0.909) * ig * ig -
            R(0.818) * ig - R(0.246);
     br = br < R(0) ? R(0) : br;
     const R de = h.K_ion / beta * br;
@@ -221,7 +221,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     const U4 r0 = philox10(sc.step, id, 0u, sc.target, sc.key0, sc.key1);
     const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
     const R gam = m_sqrt(R(1) + un * un);
-    R lg = m_log(h.K_lg * un);
+    R lg = m_flog(h.K_lg * un);
     lg = lg < R(0) ? R(0) : lg;
     const R sig = m_sqrt(h.K_sc * gam / (un * un * un) * lg);
     R s1, c1, s2, c2, st, ct;
@@ -332,16 +332,36 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
 }
 
 // ---------------------------------------------------------------- warp deposits
-// Electrons sorted by cell sit in contiguous runs of lanes with equal keys.
-// A run's contributions are summed by a segmented shuffle reduction and its
-// first lane (the head) adds the sums to L2, so a cell holding many
-// electrons costs one atomic per node instead of one per electron.
+// A warp's 32 electrons can sit in one cell (just after a cell sort) or in a
+// dozen (many steps later).  Atomics from one instruction that hit the same
+// address serialise in L2, so each warp first sorts its (cell, lane) keys
+// with a 32-wide bitonic network in registers, moves every electron's
+// deposit inputs to its sorted lane, sums each cell's contributions with a
+// segmented shuffle reduction and lets the first lane of each cell issue
+// the atomics: within one instruction every address is distinct.
+constexpr uint32_t kNoCell = (1u << 27) - 1u;  // key of a lane with nothing to deposit
+
+// ascending sort of one 32-bit value per lane across the warp
+__device__ __forceinline__ uint32_t warp_sort32(uint32_t c) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint32_t o = __shfl_xor_sync(0xffffffffu, c, j);
+      const bool keep_min = ((lane & k) == 0) == ((lane & j) == 0);
+      c = keep_min ? min(c, o) : max(c, o);
+    }
+  }
+  return c;
+}
+
 struct Runs {
   bool head;  // first lane of its run
   int end;    // last lane of the run
-  int count;  // runs in the warp
 };
 
+// runs of equal keys in lane order (the keys are sorted)
 __device__ __forceinline__ Runs runs_of(uint32_t key) {
   const int lane = threadIdx.x & 31;
   const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
@@ -350,7 +370,6 @@ __device__ __forceinline__ Runs runs_of(uint32_t key) {
   const unsigned heads = __ballot_sync(0xffffffffu, r.head);
   const unsigned after = heads & ~((2u << lane) - 1u);  // heads after this lane
   r.end = after ? __ffs(after) - 2 : 31;
-  r.count = __popc(heads);
   return r;
 }
 
@@ -370,10 +389,13 @@ __device__ __forceinline__ R seg_sum(R v, int end) {
 template <typename R>
 __device__ __forceinline__ void warp_heat(const Grid<R> &g, R heat, int heat_cell) {
   const int lane = threadIdx.x & 31;
-  const uint32_t key = heat_cell >= 0 ? (uint32_t)heat_cell : 0x80000000u + lane;
-  const Runs r = runs_of(key);
-  const R s = r.count == 32 ? heat : seg_sum(heat, r.end);
-  if (r.head && heat_cell >= 0 && s != R(0)) atomicAdd(g.H + heat_cell, (double)s);
+  const uint32_t key = heat_cell >= 0 ? (uint32_t)heat_cell : kNoCell;
+  const uint32_t c = warp_sort32((key << 5) | (uint32_t)lane);
+  const uint32_t skey = c >> 5;
+  const R v = __shfl_sync(0xffffffffu, heat, (int)(c & 31u));
+  const Runs r = runs_of(skey);
+  const R s = seg_sum(v, r.end);
+  if (r.head && skey != kNoCell && s != R(0)) atomicAdd(g.H + skey, (double)s);
 }
 
 // Per-axis weights of one electron on the 3 nodes iN-1, iN, iN+1: the
@@ -381,37 +403,57 @@ __device__ __forceinline__ void warp_heat(const Grid<R> &g, R heat, int heat_cel
 // off+1 with off = iS - iN + 1.
 template <typename R>
 struct Slots {
-  R n[3], s[3];
+  R n1, n2, s0, s1, s2;
 };
 
 template <typename R>
 __device__ __forceinline__ Slots<R> slots_of(const Axis<R> &a) {
   Slots<R> w;
-  w.n[0] = R(0);
-  w.n[1] = R(1) - a.fN;
-  w.n[2] = a.fN;
+  w.n1 = R(1) - a.fN;
+  w.n2 = a.fN;
   const int off = a.iS - a.iN + 1;  // 0 or 1
-  w.s[0] = off == 0 ? R(1) - a.fS : R(0);
-  w.s[1] = off == 0 ? a.fS : R(1) - a.fS;
-  w.s[2] = off == 0 ? R(0) : a.fS;
+  w.s0 = off == 0 ? R(1) - a.fS : R(0);
+  w.s1 = off == 0 ? a.fS : R(1) - a.fS;
+  w.s2 = off == 0 ? R(0) : a.fS;
   return w;
 }
 
-// one current component over its 12-node frame: staggered along axis SA
+template <typename R>
+__device__ __forceinline__ Slots<R> shfl_slots(const Slots<R> &w, int src) {
+  Slots<R> o;
+  o.n1 = __shfl_sync(0xffffffffu, w.n1, src);
+  o.n2 = __shfl_sync(0xffffffffu, w.n2, src);
+  o.s0 = __shfl_sync(0xffffffffu, w.s0, src);
+  o.s1 = __shfl_sync(0xffffffffu, w.s1, src);
+  o.s2 = __shfl_sync(0xffffffffu, w.s2, src);
+  return o;
+}
+
+template <typename R>
+__device__ __forceinline__ R slot_n(const Slots<R> &w, int c) { return c == 1 ? w.n1 : w.n2; }
+template <typename R>
+__device__ __forceinline__ R slot_s(const Slots<R> &w, int c) {
+  return c == 0 ? w.s0 : (c == 1 ? w.s1 : w.s2);
+}
+
+// one current component over its 12-node frame, staggered along axis SA
 template <typename R, int SA>
-__device__ __forceinline__ void frame_component(const Grid<R> &g, int c, const Runs &r, bool dep,
-                                                int i, int j, int k, const Slots<R> &wx,
-                                                const Slots<R> &wy, const Slots<R> &wz, R v) {
+__device__ __forceinline__ void frame_component(const Grid<R> &g, int c, const Runs &r,
+                                                bool valid, int i, int j, int k,
+                                                const Slots<R> &wx, const Slots<R> &wy,
+                                                const Slots<R> &wz, R v) {
 #pragma unroll
   for (int cz = (SA == 2 ? 0 : 1); cz < 3; ++cz)
 #pragma unroll
     for (int cy = (SA == 1 ? 0 : 1); cy < 3; ++cy)
 #pragma unroll
       for (int cx = (SA == 0 ? 0 : 1); cx < 3; ++cx) {
-        const R w = (SA == 0 ? wx.s[cx] : wx.n[cx]) * (SA == 1 ? wy.s[cy] : wy.n[cy]) *
-                    (SA == 2 ? wz.s[cz] : wz.n[cz]);
-        const R s = seg_sum(dep ? v * w : R(0), r.end);
-        if (r.head && dep && s != R(0)) atomicAdd(g.J[c] + g.node(i - 1 + cx, j - 1 + cy, k - 1 + cz), s);
+        const R w = (SA == 0 ? slot_s(wx, cx) : slot_n(wx, cx)) *
+                    (SA == 1 ? slot_s(wy, cy) : slot_n(wy, cy)) *
+                    (SA == 2 ? slot_s(wz, cz) : slot_n(wz, cz));
+        const R s = seg_sum(v * w, r.end);
+        if (r.head && valid && s != R(0))
+          atomicAdd(g.J[c] + g.node(i - 1 + cx, j - 1 + cy, k - 1 + cz), s);
       }
 }
 
@@ -420,32 +462,37 @@ template <typename R>
 __device__ __forceinline__ void warp_current(const Consts &K, const HotK<R> &h, const Grid<R> &g,
                                              bool dep, R X, R Y, R Zc, R ux, R uy, R uz) {
   const int lane = threadIdx.x & 31;
-  Axis<R> bx{}, by{}, bz{};
+  Slots<R> wx{}, wy{}, wz{};
   R vx = R(0), vy = R(0), vz = R(0);
-  uint32_t key = 0x80000000u + lane;
+  uint32_t key = kNoCell;
   if (dep) {
     const R ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
-    bx = axis_weights(X, K.nx);
-    by = axis_weights(Y, K.ny);
-    bz = axis_weights(Zc, K.nz);
+    const Axis<R> bx = axis_weights(X, K.nx), by = axis_weights(Y, K.ny), bz = axis_weights(Zc, K.nz);
+    wx = slots_of(bx);
+    wy = slots_of(by);
+    wz = slots_of(bz);
     vx = h.w * ux * ig;
     vy = h.w * uy * ig;
     vz = h.w * uz * ig;
     key = (uint32_t)(bx.iN + K.nx * (by.iN + K.ny * bz.iN));
   }
-  const Runs r = runs_of(key);
-  if (r.count > 16) {  // sparse warp: one atomic per node and electron
-    if (dep) {
-      spread(g, 0, g.node(bx.iS, by.iN, bz.iN), bx.fS, by.fN, bz.fN, vx);
-      spread(g, 1, g.node(bx.iN, by.iS, bz.iN), bx.fN, by.fS, bz.fN, vy);
-      spread(g, 2, g.node(bx.iN, by.iN, bz.iS), bx.fN, by.fN, bz.fS, vz);
-    }
-    return;
-  }
-  const Slots<R> wx = slots_of(bx), wy = slots_of(by), wz = slots_of(bz);
-  frame_component<R, 0>(g, 0, r, dep, bx.iN, by.iN, bz.iN, wx, wy, wz, vx);
-  frame_component<R, 1>(g, 1, r, dep, bx.iN, by.iN, bz.iN, wx, wy, wz, vy);
-  frame_component<R, 2>(g, 2, r, dep, bx.iN, by.iN, bz.iN, wx, wy, wz, vz);
+  const uint32_t c = warp_sort32((key << 5) | (uint32_t)lane);
+  const uint32_t skey = c >> 5;
+  const int src = (int)(c & 31u);
+  wx = shfl_slots(wx, src);
+  wy = shfl_slots(wy, src);
+  wz = shfl_slots(wz, src);
+  vx = __shfl_sync(0xffffffffu, vx, src);
+  vy = __shfl_sync(0xffffffffu, vy, src);
+  vz = __shfl_sync(0xffffffffu, vz, src);
+  const Runs r = runs_of(skey);
+  const bool valid = skey != kNoCell;
+  const int kk = (int)(skey / (uint32_t)(K.nx * K.ny));
+  const int rem = (int)skey - kk * K.nx * K.ny;
+  const int jj = rem / K.nx, ii = rem - jj * K.nx;
+  frame_component<R, 0>(g, 0, r, valid, ii, jj, kk, wx, wy, wz, vx);
+  frame_component<R, 1>(g, 1, r, valid, ii, jj, kk, wx, wy, wz, vy);
+  frame_component<R, 2>(g, 2, r, valid, ii, jj, kk, wx, wy, wz, vz);
 }
 
 // evict-first access to the streaming electron state

@@ -36,6 +36,9 @@ WORKLOAD = ("128^3 cells x 1 um Au (Z=79, n_i=5.9e28 m^-3, T0=1 eV), 1e7 e- inje
 # algorithmic bytes per particle-step of the push kernel: the SoA state is
 # read once (x,y,z,ux,uy,uz,tau + u32 id) and written once (7 reals)
 ALG_BYTES = {"fp32": 7 * 4 + 4 + 7 * 4, "fp64": 7 * 8 + 4 + 7 * 8}
+# DRAM bytes (read + write) per particle-step of k_push measured by ncu on
+# this workload (profiles/k_push_headline_fp32.md); None where not captured
+NCU_DRAM_BYTES_PER_PSTEP = {"fp32": 55.8, "fp64": None}
 SORT_INTERVAL = 20
 
 
@@ -117,13 +120,23 @@ def barrier(world):
 
 
 def allreduce(world, vals, op="max"):
+    """Max or sum of per-rank values (replica timing and work counts)."""
     if world == 1:
         return vals
     import torch
     import torch.distributed as dist
-    t = torch.tensor(vals, dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return t.tolist()
+
+
+def replica_rate(world, ms, particle_steps):
+    """Whole-job rate of N independent replicas: all ranks' particle-steps
+    over the slowest rank's time."""
+    ms_max, = allreduce(world, [ms], "max")
+    ps_sum, = allreduce(world, [particle_steps], "sum")
+    return ps_sum / (ms_max / 1e3), ms_max, ps_sum
 
 
 def oracle_rate(steps_timed: int, warmup: int, budget_s: float) -> dict:
@@ -210,9 +223,7 @@ def run_gpu(args, world, rank, local):
     hpic.hpic_profile(sim.h, False)
     launches = hpic.hpic_launch_count(sim.h) - launches0
     ps = t1["particle_steps"] - t0["particle_steps"]
-    ms_max, = allreduce(world, [ms], "max")
-    ps_sum, = allreduce(world, [ps], "sum")
-    value = ps_sum / (ms_max / 1e3)
+    value, ms_max, ps_sum = replica_rate(world, ms, ps)
 
     # end to end through the C-ABI with host buffers: upload the state from
     # host arrays, K steps, read tallies and the state back
@@ -267,14 +278,17 @@ def run_gpu(args, world, rank, local):
     pk = peaks()
     k_avg_ms = k_ms / max(k_launches, 1)
     achieved = ALG_BYTES[args.precision] * (k_ps / max(k_launches, 1)) / (k_avg_ms / 1e3) / 1e9
+    tb = NCU_DRAM_BYTES_PER_PSTEP[args.precision]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "frac": achieved / pk["hbm_gbs"],
+                "traffic": tb * k_ps / max(k_launches, 1) if tb else None,
+                "traffic_unit": "bytes per launch (ncu dram read+write, scaled by particle-steps)",
                 "kernel": "k_push (push/collide/emit/deposit)",
                 "kernel_ms_avg": k_avg_ms, "kernel_share_of_step": k_ms / ms if ms > 0 else None,
                 "bytes_per_particle_step": ALG_BYTES[args.precision], "peak_source": pk["source"]}
     cpu = None
     if not args.no_cpu_baseline:
-        r = oracle_rate(12, 2, budget_s=25.0)
+        r = oracle_rate(200, 2, budget_s=20.0)
         cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -330,8 +344,47 @@ def run_full(args):
     print(json.dumps(out), flush=True)
 
 
+def run_emission(args):
+    """Emission microbenchmark (not the headline line): 2^27 electrons in an
+    unbounded uniform gold medium, drag + scatter + bremsstrahlung only, in
+    FP32 and FP64; k_push's particle-steps/s and HBM fraction."""
+    import torch
+
+    from paper_2107_01723_gb300 import build as B
+    from paper_2107_01723_gb300 import hpic
+    from paper_2107_01723_gb300 import workloads as W
+    B.build()
+    cfg = W.config5(n_electrons=args.emission_n)
+    pk = peaks()
+    out = {"what": "emission microbenchmark: unbounded gold, drag+scatter+bremsstrahlung",
+           "electrons": cfg["n_electrons"], "steps": args.steps, "warmup": args.warmup}
+    stream = torch.cuda.Stream()
+    for name, prec in (("fp32", hpic.HPIC_FP32_MIXED), ("fp64", hpic.HPIC_FP64)):
+        sim = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec,
+                       stream=stream.cuda_stream)
+        sim.seed(cfg["n_electrons"], cfg["mean_energy"])
+        sim.step(args.warmup)
+        hpic.hpic_profile(sim.h, True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        km, kl, kp = hpic.hpic_kernel_time(sim.h)
+        gbs = ALG_BYTES[name] * kp / (km / 1e3) / 1e9
+        out[name] = {"particle_steps_per_s": kp / (ms / 1e3), "ms_per_step": ms / args.steps,
+                     "k_push_ms": km / kl, "achieved_GBs": gbs, "frac_of_hbm": gbs / pk["hbm_gbs"],
+                     "peak_source": pk["source"], "emissions": sim.tallies()["n_emitted"]}
+        sim.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="headline", choices=["headline", "emission"])
+    ap.add_argument("--emission-n", type=int, default=2 ** 27)
     ap.add_argument("--full-run", action="store_true",
                     help="run the whole headline workload in FP32 and FP64 and compare CE")
     ap.add_argument("--full-steps", type=int, default=0)
@@ -347,6 +400,9 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.full_run:
         run_full(args)
+        return
+    if args.workload == "emission":
+        run_emission(args)
         return
     if args.impl == "reference":
         # the oracle runs on rank 0 only; other ranks exit without work

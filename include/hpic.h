@@ -68,7 +68,10 @@ enum {
   HPIC_FARADAY = 16, /* B from Eq. (A3) every step (else B is held: the
                         paper's B = 0 test, Sec. III.A) */
   HPIC_HEATING = 32, /* T and eta update, Eqs. (A4)-(A8) */
-  HPIC_ALL = 63
+  HPIC_ALL = 63,
+  /* unbounded uniform medium: no field gather, no faces, nothing deposited
+   * on the grid; drag, scatter and emission only (the emission benchmark) */
+  HPIC_UNBOUNDED = 64
 };
 
 /* grid codes for hpic_read_grid / hpic_write_grid */
@@ -168,6 +171,14 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *target,
  * (a laser was already scheduled). */
 int hpic_inject_electrons(hpic_ctx *ctx, const hpic_laser_desc *laser);
 
+/* Append n electrons uniform in the box, with directions uniform on the
+ * sphere, kinetic energies exponential with mean mean_energy_J and fresh
+ * optical depths (Philox blocks 10 and 11 at the current step; ids from the
+ * id counter; weight: the laser's macro weight, or 1 without a laser).  The
+ * bulk initial state of the emission benchmark.  Errors: HPIC_EINVAL,
+ * HPIC_ENOMEM, HPIC_ECUDA. */
+int hpic_seed_electrons(hpic_ctx *ctx, int64_t n, double mean_energy_J);
+
 /* Advance n_steps >= 0 steps (asynchronous).  Errors: HPIC_EINVAL, HPIC_ECUDA. */
 int hpic_step(hpic_ctx *ctx, int64_t n_steps);
 
@@ -201,8 +212,8 @@ int hpic_read_particles(hpic_ctx *ctx, double *x, double *y, double *z,
                         double *ux, double *uy, double *uz, double *tau,
                         uint32_t *id, int64_t cap, int64_t *n);
 /* Replace the electron population with n host electrons (same units).
- * Positions must lie in [0, n*dx] on each axis.  Errors: HPIC_EINVAL,
- * HPIC_ENOMEM. */
+ * Positions must lie in [0, n*dx] on each axis (any finite position with
+ * HPIC_UNBOUNDED).  Errors: HPIC_EINVAL, HPIC_ENOMEM. */
 int hpic_load_particles(hpic_ctx *ctx, int64_t n, const double *x, const double *y,
                         const double *z, const double *ux, const double *uy,
                         const double *uz, const double *tau, const uint32_t *id);

@@ -38,7 +38,10 @@ enum {
   ORC_FIELDS = 8,   /* E from Ohm's law with return current, Eq. (A2) */
   ORC_FARADAY = 16, /* B update, Eq. (A3); clear to hold B fixed */
   ORC_HEATING = 32, /* temperature and resistivity update, Eqs. (A4)-(A8) */
-  ORC_ALL = 63
+  ORC_ALL = 63,
+  /* unbounded uniform medium: no fields are gathered, no faces, no current
+   * or heat deposited on the grid (collisions and emission only) */
+  ORC_UNBOUNDED = 64
 };
 
 /* grid component codes */
@@ -112,6 +115,10 @@ int orc_step(orc_sim *s, int64_t n);
 /* field solve and heating on the current grids only (no particles, clock
  * unchanged): exposes Eqs. (A2)-(A8) to the pins */
 void orc_fields(orc_sim *s);
+/* append n electrons uniform in the box, isotropic, kinetic energy
+ * exponential with mean `mean_eps` (J), fresh optical depths; Philox
+ * blocks 10 and 11 at the current step, ids from the id counter */
+void orc_seed(orc_sim *s, int64_t n, double mean_eps);
 int64_t orc_n_particles(const orc_sim *s);
 /* particles in storage order; x in m, u = p/(m_e c); tau = remaining optical depth */
 void orc_get_particles(const orc_sim *s, double *x, double *y, double *z,

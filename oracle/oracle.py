@@ -19,6 +19,7 @@ SOURCES = ["physics.c", "sim.c"]
 
 ORC_DRAG, ORC_SCATTER, ORC_BREM, ORC_FIELDS, ORC_FARADAY, ORC_HEATING = 1, 2, 4, 8, 16, 32
 ORC_ALL = 63
+ORC_UNBOUNDED = 64
 GRID = {"T": 0, "eta": 1, "Ex": 2, "Ey": 3, "Ez": 4, "Bx": 5, "By": 6, "Bz": 7,
         "jx": 8, "jy": 9, "jz": 10, "heat": 11}
 
@@ -90,6 +91,7 @@ def lib():
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_step.argtypes = [C.c_void_p, C.c_int64]
         L.orc_fields.argtypes = [C.c_void_p]
+        L.orc_seed.argtypes = [C.c_void_p, C.c_int64, C.c_double]
         L.orc_n_particles.restype = C.c_int64
         L.orc_n_particles.argtypes = [C.c_void_p]
         L.orc_get_particles.argtypes = [C.c_void_p] + [dp] * 7 + [up]
@@ -182,6 +184,9 @@ class OracleSim:
 
     def fields(self) -> None:
         lib().orc_fields(self.h)
+
+    def seed(self, n: int, mean_eps: float) -> None:
+        lib().orc_seed(self.h, int(n), float(mean_eps))
 
     @property
     def n(self) -> int:

@@ -161,7 +161,7 @@ static void tally_photon(orc_sim *s, double k, double theta, double wph) {
 
 /* ---------------- one electron, one step ---------------- */
 static void kill_with_heat(orc_sim *s, int64_t ip, int64_t cell, double eps) {
-  s->g[ORC_HEAT][cell] += s->w * eps;
+  if (!(s->r.physics & ORC_UNBOUNDED)) s->g[ORC_HEAT][cell] += s->w * eps;
   s->tal.E_drag += s->w * eps;
   s->tal.n_cut += 1.0;
   s->alive[ip] = 0;
@@ -178,15 +178,20 @@ static void particle_update(orc_sim *s, int64_t ip) {
   s->tal.particle_steps += 1.0;
 
   /* field gather at x^n */
-  double E[3], B[3];
-  for (int c = 0; c < 3; ++c) {
-    E[c] = gather(s, ORC_EX + c, X);
-    B[c] = gather(s, ORC_BX + c, X);
-  }
+  const int unbounded = (r->physics & ORC_UNBOUNDED) != 0;
+  double E[3] = {0.0, 0.0, 0.0}, B[3] = {0.0, 0.0, 0.0};
+  if (!unbounded)
+    for (int c = 0; c < 3; ++c) {
+      E[c] = gather(s, ORC_EX + c, X);
+      B[c] = gather(s, ORC_BX + c, X);
+    }
   int ci = (int)floor(X[0]), cj = (int)floor(X[1]), ck = (int)floor(X[2]);
   if (ci > t->nx - 1) ci = t->nx - 1;
   if (cj > t->ny - 1) cj = t->ny - 1;
   if (ck > t->nz - 1) ck = t->nz - 1;
+  if (ci < 0) ci = 0;
+  if (cj < 0) cj = 0;
+  if (ck < 0) ck = 0;
   int64_t cell = cidx(s, ci, cj, ck);
 
   /* relativistic push; the energy change is the work of E */
@@ -206,7 +211,7 @@ static void particle_update(orc_sim *s, int64_t ip) {
     double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     double scale = u_of_eps(eps1) / un;
     for (int c = 0; c < 3; ++c) u[c] *= scale;
-    s->g[ORC_HEAT][cell] += w * de;
+    if (!unbounded) s->g[ORC_HEAT][cell] += w * de;
     s->tal.E_drag += w * de;
     eps = eps1;
   }
@@ -256,7 +261,7 @@ static void particle_update(orc_sim *s, int64_t ip) {
 
   /* escape or reflux at each face crossed, x then y then z */
   int n[3] = {t->nx, t->ny, t->nz};
-  for (int a = 0; a < 3; ++a) {
+  for (int a = 0; a < 3 && !unbounded; ++a) {
     double L = (double)n[a] * dx;
     if (pos[a] >= 0.0 && pos[a] <= L) continue;
     double e_out = kinetic(u);
@@ -297,6 +302,7 @@ static void particle_update(orc_sim *s, int64_t ip) {
   s->uz[ip] = u[2];
 
   /* hot-electron current j_h = q w v S(x) / V at x^{n+1}, q = -e */
+  if (unbounded) return;
   gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   double Xn[3] = {pos[0] / dx, pos[1] / dx, pos[2] / dx};
   double jfac = -Q_E * w / (dx * dx * dx) * C_L / gam;
@@ -448,6 +454,42 @@ static void inject(orc_sim *s) {
   }
   s->n += cnt;
   s->next_id += cnt;
+}
+
+/* ---------------- bulk seeding ----------------
+ * n electrons uniform in the box, directions uniform on the sphere
+ * (cos theta = 2u - 1), kinetic energy exponential with mean mean_eps,
+ * fresh optical depth; draws: block 10 = (eps, cos theta, phi, x),
+ * block 11 = (y, z, tau, unused) at the current step. */
+void orc_seed(orc_sim *s, int64_t n, double mean_eps) {
+  reserve(s, s->n + n);
+  const double Lx = s->t.nx * s->t.dx, Ly = s->t.ny * s->t.dx, Lz = s->t.nz * s->t.dx;
+  for (int64_t i = 0; i < n; ++i) {
+    uint32_t id = (uint32_t)(s->next_id + i);
+    double R10[4], R11[4];
+    draw(s, id, 10, R10);
+    draw(s, id, 11, R11);
+    double eps = -mean_eps * log(1.0 - R10[0]);
+    double ct = 2.0 * R10[1] - 1.0;
+    double st = sqrt((1.0 - ct) * (1.0 + ct));
+    double ph = 2.0 * PI * R10[2];
+    double un = u_of_eps(eps);
+    int64_t q = s->n + i;
+    s->x[q] = Lx * R10[3];
+    s->y[q] = Ly * R11[0];
+    s->z[q] = Lz * R11[1];
+    s->ux[q] = un * ct;
+    s->uy[q] = un * st * cos(ph);
+    s->uz[q] = un * st * sin(ph);
+    s->tau[q] = -log(1.0 - R11[2]);
+    s->id[q] = id;
+    s->alive[q] = 1;
+    s->tal.E_injected += s->w * eps;
+    s->tal.N_injected += s->w;
+    s->tal.n_injected += 1.0;
+  }
+  s->n += n;
+  s->next_id += n;
 }
 
 /* ---------------- public ---------------- */

@@ -331,9 +331,12 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
                            : reinterpret_cast<const R *>(ctx->t64);
   const int gp = grid_blocks(ctx, ctx->cap);
   const int gg = grid_blocks(ctx, ctx->K.nvec);
+  const bool grid_on = !(ctx->K.physics & hpic::P_UNBOUNDED);
   for (long long s = 0; s < nsteps; ++s) {
-    CK(cudaMemsetAsync(G.J[0], 0, 3 * ctx->vstride * ctx->rsz, ctx->stream));
-    CK(cudaMemsetAsync(ctx->H, 0, ctx->K.ncell * sizeof(double), ctx->stream));
+    if (grid_on) {
+      CK(cudaMemsetAsync(G.J[0], 0, 3 * ctx->vstride * ctx->rsz, ctx->stream));
+      CK(cudaMemsetAsync(ctx->H, 0, ctx->K.ncell * sizeof(double), ctx->stream));
+    }
     if (ctx->prof) {
       if (ctx->ev_used + 2 > ctx->ev.size()) {
         for (int q = 0; q < 64; ++q) {
@@ -351,12 +354,14 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
       ctx->ev_used += 2;
       ctx->prof_launches += 1;
     }
-    if (ctx->K.physics & hpic::P_FIELDS) {
+    if (grid_on && (ctx->K.physics & hpic::P_FIELDS)) {
       hpic::launch_efield<R>(ctx->K, G, gg, ctx->stream);
       ctx->launches += 1;
     }
-    hpic::launch_bheat<R>(ctx->K, G, tv, gg, ctx->stream);
-    ctx->launches += 1;
+    if (grid_on) {
+      hpic::launch_bheat<R>(ctx->K, G, tv, gg, ctx->stream);
+      ctx->launches += 1;
+    }
     if (ctx->have_laser && ctx->host_step < ctx->K.n_inj_steps && ctx->K.n_macro > 0) {
       const long long S = ctx->K.n_inj_steps, N = ctx->K.n_macro, st = ctx->host_step;
       const long long c = (N * (st + 1)) / S - (N * st) / S;
@@ -433,10 +438,11 @@ int load_particles_impl(hpic_ctx *ctx, int64_t n, const double *x, const double 
   const double dx = ctx->tgt.dx_m;
   const int nn[3] = {ctx->tgt.nx, ctx->tgt.ny, ctx->tgt.nz};
   const double *pos[3] = {x, y, z};
+  const bool unbounded = (ctx->K.physics & hpic::P_UNBOUNDED) != 0;
   for (int64_t i = 0; i < n; ++i) {
     for (int a = 0; a < 3; ++a) {
       const double X = pos[a][i] / dx;
-      if (!(X >= 0.0 && X <= (double)nn[a]))
+      if (unbounded ? !std::isfinite(X) : !(X >= 0.0 && X <= (double)nn[a]))
         return fail(ctx, HPIC_EINVAL, "particle position outside the target");
     }
     if (id[i] == hpic::kDead) return fail(ctx, HPIC_EINVAL, "id 0xFFFFFFFF is reserved");
@@ -490,7 +496,7 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
       r->n_Ebins < 1 || r->n_thbins < 1 || !(r->tally_Emax_J > r->tally_Emin_J) ||
       !(r->tally_Emin_J > 0) || r->max_history < 0 || r->sort_interval < 0 ||
       r->kappa_esc < 0 || r->kappa_tnsa < 0 || r->sigma_dtheta_rad < 0 ||
-      (r->physics & ~HPIC_ALL) != 0)
+      (r->physics & ~(HPIC_ALL | HPIC_UNBOUNDED)) != 0)
     return fail(nullptr, HPIC_EINVAL, "run parameters out of range");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -584,6 +590,29 @@ int hpic_inject_electrons(hpic_ctx *ctx, const hpic_laser_desc *l) {
   ctx->laser = *l;
   ctx->have_laser = true;
   fold_constants(ctx);
+  return HPIC_OK;
+}
+
+int hpic_seed_electrons(hpic_ctx *ctx, int64_t n, double mean_energy_J) {
+  if (!ctx) return HPIC_EINVAL;
+  if (n < 0 || !(mean_energy_J > 0)) return fail(ctx, HPIC_EINVAL, "bad seeding arguments");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  hpic::Counters h;
+  int rc = read_counters(ctx, &h);
+  if (rc) return rc;
+  if (h.next_id + n >= 0xFFFFFFFFll) return fail(ctx, HPIC_EINVAL, "id space exhausted");
+  rc = reserve(ctx, h.n + n + (ctx->have_laser ? ctx->K.n_macro : 0));
+  if (rc) return rc;
+  if (n == 0) return HPIC_OK;
+  const int grid = grid_blocks(ctx, n);
+  if (ctx->fp32)
+    hpic::launch_seed<float>(ctx->K, pview<float>(ctx, ctx->cur), ctx->cnt, ctx->cap, n,
+                             mean_energy_J / MC2, tview(ctx), grid, ctx->stream);
+  else
+    hpic::launch_seed<double>(ctx->K, pview<double>(ctx, ctx->cur), ctx->cnt, ctx->cap, n,
+                              mean_energy_J / MC2, tview(ctx), grid, ctx->stream);
+  ctx->launches += 2;
+  CK(cudaGetLastError());
   return HPIC_OK;
 }
 

@@ -71,7 +71,10 @@ struct Consts {
   int physics;
 };
 
-enum { P_DRAG = 1, P_SCATTER = 2, P_BREM = 4, P_FIELDS = 8, P_FARADAY = 16, P_HEATING = 32 };
+enum {
+  P_DRAG = 1, P_SCATTER = 2, P_BREM = 4, P_FIELDS = 8, P_FARADAY = 16, P_HEATING = 32,
+  P_UNBOUNDED = 64
+};
 
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds, each two

@@ -45,6 +45,10 @@ template <typename R>
 void launch_inject(const Consts &K, PView<R> p, Counters *cnt, long long cap, TallyView tv,
                    int grid, cudaStream_t st);
 void launch_advance(Counters *cnt, long long cap, cudaStream_t st);
+// bulk seeding (two launches); mean kinetic energy in m_e c^2
+template <typename R>
+void launch_seed(const Consts &K, PView<R> p, Counters *cnt, long long cap, long long count,
+                 double mean, TallyView tv, int grid, cudaStream_t st);
 
 template <typename R>
 void launch_efield(const Consts &K, GView<R> g, int grid, cudaStream_t st);

@@ -20,6 +20,7 @@ HPIC_OK, HPIC_EINVAL, HPIC_ENOMEM, HPIC_ECUDA, HPIC_ETIMEOUT, HPIC_ESTATE, HPIC_
 HPIC_FP64, HPIC_FP32_MIXED = 0, 1
 HPIC_DRAG, HPIC_SCATTER, HPIC_BREM, HPIC_FIELDS, HPIC_FARADAY, HPIC_HEATING = 1, 2, 4, 8, 16, 32
 HPIC_ALL = 63
+HPIC_UNBOUNDED = 64
 GRID = {"T": 0, "eta": 1, "Ex": 2, "Ey": 3, "Ez": 4, "Bx": 5, "By": 6, "Bz": 7,
         "jx": 8, "jy": 9, "jz": 10, "heat": 11}
 
@@ -86,6 +87,7 @@ def lib() -> C.CDLL:
                                  C.POINTER(hpic_run_params), C.c_int, vp],
             "hpic_inject_electrons": [vp, C.POINTER(hpic_laser_desc)],
             "hpic_step": [vp, C.c_int64],
+            "hpic_seed_electrons": [vp, C.c_int64, C.c_double],
             "hpic_sort": [vp],
             "hpic_read_tallies": [vp, C.POINTER(hpic_tallies)],
             "hpic_reset_tallies": [vp],
@@ -166,6 +168,10 @@ def hpic_init_target(target: dict, run: dict, precision: int = HPIC_FP64, device
 def hpic_inject_electrons(h, laser: dict) -> None:
     l = laser_desc(laser)
     _check(lib().hpic_inject_electrons(h, C.byref(l)), h)
+
+
+def hpic_seed_electrons(h, n: int, mean_energy_J: float) -> None:
+    _check(lib().hpic_seed_electrons(h, int(n), float(mean_energy_J)), h)
 
 
 def hpic_step(h, n: int = 1) -> None:
@@ -307,6 +313,9 @@ class Sim:
 
     def step(self, n: int = 1) -> None:
         hpic_step(self.h, n)
+
+    def seed(self, n: int, mean_energy_J: float) -> None:
+        hpic_seed_electrons(self.h, n, mean_energy_J)
 
     def sort(self) -> None:
         hpic_sort(self.h)

@@ -72,6 +72,18 @@ def config1() -> dict:
             "run": run(seed=0, max_history=200), "steps": 200}
 
 
+def config5(n_electrons=2 ** 27, steps=1000) -> dict:
+    """Emission microbenchmark: electrons in unbounded uniform gold (no fields,
+    no faces, T fixed at 100 eV), drag + scatter + bremsstrahlung only; energies
+    exponential with mean 10 MeV, isotropic; photon tally 200 log bins over
+    10 keV-100 MeV x 180 polar bins.  The grid is nominal (unused)."""
+    t = target(n=(8, 8, 8), T0_eV=100.0)
+    physics = 1 | 2 | 4 | 64  # drag, scatter, bremsstrahlung, unbounded
+    return {"target": t, "laser": laser(t, I_Wcm2=1e20, n_macro=0, spot_r=1e-6),
+            "run": run(n_E=200, n_theta=180, physics=physics, max_history=steps),
+            "n_electrons": int(n_electrons), "mean_energy": 10.0 * MEV, "steps": steps}
+
+
 def config2() -> dict:
     """128^3 cells of 1 um gold, 1e7 electrons over 100 fs at 1e21 W/cm^2, 10 ps."""
     t = target(n=(128, 128, 128))

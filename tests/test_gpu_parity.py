@@ -246,3 +246,30 @@ def test_full_size_headline(prec):
     assert hN.sum() == pytest.approx(t["n_emitted"] * w / cfg["run"]["brem_boost"], rel=1e-9)
     assert g.history().sum() == pytest.approx(t["E_xray_above"], rel=1e-9)
     g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_emission_benchmark_mode(prec):
+    """Unbounded medium (the emission benchmark's mode): bulk seeding and one
+    step of drag, scatter and bremsstrahlung against the oracle."""
+    cfg = W.config5(n_electrons=20000, steps=4)
+    prec_id, tol, abs_frac = PREC[prec]
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    o.seed(cfg["n_electrons"], cfg["mean_energy"])
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec_id)
+    g.seed(cfg["n_electrons"], cfg["mean_energy"])
+    dx = cfg["target"]["dx"]
+    assert_particles_close(g.particles(), o.particles(), tol, dx)  # the seeded state
+    o.step(2)                                                       # oracle moves on
+    g2 = gpu_from_oracle(o, cfg, prec_id)
+    t0 = o.tallies()
+    o.step(1)
+    g2.step(1)
+    assert_particles_close(g2.particles(), o.particles(), tol, dx)
+    ot = tally_delta(o.tallies(), t0)
+    assert ot["n_emitted"] > 0
+    assert_tallies_close(g2.tallies(), ot, tol, abs_frac * t0["E_live"])
+    ghE, _ = g2.hist()
+    assert ghE.shape == (202, 180)
+    g.close()
+    g2.close()

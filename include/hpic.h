@@ -154,6 +154,7 @@ typedef struct {
 } hpic_tallies;
 
 typedef struct hpic_ctx hpic_ctx;
+typedef struct hpic_batch hpic_batch;
 
 /* Create a context for one target on `device`, with work on `cuda_stream`
  * (a cudaStream_t, or NULL).  Builds the photon inverse-CDF table on the
@@ -257,6 +258,83 @@ int hpic_sort_cells_noalloc(int32_t nx, int32_t ny, int32_t nz, int32_t precisio
 int hpic_destroy(hpic_ctx *ctx);
 /* Last error of ctx, or of the last failed creation when ctx is NULL. */
 const char *hpic_last_error(const hpic_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent targets advanced together.
+ *
+ * The paper's scans (Sec. III: thickness, material and intensity) are many
+ * independent runs of the step above.  A batch holds n_targets such runs of
+ * uneven size on one GPU and advances all of them with one launch per kernel
+ * kind per step: the particle kernel is persistent (a fixed grid of
+ * blocks_per_sm blocks per SM walks the warp-sized tasks of every target),
+ * the field kernels walk the concatenated grids, and the whole step is
+ * replayed from a captured CUDA graph.  Physics per target is identical to
+ * a single context made with the same target, laser and run parameters and
+ * run.target_index + t: target t draws the same random numbers, so in FP64
+ * its results match such a context to rounding (only the order of
+ * floating-point atomic additions differs).
+ *
+ * Memory: every target gets n_macro + spare_slots particle slots, fixed at
+ * creation, and its own grid, tallies and counters; all of it is one device
+ * allocation owned by the batch.
+ * ------------------------------------------------------------------------ */
+#define HPIC_BATCH_MAX_TARGETS 256
+
+typedef struct {
+  int32_t blocks_per_sm;   /* persistent particle-kernel blocks per SM (1..3; FP64 1..2) */
+  int32_t sort_interval;   /* steps between cell sorts (0: never) */
+  int32_t use_graph;       /* replay captured CUDA graphs (1) or launch directly (0) */
+  int32_t reserved;
+  double ms_per_step;      /* autotuner: measured time of the chosen setting */
+} hpic_batch_tuning;
+
+/* Create a batch of n_targets (1..HPIC_BATCH_MAX_TARGETS) targets sharing the
+ * run parameters `run` (time step, precision, physics, tallies, table; the
+ * run's sort_interval is the initial tuning).  lasers[t] schedules target t's
+ * injection as hpic_inject_electrons does (lasers may be NULL: no injection).
+ * Work goes to cuda_stream, or to a stream the batch creates if NULL (a
+ * captured graph needs a stream other than the legacy default). */
+int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc *targets,
+                    const hpic_laser_desc *lasers, const hpic_run_params *run,
+                    int64_t spare_slots, int device, void *cuda_stream);
+
+/* Borrow target t's context.  On it the read/write calls work as on a
+ * single context (hpic_read_tallies, hpic_read_hist, hpic_read_history,
+ * hpic_read_grid, hpic_write_grid, hpic_read_particles,
+ * hpic_count_particles, hpic_load_particles within the slots,
+ * hpic_get_clock, hpic_set_clock, hpic_launch_count); the calls that step,
+ * sort, inject, seed, profile or destroy return HPIC_ESTATE.  The handle
+ * stays valid until hpic_batch_destroy. */
+int hpic_batch_target(hpic_batch *b, int32_t t, hpic_ctx **out);
+
+/* Advance every target by n steps (asynchronous on the batch stream). */
+int hpic_batch_step(hpic_batch *b, int64_t n_steps);
+
+/* Current tuning, and a manual override (validated; graphs re-captured). */
+int hpic_batch_get_tuning(const hpic_batch *b, hpic_batch_tuning *out);
+int hpic_batch_set_tuning(hpic_batch *b, const hpic_batch_tuning *in);
+
+/* Autotuner: from a snapshot of the whole batch state, time trial_steps
+ * steps (>= 1) for every candidate (blocks_per_sm x sort_interval in
+ * {5, 10, 20, 40}, graphs on), restore the snapshot after each trial, and
+ * keep the fastest.  The simulation is left exactly where it was.  Needs
+ * device memory for one copy of the batch state; the result is written to
+ * *out when out is not NULL. */
+int hpic_batch_autotune(hpic_batch *b, int32_t trial_steps, hpic_batch_tuning *out);
+
+/* Timing of the particle kernel, as hpic_profile / hpic_kernel_time (while
+ * enabled the step is launched directly, not from a graph, so that events
+ * can bracket the kernel).  particle_steps sums all targets. */
+int hpic_batch_profile(hpic_batch *b, int enable);
+int hpic_batch_kernel_time(hpic_batch *b, double *ms, int64_t *launches,
+                           double *particle_steps);
+
+/* Kernels launched by the batch (graph replays count their kernels). */
+int hpic_batch_launch_count(const hpic_batch *b, int64_t *launches);
+
+int hpic_batch_destroy(hpic_batch *b);
+/* Last error of b, or of the last failed batch creation when b is NULL. */
+const char *hpic_batch_last_error(const hpic_batch *b);
 
 #ifdef __cplusplus
 }

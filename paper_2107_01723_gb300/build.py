@@ -2,7 +2,7 @@
 
     python -m paper_2107_01723_gb300.build [--force]
 
-The three translation units compile in parallel, then link into
+The translation units compile in parallel, then link into
 paper_2107_01723_gb300/_build/libhpic.so (static CUDA runtime).
 """
 from __future__ import annotations
@@ -17,11 +17,12 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libhpic.so")
-SOURCES = ["api.cu", "particles.cu", "grid.cu", "sort_static.cu"]
-HEADERS = ["common.cuh", "kernels.h"]
+SOURCES = ["api.cu", "particles.cu", "grid.cu", "sort_static.cu", "batch_push.cu", "batch.cu"]
+HEADERS = ["common.cuh", "kernels.h", "ctx.h", "push.cuh", "fields.cuh"]
 # FP32 division and square root in the per-electron kernels to <= 2 ulp
 # (the FP32 path's parity bar is 1e-5; FP64 arithmetic is unaffected)
-PER_FILE = {"particles.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
+FAST_FP32 = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+PER_FILE = {"particles.cu": FAST_FP32, "batch_push.cu": FAST_FP32}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -7,8 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "hpic.h"
-#include "kernels.h"
+#include "ctx.h"
 
 namespace {
 
@@ -30,44 +29,6 @@ thread_local std::string g_create_error;
 
 void hpic::set_global_error(const char *msg) { g_create_error = msg; }
 
-struct hpic_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  hpic_target_desc tgt{};
-  hpic_run_params run{};
-  hpic_laser_desc laser{};
-  bool have_laser = false;
-  bool fp32 = false;
-  size_t rsz = 8;  // bytes per particle/field real
-  hpic::Consts K{};
-  int sm_count = 1;
-  // particles: two SoA buffers (the sort ping-pongs between them)
-  long long cap = 0;
-  long long stride = 0;  // elements per array inside a buffer
-  void *pbuf[2] = {nullptr, nullptr};
-  int cur = 0;
-  uint32_t *keys = nullptr;
-  uint32_t *counts = nullptr;
-  uint32_t *partials = nullptr;
-  // grid
-  void *fields = nullptr;  // E[3], B[3], J[3] of R, each nvec long, vstride apart
-  long long vstride = 0;   // nvec + >= 4 padding, a multiple of 64 (aligned vector access)
-  double *T = nullptr, *eta = nullptr, *H = nullptr;
-  // tallies and tables
-  double *tal = nullptr, *hist = nullptr, *history = nullptr, *scratch = nullptr;
-  double *t64 = nullptr;
-  float *t32 = nullptr;
-  hpic::Counters *cnt = nullptr;
-  long long host_step = 0;
-  long long launches = 0;
-  // profiling of the particle kernel
-  bool prof = false;
-  std::vector<cudaEvent_t> ev;
-  size_t ev_used = 0;
-  long long prof_launches = 0;
-  double prof_ps0 = 0.0;
-  std::string err;
-};
 
 namespace {
 
@@ -90,40 +51,6 @@ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
 int n_rows(const hpic_ctx *c) { return c->run.n_Ebins + 2; }
 long long hist_len(const hpic_ctx *c) { return (long long)n_rows(c) * c->run.n_thbins; }
-
-template <typename R>
-hpic::PView<R> pview(const hpic_ctx *c, int which) {
-  char *b = static_cast<char *>(c->pbuf[which]);
-  const size_t s = (size_t)c->stride * sizeof(R);
-  hpic::PView<R> v;
-  v.x = reinterpret_cast<R *>(b);
-  v.y = reinterpret_cast<R *>(b + s);
-  v.z = reinterpret_cast<R *>(b + 2 * s);
-  v.ux = reinterpret_cast<R *>(b + 3 * s);
-  v.uy = reinterpret_cast<R *>(b + 4 * s);
-  v.uz = reinterpret_cast<R *>(b + 5 * s);
-  v.tau = reinterpret_cast<R *>(b + 6 * s);
-  v.id = reinterpret_cast<uint32_t *>(b + 7 * s);
-  return v;
-}
-
-template <typename R>
-hpic::GView<R> gview(const hpic_ctx *c) {
-  hpic::GView<R> g;
-  R *f = static_cast<R *>(c->fields);
-  const long long nv = c->vstride;
-  for (int a = 0; a < 3; ++a) {
-    g.E[a] = f + a * nv;
-    g.B[a] = f + (3 + a) * nv;
-    g.J[a] = f + (6 + a) * nv;
-  }
-  g.T = c->T;
-  g.eta = c->eta;
-  g.H = c->H;
-  return g;
-}
-
-hpic::TallyView tview(const hpic_ctx *c) { return hpic::TallyView{c->tal, c->hist, c->history}; }
 
 int grid_blocks(const hpic_ctx *c, long long work) {
   const long long want = (work + 255) / 256;
@@ -151,6 +78,7 @@ int write_counters(hpic_ctx *ctx, const hpic::Counters *h) {
 // grow particle storage to hold `need` slots, keeping the first n
 int reserve(hpic_ctx *ctx, long long need) {
   if (need <= ctx->cap) return HPIC_OK;
+  if (ctx->owner) return fail(ctx, HPIC_ENOMEM, "more particles than the target's slots in the batch");
   hpic::Counters h;
   int rc = read_counters(ctx, &h);
   if (rc) return rc;
@@ -193,11 +121,11 @@ int reserve(hpic_ctx *ctx, long long need) {
   return HPIC_OK;
 }
 
-// fold the paper's SI coefficients into normalised kernel constants
-void fold_constants(hpic_ctx *c) {
-  const hpic_target_desc &t = c->tgt;
-  const hpic_run_params &r = c->run;
-  hpic::Consts &K = c->K;
+}  // namespace
+
+// fold the paper's SI coefficients of one target into normalised constants
+void hpic::fold(const hpic_target_desc &t, const hpic_run_params &r, const hpic_laser_desc *laser,
+                Consts &K) {
   const double dx = t.dx_m, dt = r.dt_s, Z = t.Z, ni = t.n_i_m3;
   K.nx = t.nx; K.ny = t.ny; K.nz = t.nz;
   K.nvec = (long long)(t.nx + 1) * (t.ny + 1) * (t.nz + 1);
@@ -254,8 +182,8 @@ void fold_constants(hpic_ctx *c) {
   K.physics = r.physics;
   // laser-dependent terms; without a laser a0 = 0 and the weight is 1
   double a0 = 0.0, w = 1.0;
-  if (c->have_laser) {
-    const hpic_laser_desc &l = c->laser;
+  if (laser) {
+    const hpic_laser_desc &l = *laser;
     a0 = 8.5e-6 * std::sqrt(l.I0_Wm2 * l.lambda_m * l.lambda_m);  // Eq. (1)
     if (l.n_macro > 0 && a0 > 0.0) {
       const double N_real = l.eta_l2e * l.I0_Wm2 * PI * l.spot_radius_m * l.spot_radius_m *
@@ -279,8 +207,50 @@ void fold_constants(hpic_ctx *c) {
   K.du_reflux = r.kappa_tnsa * a0;
 }
 
-double eta_host(const hpic_ctx *c, double T) {
-  const hpic::Consts &K = c->K;
+const char *hpic::check_target(const hpic_target_desc &t, const hpic_run_params &r) {
+  if (t.nx < 2 || t.ny < 2 || t.nz < 2) return "each dimension must be >= 2";
+  if ((long long)(t.nx + 4) * (t.ny + 4) * (t.nz + 4) >= 0x7FFFFFFFll ||
+      (long long)t.nx * t.ny * t.nz >= (1ll << 27) - 1)
+    return "grid too large (at most 2^27 - 2 cells)";
+  if (!(t.dx_m > 0) || !(r.dt_s > 0) || CL * r.dt_s >= t.dx_m) return "need dx > c dt > 0";
+  if (!(t.Z > 0) || !(t.n_i_m3 > 0) || !(t.I_ex_J > 0) || !(t.Zstar > 0) ||
+      !(t.lnLambda > 0) || !(t.eta_max_ohm_m > 0) || !(t.lambda2 > 0) || !(t.T0_K > 0) ||
+      t.lambda1 < 0)
+    return "material parameters must be positive";
+  if (r.precision != HPIC_FP64 && r.precision != HPIC_FP32_MIXED) return "unknown precision";
+  if (!(r.brem_boost > 0) || !(r.k_min_J > 0) || !(r.E_cut_J > 0) ||
+      !(r.table_Emax_J > r.k_min_J) || r.table_rows < 2 || r.table_cols < 2 ||
+      r.n_Ebins < 1 || r.n_thbins < 1 || !(r.tally_Emax_J > r.tally_Emin_J) ||
+      !(r.tally_Emin_J > 0) || r.max_history < 0 || r.sort_interval < 0 ||
+      r.kappa_esc < 0 || r.kappa_tnsa < 0 || r.sigma_dtheta_rad < 0 ||
+      (r.physics & ~(HPIC_ALL | HPIC_UNBOUNDED)) != 0)
+    return "run parameters out of range";
+  return nullptr;
+}
+
+const char *hpic::check_laser(const hpic_laser_desc &l, const hpic_target_desc &t) {
+  if (!(l.I0_Wm2 >= 0) || !(l.lambda_m > 0) || !(l.eta_l2e >= 0) || !(l.spot_radius_m >= 0) ||
+      !(l.t_inj_s >= 0) || l.n_macro < 0 || l.n_macro >= 0xFFFFFFFFll ||
+      !(l.cone_half_angle_rad >= 0) || l.cone_half_angle_rad > PI)
+    return "laser parameters out of range";
+  const double Ly = t.ny * t.dx_m, Lz = t.nz * t.dx_m;
+  if (l.spot_y_m - l.spot_radius_m < 0 || l.spot_y_m + l.spot_radius_m > Ly ||
+      l.spot_z_m - l.spot_radius_m < 0 || l.spot_z_m + l.spot_radius_m > Lz)
+    return "injection disc does not fit on the x = 0 face";
+  return nullptr;
+}
+
+namespace {
+
+void fold_constants(hpic_ctx *c) {
+  hpic::fold(c->tgt, c->run, c->have_laser ? &c->laser : nullptr, c->K);
+}
+
+double eta_host(const hpic_ctx *c, double T) { return hpic::eta_of(c->K, T); }
+
+}  // namespace
+
+double hpic::eta_of(const Consts &K, double T) {
   const double kT = KB * T;
   double tau = K.A_hot * kT * std::sqrt(kT);
   if (K.lambda1 > 0.0) {
@@ -290,6 +260,8 @@ double eta_host(const hpic_ctx *c, double T) {
   const double e = K.eta_num / tau;
   return e < K.eta_max ? e : K.eta_max;
 }
+
+namespace {
 
 void destroy_all(hpic_ctx *c) {
   cudaFree(c->pbuf[0]);
@@ -470,6 +442,18 @@ int load_particles_impl(hpic_ctx *ctx, int64_t n, const double *x, const double 
 
 bool valid_grid(int which) { return which >= HPIC_GRID_T && which <= HPIC_GRID_HEAT; }
 
+// device array of a vector-field component (HPIC_GRID_EX .. HPIC_GRID_JZ)
+void *vector_array(const hpic_ctx *ctx, int which) {
+  const int slot = which - HPIC_GRID_EX;  // 0..8: E, B, J
+  char *base = static_cast<char *>(slot < 6 ? ctx->fields : ctx->jfield);
+  return base + (slot % 6) * ctx->vstride * ctx->rsz;
+}
+
+// entry points that step or reshape a context are the batch's business
+int refuse_batch_target(hpic_ctx *ctx) {
+  return fail(ctx, HPIC_ESTATE, "this context is a target of a batch: use the hpic_batch_* calls");
+}
+
 }  // namespace
 
 extern "C" {
@@ -479,25 +463,7 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
   if (!out) return fail(nullptr, HPIC_EINVAL, "out is NULL");
   *out = nullptr;
   if (!t || !r) return fail(nullptr, HPIC_EINVAL, "target or run params NULL");
-  if (t->nx < 2 || t->ny < 2 || t->nz < 2) return fail(nullptr, HPIC_EINVAL, "each dimension must be >= 2");
-  if ((long long)(t->nx + 4) * (t->ny + 4) * (t->nz + 4) >= 0x7FFFFFFFll ||
-      (long long)t->nx * t->ny * t->nz >= (1ll << 27) - 1)
-    return fail(nullptr, HPIC_EINVAL, "grid too large (at most 2^27 - 2 cells)");
-  if (!(t->dx_m > 0) || !(r->dt_s > 0) || CL * r->dt_s >= t->dx_m)
-    return fail(nullptr, HPIC_EINVAL, "need dx > c dt > 0");
-  if (!(t->Z > 0) || !(t->n_i_m3 > 0) || !(t->I_ex_J > 0) || !(t->Zstar > 0) ||
-      !(t->lnLambda > 0) || !(t->eta_max_ohm_m > 0) || !(t->lambda2 > 0) || !(t->T0_K > 0) ||
-      t->lambda1 < 0)
-    return fail(nullptr, HPIC_EINVAL, "material parameters must be positive");
-  if (r->precision != HPIC_FP64 && r->precision != HPIC_FP32_MIXED)
-    return fail(nullptr, HPIC_EINVAL, "unknown precision");
-  if (!(r->brem_boost > 0) || !(r->k_min_J > 0) || !(r->E_cut_J > 0) ||
-      !(r->table_Emax_J > r->k_min_J) || r->table_rows < 2 || r->table_cols < 2 ||
-      r->n_Ebins < 1 || r->n_thbins < 1 || !(r->tally_Emax_J > r->tally_Emin_J) ||
-      !(r->tally_Emin_J > 0) || r->max_history < 0 || r->sort_interval < 0 ||
-      r->kappa_esc < 0 || r->kappa_tnsa < 0 || r->sigma_dtheta_rad < 0 ||
-      (r->physics & ~(HPIC_ALL | HPIC_UNBOUNDED)) != 0)
-    return fail(nullptr, HPIC_EINVAL, "run parameters out of range");
+  if (const char *why = hpic::check_target(*t, *r)) return fail(nullptr, HPIC_EINVAL, why);
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();
@@ -542,6 +508,7 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
     fail(ctx, HPIC_ENOMEM, "device allocation failed");
     return bail(HPIC_ENOMEM);
   }
+  ctx->jfield = static_cast<char *>(ctx->fields) + 6 * ctx->vstride * ctx->rsz;
   int rc = reserve(ctx, 1024);
   if (rc) return bail(rc);
   cudaStream_t st = ctx->stream;
@@ -571,15 +538,9 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
 
 int hpic_inject_electrons(hpic_ctx *ctx, const hpic_laser_desc *l) {
   if (!ctx || !l) return fail(ctx, HPIC_EINVAL, "NULL argument");
+  if (ctx->owner) return refuse_batch_target(ctx);
   if (ctx->have_laser) return fail(ctx, HPIC_ESTATE, "a laser is already scheduled");
-  if (!(l->I0_Wm2 >= 0) || !(l->lambda_m > 0) || !(l->eta_l2e >= 0) || !(l->spot_radius_m >= 0) ||
-      !(l->t_inj_s >= 0) || l->n_macro < 0 || l->n_macro >= 0xFFFFFFFFll ||
-      !(l->cone_half_angle_rad >= 0) || l->cone_half_angle_rad > PI)
-    return fail(ctx, HPIC_EINVAL, "laser parameters out of range");
-  const double Ly = ctx->tgt.ny * ctx->tgt.dx_m, Lz = ctx->tgt.nz * ctx->tgt.dx_m;
-  if (l->spot_y_m - l->spot_radius_m < 0 || l->spot_y_m + l->spot_radius_m > Ly ||
-      l->spot_z_m - l->spot_radius_m < 0 || l->spot_z_m + l->spot_radius_m > Lz)
-    return fail(ctx, HPIC_EINVAL, "injection disc does not fit on the x = 0 face");
+  if (const char *why = hpic::check_laser(*l, ctx->tgt)) return fail(ctx, HPIC_EINVAL, why);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   hpic::Counters h;
   int rc = read_counters(ctx, &h);
@@ -595,6 +556,7 @@ int hpic_inject_electrons(hpic_ctx *ctx, const hpic_laser_desc *l) {
 
 int hpic_seed_electrons(hpic_ctx *ctx, int64_t n, double mean_energy_J) {
   if (!ctx) return HPIC_EINVAL;
+  if (ctx->owner) return refuse_batch_target(ctx);
   if (n < 0 || !(mean_energy_J > 0)) return fail(ctx, HPIC_EINVAL, "bad seeding arguments");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   hpic::Counters h;
@@ -618,6 +580,7 @@ int hpic_seed_electrons(hpic_ctx *ctx, int64_t n, double mean_energy_J) {
 
 int hpic_step(hpic_ctx *ctx, int64_t n) {
   if (!ctx) return HPIC_EINVAL;
+  if (ctx->owner) return refuse_batch_target(ctx);
   if (n < 0) return fail(ctx, HPIC_EINVAL, "negative step count");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   return ctx->fp32 ? step_impl<float>(ctx, n) : step_impl<double>(ctx, n);
@@ -625,6 +588,7 @@ int hpic_step(hpic_ctx *ctx, int64_t n) {
 
 int hpic_sort(hpic_ctx *ctx) {
   if (!ctx) return HPIC_EINVAL;
+  if (ctx->owner) return refuse_batch_target(ctx);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   return ctx->fp32 ? sort_impl<float>(ctx) : sort_impl<double>(ctx);
 }
@@ -723,8 +687,7 @@ int hpic_read_grid(hpic_ctx *ctx, int which, double *out) {
     for (int64_t i = 0; i < L; ++i) out[i] *= s;
     return HPIC_OK;
   }
-  const int slot = which - HPIC_GRID_EX;  // 0..8: E, B, J
-  const char *src = static_cast<const char *>(ctx->fields) + slot * ctx->vstride * ctx->rsz;
+  const char *src = static_cast<const char *>(vector_array(ctx, which));
   if (ctx->fp32) {
     std::vector<float> b(L);
     CK(cudaMemcpyAsync(b.data(), src, L * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
@@ -752,8 +715,7 @@ int hpic_write_grid(hpic_ctx *ctx, int which, const double *in) {
     CK(cudaStreamSynchronize(ctx->stream));
     return HPIC_OK;
   }
-  const int slot = which - HPIC_GRID_EX;
-  char *dst = static_cast<char *>(ctx->fields) + slot * ctx->vstride * ctx->rsz;
+  char *dst = static_cast<char *>(vector_array(ctx, which));
   if (ctx->fp32) {
     std::vector<float> b(L);
     for (int64_t i = 0; i < L; ++i) b[i] = (float)(in[i] * s);
@@ -775,10 +737,9 @@ int hpic_count_particles(hpic_ctx *ctx, int64_t *n) {
   int rc = read_counters(ctx, &h);
   if (rc) return rc;
   std::vector<uint32_t> ids(h.n);
-  const char *b = static_cast<const char *>(ctx->pbuf[ctx->cur]);
+  const uint32_t *src = ctx->fp32 ? pview<float>(ctx, ctx->cur).id : pview<double>(ctx, ctx->cur).id;
   if (h.n) {
-    CK(cudaMemcpyAsync(ids.data(), b + 7 * (size_t)ctx->stride * ctx->rsz, h.n * sizeof(uint32_t),
-                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ids.data(), src, h.n * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
   }
   long long live = 0;
@@ -831,6 +792,7 @@ int hpic_set_clock(hpic_ctx *ctx, int64_t step, int64_t next_id) {
 
 int hpic_profile(hpic_ctx *ctx, int enable) {
   if (!ctx) return HPIC_EINVAL;
+  if (ctx->owner) return refuse_batch_target(ctx);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->prof = enable != 0;
@@ -844,6 +806,7 @@ int hpic_profile(hpic_ctx *ctx, int enable) {
 
 int hpic_kernel_time(hpic_ctx *ctx, double *ms, int64_t *launches, double *psteps) {
   if (!ctx) return HPIC_EINVAL;
+  if (ctx->owner) return refuse_batch_target(ctx);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   CK(cudaStreamSynchronize(ctx->stream));
   double total = 0.0;
@@ -871,6 +834,7 @@ int hpic_launch_count(const hpic_ctx *ctx, int64_t *launches) {
 
 int hpic_destroy(hpic_ctx *ctx) {
   if (!ctx) return HPIC_EINVAL;
+  if (ctx->owner) return refuse_batch_target(ctx);
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   destroy_all(ctx);

@@ -1,0 +1,319 @@
+// Batched particle kernels: many independent targets advanced by one launch
+// per kernel kind (the paper's parameter scans, Sec. III, as one job).
+//
+// Every target owns a fixed range of slots in one shared structure of
+// arrays.  Per step a one-block plan turns the targets' live counts into a
+// prefix of warp-sized tasks (32 consecutive slots of one target); the
+// persistent push kernel's warps take tasks in a global sweep (task w,
+// w + all warps, ...), so at any moment the whole GPU works on a narrow
+// window of slots and each target's grid stays hot in L2 while it is swept.
+// A warp meets each target once per sweep: it then copies the target's
+// constants into shared memory and, when it moves on, adds its tally sums to
+// a per-block shared array indexed by target, flushed to the targets'
+// device tallies once at the end.  The per-electron physics is the same
+// device code as the single-target kernel (push.cuh).
+#include "push.cuh"
+
+namespace hpic {
+
+constexpr int kBatchWarps = 8;  // 256-thread blocks
+
+// ---------------------------------------------------------------- plan
+// wpref: warp tasks from the live slot counts; ipref: electrons injected in
+// this step (Eq. (B1), flat-top: floor((s+1)N/S) - floor(sN/S) at step s < S)
+template <typename R>
+__global__ void __launch_bounds__(256) k_batch_plan(const BatchItem<R> *items, BatchDev d) {
+  __shared__ long long wt[HPIC_BATCH_MAX_TARGETS], ct[HPIC_BATCH_MAX_TARGETS];
+  for (int t = threadIdx.x; t < d.n; t += blockDim.x) {
+    const BatchItem<R> &it = items[t];
+    const long long n = it.cnt->n, st = it.cnt->step;
+    wt[t] = (n + 31) / 32;
+    const long long S = it.K.n_inj_steps, N = it.K.n_macro;
+    ct[t] = (N > 0 && st < S) ? (N * (st + 1)) / S - (N * st) / S : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long a = 0, b = 0;
+    for (int t = 0; t < d.n; ++t) {
+      d.wpref[t] = a;
+      d.ipref[t] = b;
+      a += wt[t];
+      b += ct[t];
+    }
+    d.wpref[d.n] = a;
+    d.ipref[d.n] = b;
+  }
+}
+
+// ---------------------------------------------------------------- push
+template <typename R>
+__device__ __forceinline__ void flush_acc(const Acc<R> &acc, double *dst) {
+  double v[kAccN];
+  acc.values(v);
+#pragma unroll
+  for (int q = 0; q < kAccN; ++q) {
+    const double s = warp_sum(v[q]);
+    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(dst + q, s);
+  }
+}
+
+// MINB = the blocks per SM the launch asks for: the register budget follows
+// (3: 80 registers, the FP32 state then spills a little; 2: 128; 1: 255), and
+// the autotuner picks among the variants by timing them
+template <typename R, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+k_batch_push(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
+             const R *__restrict__ tab) {
+  __shared__ BatchItem<R> wc[kBatchWarps];  // each warp's current target
+  extern __shared__ double tal_s[];         // n x kAccN sums, then the task prefix
+  long long *wpref_s = reinterpret_cast<long long *>(tal_s + d.n * kAccN);
+  for (int i = threadIdx.x; i < d.n * kAccN; i += blockDim.x) tal_s[i] = 0.0;
+  for (int t = threadIdx.x; t <= d.n; t += blockDim.x) wpref_s[t] = d.wpref[t];
+  __syncthreads();
+
+  __shared__ long long wstate[kBatchWarps][2];  // the target's step and slot count
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long ntask = wpref_s[d.n];
+  const long long nwarps = (long long)gridDim.x * kBatchWarps;
+  BatchItem<R> &it = wc[warp];
+  int t = -1;
+  Acc<R> acc;
+  for (long long w = blockIdx.x * (long long)kBatchWarps + warp; w < ntask; w += nwarps) {
+    int tn = t < 0 ? 0 : t;
+    while (wpref_s[tn + 1] <= w) ++tn;
+    if (tn != t) {  // warp-uniform: a new target
+      if (t >= 0) {
+        flush_acc(acc, tal_s + t * kAccN);
+        acc = Acc<R>();
+      }
+      t = tn;
+      __syncwarp();
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(items + t);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(&it);
+      for (int k = lane; k < (int)(sizeof(BatchItem<R>) / 4); k += 32) dst[k] = __ldg(src + k);
+      if (lane == 0) {
+        wstate[warp][0] = items[t].cnt->step;
+        wstate[warp][1] = items[t].cnt->n;
+      }
+      __syncwarp();
+    }
+    // rebuilt per task from shared memory rather than held in registers
+    StepCtx sc;
+    sc.step_ll = wstate[warp][0];
+    sc.step = (uint32_t)sc.step_ll;
+    sc.key0 = it.K.key0;
+    sc.key1 = it.K.key1;
+    sc.target = it.K.target_index;
+    const long long local = (w - wpref_s[t]) * 32 + lane;
+    push_warp(it.K, it.h, make_grid(it.K, it.g), tab, it.tv, sc, p, it.off + local,
+              local < wstate[warp][1], acc);
+  }
+  if (t >= 0) flush_acc(acc, tal_s + t * kAccN);
+  __syncthreads();
+  for (int i = threadIdx.x; i < d.n * kAccN; i += blockDim.x)
+    if (tal_s[i] != 0.0) atomicAdd(items[i / kAccN].tv.tal + kAccSlot[i % kAccN], tal_s[i]);
+}
+
+// ---------------------------------------------------------------- injection
+__device__ __forceinline__ int forward_target(const long long *pref, int t, int n, long long q) {
+  while (t + 1 < n && pref[t + 1] <= q) ++t;
+  return t;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_batch_inject(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p) {
+  extern __shared__ long long ipref_s[];  // n + 1 prefix, then 3 sums per target
+  double *sum_s = reinterpret_cast<double *>(ipref_s + d.n + 1);
+  for (int t = threadIdx.x; t <= d.n; t += blockDim.x) ipref_s[t] = d.ipref[t];
+  for (int t = threadIdx.x; t < 3 * d.n; t += blockDim.x) sum_s[t] = 0.0;
+  __syncthreads();
+  const long long C = ipref_s[d.n];
+  int t = 0;
+  double e_inj = 0.0, n_inj = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < C;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int tn = forward_target(ipref_s, t, d.n, i);
+    if (tn != t) {
+      if (n_inj > 0.0) {
+        atomicAdd(sum_s + 3 * t, e_inj);
+        atomicAdd(sum_s + 3 * t + 1, n_inj * items[t].K.w);
+        atomicAdd(sum_s + 3 * t + 2, n_inj);
+      }
+      e_inj = n_inj = 0.0;
+      t = tn;
+    }
+    const BatchItem<R> &it = items[t];
+    const long long local = i - ipref_s[t];
+    const long long q = it.cnt->n + local;
+    if (q >= it.cap) {
+      atomicOr(&it.cnt->flags, 1u);
+      continue;
+    }
+    const uint32_t id = (uint32_t)(it.cnt->next_id + local);
+    const R eps = inject_one(it.K, p, it.off + q, id, (uint32_t)it.cnt->step);
+    e_inj += it.K.w * (double)eps;
+    n_inj += 1.0;
+  }
+  if (n_inj > 0.0) {
+    atomicAdd(sum_s + 3 * t, e_inj);
+    atomicAdd(sum_s + 3 * t + 1, n_inj * items[t].K.w);
+    atomicAdd(sum_s + 3 * t + 2, n_inj);
+  }
+  __syncthreads();
+  const int slot[3] = {T_E_INJ, T_N_INJ, T_N_INJECTED};
+  for (int u = threadIdx.x; u < 3 * d.n; u += blockDim.x)
+    if (sum_s[u] != 0.0) atomicAdd(items[u / 3].tv.tal + slot[u % 3], sum_s[u]);
+}
+
+// closes a step of every target: append the injected electrons, advance the clock
+template <typename R>
+__global__ void k_batch_advance(const BatchItem<R> *items, BatchDev d) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d.n; t += gridDim.x * blockDim.x) {
+    Counters *cnt = items[t].cnt;
+    const long long c = d.ipref[t + 1] - d.ipref[t];
+    const long long n = cnt->n + c, cap = items[t].cap;
+    cnt->n = n < cap ? n : cap;
+    cnt->next_id += c;
+    cnt->step += 1;
+    cnt->inj_cnt = 0;
+  }
+}
+
+// ---------------------------------------------------------------- sort
+// Counting sort of every target's slots by (target, 4x4x4 cell tile) over
+// the concatenated key ranges (prefix d.kpref; the last key of each target's
+// range is its dead bin).  Each target's electrons land in its own slots.
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_batch_sort_keys(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
+                  uint32_t *keys, uint32_t *counts) {
+  const long long nslot = d.wpref[d.n] * 32;
+  int t = 0;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot;
+       s += (long long)gridDim.x * blockDim.x) {
+    t = forward_target(d.wpref, t, d.n, s >> 5);  // uniform over the warp
+    const BatchItem<R> &it = items[t];
+    const long long local = s - d.wpref[t] * 32;
+    if (local >= it.cnt->n) continue;
+    const long long ip = it.off + local;
+    uint32_t key = (uint32_t)(d.kpref[t] + it.K.nkeys);
+    if (p.id[ip] != kDead) {
+      int i = (int)m_floor(p.x[ip]), j = (int)m_floor(p.y[ip]), k = (int)m_floor(p.z[ip]);
+      i = min(max(i, 0), it.K.nx - 1);
+      j = min(max(j, 0), it.K.ny - 1);
+      k = min(max(k, 0), it.K.nz - 1);
+      key = (uint32_t)d.kpref[t] + tile_key(i, j, k, it.K.nti, it.K.ntj);
+    }
+    keys[ip] = key;
+    agg_inc(counts, key);
+  }
+}
+
+// after the scan: each target's first offset and the slots it keeps (the
+// exclusive offset of its dead bin minus its first offset)
+template <typename R>
+__global__ void k_batch_sort_starts(const BatchItem<R> *items, BatchDev d, const uint32_t *offs) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d.n; t += gridDim.x * blockDim.x) {
+    const long long k0 = d.kpref[t];
+    d.sstart[t] = offs[k0];
+    d.snew[t] = (long long)offs[k0 + items[t].K.nkeys] - (long long)offs[k0];
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_batch_sort_scatter(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> src,
+                     PView<R> dst, const uint32_t *keys, uint32_t *offs) {
+  const long long nslot = d.wpref[d.n] * 32;
+  int t = 0;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot;
+       s += (long long)gridDim.x * blockDim.x) {
+    t = forward_target(d.wpref, t, d.n, s >> 5);
+    const BatchItem<R> &it = items[t];
+    const long long local = s - d.wpref[t] * 32;
+    if (local >= it.cnt->n) continue;
+    const long long ip = it.off + local;
+    const uint32_t key = keys[ip];
+    if (key == (uint32_t)(d.kpref[t] + it.K.nkeys)) continue;  // dead
+    const long long q = it.off + (long long)agg_inc(offs, key) - d.sstart[t];
+    dst.x[q] = src.x[ip];
+    dst.y[q] = src.y[ip];
+    dst.z[q] = src.z[ip];
+    dst.ux[q] = src.ux[ip];
+    dst.uy[q] = src.uy[ip];
+    dst.uz[q] = src.uz[ip];
+    dst.tau[q] = src.tau[ip];
+    dst.id[q] = src.id[ip];
+  }
+}
+
+template <typename R>
+__global__ void k_batch_sort_finish(const BatchItem<R> *items, BatchDev d) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d.n; t += gridDim.x * blockDim.x)
+    items[t].cnt->n = d.snew[t];
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename R>
+void launch_batch_plan(const BatchItem<R> *items, BatchDev d, cudaStream_t st) {
+  k_batch_plan<R><<<1, 256, 0, st>>>(items, d);
+}
+
+template <typename R>
+void launch_batch_push(const BatchItem<R> *items, BatchDev d, PView<R> p, const R *table,
+                       int sm_count, int blocks_per_sm, cudaStream_t st) {
+  const size_t sm = (size_t)d.n * kAccN * sizeof(double) + (d.n + 1) * sizeof(long long);
+  const int grid = sm_count * blocks_per_sm;
+  if (blocks_per_sm <= 1) {
+    k_batch_push<R, 1><<<grid, 256, sm, st>>>(items, d, p, table);
+  } else if constexpr (sizeof(R) == 8) {  // FP64: at most two blocks per SM
+    k_batch_push<R, 2><<<grid, 256, sm, st>>>(items, d, p, table);
+  } else if (blocks_per_sm == 2) {
+    k_batch_push<R, 2><<<grid, 256, sm, st>>>(items, d, p, table);
+  } else {
+    k_batch_push<R, 3><<<grid, 256, sm, st>>>(items, d, p, table);
+  }
+}
+
+template <typename R>
+void launch_batch_inject(const BatchItem<R> *items, BatchDev d, PView<R> p, int grid,
+                         cudaStream_t st) {
+  const size_t sm = (d.n + 1) * sizeof(long long) + 3 * d.n * sizeof(double);
+  k_batch_inject<R><<<grid, 256, sm, st>>>(items, d, p);
+}
+
+template <typename R>
+void launch_batch_advance(const BatchItem<R> *items, BatchDev d, cudaStream_t st) {
+  k_batch_advance<R><<<1, 256, 0, st>>>(items, d);
+}
+
+template <typename R>
+int launch_batch_sort(const BatchItem<R> *items, BatchDev d, PView<R> src, PView<R> dst,
+                      uint32_t *keys, uint32_t *counts, uint32_t *partials, long long nkeys_total,
+                      int grid, cudaStream_t st) {
+  k_batch_plan<R><<<1, 256, 0, st>>>(items, d);  // tasks from the current counts
+  cudaMemsetAsync(counts, 0, nkeys_total * sizeof(uint32_t), st);
+  k_batch_sort_keys<R><<<grid, 256, 0, st>>>(items, d, src, keys, counts);
+  int launches = 2 + launch_scan(counts, nkeys_total, partials, st);
+  k_batch_sort_starts<R><<<1, 256, 0, st>>>(items, d, counts);
+  k_batch_sort_scatter<R><<<grid, 256, 0, st>>>(items, d, src, dst, keys, counts);
+  k_batch_sort_finish<R><<<1, 256, 0, st>>>(items, d);
+  return launches + 3;
+}
+
+#define HPIC_INST(R)                                                                            \
+  template void launch_batch_plan<R>(const BatchItem<R> *, BatchDev, cudaStream_t);             \
+  template void launch_batch_push<R>(const BatchItem<R> *, BatchDev, PView<R>, const R *, int,  \
+                                     int, cudaStream_t);                                        \
+  template void launch_batch_inject<R>(const BatchItem<R> *, BatchDev, PView<R>, int,           \
+                                       cudaStream_t);                                           \
+  template void launch_batch_advance<R>(const BatchItem<R> *, BatchDev, cudaStream_t);          \
+  template int launch_batch_sort<R>(const BatchItem<R> *, BatchDev, PView<R>, PView<R>,         \
+                                    uint32_t *, uint32_t *, uint32_t *, long long, int,         \
+                                    cudaStream_t);
+HPIC_INST(float)
+HPIC_INST(double)
+#undef HPIC_INST
+
+}  // namespace hpic

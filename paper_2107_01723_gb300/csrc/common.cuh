@@ -160,6 +160,19 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// warp-aggregated atomic increment: lanes with equal keys share one atomic
+__device__ __forceinline__ uint32_t agg_inc(uint32_t *ctr, uint32_t key) {
+  const unsigned mask = __activemask();
+  const unsigned peers = __match_any_sync(mask, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(ctr + key, (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + rank;
+}
+
 // Sum `nq` per-thread values over the block and add them to dst[slot[q]].
 // smem must hold nq * 32 doubles.  All threads of the block must call it.
 template <int NQ>

@@ -1,0 +1,109 @@
+// Per-node device code of the field solve and heating (arXiv 2107.01723,
+// Eqs. (A2)-(A8)), shared by the single-target and the batched kernels.
+#pragma once
+
+#include "kernels.h"
+
+namespace hpic {
+
+__device__ __forceinline__ void node_of(long long q, int nx, int ny, int &i, int &j, int &k) {
+  const long long sy = nx + 1, sz = (long long)(nx + 1) * (ny + 1);
+  k = (int)(q / sz);
+  const long long r = q - (long long)k * sz;
+  j = (int)(r / sy);
+  i = (int)(r - (long long)j * sy);
+}
+
+// ---------------------------------------------------------------- E, Eq. (A2)
+// E on the three edges owned by node q (tangential E = 0 on the walls)
+template <typename R>
+__device__ __forceinline__ void efield_node(const Consts &K, const GView<R> &g, long long q) {
+  const int nx = K.nx, ny = K.ny, nz = K.nz;
+  const int sy = nx + 1;
+  const long long sz = (long long)(nx + 1) * (ny + 1);
+  const long long cy = nx, cz = (long long)nx * ny;
+  const R Fc = R(K.F_curl), Fj = R(K.F_j);
+  const R *Bx = g.B[0], *By = g.B[1], *Bz = g.B[2];
+  int i, j, k;
+  node_of(q, nx, ny, i, j, k);
+  R ex = 0, ey = 0, ez = 0;
+  const long long c = i + cy * j + cz * k;  // cell (i, j, k)
+  if (i < nx && j >= 1 && j <= ny - 1 && k >= 1 && k <= nz - 1) {
+    const R curl = (Bz[q] - Bz[q - sy]) - (By[q] - By[q - sz]);
+    const R eta = R(0.25 * (g.eta[c - cy - cz] + g.eta[c - cz] + g.eta[c - cy] + g.eta[c]));
+    ex = eta * (Fc * curl - Fj * g.J[0][q]);
+  }
+  if (j < ny && i >= 1 && i <= nx - 1 && k >= 1 && k <= nz - 1) {
+    const R curl = (Bx[q] - Bx[q - sz]) - (Bz[q] - Bz[q - 1]);
+    const R eta = R(0.25 * (g.eta[c - 1 - cz] + g.eta[c - cz] + g.eta[c - 1] + g.eta[c]));
+    ey = eta * (Fc * curl - Fj * g.J[1][q]);
+  }
+  if (k < nz && i >= 1 && i <= nx - 1 && j >= 1 && j <= ny - 1) {
+    const R curl = (By[q] - By[q - 1]) - (Bx[q] - Bx[q - sy]);
+    const R eta = R(0.25 * (g.eta[c - 1 - cy] + g.eta[c - cy] + g.eta[c - 1] + g.eta[c]));
+    ez = eta * (Fc * curl - Fj * g.J[2][q]);
+  }
+  g.E[0][q] = ex;
+  g.E[1][q] = ey;
+  g.E[2][q] = ez;
+}
+
+// heat capacity, Eq. (A8): T' = (k_B T/e) Z^(-4/3)
+__device__ __forceinline__ double heat_capacity(double T, double Tp_fac) {
+  const double tp = T * Tp_fac;
+  return 0.3 + 1.2 * tp * (2.2 + tp) / ((1.1 + tp) * (1.1 + tp));
+}
+
+// reduced Lee-More resistivity, Eqs. (A4)-(A6), capped
+__device__ __forceinline__ double resistivity(const Consts &K, double T) {
+  const double kT = 1.380649e-23 * T;
+  double tau = K.A_hot * kT * sqrt(kT);
+  if (K.lambda1 > 0.0) {
+    const double tc = K.B_cold / sqrt(kT);
+    tau = tc > tau ? tc : tau;
+  }
+  const double eta = K.eta_num / tau;
+  return eta < K.eta_max ? eta : K.eta_max;
+}
+
+// ---------------------------------------------------------------- B, Eq. (A3), and heating
+// Faraday on the faces owned by node q, then heating of cell q; returns the
+// cell's Ohmic energy (J)
+template <typename R>
+__device__ __forceinline__ double bheat_node(const Consts &K, const GView<R> &g, long long q) {
+  const int nx = K.nx, ny = K.ny, nz = K.nz;
+  const int sy = nx + 1;
+  const long long sz = (long long)(nx + 1) * (ny + 1);
+  const R cdt = R(K.cdt_dx);
+  const R *Ex = g.E[0], *Ey = g.E[1], *Ez = g.E[2];
+  double e_ohm = 0.0;
+  int i, j, k;
+  node_of(q, nx, ny, i, j, k);
+  if (K.physics & P_FARADAY) {
+    if (j < ny && k < nz) g.B[0][q] -= cdt * ((Ez[q + sy] - Ez[q]) - (Ey[q + sz] - Ey[q]));
+    if (i < nx && k < nz) g.B[1][q] -= cdt * ((Ex[q + sz] - Ex[q]) - (Ez[q + 1] - Ez[q]));
+    if (i < nx && j < ny) g.B[2][q] -= cdt * ((Ey[q + 1] - Ey[q]) - (Ex[q + sy] - Ex[q]));
+  }
+  if (i < nx && j < ny && k < nz) {
+    const long long c = i + (long long)nx * (j + (long long)ny * k);
+    double rho = g.H[c] * K.F_H;
+    if (K.physics & P_FIELDS) {
+      const R *Jx = g.J[0], *Jy = g.J[1], *Jz = g.J[2];
+      const double jbx = 0.25 * ((double)Jx[q] + Jx[q + sy] + Jx[q + sz] + Jx[q + sy + sz]);
+      const double jby = 0.25 * ((double)Jy[q] + Jy[q + 1] + Jy[q + sz] + Jy[q + 1 + sz]);
+      const double jbz = 0.25 * ((double)Jz[q] + Jz[q + 1] + Jz[q + sy] + Jz[q + 1 + sy]);
+      const double ro = g.eta[c] * K.F_ohm * (jbx * jbx + jby * jby + jbz * jbz);
+      e_ohm = ro * K.dx3;
+      rho += ro;
+    }
+    if ((K.physics & P_HEATING) && rho != 0.0) {  // rho = 0 leaves T and eta(T) as they are
+      const double T = g.T[c];
+      const double Tn = T + rho / (K.heat_den * heat_capacity(T, K.Tp_fac));
+      g.T[c] = Tn;
+      g.eta[c] = resistivity(K, Tn);
+    }
+  }
+  return e_ohm;
+}
+
+}  // namespace hpic

@@ -6,130 +6,79 @@
 //              eta j_h.j_h dt + ionisation heat, and eta(T), Eqs. (A4)-(A6)
 //   sort     : counting sort of electrons by cell (GPU data layout)
 //   k_table  : inverse-CDF bremsstrahlung table from the closed-form CDF
-#include "kernels.h"
+#include "fields.cuh"
 
 namespace hpic {
 
-__device__ __forceinline__ void node_of(long long q, int nx, int ny, int &i, int &j, int &k) {
-  const long long sy = nx + 1, sz = (long long)(nx + 1) * (ny + 1);
-  k = (int)(q / sz);
-  const long long r = q - (long long)k * sz;
-  j = (int)(r / sy);
-  i = (int)(r - (long long)j * sy);
-}
-
-// ---------------------------------------------------------------- E, Eq. (A2)
 template <typename R>
 __global__ void __launch_bounds__(256) k_efield(const Consts K, GView<R> g) {
-  const int nx = K.nx, ny = K.ny, nz = K.nz;
-  const int sy = nx + 1;
-  const long long sz = (long long)(nx + 1) * (ny + 1);
-  const long long cy = nx, cz = (long long)nx * ny;
-  const R Fc = R(K.F_curl), Fj = R(K.F_j);
-  const R *Bx = g.B[0], *By = g.B[1], *Bz = g.B[2];
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < K.nvec;
-       q += (long long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    node_of(q, nx, ny, i, j, k);
-    R ex = 0, ey = 0, ez = 0;
-    const long long c = i + cy * j + cz * k;  // cell (i, j, k)
-    if (i < nx && j >= 1 && j <= ny - 1 && k >= 1 && k <= nz - 1) {
-      const R curl = (Bz[q] - Bz[q - sy]) - (By[q] - By[q - sz]);
-      const R eta = R(0.25 * (g.eta[c - cy - cz] + g.eta[c - cz] + g.eta[c - cy] + g.eta[c]));
-      ex = eta * (Fc * curl - Fj * g.J[0][q]);
-    }
-    if (j < ny && i >= 1 && i <= nx - 1 && k >= 1 && k <= nz - 1) {
-      const R curl = (Bx[q] - Bx[q - sz]) - (Bz[q] - Bz[q - 1]);
-      const R eta = R(0.25 * (g.eta[c - 1 - cz] + g.eta[c - cz] + g.eta[c - 1] + g.eta[c]));
-      ey = eta * (Fc * curl - Fj * g.J[1][q]);
-    }
-    if (k < nz && i >= 1 && i <= nx - 1 && j >= 1 && j <= ny - 1) {
-      const R curl = (By[q] - By[q - 1]) - (Bx[q] - Bx[q - sy]);
-      const R eta = R(0.25 * (g.eta[c - 1 - cy] + g.eta[c - cy] + g.eta[c - 1] + g.eta[c]));
-      ez = eta * (Fc * curl - Fj * g.J[2][q]);
-    }
-    g.E[0][q] = ex;
-    g.E[1][q] = ey;
-    g.E[2][q] = ez;
-  }
+       q += (long long)gridDim.x * blockDim.x)
+    efield_node(K, g, q);
 }
 
-// heat capacity, Eq. (A8): T' = (k_B T/e) Z^(-4/3)
-__device__ __forceinline__ double heat_capacity(double T, double Tp_fac) {
-  const double tp = T * Tp_fac;
-  return 0.3 + 1.2 * tp * (2.2 + tp) / ((1.1 + tp) * (1.1 + tp));
-}
-
-// reduced Lee-More resistivity, Eqs. (A4)-(A6), capped
-__device__ __forceinline__ double resistivity(const Consts &K, double T) {
-  const double kT = 1.380649e-23 * T;
-  double tau = K.A_hot * kT * sqrt(kT);
-  if (K.lambda1 > 0.0) {
-    const double tc = K.B_cold / sqrt(kT);
-    tau = tc > tau ? tc : tau;
-  }
-  const double eta = K.eta_num / tau;
-  return eta < K.eta_max ? eta : K.eta_max;
-}
-
-// ---------------------------------------------------------------- B, Eq. (A3), and heating
 template <typename R>
 __global__ void __launch_bounds__(256) k_bheat(const Consts K, GView<R> g, TallyView tv) {
   __shared__ double smem[32];
-  const int nx = K.nx, ny = K.ny, nz = K.nz;
-  const int sy = nx + 1;
-  const long long sz = (long long)(nx + 1) * (ny + 1);
-  const R cdt = R(K.cdt_dx);
-  const R *Ex = g.E[0], *Ey = g.E[1], *Ez = g.E[2];
   double e_ohm = 0.0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < K.nvec;
-       q += (long long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    node_of(q, nx, ny, i, j, k);
-    if (K.physics & P_FARADAY) {
-      if (j < ny && k < nz) g.B[0][q] -= cdt * ((Ez[q + sy] - Ez[q]) - (Ey[q + sz] - Ey[q]));
-      if (i < nx && k < nz) g.B[1][q] -= cdt * ((Ex[q + sz] - Ex[q]) - (Ez[q + 1] - Ez[q]));
-      if (i < nx && j < ny) g.B[2][q] -= cdt * ((Ey[q + 1] - Ey[q]) - (Ex[q + sy] - Ex[q]));
-    }
-    if (i < nx && j < ny && k < nz) {
-      const long long c = i + (long long)nx * (j + (long long)ny * k);
-      double rho = g.H[c] * K.F_H;
-      if (K.physics & P_FIELDS) {
-        const R *Jx = g.J[0], *Jy = g.J[1], *Jz = g.J[2];
-        const double jbx = 0.25 * ((double)Jx[q] + Jx[q + sy] + Jx[q + sz] + Jx[q + sy + sz]);
-        const double jby = 0.25 * ((double)Jy[q] + Jy[q + 1] + Jy[q + sz] + Jy[q + 1 + sz]);
-        const double jbz = 0.25 * ((double)Jz[q] + Jz[q + 1] + Jz[q + sy] + Jz[q + 1 + sy]);
-        const double ro = g.eta[c] * K.F_ohm * (jbx * jbx + jby * jby + jbz * jbz);
-        e_ohm += ro * K.dx3;
-        rho += ro;
-      }
-      if ((K.physics & P_HEATING) && rho != 0.0) {  // rho = 0 leaves T and eta(T) as they are
-        const double T = g.T[c];
-        const double Tn = T + rho / (K.heat_den * heat_capacity(T, K.Tp_fac));
-        g.T[c] = Tn;
-        g.eta[c] = resistivity(K, Tn);
-      }
-    }
-  }
+       q += (long long)gridDim.x * blockDim.x)
+    e_ohm += bheat_node(K, g, q);
   const double v[1] = {e_ohm};
   const int slot[1] = {T_E_OHMIC};
   block_flush<1>(v, slot, tv.tal, smem);
 }
 
-// ---------------------------------------------------------------- counting sort
-// warp-aggregated atomic increment: lanes with equal keys share one atomic
-__device__ __forceinline__ uint32_t agg_inc(uint32_t *ctr, uint32_t key) {
-  const unsigned mask = __activemask();
-  const unsigned peers = __match_any_sync(mask, key);
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(ctr + key, (uint32_t)__popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  return base + rank;
+// ---------------------------------------------------------------- batched field kernels
+// The targets' node ranges are concatenated (prefix d.npref); a thread walks
+// its grid-stride nodes in increasing order, so its target index only moves
+// forward.  Shared memory holds the prefix and the per-target Ohmic sums.
+__device__ __forceinline__ int advance_target(const long long *pref, int t, int n, long long q) {
+  while (t + 1 < n && pref[t + 1] <= q) ++t;
+  return t;
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) k_batch_efield(const BatchItem<R> *items, BatchDev d) {
+  extern __shared__ long long npref_s[];
+  for (int t = threadIdx.x; t <= d.n; t += blockDim.x) npref_s[t] = d.npref[t];
+  __syncthreads();
+  const long long N = npref_s[d.n];
+  int t = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
+       q += (long long)gridDim.x * blockDim.x) {
+    t = advance_target(npref_s, t, d.n, q);
+    efield_node(items[t].K, items[t].g, q - npref_s[t]);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_batch_bheat(const BatchItem<R> *items, BatchDev d) {
+  extern __shared__ long long npref_s[];
+  double *ohm_s = reinterpret_cast<double *>(npref_s + d.n + 1);
+  for (int t = threadIdx.x; t <= d.n; t += blockDim.x) npref_s[t] = d.npref[t];
+  for (int t = threadIdx.x; t < d.n; t += blockDim.x) ohm_s[t] = 0.0;
+  __syncthreads();
+  const long long N = npref_s[d.n];
+  int t = 0;
+  double e_ohm = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int tn = advance_target(npref_s, t, d.n, q);
+    if (tn != t) {
+      if (e_ohm != 0.0) atomicAdd(ohm_s + t, e_ohm);
+      e_ohm = 0.0;
+      t = tn;
+    }
+    e_ohm += bheat_node(items[t].K, items[t].g, q - npref_s[t]);
+  }
+  if (e_ohm != 0.0) atomicAdd(ohm_s + t, e_ohm);
+  __syncthreads();
+  for (int u = threadIdx.x; u < d.n; u += blockDim.x)
+    if (ohm_s[u] != 0.0) atomicAdd(items[u].tv.tal + T_E_OHMIC, ohm_s[u]);
+}
+
+// ---------------------------------------------------------------- counting sort
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_sort_keys(const Consts K, PView<R> p, const Counters *cnt, uint32_t *keys, uint32_t *counts) {
@@ -357,16 +306,21 @@ void launch_bheat(const Consts &K, GView<R> g, TallyView tv, int grid, cudaStrea
   k_bheat<R><<<grid, 256, 0, st>>>(K, g, tv);
 }
 
+int launch_scan(uint32_t *counts, long long m, uint32_t *partials, cudaStream_t st) {
+  const int ntiles = (int)((m + kScanTile - 1) / kScanTile);
+  k_scan_tiles<<<ntiles, 1024, 0, st>>>(counts, m, partials);
+  k_scan_top<<<1, 1024, 0, st>>>(partials, ntiles);
+  k_scan_apply<<<ntiles, 1024, 0, st>>>(counts, m, partials);
+  return 3;
+}
+
 template <typename R>
 int launch_sort(const Consts &K, PView<R> src, PView<R> dst, Counters *cnt, uint32_t *keys,
                 uint32_t *counts, uint32_t *partials, int grid, cudaStream_t st) {
   const long long m = K.nkeys + 1;
-  const int ntiles = (int)((m + kScanTile - 1) / kScanTile);
   cudaMemsetAsync(counts, 0, m * sizeof(uint32_t), st);
   k_sort_keys<R><<<grid, 256, 0, st>>>(K, src, cnt, keys, counts);
-  k_scan_tiles<<<ntiles, 1024, 0, st>>>(counts, m, partials);
-  k_scan_top<<<1, 1024, 0, st>>>(partials, ntiles);
-  k_scan_apply<<<ntiles, 1024, 0, st>>>(counts, m, partials);
+  launch_scan(counts, m, partials, st);
   k_sort_scatter<R><<<grid, 256, 0, st>>>(K, src, dst, cnt, keys, counts);
   k_sort_finish<<<1, 32, 0, st>>>(cnt, counts, K.nkeys);
   return 6;
@@ -377,6 +331,17 @@ void launch_table(const Consts &K, double k_min, double E_max, double *t64, floa
   const long long nt = (long long)K.t_rows * K.t_cols;
   const int grid = (int)((nt + 255) / 256);
   k_table<<<grid, 256, 0, st>>>(K.t_rows, K.t_cols, k_min, E_max, t64, t32);
+}
+
+template <typename R>
+void launch_batch_efield(const BatchItem<R> *items, BatchDev d, int grid, cudaStream_t st) {
+  k_batch_efield<R><<<grid, 256, (d.n + 1) * sizeof(long long), st>>>(items, d);
+}
+
+template <typename R>
+void launch_batch_bheat(const BatchItem<R> *items, BatchDev d, int grid, cudaStream_t st) {
+  const size_t sm = (d.n + 1) * sizeof(long long) + d.n * sizeof(double);
+  k_batch_bheat<R><<<grid, 256, sm, st>>>(items, d);
 }
 
 template <typename R>
@@ -397,7 +362,9 @@ void launch_field_energy(const Consts &K, GView<R> g, double *dst, int grid, cud
                               uint32_t *, uint32_t *, int, cudaStream_t);                     \
   template void launch_live_energy<R>(const Consts &, PView<R>, Counters *, double *, int,    \
                                       cudaStream_t);                                          \
-  template void launch_field_energy<R>(const Consts &, GView<R>, double *, int, cudaStream_t);
+  template void launch_field_energy<R>(const Consts &, GView<R>, double *, int, cudaStream_t); \
+  template void launch_batch_efield<R>(const BatchItem<R> *, BatchDev, int, cudaStream_t);     \
+  template void launch_batch_bheat<R>(const BatchItem<R> *, BatchDev, int, cudaStream_t);
 HPIC_INST(float)
 HPIC_INST(double)
 #undef HPIC_INST

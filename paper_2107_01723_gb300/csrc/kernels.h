@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "hpic.h"
 
 namespace hpic {
 
@@ -35,8 +36,39 @@ struct HotK {
   R eps_esc, du_reflux, sigma_dtheta, tE_min, tE_max, inv_dlogE, th_scale, t_inv_dlog;
 };
 
+// the hot constants in precision R
+template <typename R>
+inline HotK<R> make_hot(const Consts &K) {
+  HotK<R> h;
+  h.w = R(K.w);
+  h.cdt = R(K.cdt_dx);
+  h.E_cut = R(K.E_cut);
+  h.K_ion = R(K.K_ion);
+  h.L_I = R(K.L_I);
+  h.K_sc = R(K.K_sc);
+  h.K_lg = R(K.K_lg);
+  h.K_tau = R(K.K_tau);
+  h.k_min = R(K.k_min);
+  h.inv_boost = R(K.inv_boost);
+  h.eps_esc = R(K.eps_esc);
+  h.du_reflux = R(K.du_reflux);
+  h.sigma_dtheta = R(K.sigma_dtheta);
+  h.tE_min = R(K.tE_min);
+  h.tE_max = R(K.tE_max);
+  h.inv_dlogE = R(K.inv_dlogE);
+  h.th_scale = R(K.n_th / 3.14159265358979323846);
+  h.t_inv_dlog = R(K.t_inv_dlog);
+  return h;
+}
+
 // message returned by hpic_last_error(NULL) (entry points without a context)
 void set_global_error(const char *msg);
+
+// fold one target's SI parameters into normalised kernel constants (laser may
+// be NULL: a0 = 0, weight 1), and the resistivity eta(T) of Eqs. (A4)-(A6)
+void fold(const hpic_target_desc &t, const hpic_run_params &r, const hpic_laser_desc *laser,
+          Consts &K);
+double eta_of(const Consts &K, double T);
 
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
@@ -68,5 +100,54 @@ void launch_live_energy(const Consts &K, PView<R> p, Counters *cnt, double *dst,
                         cudaStream_t st);
 template <typename R>
 void launch_field_energy(const Consts &K, GView<R> g, double *dst, int grid, cudaStream_t st);
+
+// ---------------------------------------------------------------- batches
+// One target of a batch as the batched kernels see it (a device array of
+// these, one per target).
+template <typename R>
+struct BatchItem {
+  Consts K;
+  HotK<R> h;
+  GView<R> g;
+  TallyView tv;
+  Counters *cnt;
+  long long off, cap;  // particle slots [off, off + cap) of the shared arrays
+};
+
+// device arrays shared by the batched kernels (n + 1 prefix sums over targets)
+struct BatchDev {
+  int n;                  // targets
+  long long *wpref;       // warp-sized particle tasks, from the live counts
+  long long *ipref;       // electrons injected in this step
+  const long long *npref; // vector-grid nodes
+  const long long *kpref; // sort keys (each target's tile keys, then its dead bin)
+  long long *sstart;      // sort: first sorted offset of each target (n entries)
+  long long *snew;        // sort: slots kept per target (n entries)
+};
+
+// counts per step and per target: warp tasks and injections (one block)
+template <typename R>
+void launch_batch_plan(const BatchItem<R> *items, BatchDev d, cudaStream_t st);
+// persistent particle kernel, sm_count * blocks_per_sm blocks
+template <typename R>
+void launch_batch_push(const BatchItem<R> *items, BatchDev d, PView<R> p, const R *table,
+                       int sm_count, int blocks_per_sm, cudaStream_t st);
+template <typename R>
+void launch_batch_inject(const BatchItem<R> *items, BatchDev d, PView<R> p, int grid,
+                         cudaStream_t st);
+template <typename R>
+void launch_batch_advance(const BatchItem<R> *items, BatchDev d, cudaStream_t st);
+template <typename R>
+void launch_batch_efield(const BatchItem<R> *items, BatchDev d, int grid, cudaStream_t st);
+template <typename R>
+void launch_batch_bheat(const BatchItem<R> *items, BatchDev d, int grid, cudaStream_t st);
+// cell sort of every target inside its own slots; returns launches made
+template <typename R>
+int launch_batch_sort(const BatchItem<R> *items, BatchDev d, PView<R> src, PView<R> dst,
+                      uint32_t *keys, uint32_t *counts, uint32_t *partials, long long nkeys_total,
+                      int grid, cudaStream_t st);
+// exclusive scan of counts[0, m) in place (partials: scratch of
+// ceil(m / 4096) + 1 words); returns launches made
+int launch_scan(uint32_t *counts, long long m, uint32_t *partials, cudaStream_t st);
 
 }  // namespace hpic

@@ -18,492 +18,9 @@
 // through the read-only path and the current is added by reductions in L2.
 // Electrons are kept sorted by 4x4x4 cell tiles, so a warp's gathers and
 // reductions fall on few L2 lines.
-#include "kernels.h"
+#include "push.cuh"
 
 namespace hpic {
-
-// ---------------------------------------------------------------- geometry
-template <typename R>
-struct Axis {
-  int iN, iS;  // base node of the node-centred / half-staggered lattice
-  R fN, fS;    // fractional offsets
-};
-
-// linear weights along one axis; X in cells, n cells.  The half-staggered
-// lattice is held at its outermost value within half a cell of a wall.
-template <typename R>
-__device__ __forceinline__ Axis<R> axis_weights(R X, int n) {
-  Axis<R> a;
-  int i = (int)m_floor(X);
-  i = min(max(i, 0), n - 1);
-  a.iN = i;
-  a.fN = X - R(i);
-  R q = X - R(0.5);
-  q = q < R(0) ? R(0) : q;
-  q = q > R(n - 1) ? R(n - 1) : q;
-  int is = (int)m_floor(q);
-  is = min(max(is, 0), n - 1);
-  a.iS = is;
-  a.fS = q - R(is);
-  return a;
-}
-
-// the x-neighbour pair (G[q], G[q+1]) through the read-only path.  (Aligned
-// 16-byte pair loads and v4 vector reductions were measured slower here:
-// the per-lane alignment selects and the +0 lanes cost more than they save.)
-template <typename R>
-__device__ __forceinline__ void ld_pair(const R *G, int q, R &v0, R &v1) {
-  v0 = __ldg(G + q);
-  v1 = __ldg(G + q + 1);
-}
-
-template <typename R>
-__device__ __forceinline__ void red_pair(R *G, int q, R v0, R v1) {
-  atomicAdd(G + q, v0);
-  atomicAdd(G + q + 1, v1);
-}
-
-// the grid as the push kernel sees it; node (i, j, k) lives at i + sy*j + sz*k
-template <typename R>
-struct Grid {
-  const R *F[6];  // Ex Ey Ez Bx By Bz
-  R *J[3];
-  double *H;
-  int sy, sz, nx, ny;
-  __device__ __forceinline__ int node(int i, int j, int k) const { return i + sy * j + sz * k; }
-};
-
-template <typename R>
-__device__ __forceinline__ R trilerp(const Grid<R> &g, int c, int b, R fx, R fy, R fz) {
-  const R gx = R(1) - fx;
-  R a0, a1, b0, b1, c0, c1, d0, d1;
-  ld_pair(g.F[c], b, a0, a1);
-  ld_pair(g.F[c], b + g.sy, b0, b1);
-  ld_pair(g.F[c], b + g.sz, c0, c1);
-  ld_pair(g.F[c], b + g.sz + g.sy, d0, d1);
-  const R e00 = a0 * gx + a1 * fx;
-  const R e10 = b0 * gx + b1 * fx;
-  const R e01 = c0 * gx + c1 * fx;
-  const R e11 = d0 * gx + d1 * fx;
-  const R e0 = e00 * (R(1) - fy) + e10 * fy;
-  const R e1 = e01 * (R(1) - fy) + e11 * fy;
-  return e0 * (R(1) - fz) + e1 * fz;
-}
-
-template <typename R>
-__device__ __forceinline__ void spread(const Grid<R> &g, int c, int b, R fx, R fy, R fz, R v) {
-  const R gx = R(1) - fx, gy = R(1) - fy, gz = R(1) - fz;
-  const R v0 = v * gz, v1 = v * fz;
-  R *G = g.J[c];
-  red_pair(G, b, v0 * gy * gx, v0 * gy * fx);
-  red_pair(G, b + g.sy, v0 * fy * gx, v0 * fy * fx);
-  red_pair(G, b + g.sz, v1 * gy * gx, v1 * gy * fx);
-  red_pair(G, b + g.sz + g.sy, v1 * fy * gx, v1 * fy * fx);
-}
-
-// G(u0) = integral_{u0}^{1} s(u)/u du for s(u) = (4/3)(1-u) + u^2
-template <typename R>
-__device__ __forceinline__ R shape_G(R u0) {
-  return R(4.0 / 3.0) * (-m_flog(u0) - (R(1) - u0)) + R(0.5) * (R(1) - u0 * u0);
-}
-
-// photon energy from the inverse-CDF table (rows: ln eps, columns: r)
-template <typename R>
-__device__ __forceinline__ R sample_k(const HotK<R> &h, int rows, int cols,
-                                      const R *__restrict__ tab, R eps, R r) {
-  const R lr = m_log(eps / h.k_min);
-  R L = lr * h.t_inv_dlog;
-  int i = (int)m_floor(L);
-  i = min(max(i, 0), rows - 2);
-  R f = L - R(i);
-  f = f < R(0) ? R(0) : (f > R(1) ? R(1) : f);
-  const R cpos = r * R(cols - 1);
-  int j = (int)m_floor(cpos);
-  j = min(max(j, 0), cols - 2);
-  const R g = cpos - R(j);
-  const R *t0 = tab + i * cols + j;
-  const R *t1 = t0 + cols;
-  const R va = __ldg(t0) * (R(1) - g) + __ldg(t0 + 1) * g;
-  const R vb = __ldg(t1) * (R(1) - g) + __ldg(t1 + 1) * g;
-  const R v = va * (R(1) - f) + vb * f;
-  return h.k_min * m_exp(v * lr);
-}
-
-// photon polar angle: theta = t/gamma, t ~ t/(1+t^2)^2 truncated at theta = pi
-template <typename R>
-__device__ __forceinline__ R photon_theta(R gamma, R u) {
-  const R a = R(3.14159265358979323846) * gamma;
-  const R a2 = a * a;
-  const R F = u * a2 / (R(1) + a2);
-  const R omF = (R(1) - u) + u / (R(1) + a2);
-  return m_sqrt(F / omF) / gamma;
-}
-
-// per-thread tally accumulators
-template <typename R>
-struct Acc {
-  R W = 0, drag = 0;
-  double esc = 0, ref = 0, x = 0, xa = 0;
-  int n_esc = 0, n_ref = 0, n_refabs = 0, n_cut = 0, n_emit = 0, n_steps = 0, n_nf = 0;
-};
-
-struct StepCtx {
-  uint32_t step, key0, key1, target;
-  long long step_ll;
-};
-
-// Advance one live electron through the step.  Returns false when the
-// electron is absorbed or escapes (the caller marks its slot dead).  On
-// true, the state holds x^{n+1}, u^{n+1} and tau, and its current is
-// deposited.
-template <typename R>
-__device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const Grid<R> &g,
-                                        const R *__restrict__ tab, const TallyView &tv,
-                                        const StepCtx &sc, uint32_t id, R &X, R &Y, R &Zc,
-                                        R &ux, R &uy, R &uz, R &tau, Acc<R> &acc, R &heat_out,
-                                        int &heat_cell) {
-  const int nx = K.nx, ny = K.ny, nz = K.nz;
-
-  // ---- gather at x^n
-  const bool unbounded = (K.physics & P_UNBOUNDED) != 0;
-  const Axis<R> ax = axis_weights(X, nx), ay = axis_weights(Y, ny), az = axis_weights(Zc, nz);
-  R Ex = R(0), Ey = R(0), Ez = R(0), Bx = R(0), By = R(0), Bz = R(0);
-  if (!unbounded) {
-    Ex = trilerp(g, 0, g.node(ax.iS, ay.iN, az.iN), ax.fS, ay.fN, az.fN);
-    Ey = trilerp(g, 1, g.node(ax.iN, ay.iS, az.iN), ax.fN, ay.fS, az.fN);
-    Ez = trilerp(g, 2, g.node(ax.iN, ay.iN, az.iS), ax.fN, ay.fN, az.fS);
-    Bx = trilerp(g, 3, g.node(ax.iN, ay.iS, az.iS), ax.fN, ay.fS, az.fS);
-    By = trilerp(g, 4, g.node(ax.iS, ay.iN, az.iS), ax.fS, ay.fN, az.fS);
-    Bz = trilerp(g, 5, g.node(ax.iS, ay.iS, az.iN), ax.fS, ay.fS, az.fN);
-  }
-
-  // ---- Boris push: half kick, rotation, half kick
-  const R eps0 = kinetic(ux, uy, uz);
-  {
-    const R mx = ux + R(0.5) * Ex, my = uy + R(0.5) * Ey, mz = uz + R(0.5) * Ez;
-    const R gm = m_sqrt(R(1) + mx * mx + my * my + mz * mz);
-    const R hh = R(0.5) / gm;
-    const R tx = Bx * hh, ty = By * hh, tz = Bz * hh;
-    const R s2 = R(2) / (R(1) + tx * tx + ty * ty + tz * tz);
-    const R sx = tx * s2, sy_ = ty * s2, sz_ = tz * s2;
-    const R qx = mx + (my * tz - mz * ty), qy = my + (mz * tx - mx * tz), qz = mz + (mx * ty - my * tx);
-    ux = mx + (qy * sz_ - qz * sy_) + R(0.5) * Ex;
-    uy = my + (qz * sx - qx * sz_) + R(0.5) * Ey;
-    uz = mz + (qx * sy_ - qy * sx) + R(0.5) * Ez;
-  }
-  R eps = kinetic(ux, uy, uz);
-  acc.W += h.w * (eps0 - eps);
-  R heat = 0;
-  bool alive = true;
-
-  // ---- tracking cut and ionisation drag, Eq. (5)
-  if (eps < h.E_cut) {
-    heat += h.w * eps;
-    alive = false;
-  } else if (K.physics & P_DRAG) {
-    const R gam = R(1) + eps;
-    const R beta = u_of_eps(eps) / gam;
-    const R ig = R(1) / gam;
-    R br = m_flog(eps) + h.L_I + R(0.5) * m_flog(gam + R(1)) + R(0.909) * ig * ig -
-           R(0.818) * ig - R(0.246);
-    br = br < R(0) ? R(0) : br;
-    const R de = h.K_ion / beta * br;
-    const R eps1 = eps - de;
-    if (eps1 < h.E_cut) {
-      heat += h.w * eps;
-      alive = false;
-    } else {
-      const R s = u_of_eps(eps1) / m_sqrt(ux * ux + uy * uy + uz * uz);
-      ux *= s; uy *= s; uz *= s;
-      heat += h.w * de;
-      eps = eps1;
-    }
-  }
-
-  // ---- Davies scatter, Eq. (B4): polar Gamma*sigma, azimuth uniform
-  if (alive && (K.physics & P_SCATTER)) {
-    const U4 r0 = philox10(sc.step, id, 0u, sc.target, sc.key0, sc.key1);
-    const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
-    const R gam = m_sqrt(R(1) + un * un);
-    R lg = m_flog(h.K_lg * un);
-    lg = lg < R(0) ? R(0) : lg;
-    const R sig = m_sqrt(h.K_sc * gam / (un * un * un) * lg);
-    R s1, c1, s2, c2, st, ct;
-    m_sincos2pi(unif<R>(r0.b), &s1, &c1);
-    const R gauss = m_sqrt(R(-2) * m_log(unif<R>(r0.a))) * c1;
-    m_sincos(gauss * sig, &st, &ct);
-    m_sincos2pi(unif<R>(r0.c), &s2, &c2);
-    const R inv = R(1) / un;
-    R dx = ux * inv, dy = uy * inv, dz = uz * inv;
-    rotate(dx, dy, dz, ct, st, c2, s2);
-    ux = un * dx; uy = un * dy; uz = un * dz;
-  }
-
-  // ---- bremsstrahlung by optical depth (App. B)
-  if (alive && (K.physics & P_BREM) && eps > h.k_min) {
-    tau -= h.K_tau * u_of_eps(eps) / eps * shape_G(h.k_min / eps);
-    if (tau <= R(0)) {
-      const U4 r1 = philox10(sc.step, id, 1u, sc.target, sc.key0, sc.key1);
-      const R k = sample_k(h, K.t_rows, K.t_cols, tab, eps, unif<R>(r1.a));
-      const R thg = photon_theta(R(1) + eps, unif<R>(r1.b));
-      const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
-      R dx = ux / un, dy = uy / un, dz = uz / un;
-      R st, ct, sp, cp;
-      m_sincos(thg, &st, &ct);
-      m_sincos2pi(unif<R>(r1.c), &sp, &cp);
-      rotate(dx, dy, dz, ct, st, cp, sp);
-      const R th = m_atan2(m_sqrt(dy * dy + dz * dz), dx);  // polar angle from +x
-      // photon tally: energy row (underflow, log bins, overflow) x polar bin
-      int row;
-      if (k < h.tE_min) row = 0;
-      else if (k >= h.tE_max) row = K.n_E + 1;
-      else row = min(max(1 + (int)m_floor(h.inv_dlogE * m_log(k / h.tE_min)), 1), K.n_E);
-      const int col = min(max((int)m_floor(th * h.th_scale), 0), K.n_th - 1);
-      const double wph = K.w * K.inv_boost;
-      const double ek = wph * (double)k;
-      const int hb = row * K.n_th + col;
-      atomicAdd(tv.hist + hb, ek);
-      atomicAdd(tv.hist + (K.n_E + 2) * K.n_th + hb, wph);
-      acc.x += ek;
-      if ((double)k >= K.ce_thr) {
-        acc.xa += ek;
-        if (sc.step_ll < K.max_history) atomicAdd(tv.history + sc.step_ll, ek);
-      }
-      ++acc.n_emit;
-      tau = -m_log(R(1) - unif<R>(r1.d));
-      eps -= k * h.inv_boost;
-      if (eps < h.E_cut) {
-        heat += h.w * eps;
-        alive = false;
-      } else {
-        const R s = u_of_eps(eps) / un;
-        ux *= s; uy *= s; uz *= s;
-      }
-    }
-  }
-
-  acc.drag += heat;
-  heat_out = heat;  // deposited by the warp in the cell of x^n
-  heat_cell = ax.iN + nx * (ay.iN + ny * az.iN);
-  if (!alive) {
-    ++acc.n_cut;
-    return false;
-  }
-
-  // ---- move, then escape or reflux at each face crossed (x, y, z)
-  R ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
-  R pos[3] = {X + ux * ig * h.cdt, Y + uy * ig * h.cdt, Zc + uz * ig * h.cdt};
-  R u[3] = {ux, uy, uz};
-  const int nn[3] = {nx, ny, nz};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const R L = R(nn[a]);
-    if (unbounded || (pos[a] >= R(0) && pos[a] <= L)) continue;
-    const R e_out = kinetic(u[0], u[1], u[2]);
-    if (e_out >= h.eps_esc) {
-      acc.esc += (double)(h.w * e_out);
-      ++acc.n_esc;
-      return false;
-    }
-    const bool low = pos[a] < R(0);
-    pos[a] = low ? -pos[a] : R(2) * L - pos[a];
-    u[a] = -u[a];
-    const R un = m_sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const R un2 = un - h.du_reflux;
-    if (un2 <= R(0)) {
-      acc.ref += (double)(h.w * e_out);
-      ++acc.n_refabs;
-      return false;
-    }
-    const U4 r2 = philox10(sc.step, id, 2u + a, sc.target, sc.key0, sc.key1);
-    const R xi = h.sigma_dtheta * (unif<R>(r2.a) - R(0.5));
-    R st, ct, sp, cp;
-    m_sincos(xi, &st, &ct);
-    m_sincos2pi(unif<R>(r2.b), &sp, &cp);
-    const R inv = R(1) / un;
-    R d[3] = {u[0] * inv, u[1] * inv, u[2] * inv};
-    rotate(d[0], d[1], d[2], ct, st, cp, sp);
-    if (low && d[a] < R(0)) d[a] = -d[a];
-    if (!low && d[a] > R(0)) d[a] = -d[a];
-    u[0] = un2 * d[0]; u[1] = un2 * d[1]; u[2] = un2 * d[2];
-    acc.ref += (double)(h.w * (e_out - kinetic(u[0], u[1], u[2])));
-    ++acc.n_ref;
-  }
-  X = pos[0]; Y = pos[1]; Zc = pos[2];
-  ux = u[0]; uy = u[1]; uz = u[2];
-
-  return true;  // the caller's warp deposits the current at x^{n+1}
-}
-
-// ---------------------------------------------------------------- warp deposits
-// A warp's 32 electrons can sit in one cell (just after a cell sort) or in a
-// dozen (many steps later).  Atomics from one instruction that hit the same
-// address serialise in L2, so each warp first sorts its (cell, lane) keys
-// with a 32-wide bitonic network in registers, moves every electron's
-// deposit inputs to its sorted lane, sums each cell's contributions with a
-// segmented shuffle reduction and lets the first lane of each cell issue
-// the atomics: within one instruction every address is distinct.
-constexpr uint32_t kNoCell = (1u << 27) - 1u;  // key of a lane with nothing to deposit
-
-// ascending sort of one 32-bit value per lane across the warp
-__device__ __forceinline__ uint32_t warp_sort32(uint32_t c) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const uint32_t o = __shfl_xor_sync(0xffffffffu, c, j);
-      const bool keep_min = ((lane & k) == 0) == ((lane & j) == 0);
-      c = keep_min ? min(c, o) : max(c, o);
-    }
-  }
-  return c;
-}
-
-struct Runs {
-  bool head;  // first lane of its run
-  int end;    // last lane of the run
-};
-
-// runs of equal keys in lane order (the keys are sorted)
-__device__ __forceinline__ Runs runs_of(uint32_t key) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-  Runs r;
-  r.head = lane == 0 || prev != key;
-  const unsigned heads = __ballot_sync(0xffffffffu, r.head);
-  const unsigned after = heads & ~((2u << lane) - 1u);  // heads after this lane
-  r.end = after ? __ffs(after) - 2 : 31;
-  return r;
-}
-
-// sum of v over [lane, end]; at a head lane, the whole run
-template <typename R>
-__device__ __forceinline__ R seg_sum(R v, int end) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const R y = __shfl_down_sync(0xffffffffu, v, off);
-    if (lane + off <= end) v += y;
-  }
-  return v;
-}
-
-// drag heat into the cell of x^n (heat_cell < 0: nothing to add)
-template <typename R>
-__device__ __forceinline__ void warp_heat(const Grid<R> &g, R heat, int heat_cell) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t key = heat_cell >= 0 ? (uint32_t)heat_cell : kNoCell;
-  const uint32_t c = warp_sort32((key << 5) | (uint32_t)lane);
-  const uint32_t skey = c >> 5;
-  const R v = __shfl_sync(0xffffffffu, heat, (int)(c & 31u));
-  const Runs r = runs_of(skey);
-  const R s = seg_sum(v, r.end);
-  if (r.head && skey != kNoCell && s != R(0)) atomicAdd(g.H + skey, (double)s);
-}
-
-// Per-axis weights of one electron on the 3 nodes iN-1, iN, iN+1: the
-// node-centred lattice uses slots 1, 2; the half-staggered one slots off,
-// off+1 with off = iS - iN + 1.
-template <typename R>
-struct Slots {
-  R n1, n2, s0, s1, s2;
-};
-
-template <typename R>
-__device__ __forceinline__ Slots<R> slots_of(const Axis<R> &a) {
-  Slots<R> w;
-  w.n1 = R(1) - a.fN;
-  w.n2 = a.fN;
-  const int off = a.iS - a.iN + 1;  // 0 or 1
-  w.s0 = off == 0 ? R(1) - a.fS : R(0);
-  w.s1 = off == 0 ? a.fS : R(1) - a.fS;
-  w.s2 = off == 0 ? R(0) : a.fS;
-  return w;
-}
-
-template <typename R>
-__device__ __forceinline__ Slots<R> shfl_slots(const Slots<R> &w, int src) {
-  Slots<R> o;
-  o.n1 = __shfl_sync(0xffffffffu, w.n1, src);
-  o.n2 = __shfl_sync(0xffffffffu, w.n2, src);
-  o.s0 = __shfl_sync(0xffffffffu, w.s0, src);
-  o.s1 = __shfl_sync(0xffffffffu, w.s1, src);
-  o.s2 = __shfl_sync(0xffffffffu, w.s2, src);
-  return o;
-}
-
-template <typename R>
-__device__ __forceinline__ R slot_n(const Slots<R> &w, int c) { return c == 1 ? w.n1 : w.n2; }
-template <typename R>
-__device__ __forceinline__ R slot_s(const Slots<R> &w, int c) {
-  return c == 0 ? w.s0 : (c == 1 ? w.s1 : w.s2);
-}
-
-// one current component over its 12-node frame, staggered along axis SA
-template <typename R, int SA>
-__device__ __forceinline__ void frame_component(const Grid<R> &g, int c, const Runs &r,
-                                                bool valid, int i, int j, int k,
-                                                const Slots<R> &wx, const Slots<R> &wy,
-                                                const Slots<R> &wz, R v) {
-#pragma unroll
-  for (int cz = (SA == 2 ? 0 : 1); cz < 3; ++cz)
-#pragma unroll
-    for (int cy = (SA == 1 ? 0 : 1); cy < 3; ++cy)
-#pragma unroll
-      for (int cx = (SA == 0 ? 0 : 1); cx < 3; ++cx) {
-        const R w = (SA == 0 ? slot_s(wx, cx) : slot_n(wx, cx)) *
-                    (SA == 1 ? slot_s(wy, cy) : slot_n(wy, cy)) *
-                    (SA == 2 ? slot_s(wz, cz) : slot_n(wz, cz));
-        const R s = seg_sum(v * w, r.end);
-        if (r.head && valid && s != R(0))
-          atomicAdd(g.J[c] + g.node(i - 1 + cx, j - 1 + cy, k - 1 + cz), s);
-      }
-}
-
-// current J += w (u/gamma) S(x) at x^{n+1} for the lanes with dep set
-template <typename R>
-__device__ __forceinline__ void warp_current(const Consts &K, const HotK<R> &h, const Grid<R> &g,
-                                             bool dep, R X, R Y, R Zc, R ux, R uy, R uz) {
-  const int lane = threadIdx.x & 31;
-  Slots<R> wx{}, wy{}, wz{};
-  R vx = R(0), vy = R(0), vz = R(0);
-  uint32_t key = kNoCell;
-  if (dep) {
-    const R ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
-    const Axis<R> bx = axis_weights(X, K.nx), by = axis_weights(Y, K.ny), bz = axis_weights(Zc, K.nz);
-    wx = slots_of(bx);
-    wy = slots_of(by);
-    wz = slots_of(bz);
-    vx = h.w * ux * ig;
-    vy = h.w * uy * ig;
-    vz = h.w * uz * ig;
-    key = (uint32_t)(bx.iN + K.nx * (by.iN + K.ny * bz.iN));
-  }
-  const uint32_t c = warp_sort32((key << 5) | (uint32_t)lane);
-  const uint32_t skey = c >> 5;
-  const int src = (int)(c & 31u);
-  wx = shfl_slots(wx, src);
-  wy = shfl_slots(wy, src);
-  wz = shfl_slots(wz, src);
-  vx = __shfl_sync(0xffffffffu, vx, src);
-  vy = __shfl_sync(0xffffffffu, vy, src);
-  vz = __shfl_sync(0xffffffffu, vz, src);
-  const Runs r = runs_of(skey);
-  const bool valid = skey != kNoCell;
-  const int kk = (int)(skey / (uint32_t)(K.nx * K.ny));
-  const int rem = (int)skey - kk * K.nx * K.ny;
-  const int jj = rem / K.nx, ii = rem - jj * K.nx;
-  frame_component<R, 0>(g, 0, r, valid, ii, jj, kk, wx, wy, wz, vx);
-  frame_component<R, 1>(g, 1, r, valid, ii, jj, kk, wx, wy, wz, vy);
-  frame_component<R, 2>(g, 2, r, valid, ii, jj, kk, wx, wy, wz, vz);
-}
-
-// evict-first access to the streaming electron state
-template <typename R>
-__device__ __forceinline__ R ld_stream(const R *p) { return __ldcs(p); }
-template <typename R>
-__device__ __forceinline__ void st_stream(R *p, R v) { __stcs(p, v); }
 
 template <typename R>
 // FP32: three 256-thread blocks per SM (80 registers, no spills) measured
@@ -512,7 +29,7 @@ template <typename R>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2)
 k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__restrict__ tab,
        Counters *cnt, TallyView tv) {
-  __shared__ double red[13 * 32];
+  __shared__ double red[kAccN * 32];
   const long long n = cnt->n;
   StepCtx sc;
   sc.step_ll = cnt->step;
@@ -521,75 +38,24 @@ k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__rest
   sc.key1 = K.key1;
   sc.target = K.target_index;
 
-  Grid<R> g;
-  for (int c = 0; c < 3; ++c) {
-    g.F[c] = gv.E[c];
-    g.F[3 + c] = gv.B[c];
-    g.J[c] = gv.J[c];
-  }
-  g.H = gv.H;
-  g.sy = K.nx + 1;
-  g.sz = (K.nx + 1) * (K.ny + 1);
-  g.nx = K.nx;
-  g.ny = K.ny;
+  const Grid<R> g = make_grid(K, gv);
   Acc<R> acc;
 
   // warp-uniform loop: every lane reaches the warp-cooperative deposits
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); base < n;
-       base += stride) {
-    const long long ip = base + lane;
-    bool live = false, dep = false;
-    uint32_t id = kDead;
-    R X = 0, Y = 0, Zc = 0, ux = 0, uy = 0, uz = 0, tau = 0, heat = 0;
-    int heat_cell = -1;
-    if (ip < n) {
-      id = ld_stream(p.id + ip);
-      if (id != kDead) {
-        X = ld_stream(p.x + ip); Y = ld_stream(p.y + ip); Zc = ld_stream(p.z + ip);
-        ux = ld_stream(p.ux + ip); uy = ld_stream(p.uy + ip); uz = ld_stream(p.uz + ip);
-        tau = ld_stream(p.tau + ip);
-        if (isfinite(X) && isfinite(Y) && isfinite(Zc) && isfinite(ux) && isfinite(uy) &&
-            isfinite(uz) && isfinite(tau)) {
-          live = true;
-        } else {
-          p.id[ip] = kDead;
-          ++acc.n_nf;
-        }
-      }
-    }
-    if (live) {
-      ++acc.n_steps;
-      dep = advance(K, h, g, tab, tv, sc, id, X, Y, Zc, ux, uy, uz, tau, acc, heat, heat_cell);
-      if (dep) {
-        st_stream(p.x + ip, X); st_stream(p.y + ip, Y); st_stream(p.z + ip, Zc);
-        st_stream(p.ux + ip, ux); st_stream(p.uy + ip, uy); st_stream(p.uz + ip, uz);
-        st_stream(p.tau + ip, tau);
-      } else {
-        p.id[ip] = kDead;
-      }
-    }
-    if (!(K.physics & P_UNBOUNDED)) {  // uniform over the grid
-      warp_heat(g, heat, heat != R(0) ? heat_cell : -1);
-      warp_current(K, h, g, dep, X, Y, Zc, ux, uy, uz);
-    }
-  }
+       base += stride)
+    push_warp(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc);
 
-  const double v[13] = {(double)acc.W, (double)acc.drag, acc.esc, acc.ref, acc.x, acc.xa,
-                        (double)acc.n_esc, (double)acc.n_ref, (double)acc.n_refabs,
-                        (double)acc.n_cut, (double)acc.n_emit, (double)acc.n_steps,
-                        (double)acc.n_nf};
-  const int slot[13] = {T_W_FIELD, T_E_DRAG, T_E_ESC, T_E_REFLUX, T_E_XRAY, T_E_XRAY_ABOVE,
-                        T_N_ESC, T_N_REFLUX, T_N_REFLUX_ABS, T_N_CUT, T_N_EMIT, T_PSTEPS,
-                        T_N_NONFINITE};
-  block_flush<13>(v, slot, tv.tal, red);
+  double v[kAccN];
+  acc.values(v);
+  block_flush<kAccN>(v, kAccSlot, tv.tal, red);
 }
 
 // ---------------------------------------------------------------- injection
 // Eq. (B1) with flat-top envelopes: step s < S injects floor((s+1)N/S) -
-// floor(sN/S) electrons at x = 1e-6 cells on a disc, energies exponential
-// with mean a0 m_e c^2 (App. B), directions uniform in solid angle in a cone.
+// floor(sN/S) electrons (inject_one places each).
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_inject(const Consts K, PView<R> p, Counters *cnt, long long cap, TallyView tv) {
@@ -608,27 +74,7 @@ k_inject(const Consts K, PView<R> p, Counters *cnt, long long cap, TallyView tv)
       atomicOr(&cnt->flags, 1u);
       continue;
     }
-    const uint32_t id = (uint32_t)(id0 + i);
-    const U4 r8 = philox10(step, id, 8u, K.target_index, K.key0, K.key1);
-    const U4 r9 = philox10(step, id, 9u, K.target_index, K.key0, K.key1);
-    const R rr = R(K.spot_r) * m_sqrt(unif<R>(r8.a));
-    R sp, cp;
-    m_sincos2pi(unif<R>(r8.b), &sp, &cp);
-    const R eps = -R(K.T_hot) * m_log(R(1) - unif<R>(r8.c));
-    const R omc = unif<R>(r8.d) * R(K.omc_cone);  // 1 - cos(theta)
-    const R ct = R(1) - omc;
-    const R stt = m_sqrt(omc * (R(2) - omc));
-    R sc, cc;
-    m_sincos2pi(unif<R>(r9.a), &sc, &cc);
-    const R un = u_of_eps(eps);
-    p.x[q] = R(1e-6);
-    p.y[q] = R(K.spot_y) + rr * cp;
-    p.z[q] = R(K.spot_z) + rr * sp;
-    p.ux[q] = un * ct;
-    p.uy[q] = un * stt * cc;
-    p.uz[q] = un * stt * sc;
-    p.tau[q] = -m_log(R(1) - unif<R>(r9.b));
-    p.id[q] = id;
+    const R eps = inject_one(K, p, q, (uint32_t)(id0 + i), step);
     e_inj += K.w * (double)eps;
     n_inj += 1.0;
   }
@@ -713,29 +159,6 @@ __global__ void k_advance(Counters *cnt, long long cap) {
 }
 
 // ---------------------------------------------------------------- launchers
-template <typename R>
-HotK<R> make_hot(const Consts &K) {
-  HotK<R> h;
-  h.w = R(K.w);
-  h.cdt = R(K.cdt_dx);
-  h.E_cut = R(K.E_cut);
-  h.K_ion = R(K.K_ion);
-  h.L_I = R(K.L_I);
-  h.K_sc = R(K.K_sc);
-  h.K_lg = R(K.K_lg);
-  h.K_tau = R(K.K_tau);
-  h.k_min = R(K.k_min);
-  h.inv_boost = R(K.inv_boost);
-  h.eps_esc = R(K.eps_esc);
-  h.du_reflux = R(K.du_reflux);
-  h.sigma_dtheta = R(K.sigma_dtheta);
-  h.tE_min = R(K.tE_min);
-  h.tE_max = R(K.tE_max);
-  h.inv_dlogE = R(K.inv_dlogE);
-  h.th_scale = R(K.n_th / 3.14159265358979323846);
-  h.t_inv_dlog = R(K.t_inv_dlog);
-  return h;
-}
 
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,

@@ -21,6 +21,7 @@ HPIC_FP64, HPIC_FP32_MIXED = 0, 1
 HPIC_DRAG, HPIC_SCATTER, HPIC_BREM, HPIC_FIELDS, HPIC_FARADAY, HPIC_HEATING = 1, 2, 4, 8, 16, 32
 HPIC_ALL = 63
 HPIC_UNBOUNDED = 64
+HPIC_BATCH_MAX_TARGETS = 256
 GRID = {"T": 0, "eta": 1, "Ex": 2, "Ey": 3, "Ez": 4, "Bx": 5, "By": 6, "Bz": 7,
         "jx": 8, "jy": 9, "jz": 10, "heat": 11}
 
@@ -61,6 +62,11 @@ _TALLY_NAMES = ("E_injected", "N_injected", "W_field", "E_drag", "E_xray", "E_xr
                 "E_escaped", "E_reflux", "E_ohmic_grid", "n_injected", "n_escaped", "n_refluxed",
                 "n_reflux_absorbed", "n_cut", "n_emitted", "particle_steps", "n_nonfinite",
                 "E_live", "E_B_field")
+
+
+class hpic_batch_tuning(C.Structure):
+    _fields_ = [("blocks_per_sm", C.c_int32), ("sort_interval", C.c_int32),
+                ("use_graph", C.c_int32), ("reserved", C.c_int32), ("ms_per_step", C.c_double)]
 
 
 class hpic_tallies(C.Structure):
@@ -105,6 +111,18 @@ def lib() -> C.CDLL:
             "hpic_kernel_time": [vp, _DP, _I64P, _DP],
             "hpic_launch_count": [vp, _I64P],
             "hpic_destroy": [vp],
+            "hpic_batch_init": [C.POINTER(vp), C.c_int32, C.POINTER(hpic_target_desc),
+                                C.POINTER(hpic_laser_desc), C.POINTER(hpic_run_params),
+                                C.c_int64, C.c_int, vp],
+            "hpic_batch_target": [vp, C.c_int32, C.POINTER(vp)],
+            "hpic_batch_step": [vp, C.c_int64],
+            "hpic_batch_get_tuning": [vp, C.POINTER(hpic_batch_tuning)],
+            "hpic_batch_set_tuning": [vp, C.POINTER(hpic_batch_tuning)],
+            "hpic_batch_autotune": [vp, C.c_int32, C.POINTER(hpic_batch_tuning)],
+            "hpic_batch_profile": [vp, C.c_int],
+            "hpic_batch_kernel_time": [vp, _DP, _I64P, _DP],
+            "hpic_batch_launch_count": [vp, _I64P],
+            "hpic_batch_destroy": [vp],
         }
         sig["hpic_sort_cells_noalloc"] = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
                                           C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
@@ -115,6 +133,8 @@ def lib() -> C.CDLL:
             f.restype = C.c_int
         L.hpic_last_error.argtypes = [vp]
         L.hpic_last_error.restype = C.c_char_p
+        L.hpic_batch_last_error.argtypes = [vp]
+        L.hpic_batch_last_error.restype = C.c_char_p
         _lib = L
     return _lib
 
@@ -122,6 +142,13 @@ def lib() -> C.CDLL:
 def _check(code: int, h=None) -> int:
     if code != HPIC_OK:
         msg = lib().hpic_last_error(h)
+        raise HpicError(code, msg.decode() if msg else "")
+    return code
+
+
+def _bcheck(code: int, b=None) -> int:
+    if code != HPIC_OK:
+        msg = lib().hpic_batch_last_error(b)
         raise HpicError(code, msg.decode() if msg else "")
     return code
 
@@ -290,35 +317,79 @@ def hpic_destroy(h) -> None:
         _check(lib().hpic_destroy(h))
 
 
-class Sim:
-    """One target on the GPU: the C-ABI calls bundled with their workload dicts."""
+# ---- batches ----
+def hpic_batch_init(targets: list, lasers: list | None, run: dict, precision: int = HPIC_FP64,
+                    spare_slots: int = 0, device: int = 0, stream: int = 0,
+                    sort_interval: int = 0) -> C.c_void_p:
+    n = len(targets)
+    T = (hpic_target_desc * n)(*[target_desc(t) for t in targets])
+    Lz = (hpic_laser_desc * n)(*[laser_desc(l) for l in lasers]) if lasers is not None else None
+    r = run_params(run, precision, sort_interval)
+    b = C.c_void_p()
+    _bcheck(lib().hpic_batch_init(C.byref(b), n, T, Lz, C.byref(r), spare_slots, device,
+                                  C.c_void_p(stream) if stream else None))
+    return b
 
-    def __init__(self, target: dict, laser: dict | None, run: dict, precision: int = HPIC_FP64,
-                 device: int = 0, stream: int = 0, sort_interval: int = 0):
-        self.target, self.run = dict(target), dict(run)
-        self.h = hpic_init_target(target, run, precision, device, stream, sort_interval)
-        if laser is not None:
-            hpic_inject_electrons(self.h, laser)
 
-    def close(self) -> None:
-        if getattr(self, "h", None):
-            hpic_destroy(self.h)
-            self.h = None
+def hpic_batch_target(b, t: int) -> C.c_void_p:
+    h = C.c_void_p()
+    _bcheck(lib().hpic_batch_target(b, t, C.byref(h)), b)
+    return h
 
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
 
-    def step(self, n: int = 1) -> None:
-        hpic_step(self.h, n)
+def hpic_batch_step(b, n: int = 1) -> None:
+    _bcheck(lib().hpic_batch_step(b, n), b)
 
-    def seed(self, n: int, mean_energy_J: float) -> None:
-        hpic_seed_electrons(self.h, n, mean_energy_J)
 
-    def sort(self) -> None:
-        hpic_sort(self.h)
+def _tuning_dict(t: hpic_batch_tuning) -> dict:
+    return {"blocks_per_sm": t.blocks_per_sm, "sort_interval": t.sort_interval,
+            "use_graph": bool(t.use_graph), "ms_per_step": t.ms_per_step}
+
+
+def hpic_batch_get_tuning(b) -> dict:
+    t = hpic_batch_tuning()
+    _bcheck(lib().hpic_batch_get_tuning(b, C.byref(t)), b)
+    return _tuning_dict(t)
+
+
+def hpic_batch_set_tuning(b, blocks_per_sm: int, sort_interval: int, use_graph: bool = True) -> None:
+    t = hpic_batch_tuning(blocks_per_sm, sort_interval, int(use_graph), 0, 0.0)
+    _bcheck(lib().hpic_batch_set_tuning(b, C.byref(t)), b)
+
+
+def hpic_batch_autotune(b, trial_steps: int) -> dict:
+    t = hpic_batch_tuning()
+    _bcheck(lib().hpic_batch_autotune(b, trial_steps, C.byref(t)), b)
+    return _tuning_dict(t)
+
+
+def hpic_batch_profile(b, enable: bool) -> None:
+    _bcheck(lib().hpic_batch_profile(b, int(enable)), b)
+
+
+def hpic_batch_kernel_time(b):
+    ms, ps = C.c_double(), C.c_double()
+    nl = C.c_int64()
+    _bcheck(lib().hpic_batch_kernel_time(b, C.byref(ms), C.byref(nl), C.byref(ps)), b)
+    return ms.value, nl.value, ps.value
+
+
+def hpic_batch_launch_count(b) -> int:
+    v = C.c_int64()
+    _bcheck(lib().hpic_batch_launch_count(b, C.byref(v)), b)
+    return v.value
+
+
+def hpic_batch_destroy(b) -> None:
+    if b:
+        _bcheck(lib().hpic_batch_destroy(b))
+
+
+class Target:
+    """Reads and writes of one target's state through a context handle."""
+
+    def __init__(self, h, target: dict, run: dict):
+        self.h, self.target, self.run = h, dict(target), dict(run)
 
     def tallies(self) -> dict:
         return hpic_read_tallies(self.h)
@@ -353,3 +424,79 @@ class Sim:
 
     def set_clock(self, step: int, next_id: int) -> None:
         hpic_set_clock(self.h, step, next_id)
+
+
+class Sim(Target):
+    """One target on the GPU: the C-ABI calls bundled with their workload dicts."""
+
+    def __init__(self, target: dict, laser: dict | None, run: dict, precision: int = HPIC_FP64,
+                 device: int = 0, stream: int = 0, sort_interval: int = 0):
+        super().__init__(None, target, run)
+        self.h = hpic_init_target(target, run, precision, device, stream, sort_interval)
+        if laser is not None:
+            hpic_inject_electrons(self.h, laser)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            hpic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1) -> None:
+        hpic_step(self.h, n)
+
+    def seed(self, n: int, mean_energy_J: float) -> None:
+        hpic_seed_electrons(self.h, n, mean_energy_J)
+
+    def sort(self) -> None:
+        hpic_sort(self.h)
+
+
+class Batch:
+    """Many targets stepped together; batch.target(t) reads target t."""
+
+    def __init__(self, targets: list, lasers: list | None, run: dict,
+                 precision: int = HPIC_FP64, spare_slots: int = 0, device: int = 0,
+                 stream: int = 0, sort_interval: int = 0):
+        self.run = dict(run)
+        self.b = hpic_batch_init(targets, lasers, run, precision, spare_slots, device, stream,
+                                 sort_interval)
+        self.targets = [Target(hpic_batch_target(self.b, t), targets[t],
+                               dict(run, target_index=int(run.get("target_index", 0)) + t))
+                        for t in range(len(targets))]
+
+    def __len__(self) -> int:
+        return len(self.targets)
+
+    def target(self, t: int) -> Target:
+        return self.targets[t]
+
+    def step(self, n: int = 1) -> None:
+        hpic_batch_step(self.b, n)
+
+    def tuning(self) -> dict:
+        return hpic_batch_get_tuning(self.b)
+
+    def set_tuning(self, blocks_per_sm: int, sort_interval: int, use_graph: bool = True) -> None:
+        hpic_batch_set_tuning(self.b, blocks_per_sm, sort_interval, use_graph)
+
+    def autotune(self, trial_steps: int = 40) -> dict:
+        return hpic_batch_autotune(self.b, trial_steps)
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            for t in self.targets:
+                t.h = None
+            hpic_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

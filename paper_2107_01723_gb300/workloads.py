@@ -89,3 +89,47 @@ def config2() -> dict:
     t = target(n=(128, 128, 128))
     return {"target": t, "laser": laser(t, I_Wcm2=1e21, n_macro=10_000_000),
             "run": run(seed=0, max_history=20_000), "steps": 20_000}
+
+
+def macro_split(weights, total: int, lo: int, hi: int) -> list:
+    """Integers proportional to `weights`, each clamped to [lo, hi], summing to
+    `total` (the scale is re-solved after clamping, so the unclamped shares
+    stay proportional)."""
+    w = [float(x) for x in weights]
+    if not (lo * len(w) <= total <= hi * len(w)):
+        raise ValueError("total outside [lo, hi] x count")
+
+    def filled(s):
+        return sum(min(max(s * x, lo), hi) for x in w)
+
+    a, b = 0.0, 1.0
+    while filled(b) < total:
+        b *= 2.0
+    for _ in range(200):
+        m = 0.5 * (a + b)
+        a, b = (m, b) if filled(m) < total else (a, m)
+    n = [int(round(min(max(b * x, lo), hi))) for x in w]
+    free = [i for i in range(len(w)) if lo < n[i] < hi] or list(range(len(w)))
+    n[max(free, key=lambda i: n[i])] += total - sum(n)
+    return n
+
+
+def config4(n_targets=64, seed=1, total_macro=60_000_000, lo=100_000, hi=4_000_000,
+            steps=2000, cross=64, thickness=(5, 200)) -> dict:
+    """Batched scan: n_targets independent targets drawn from a Philox stream:
+    thickness uniform in [5, 200] cells of 1 um along x on a cross x cross
+    section, element uniform over Al, Cu, Au at solid density, log10 I
+    uniform in [20, 22] (W/cm^2), macro-electrons proportional to the laser
+    energy (I at fixed spot and duration) scaled to total_macro and clamped to
+    [lo, hi]; 5 um flat-top spot, 100 fs injection, 1 ps window."""
+    import numpy as np
+
+    g = np.random.Generator(np.random.Philox(seed))
+    L = g.integers(thickness[0], thickness[1] + 1, size=n_targets)
+    mats = g.choice(["Al", "Cu", "Au"], size=n_targets)
+    I = 10.0 ** g.uniform(20.0, 22.0, size=n_targets)
+    n_macro = macro_split(I, total_macro, lo, hi)
+    targets = [target(n=(int(L[i]), cross, cross), material=str(mats[i])) for i in range(n_targets)]
+    lasers = [laser(targets[i], I_Wcm2=float(I[i]), n_macro=n_macro[i]) for i in range(n_targets)]
+    return {"targets": targets, "lasers": lasers, "run": run(seed=0, max_history=steps),
+            "steps": steps, "I_Wcm2": [float(x) for x in I], "materials": [str(m) for m in mats]}

@@ -40,17 +40,19 @@ def test_struct_layouts_match_header(tmp_path):
     prog = tmp_path / "layout.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "hpic.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(hpic_target_desc), sizeof(hpic_laser_desc), sizeof(hpic_run_params),"
         "sizeof(hpic_tallies), offsetof(hpic_run_params, kappa_esc),"
-        "offsetof(hpic_run_params, max_history), offsetof(hpic_laser_desc, n_macro));return 0;}\n")
+        "offsetof(hpic_run_params, max_history), offsetof(hpic_laser_desc, n_macro),"
+        "sizeof(hpic_batch_tuning), offsetof(hpic_batch_tuning, ms_per_step));return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [C.sizeof(hpic.hpic_target_desc), C.sizeof(hpic.hpic_laser_desc),
             C.sizeof(hpic.hpic_run_params), C.sizeof(hpic.hpic_tallies),
             hpic.hpic_run_params.kappa_esc.offset, hpic.hpic_run_params.max_history.offset,
-            hpic.hpic_laser_desc.n_macro.offset]
+            hpic.hpic_laser_desc.n_macro.offset, C.sizeof(hpic.hpic_batch_tuning),
+            hpic.hpic_batch_tuning.ms_per_step.offset]
     assert got == want
 
 
@@ -95,3 +97,41 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(hpic, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(FileNotFoundError):
         hpic.lib()
+
+
+def _bad_batch(lib, targets, lasers, run, spare=0):
+    b = C.c_void_p()
+    n = len(targets)
+    T = (hpic.hpic_target_desc * max(n, 1))(*[hpic.target_desc(t) for t in targets])
+    L = (hpic.hpic_laser_desc * max(n, 1))(*[hpic.laser_desc(l) for l in lasers]) if lasers else None
+    r = hpic.run_params(run)
+    code = lib.hpic_batch_init(C.byref(b), n, T, L, C.byref(r), spare, 0, None)
+    assert not b.value
+    return code, lib.hpic_batch_last_error(None).decode()
+
+
+def test_batch_validation_rejects_bad_arguments(lib):
+    c = W.config_small()
+    t, l, r = c["target"], c["laser"], c["run"]
+    assert _bad_batch(lib, [], None, r)[0] == hpic.HPIC_EINVAL
+    assert _bad_batch(lib, [t] * (hpic.HPIC_BATCH_MAX_TARGETS + 1), None, r)[0] == hpic.HPIC_EINVAL
+    code, msg = _bad_batch(lib, [t, dict(t, nx=1)], None, r)
+    assert code == hpic.HPIC_EINVAL and msg.startswith("target 1:")
+    code, msg = _bad_batch(lib, [t, t], [l, dict(l, spot_r=1.0)], r)
+    assert code == hpic.HPIC_EINVAL and msg.startswith("laser 1:")
+    assert _bad_batch(lib, [t], [l], r, spare=-1)[0] == hpic.HPIC_EINVAL
+    assert lib.hpic_batch_step(None, 1) == hpic.HPIC_EINVAL
+    assert lib.hpic_batch_destroy(None) == hpic.HPIC_EINVAL
+    assert lib.hpic_batch_target(None, 0, None) == hpic.HPIC_EINVAL
+
+
+def test_batch_without_device_is_an_error(lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    c = W.config_small()
+    code, _ = _bad_batch(lib, [c["target"]] * 2, [c["laser"]] * 2, c["run"])
+    assert code == hpic.HPIC_ECUDA

@@ -394,7 +394,8 @@ def run_batch(args):
     from paper_2107_01723_gb300 import hpic
     from paper_2107_01723_gb300 import workloads as W
     B.build()
-    cfg = W.config4()
+    cfg = W.config4(n_targets=args.batch_targets,
+                    total_macro=int(6e7 * args.batch_targets / 64))
     prec_name = args.precision
     prec = hpic.HPIC_FP32_MIXED if prec_name == "fp32" else hpic.HPIC_FP64
     warm = args.warmup if args.warmup >= 200 else 200
@@ -403,7 +404,12 @@ def run_batch(args):
     b = hpic.Batch(cfg["targets"], cfg["lasers"], cfg["run"], precision=prec,
                    stream=stream.cuda_stream, sort_interval=SORT_INTERVAL)
     b.step(warm)
-    tune = b.autotune(trial_steps=40)
+    if args.batch_tuning:
+        bps, si = (int(v) for v in args.batch_tuning.split(","))
+        b.set_tuning(bps, si)
+        tune = dict(b.tuning(), chosen="fixed by --batch-tuning")
+    else:
+        tune = dict(b.autotune(trial_steps=40), chosen="autotuned")
     b.step(1)  # captures and uploads the graphs of the chosen tuning
     torch.cuda.synchronize()
     live = sum(b.target(t).n for t in range(len(b)))
@@ -435,9 +441,10 @@ def run_batch(args):
             "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": ms / steps,
             "higher_is_better": True, "dtype": "f32" if prec_name == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": ("64 targets: thickness U{5..200} x 64 x 64 cells of 1 um, "
+            "config": {"workload": (f"{len(b)} targets: thickness U{{5..200}} x 64 x 64 cells of 1 um, "
                                     "Z in {13, 29, 79}, log10 I ~ U[20, 22] W/cm^2, "
-                                    "6e7 e- in all (1e5..3e6 per target), 1 ps window"),
+                                    f"{sum(l['n_macro'] for l in cfg['lasers']):.3g} e- in all "
+                                    "(1e5..4e6 per target), 1 ps window"),
                        "live_electrons_at_start": live, "tuning": tune,
                        "graphs": "step and sort replayed from captured CUDA graphs"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -455,6 +462,10 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="headline", choices=["headline", "emission", "batch"])
     ap.add_argument("--emission-n", type=int, default=2 ** 27)
+    ap.add_argument("--batch-targets", type=int, default=64,
+                    help="batched scan: targets (electrons scale with the count)")
+    ap.add_argument("--batch-tuning", default="",
+                    help="batched scan: 'blocks_per_sm,sort_interval' instead of the autotuner")
     ap.add_argument("--full-run", action="store_true",
                     help="run the whole headline workload in FP32 and FP64 and compare CE")
     ap.add_argument("--full-steps", type=int, default=0)

@@ -176,6 +176,16 @@ void hpic::fold(const hpic_target_desc &t, const hpic_run_params &r, const hpic_
   K.B_cold = std::cbrt(3.0 / (4.0 * PI * ni)) * t.lambda1 * std::sqrt(ME / 3.0);
   K.eta_max = t.eta_max_ohm_m;
   K.lambda1 = t.lambda1;
+  // eta = eta_max exactly while tau <= eta_num/eta_max: tau_hot = A_hot (k T)^1.5
+  // grows with T, tau_cold = B_cold/sqrt(k T) falls; the band is narrowed by a
+  // relative 1e-6 so that inside it the full formula is capped with room to spare
+  {
+    const double X = K.eta_num / K.eta_max;
+    const double T_hot = std::pow(X / K.A_hot, 2.0 / 3.0) / KB;
+    const double T_cold = t.lambda1 > 0.0 ? std::pow(K.B_cold / X, 2.0) / KB : 0.0;
+    K.eta_Tlo = T_cold * (1.0 + 1e-6);
+    K.eta_Thi = T_hot * (1.0 - 1e-6);
+  }
   K.key0 = (uint32_t)(r.seed & 0xFFFFFFFFull);
   K.key1 = (uint32_t)(r.seed >> 32);
   K.target_index = r.target_index;
@@ -272,6 +282,7 @@ void destroy_all(hpic_ctx *c) {
   cudaFree(c->fields);
   cudaFree(c->T);
   cudaFree(c->eta);
+  cudaFree(c->eta_r);
   cudaFree(c->H);
   cudaFree(c->tal);
   cudaFree(c->hist);
@@ -493,6 +504,7 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
   bool ok = cudaMalloc(&ctx->fields, 9 * ctx->vstride * ctx->rsz) == cudaSuccess &&
             cudaMalloc(&ctx->T, K.ncell * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ctx->eta, K.ncell * sizeof(double)) == cudaSuccess &&
+            (!ctx->fp32 || cudaMalloc(&ctx->eta_r, K.ncell * sizeof(float)) == cudaSuccess) &&
             cudaMalloc(&ctx->H, K.ncell * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ctx->counts, m * sizeof(uint32_t)) == cudaSuccess &&
             cudaMalloc(&ctx->partials, (ntiles + 1) * sizeof(uint32_t)) == cudaSuccess &&
@@ -513,6 +525,7 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
   if (rc) return bail(rc);
   cudaStream_t st = ctx->stream;
   std::vector<double> T0(K.ncell, t->T0_K), E0(K.ncell, eta_host(ctx, t->T0_K));
+  std::vector<float> E0f(ctx->fp32 ? K.ncell : 0, (float)E0[0]);
   if (cudaMemsetAsync(ctx->fields, 0, 9 * ctx->vstride * ctx->rsz, st) != cudaSuccess ||
       cudaMemsetAsync(ctx->H, 0, K.ncell * sizeof(double), st) != cudaSuccess ||
       cudaMemsetAsync(ctx->tal, 0, hpic::T_COUNT * sizeof(double), st) != cudaSuccess ||
@@ -520,7 +533,8 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
       cudaMemsetAsync(ctx->history, 0, (r->max_history > 0 ? r->max_history : 1) * sizeof(double), st) != cudaSuccess ||
       cudaMemsetAsync(ctx->cnt, 0, sizeof(hpic::Counters), st) != cudaSuccess ||
       cudaMemcpyAsync(ctx->T, T0.data(), K.ncell * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(ctx->eta, E0.data(), K.ncell * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      cudaMemcpyAsync(ctx->eta, E0.data(), K.ncell * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      (ctx->fp32 && cudaMemcpyAsync(ctx->eta_r, E0f.data(), K.ncell * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)) {
     cuda_fail(ctx, cudaGetLastError(), "initialisation");
     return bail(HPIC_ECUDA);
   }
@@ -712,6 +726,11 @@ int hpic_write_grid(hpic_ctx *ctx, int which, const double *in) {
     std::vector<double> b(in, in + L);
     for (auto &v : b) v *= s;
     CK(cudaMemcpyAsync(dst, b.data(), L * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (which == HPIC_GRID_ETA && ctx->fp32) {  // the field solve's FP32 copy
+      std::vector<float> f(b.begin(), b.end());
+      CK(cudaMemcpyAsync(ctx->eta_r, f.data(), L * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     return HPIC_OK;
   }

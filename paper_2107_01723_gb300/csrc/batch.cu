@@ -414,6 +414,7 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
   const size_t o_eb = take(eb * b->rsz), o_j = take(jv * b->rsz);
   const size_t o_T = take(cells * sizeof(double)), o_eta = take(cells * sizeof(double));
   const size_t o_H = take(cells * sizeof(double));
+  const size_t o_er = take(b->fp32 ? cells * sizeof(float) : 0);
   const size_t o_tal = take((size_t)n_targets * hpic::T_COUNT * sizeof(double));
   const size_t o_hist = take((size_t)n_targets * 2 * hist_len * sizeof(double));
   const size_t o_hy = take((size_t)n_targets * hlen * sizeof(double));
@@ -472,6 +473,7 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
     c->jfield = A + o_j + j_at * b->rsz;
     c->T = reinterpret_cast<double *>(A + o_T) + c_at;
     c->eta = reinterpret_cast<double *>(A + o_eta) + c_at;
+    if (b->fp32) c->eta_r = reinterpret_cast<float *>(A + o_er) + c_at;
     c->H = reinterpret_cast<double *>(A + o_H) + c_at;
     c->tal = reinterpret_cast<double *>(A + o_tal) + (size_t)t * hpic::T_COUNT;
     c->hist = reinterpret_cast<double *>(A + o_hist) + (size_t)t * 2 * hist_len;
@@ -496,11 +498,14 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
     std::fill(E0.begin() + c_at, E0.begin() + c_at + c->K.ncell, e0);
     c_at += c->K.ncell;
   }
+  std::vector<float> E0f(b->fp32 ? cells : 0);
+  for (size_t i = 0; i < E0f.size(); ++i) E0f[i] = (float)E0[i];
   std::vector<char> items;
   if (b->fp32) fill_items<float>(b, items); else fill_items<double>(b, items);
   if (cudaMemsetAsync(b->arena, 0, b->arena_bytes, st) != cudaSuccess ||
       cudaMemcpyAsync(b->tg[0]->T, T0.data(), cells * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(b->tg[0]->eta, E0.data(), cells * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      (b->fp32 && cudaMemcpyAsync(b->tg[0]->eta_r, E0f.data(), cells * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) ||
       cudaMemcpyAsync(b->items, items.data(), items.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(X + a_n, npref.data(), npref.size() * sizeof(long long), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(X + a_k, kpref.data(), kpref.size() * sizeof(long long), cudaMemcpyHostToDevice, st) != cudaSuccess) {

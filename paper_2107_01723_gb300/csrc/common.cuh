@@ -63,6 +63,7 @@ struct Consts {
   // heating, Eqs. (A4)-(A8), SI
   double F_ohm, F_H, dx3, heat_den, Tp_fac;
   double eta_num, A_hot, B_cold, eta_max, lambda1;
+  double eta_Tlo, eta_Thi;            // eta(T) is at its cap for eta_Tlo < T < eta_Thi (K)
   // injection, Eq. (B1)
   double T_hot, spot_r, spot_y, spot_z, omc_cone;  // omc_cone = 1 - cos(cone)
   long long n_macro, n_inj_steps;

@@ -41,6 +41,7 @@ struct hpic_ctx {
   void *jfield = nullptr;  // J[3], vstride apart (just after B in a single context)
   long long vstride = 0;   // nvec + >= 4 padding, a multiple of 64 (aligned vector access)
   double *T = nullptr, *eta = nullptr, *H = nullptr;
+  void *eta_r = nullptr;  // FP32 copy of eta read by the FP32 field solve (mixed precision)
   // tallies and tables
   double *tal = nullptr, *hist = nullptr, *history = nullptr, *scratch = nullptr;
   double *t64 = nullptr;
@@ -91,6 +92,7 @@ inline hpic::GView<R> gview(const hpic_ctx *c) {
   }
   g.T = c->T;
   g.eta = c->eta;
+  g.eta_r = c->fp32 ? static_cast<R *>(c->eta_r) : reinterpret_cast<R *>(c->eta);
   g.H = c->H;
   return g;
 }

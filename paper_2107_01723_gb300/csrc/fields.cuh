@@ -6,12 +6,14 @@
 
 namespace hpic {
 
+// (i, j, k) of node q; node counts stay below 2^31 (checked at creation), so
+// 32-bit division suffices
 __device__ __forceinline__ void node_of(long long q, int nx, int ny, int &i, int &j, int &k) {
-  const long long sy = nx + 1, sz = (long long)(nx + 1) * (ny + 1);
-  k = (int)(q / sz);
-  const long long r = q - (long long)k * sz;
-  j = (int)(r / sy);
-  i = (int)(r - (long long)j * sy);
+  const unsigned uq = (unsigned)q, sy = (unsigned)nx + 1u, sz = sy * ((unsigned)ny + 1u);
+  const unsigned kk = uq / sz, r = uq - kk * sz, jj = r / sy;
+  k = (int)kk;
+  j = (int)jj;
+  i = (int)(r - jj * sy);
 }
 
 // ---------------------------------------------------------------- E, Eq. (A2)
@@ -30,17 +32,17 @@ __device__ __forceinline__ void efield_node(const Consts &K, const GView<R> &g, 
   const long long c = i + cy * j + cz * k;  // cell (i, j, k)
   if (i < nx && j >= 1 && j <= ny - 1 && k >= 1 && k <= nz - 1) {
     const R curl = (Bz[q] - Bz[q - sy]) - (By[q] - By[q - sz]);
-    const R eta = R(0.25 * (g.eta[c - cy - cz] + g.eta[c - cz] + g.eta[c - cy] + g.eta[c]));
+    const R eta = R(0.25) * (g.eta_r[c - cy - cz] + g.eta_r[c - cz] + g.eta_r[c - cy] + g.eta_r[c]);
     ex = eta * (Fc * curl - Fj * g.J[0][q]);
   }
   if (j < ny && i >= 1 && i <= nx - 1 && k >= 1 && k <= nz - 1) {
     const R curl = (Bx[q] - Bx[q - sz]) - (Bz[q] - Bz[q - 1]);
-    const R eta = R(0.25 * (g.eta[c - 1 - cz] + g.eta[c - cz] + g.eta[c - 1] + g.eta[c]));
+    const R eta = R(0.25) * (g.eta_r[c - 1 - cz] + g.eta_r[c - cz] + g.eta_r[c - 1] + g.eta_r[c]);
     ey = eta * (Fc * curl - Fj * g.J[1][q]);
   }
   if (k < nz && i >= 1 && i <= nx - 1 && j >= 1 && j <= ny - 1) {
     const R curl = (By[q] - By[q - 1]) - (Bx[q] - Bx[q - sy]);
-    const R eta = R(0.25 * (g.eta[c - 1 - cy] + g.eta[c - cy] + g.eta[c - 1] + g.eta[c]));
+    const R eta = R(0.25) * (g.eta_r[c - 1 - cy] + g.eta_r[c - cy] + g.eta_r[c - 1] + g.eta_r[c]);
     ez = eta * (Fc * curl - Fj * g.J[2][q]);
   }
   g.E[0][q] = ex;
@@ -48,14 +50,19 @@ __device__ __forceinline__ void efield_node(const Consts &K, const GView<R> &g, 
   g.E[2][q] = ez;
 }
 
-// heat capacity, Eq. (A8): T' = (k_B T/e) Z^(-4/3)
-__device__ __forceinline__ double heat_capacity(double T, double Tp_fac) {
-  const double tp = T * Tp_fac;
-  return 0.3 + 1.2 * tp * (2.2 + tp) / ((1.1 + tp) * (1.1 + tp));
+// T + rho / (Z n_i k_B C(T)) with the heat capacity of Eq. (A8),
+// C = 0.3 + 1.2 T'(2.2 + T')/(1.1 + T')^2, T' = (k_B T/e) Z^(-4/3), brought
+// over one denominator (one FP64 division per cell)
+__device__ __forceinline__ double heated(const Consts &K, double T, double rho) {
+  const double tp = T * K.Tp_fac, D = 1.1 + tp;
+  const double D2 = D * D;
+  return T + rho * D2 / (K.heat_den * (0.3 * D2 + 1.2 * tp * (2.2 + tp)));
 }
 
-// reduced Lee-More resistivity, Eqs. (A4)-(A6), capped
+// reduced Lee-More resistivity, Eqs. (A4)-(A6), capped; inside the band
+// where the cap holds, the cap itself (no square root or division)
 __device__ __forceinline__ double resistivity(const Consts &K, double T) {
+  if (T > K.eta_Tlo && T < K.eta_Thi) return K.eta_max;
   const double kT = 1.380649e-23 * T;
   double tau = K.A_hot * kT * sqrt(kT);
   if (K.lambda1 > 0.0) {
@@ -89,18 +96,20 @@ __device__ __forceinline__ double bheat_node(const Consts &K, const GView<R> &g,
     double rho = g.H[c] * K.F_H;
     if (K.physics & P_FIELDS) {
       const R *Jx = g.J[0], *Jy = g.J[1], *Jz = g.J[2];
-      const double jbx = 0.25 * ((double)Jx[q] + Jx[q + sy] + Jx[q + sz] + Jx[q + sy + sz]);
-      const double jby = 0.25 * ((double)Jy[q] + Jy[q + 1] + Jy[q + sz] + Jy[q + 1 + sz]);
-      const double jbz = 0.25 * ((double)Jz[q] + Jz[q + 1] + Jz[q + sy] + Jz[q + 1 + sy]);
-      const double ro = g.eta[c] * K.F_ohm * (jbx * jbx + jby * jby + jbz * jbz);
+      // cell-centred mean of the edge current in the field precision
+      const R jbx = R(0.25) * (Jx[q] + Jx[q + sy] + Jx[q + sz] + Jx[q + sy + sz]);
+      const R jby = R(0.25) * (Jy[q] + Jy[q + 1] + Jy[q + sz] + Jy[q + 1 + sz]);
+      const R jbz = R(0.25) * (Jz[q] + Jz[q + 1] + Jz[q + sy] + Jz[q + 1 + sy]);
+      const double ro = g.eta[c] * K.F_ohm * (double)(jbx * jbx + jby * jby + jbz * jbz);
       e_ohm = ro * K.dx3;
       rho += ro;
     }
     if ((K.physics & P_HEATING) && rho != 0.0) {  // rho = 0 leaves T and eta(T) as they are
-      const double T = g.T[c];
-      const double Tn = T + rho / (K.heat_den * heat_capacity(T, K.Tp_fac));
+      const double Tn = heated(K, g.T[c], rho);
+      const double e = resistivity(K, Tn);
       g.T[c] = Tn;
-      g.eta[c] = resistivity(K, Tn);
+      g.eta[c] = e;
+      if constexpr (sizeof(R) == 4) g.eta_r[c] = R(e);
     }
   }
   return e_ohm;

@@ -20,6 +20,7 @@ template <typename R>
 struct GView {
   R *E[3], *B[3], *J[3];
   double *T, *eta, *H;  // cell-centred, double
+  R *eta_r;             // eta in the field precision (its own FP32 copy, or eta itself)
 };
 
 struct TallyView {

@@ -107,7 +107,14 @@ def test_autotune_leaves_state_unchanged():
     assert tune["ms_per_step"] > 0
     for t in range(3):
         tal, p = before[t]
-        assert a.target(t).tallies() == tal
+        now = a.target(t).tallies()
+        # E_live and E_B_field are summed at read time by atomic reductions
+        # (their rounding order varies between reads); the rest is stored state
+        for k in tal:
+            if k in ("E_live", "E_B_field"):
+                assert now[k] == pytest.approx(tal[k], rel=1e-12, abs=0.0), (t, k)
+            else:
+                assert now[k] == tal[k], (t, k)
         q = by_id(a.target(t).particles())
         for k in p:
             assert np.array_equal(p[k], q[k]), (t, k)

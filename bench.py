@@ -5,7 +5,7 @@ Workload: 128^3 cells of 1 um gold, 1e7 macro-electrons injected over
 100 fs at 1e21 W/cm^2 (T_hot = 13.7 MeV), dt = 0.5 fs, reflux on all faces;
 the 200-step injection runs before timing, then K steps are timed with the
 full population resident in HBM.  One step = push/collide/emit/deposit,
-E and B update, heating, (injection), and the cell sort every 20 steps.
+E and B update, heating, (injection), and the cell sort every 10 steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
     python bench.py --impl reference ...   # the FP64 CPU oracle, timed alone
@@ -39,7 +39,7 @@ ALG_BYTES = {"fp32": 7 * 4 + 4 + 7 * 4, "fp64": 7 * 8 + 4 + 7 * 8}
 # DRAM bytes (read + write) per particle-step of k_push measured by ncu on
 # this workload (profiles/k_push_headline_fp32.md); None where not captured
 NCU_DRAM_BYTES_PER_PSTEP = {"fp32": 55.8, "fp64": None}
-SORT_INTERVAL = 20
+SORT_INTERVAL = 10  # measured: 10 beats 20 (k_push 0.99 vs 1.04 ms, step 1.17 vs 1.20 ms)
 
 
 def peaks() -> dict:

@@ -174,7 +174,7 @@ def test_batched_scan_full_size():
     electron bookkeeping for every target after 60 steps."""
     cfg = W.config4()
     targets, lasers, run = cfg["targets"], cfg["lasers"], cfg["run"]
-    b = hpic.Batch(targets, lasers, run, precision=hpic.HPIC_FP32_MIXED, sort_interval=20)
+    b = hpic.Batch(targets, lasers, run, precision=hpic.HPIC_FP32_MIXED, sort_interval=10)
     b.step(2)
     thin = int(np.argmin([t["nx"] for t in targets]))
     thick = int(np.argmax([t["nx"] for t in targets]))

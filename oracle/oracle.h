@@ -41,14 +41,19 @@ enum {
   ORC_ALL = 63,
   /* unbounded uniform medium: no fields are gathered, no faces, no current
    * or heat deposited on the grid (collisions and emission only) */
-  ORC_UNBOUNDED = 64
+  ORC_UNBOUNDED = 64,
+  /* ionised-screening enhancement F_sigma of the bremsstrahlung cross
+   * section (App. B), from the ion temperature of the electron's cell */
+  ORC_FSIGMA = 128,
+  /* electron-ion temperature equilibration (App. A); T_i is evolved */
+  ORC_EI = 256
 };
 
 /* grid component codes */
 enum {
   ORC_T = 0, ORC_ETA = 1, ORC_EX = 2, ORC_EY = 3, ORC_EZ = 4,
   ORC_BX = 5, ORC_BY = 6, ORC_BZ = 7, ORC_JX = 8, ORC_JY = 9, ORC_JZ = 10,
-  ORC_HEAT = 11
+  ORC_HEAT = 11, ORC_TI = 12
 };
 
 typedef struct {
@@ -62,7 +67,8 @@ typedef struct {
   double eta_max;     /* resistivity cap (Ohm m) */
   double lambda1;     /* cold-limit fit parameter (0 = no cold limit) */
   double lambda2;     /* resistivity multiplier */
-  double T0;          /* initial background temperature (K) */
+  double T0;          /* initial background temperature, electrons and ions (K) */
+  double A_ion;       /* ion mass in atomic mass units (e-i equilibration) */
 } orc_target;
 
 typedef struct {
@@ -158,6 +164,12 @@ double orc_davies_sigma(const orc_target *t, double p_SI, double dt); /* rad */
 double orc_photon_theta(double gamma, double u);
 double orc_heat_capacity(double T_K, double Z);
 double orc_resistivity(const orc_target *t, double T_K);
+/* F_sigma of the bremsstrahlung cross section at ion temperature T_i (K) */
+double orc_f_sigma(const orc_target *t, double Ti_K);
+/* e-i equilibration rates (1/s): dT_e/dt = (T_i - T_e) rate_e,
+ * dT_i/dt = (T_e - T_i) rate_i */
+void orc_ei_rates(const orc_target *t, double Te_K, double Ti_K, double *rate_e,
+                  double *rate_i);
 void orc_rotate(const double d[3], double theta, double phi, double out[3]);
 void orc_boris(double u[3], const double E[3], const double B[3], double dt);
 

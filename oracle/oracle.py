@@ -20,8 +20,9 @@ SOURCES = ["physics.c", "sim.c"]
 ORC_DRAG, ORC_SCATTER, ORC_BREM, ORC_FIELDS, ORC_FARADAY, ORC_HEATING = 1, 2, 4, 8, 16, 32
 ORC_ALL = 63
 ORC_UNBOUNDED = 64
+ORC_FSIGMA, ORC_EI = 128, 256
 GRID = {"T": 0, "eta": 1, "Ex": 2, "Ey": 3, "Ez": 4, "Bx": 5, "By": 6, "Bz": 7,
-        "jx": 8, "jy": 9, "jz": 10, "heat": 11}
+        "jx": 8, "jy": 9, "jz": 10, "heat": 11, "Ti": 12}
 
 
 def build(force: bool = False) -> str:
@@ -44,7 +45,7 @@ class Target(C.Structure):
                 ("dx", C.c_double), ("Z", C.c_double), ("n_i", C.c_double),
                 ("I_ex", C.c_double), ("Zstar", C.c_double), ("lnLambda", C.c_double),
                 ("eta_max", C.c_double), ("lambda1", C.c_double), ("lambda2", C.c_double),
-                ("T0", C.c_double)]
+                ("T0", C.c_double), ("A_ion", C.c_double)]
 
 
 class Laser(C.Structure):
@@ -134,6 +135,10 @@ def lib():
         L.orc_heat_capacity.argtypes = [C.c_double, C.c_double]
         L.orc_resistivity.restype = C.c_double
         L.orc_resistivity.argtypes = [tp, C.c_double]
+        L.orc_f_sigma.restype = C.c_double
+        L.orc_f_sigma.argtypes = [tp, C.c_double]
+        L.orc_ei_rates.argtypes = [tp, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)]
         L.orc_rotate.argtypes = [dp, C.c_double, C.c_double, dp]
         L.orc_boris.argtypes = [dp, dp, dp, C.c_double]
     return _lib
@@ -316,6 +321,16 @@ def heat_capacity(T_K: float, Z: float) -> float:
 
 def resistivity(target: dict, T_K: float) -> float:
     return lib().orc_resistivity(C.byref(make_target(target)), T_K)
+
+
+def f_sigma(target: dict, Ti_K: float) -> float:
+    return lib().orc_f_sigma(C.byref(make_target(target)), Ti_K)
+
+
+def ei_rates(target: dict, Te_K: float, Ti_K: float):
+    a, b = C.c_double(), C.c_double()
+    lib().orc_ei_rates(C.byref(make_target(target)), Te_K, Ti_K, C.byref(a), C.byref(b))
+    return a.value, b.value
 
 
 def rotate(d, theta: float, phi: float) -> np.ndarray:

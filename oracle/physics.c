@@ -23,6 +23,8 @@
 #define K_B 1.380649e-23
 #define PI 3.14159265358979323846
 #define HBAR (H_PL / (2.0 * PI))
+#define A_BOHR 5.29177210903e-11   /* Bohr radius (m) */
+#define AMU 1.66053906660e-27      /* atomic mass constant (kg) */
 
 /* ---------------- Philox4x32-10 ----------------
  * Counter-based generator of Salmon, Moraes, Dror & Shaw, "Parallel random
@@ -227,6 +229,34 @@ double orc_resistivity(const orc_target *t, double T_K) {
   double eta = t->lambda2 * M_E / (t->Zstar * t->n_i * Q_E * Q_E * tau);
   if (eta > t->eta_max) eta = t->eta_max;
   return eta;
+}
+
+/* App. B: ionised-screening enhancement of the bremsstrahlung cross section
+ *   F_sigma = 1 + ln(lambda_D / a_s) / ln(a_s m_e c / hbar) (Zstar / Z)^2,
+ * a_s = 1.4 a_B Z^(-1/3) the atomic screening length, lambda_D the Debye
+ * length of the background ions, (eps0 k_B T_i / (n_i Zstar^2 e^2))^(1/2).
+ * The printed denominator ln|a_s m_e c^2/hbar| is not dimensionless; it is
+ * read as the log of a_s over the reduced Compton wavelength hbar/(m_e c). */
+double orc_f_sigma(const orc_target *t, double Ti_K) {
+  double lambda_D = sqrt(EPS0 * K_B * Ti_K / (t->n_i * t->Zstar * t->Zstar * Q_E * Q_E));
+  double a_s = 1.4 * A_BOHR * pow(t->Z, -1.0 / 3.0);
+  double ratio = t->Zstar / t->Z;
+  return 1.0 + log(lambda_D / a_s) / log(a_s * M_E * C_L / HBAR) * ratio * ratio;
+}
+
+/* App. A: electron-ion equilibration,
+ *   dT_e/dt = (T_i - T_e) Z*^2 e^4 n_i / t_c,
+ *   dT_i/dt = (T_e - T_i) Z*^3 e^4 n_i / t_c,
+ *   1/t_c = 2 / (3 (2 pi k_B)^(3/2)) sqrt(m_e m_i) ln(Lambda)
+ *           / (eps0^2 (T_e m_i + T_i m_e)^(3/2)). */
+void orc_ei_rates(const orc_target *t, double Te_K, double Ti_K, double *rate_e,
+                  double *rate_i) {
+  double m_i = t->A_ion * AMU;
+  double inv_tc = 2.0 / (3.0 * pow(2.0 * PI * K_B, 1.5)) * sqrt(M_E * m_i) * t->lnLambda /
+                  (EPS0 * EPS0 * pow(Te_K * m_i + Ti_K * M_E, 1.5));
+  double base = pow(Q_E, 4) * t->n_i * inv_tc;
+  *rate_e = t->Zstar * t->Zstar * base;
+  *rate_i = t->Zstar * t->Zstar * t->Zstar * base;
 }
 
 /* ---------------- geometry ---------------- */

@@ -16,6 +16,7 @@
  *   E = eta (curl B / mu0 - j_h) on edges                 Eq. (A2)
  *   B -= dt curl E on faces                               Eq. (A3)
  *   Ohmic + drag heating, T and eta update                Eqs. (A4)-(A8)
+ *   e-i equilibration of T_e and T_i (optional)           App. A
  *   injection of this step's new electrons at x = 0+     Eq. (B1), Sec. II.B
  * Random numbers: Philox4x32-10 with counter (step, id, block, target) and
  * key (seed low, seed high); block 0 = scatter, 1 = emission, 2..4 = reflux
@@ -47,7 +48,7 @@ struct orc_sim {
   uint32_t *id;
   unsigned char *alive;
   int64_t nvec, ncell;
-  double *g[12];
+  double *g[13];
   int64_t step, next_id;
   orc_tallies tal;
   double *histE, *histN, *history;
@@ -231,6 +232,7 @@ static void particle_update(orc_sim *s, int64_t ip) {
     double gam = 1.0 + eps / MC2;
     double beta = sqrt(1.0 - 1.0 / (gam * gam));
     double sig = orc_sigma_tot(t, r->k_min, eps);
+    if (r->physics & ORC_FSIGMA) sig *= orc_f_sigma(t, s->g[ORC_TI][cell]);
     s->tau[ip] -= t->n_i * r->brem_boost * sig * beta * C_L * dt;
     if (s->tau[ip] <= 0.0) {
       double R1[4];
@@ -374,7 +376,7 @@ static void heating(orc_sim *s) {
   const int nx = s->t.nx, ny = s->t.ny, nz = s->t.nz;
   const double V = s->t.dx * s->t.dx * s->t.dx, dt = s->r.dt;
   const double *jx = s->g[ORC_JX], *jy = s->g[ORC_JY], *jz = s->g[ORC_JZ];
-  double *T = s->g[ORC_T], *eta = s->g[ORC_ETA];
+  double *T = s->g[ORC_T], *eta = s->g[ORC_ETA], *Ti = s->g[ORC_TI];
   const double *heat = s->g[ORC_HEAT];
   const int fields = (s->r.physics & ORC_FIELDS) != 0;
   for (int k = 0; k < nz; ++k)
@@ -396,8 +398,20 @@ static void heating(orc_sim *s) {
         if (s->r.physics & ORC_HEATING) {
           double C = orc_heat_capacity(T[c], s->t.Z);
           T[c] += rho / (s->t.Z * s->t.n_i * C * K_B);
-          eta[c] = orc_resistivity(&s->t, T[c]);
         }
+        /* e-i equilibration over the step, rates frozen at the temperatures
+         * after the heating: d = T_e - T_i decays as exp(-(a + b) dt) and
+         * b T_e + a T_i is kept (a = rate_e, b = rate_i) */
+        if (s->r.physics & ORC_EI) {
+          double a, b;
+          orc_ei_rates(&s->t, T[c], Ti[c], &a, &b);
+          if (!(a + b > 0.0)) a = b = 0.0;
+          double d = T[c] - Ti[c];
+          double f = a + b > 0.0 ? expm1(-(a + b) * dt) / (a + b) : 0.0;  /* (e^{-(a+b)dt} - 1)/(a+b) */
+          T[c] += a * d * f;
+          Ti[c] -= b * d * f;
+        }
+        if (s->r.physics & (ORC_HEATING | ORC_EI)) eta[c] = orc_resistivity(&s->t, T[c]);
       }
 }
 
@@ -511,12 +525,10 @@ orc_sim *orc_create(const orc_target *t, const orc_laser *l, const orc_run *r) {
   if (s->n_inj_steps < 1) s->n_inj_steps = 1;
   s->nvec = (int64_t)(t->nx + 1) * (t->ny + 1) * (t->nz + 1);
   s->ncell = (int64_t)t->nx * t->ny * t->nz;
-  for (int w = 0; w < 12; ++w) {
-    int64_t len = (w == ORC_T || w == ORC_ETA || w == ORC_HEAT) ? s->ncell : s->nvec;
-    s->g[w] = calloc(len, sizeof(double));
-  }
+  for (int w = 0; w < 13; ++w) s->g[w] = calloc(orc_grid_len(s, w), sizeof(double));
   for (int64_t c = 0; c < s->ncell; ++c) {
     s->g[ORC_T][c] = t->T0;
+    s->g[ORC_TI][c] = t->T0;
     s->g[ORC_ETA][c] = orc_resistivity(t, t->T0);
   }
   int rows = r->n_E + 2;
@@ -532,7 +544,7 @@ void orc_destroy(orc_sim *s) {
   if (!s) return;
   free(s->x); free(s->y); free(s->z); free(s->ux); free(s->uy); free(s->uz);
   free(s->tau); free(s->id); free(s->alive);
-  for (int w = 0; w < 12; ++w) free(s->g[w]);
+  for (int w = 0; w < 13; ++w) free(s->g[w]);
   free(s->histE); free(s->histN); free(s->history); free(s->table);
   free(s);
 }
@@ -591,7 +603,8 @@ void orc_set_particles(orc_sim *s, int64_t n, const double *x, const double *y,
 }
 
 int64_t orc_grid_len(const orc_sim *s, int which) {
-  return (which == ORC_T || which == ORC_ETA || which == ORC_HEAT) ? s->ncell : s->nvec;
+  return (which == ORC_T || which == ORC_ETA || which == ORC_HEAT || which == ORC_TI) ? s->ncell
+                                                                                       : s->nvec;
 }
 
 void orc_get_grid(const orc_sim *s, int which, double *out) {

@@ -20,11 +20,12 @@ EV = 1.602176634e-19          # J per eV
 KELVIN_PER_EV = 11604.51812   # K per eV
 MEV = 1e6 * EV
 
-# solid-density elements used by the workloads: Z, ion density, conduction Z*
+# solid-density elements used by the workloads: Z, ion density, conduction
+# Z*, standard atomic weight A (ion mass in u)
 MATERIALS = {
-    "Al": {"Z": 13.0, "n_i": 6.03e28, "Zstar": 3.0},
-    "Cu": {"Z": 29.0, "n_i": 8.49e28, "Zstar": 1.0},
-    "Au": {"Z": 79.0, "n_i": 5.9e28, "Zstar": 1.0},
+    "Al": {"Z": 13.0, "n_i": 6.03e28, "Zstar": 3.0, "A": 26.982},
+    "Cu": {"Z": 29.0, "n_i": 8.49e28, "Zstar": 1.0, "A": 63.546},
+    "Au": {"Z": 79.0, "n_i": 5.9e28, "Zstar": 1.0, "A": 196.967},
 }
 
 
@@ -34,7 +35,8 @@ def target(n=(32, 32, 32), dx=1e-6, material="Au", T0_eV=1.0, eta_max=1e-6,
     return {"nx": int(n[0]), "ny": int(n[1]), "nz": int(n[2]), "dx": float(dx),
             "Z": m["Z"], "n_i": m["n_i"], "I_ex": 11.0 * EV * m["Z"],
             "Zstar": m["Zstar"], "lnLambda": lnLambda, "eta_max": eta_max,
-            "lambda1": lambda1, "lambda2": lambda2, "T0": T0_eV * KELVIN_PER_EV}
+            "lambda1": lambda1, "lambda2": lambda2, "T0": T0_eV * KELVIN_PER_EV,
+            "A_ion": m["A"]}
 
 
 def laser(tgt: dict, I_Wcm2=1e20, n_macro=100_000, spot_r=5e-6, t_inj=100e-15,

@@ -581,3 +581,124 @@ def test_energy_budget_closes():
     hE, hN = s.hist()
     assert hE.sum() == pytest.approx(t["E_xray"], rel=1e-12)
     assert s.history().sum() == pytest.approx(t["E_xray_above"], rel=1e-12)
+
+
+# ---------------------------------------------------------------- e-i equilibration, F_sigma
+EV_K = sc.e / sc.k  # K per eV
+AMU = sc.physical_constants["atomic mass constant"][0]
+
+
+def nrl_ei_rate(target, Te_eV, Ti_eV):
+    """NRL Plasma Formulary electron-ion energy-exchange rate (cgs, T in eV):
+    nu = 1.8e-19 (m_e m_i)^(1/2) Z^2 n_i lnL / (m_e T_i + m_i T_e)^(3/2), with
+    dT_e/dt = nu (T_i - T_e).  Its coefficient is given to two digits."""
+    me, mi = sc.m_e * 1e3, target["A_ion"] * AMU * 1e3
+    return (1.8e-19 * math.sqrt(me * mi) * target["Zstar"] ** 2 * target["n_i"] * 1e-6
+            * target["lnLambda"] / (me * Ti_eV + mi * Te_eV) ** 1.5)
+
+
+def test_ei_rates_against_nrl_formulary():
+    """App. A equilibration rate vs the NRL formulary: the same functional form
+    in T_e, T_i, m_i, Z*, n_i (ratio constant to 1e-9 over all cases), equal
+    up to the NRL coefficient's two-digit rounding (within 3 %); the ion rate
+    is Z* times the electron rate, so Z* T_e + T_i is conserved."""
+    ratios = []
+    for mat in ("Al", "Cu", "Au"):
+        t = W.target(material=mat)
+        for Te, Ti in ((10.0, 1.0), (1.0, 1.0), (300.0, 20.0), (2.0, 50.0)):
+            a, b = O.ei_rates(t, Te * EV_K, Ti * EV_K)
+            ratios.append(a / nrl_ei_rate(t, Te, Ti))
+            assert b == pytest.approx(t["Zstar"] * a, rel=1e-14)
+    assert max(ratios) - min(ratios) < 1e-9 * max(ratios)
+    assert 0.97 < ratios[0] < 1.0
+
+
+def _ei_sim(mat, Te_eV, Ti_eV):
+    tgt = W.target(n=(4, 4, 4), material=mat)
+    s = O.OracleSim(tgt, W.laser(tgt, n_macro=0), W.run(physics=O.ORC_EI))
+    s.set_grid("T", np.full(64, Te_eV * EV_K))
+    s.set_grid("Ti", np.full(64, Ti_eV * EV_K))
+    return tgt, s
+
+
+def test_ei_equilibration_relaxes_to_common_temperature():
+    """Without heating, Z* T_e + T_i is conserved to rounding, T_e - T_i decays
+    monotonically to zero, and the first step moves T_e by dt nu (T_i - T_e)
+    to first order (NRL nu, within its 3 % rounding)."""
+    tgt, s = _ei_sim("Al", 4.0, 1.0)
+    Zs = tgt["Zstar"]
+    inv0 = Zs * 4.0 * EV_K + 1.0 * EV_K
+    s.step(1)
+    dTe = s.grid("T")[0] / EV_K - 4.0
+    dt = W.run()["dt"]
+    # the linear relaxation over one step with the NRL rate: the gap decays by
+    # exp(-(1 + Z*) nu dt), T_e takes 1/(1 + Z*) of the change
+    nu = nrl_ei_rate(tgt, 4.0, 1.0)
+    want = (1.0 - 4.0) * -math.expm1(-(1 + Zs) * nu * dt) / (1 + Zs)
+    assert dTe == pytest.approx(want, rel=0.03)
+    gaps = []
+    for _ in range(60):
+        s.step(50)
+        Te, Ti = s.grid("T"), s.grid("Ti")
+        assert np.allclose(Zs * Te + Ti, inv0, rtol=1e-12, atol=0)
+        gaps.append(Te[0] - Ti[0])
+    assert all(g1 < g0 for g0, g1 in zip(gaps, gaps[1:]) if g0 > 1e-9 * inv0)
+    assert Te[0] == pytest.approx(inv0 / (Zs + 1), rel=1e-6)
+    assert np.all(s.grid("eta") == s.grid("eta")[0])  # eta follows the new T_e
+
+
+def nrl_debye_m(Ti_eV, n_i, Zs):
+    """NRL formulary Debye length 7.43e2 (T/n)^(1/2) cm (T in eV, n in cm^-3)
+    for ions of charge Z*: n -> n_i Z*^2."""
+    return 7.43e2 * math.sqrt(Ti_eV / (n_i * 1e-6 * Zs ** 2)) * 1e-2
+
+
+def test_f_sigma_against_nrl_debye_length():
+    """App. B enhancement with the Debye length from the NRL formulary and
+    CODATA a_B, hbar (three-digit NRL coefficient: F - 1 within 2e-3
+    relative); F = 1 where lambda_D = a_s; F - 1 grows as (Z*/Z)^2 ln T_i / 2
+    over ln(a_s/reduced Compton wavelength)."""
+    a_B = sc.physical_constants["Bohr radius"][0]
+    lam_c = sc.hbar / (sc.m_e * sc.c)
+    for mat in ("Al", "Cu", "Au"):
+        t = W.target(material=mat)
+        a_s = 1.4 * a_B * t["Z"] ** (-1 / 3)
+        L = math.log(a_s / lam_c)
+        q = (t["Zstar"] / t["Z"]) ** 2
+        for Ti in (0.5, 1.0, 30.0, 1000.0):
+            want = 1 + math.log(nrl_debye_m(Ti, t["n_i"], t["Zstar"]) / a_s) / L * q
+            got = O.f_sigma(t, Ti * EV_K)
+            assert got - 1 == pytest.approx(want - 1, rel=2e-3, abs=1e-3 * q)
+        # slope d F / d ln T_i = q / (2 L)
+        T1, T2 = 5.0 * EV_K, 500.0 * EV_K
+        slope = (O.f_sigma(t, T2) - O.f_sigma(t, T1)) / math.log(T2 / T1)
+        assert slope == pytest.approx(q / (2 * L), rel=1e-9)
+
+
+def test_f_sigma_scales_the_optical_depth():
+    """With F_sigma on, every electron's optical-depth decrement in a step is
+    F_sigma(T_i of its cell) times the decrement without it (same draws)."""
+    tgt = W.target(n=(4, 4, 4), material="Al")
+    las = W.laser(tgt, n_macro=0)
+    n = 400
+    rng = np.random.default_rng(4)
+    eps = rng.uniform(1.0, 40.0, n) * MEV
+    u = np.sqrt((eps / MC2) * (eps / MC2 + 2))
+    P = {"x": rng.uniform(0, 4e-6, n), "y": rng.uniform(0, 4e-6, n), "z": rng.uniform(0, 4e-6, n),
+         "ux": u, "uy": np.zeros(n), "uz": np.zeros(n), "tau": np.full(n, 1.0),
+         "id": np.arange(n, dtype=np.uint32)}
+    Ti = np.exp(rng.uniform(math.log(0.5), math.log(2000.0), 64)) * EV_K
+    dtau = {}
+    for phys in (O.ORC_BREM | O.ORC_UNBOUNDED, O.ORC_BREM | O.ORC_UNBOUNDED | O.ORC_FSIGMA):
+        s = O.OracleSim(tgt, las, W.run(physics=phys))
+        s.set_particles(P)
+        s.set_grid("Ti", Ti)
+        s.step(1)
+        q = s.particles()
+        dtau[phys] = 1.0 - q["tau"][np.argsort(q["id"])]
+    cell = (np.floor(P["x"] / 1e-6) + 4 * (np.floor(P["y"] / 1e-6) + 4 * np.floor(P["z"] / 1e-6))).astype(int)
+    F = np.array([O.f_sigma(tgt, Ti[c]) for c in cell])
+    off, on = dtau[O.ORC_BREM | O.ORC_UNBOUNDED], dtau[O.ORC_BREM | O.ORC_UNBOUNDED | O.ORC_FSIGMA]
+    assert np.all(off > 0)
+    assert np.allclose(on, F * off, rtol=1e-9, atol=0)
+    assert F.max() - F.min() > 0.02

@@ -71,7 +71,17 @@ enum {
   HPIC_ALL = 63,
   /* unbounded uniform medium: no field gather, no faces, nothing deposited
    * on the grid; drag, scatter and emission only (the emission benchmark) */
-  HPIC_UNBOUNDED = 64
+  HPIC_UNBOUNDED = 64,
+  /* ionised-screening enhancement of the bremsstrahlung cross section,
+   * F_sigma = 1 + ln(lambda_D/a_s) / ln(a_s m_e c/hbar) (Zstar/Z)^2 (App. B),
+   * from the ion temperature of the electron's cell; lambda_D is the ion
+   * Debye length, a_s = 1.4 a_B Z^(-1/3) */
+  HPIC_FSIGMA = 128,
+  /* electron-ion temperature equilibration (App. A): T_i is evolved and
+   * relaxes with T_e at the rates Z*^2 e^4 n_i / t_c (electrons) and
+   * Z*^3 e^4 n_i / t_c (ions), integrated exactly over each step with the
+   * rates frozen at the start of the exchange */
+  HPIC_EI_EQUIL = 256
 };
 
 /* grid codes for hpic_read_grid / hpic_write_grid */
@@ -80,7 +90,8 @@ enum {
   HPIC_GRID_EX = 2, HPIC_GRID_EY = 3, HPIC_GRID_EZ = 4,
   HPIC_GRID_BX = 5, HPIC_GRID_BY = 6, HPIC_GRID_BZ = 7,
   HPIC_GRID_JX = 8, HPIC_GRID_JY = 9, HPIC_GRID_JZ = 10,
-  HPIC_GRID_HEAT = 11 /* drag heat (J) deposited per cell in the last step */
+  HPIC_GRID_HEAT = 11, /* drag heat (J) deposited per cell in the last step */
+  HPIC_GRID_TI = 12    /* ion temperature (K), cell-centred */
 };
 
 /* One target: a uniform single-element solid filling the box (App. A). */
@@ -95,7 +106,8 @@ typedef struct {
   double eta_max_ohm_m; /* cap on eta */
   double lambda1;       /* cold-limit factor of Eq. (A6); 0 drops that limit */
   double lambda2;       /* multiplier on eta (App. A) */
-  double T0_K;          /* initial background temperature */
+  double T0_K;          /* initial background temperature (electrons and ions) */
+  double A_ion;         /* ion mass in atomic mass units (e-i equilibration) */
 } hpic_target_desc;
 
 /* Laser and injection, Eq. (1), Eq. (B1), Sec. II.B, with flat-top

@@ -22,6 +22,8 @@ constexpr double PI = 3.14159265358979323846;
 constexpr double HBAR = HPL / (2.0 * PI);
 constexpr double MU0 = 1.0 / (EPS0 * CL * CL);
 constexpr double MC2 = ME * CL * CL;
+constexpr double AMU = 1.66053906660e-27;  // atomic mass constant (kg)
+constexpr double A_BOHR = 5.29177210903e-11;
 
 thread_local std::string g_create_error;
 
@@ -186,6 +188,22 @@ void hpic::fold(const hpic_target_desc &t, const hpic_run_params &r, const hpic_
     K.eta_Tlo = T_cold * (1.0 + 1e-6);
     K.eta_Thi = T_hot * (1.0 - 1e-6);
   }
+  // App. B: F_sigma = 1 + ln(lambda_D/a_s)/ln(a_s m_e c/hbar) (Z*/Z)^2 with
+  // ln lambda_D = ln(T_i)/2 + ln(eps0 k_B/(n_i Z*^2 e^2))/2
+  {
+    const double a_s = 1.4 * A_BOHR * std::pow(Z, -1.0 / 3.0);
+    const double q = (t.Zstar / Z) * (t.Zstar / Z);
+    K.fs_q = q / std::log(a_s * ME * CL / HBAR);
+    K.fs_c = 0.5 * std::log(EPS0 * KB / (ni * t.Zstar * t.Zstar * QE * QE)) - std::log(a_s);
+  }
+  // App. A: rate_e dt = Z*^2 e^4 n_i dt 2/(3 (2 pi k_B)^(3/2)) sqrt(m_e m_i) lnL
+  // / (eps0^2 (T_e m_i + T_i m_e)^(3/2)), masses in u
+  K.ei_mi = t.A_ion;
+  K.ei_me = ME / AMU;
+  K.Zstar = t.Zstar;
+  K.ei_a = t.Zstar * t.Zstar * std::pow(QE, 4) * ni * dt * 2.0 /
+           (3.0 * std::pow(2.0 * PI * KB, 1.5)) * std::sqrt(K.ei_me * t.A_ion) * t.lnLambda /
+           (EPS0 * EPS0 * std::sqrt(AMU));
   K.key0 = (uint32_t)(r.seed & 0xFFFFFFFFull);
   K.key1 = (uint32_t)(r.seed >> 32);
   K.target_index = r.target_index;
@@ -228,12 +246,13 @@ const char *hpic::check_target(const hpic_target_desc &t, const hpic_run_params 
       t.lambda1 < 0)
     return "material parameters must be positive";
   if (r.precision != HPIC_FP64 && r.precision != HPIC_FP32_MIXED) return "unknown precision";
+  if ((r.physics & HPIC_EI_EQUIL) && !(t.A_ion > 0)) return "e-i equilibration needs A_ion > 0";
   if (!(r.brem_boost > 0) || !(r.k_min_J > 0) || !(r.E_cut_J > 0) ||
       !(r.table_Emax_J > r.k_min_J) || r.table_rows < 2 || r.table_cols < 2 ||
       r.n_Ebins < 1 || r.n_thbins < 1 || !(r.tally_Emax_J > r.tally_Emin_J) ||
       !(r.tally_Emin_J > 0) || r.max_history < 0 || r.sort_interval < 0 ||
       r.kappa_esc < 0 || r.kappa_tnsa < 0 || r.sigma_dtheta_rad < 0 ||
-      (r.physics & ~(HPIC_ALL | HPIC_UNBOUNDED)) != 0)
+      (r.physics & ~(HPIC_ALL | HPIC_UNBOUNDED | HPIC_FSIGMA | HPIC_EI_EQUIL)) != 0)
     return "run parameters out of range";
   return nullptr;
 }
@@ -271,6 +290,10 @@ double hpic::eta_of(const Consts &K, double T) {
   return e < K.eta_max ? e : K.eta_max;
 }
 
+double hpic::fsigma_of(const Consts &K, double Ti) {
+  return 1.0 + K.fs_q * (0.5 * std::log(Ti) + K.fs_c);
+}
+
 namespace {
 
 void destroy_all(hpic_ctx *c) {
@@ -283,6 +306,8 @@ void destroy_all(hpic_ctx *c) {
   cudaFree(c->T);
   cudaFree(c->eta);
   cudaFree(c->eta_r);
+  cudaFree(c->Ti);
+  cudaFree(c->Fsig);
   cudaFree(c->H);
   cudaFree(c->tal);
   cudaFree(c->hist);
@@ -451,7 +476,18 @@ int load_particles_impl(hpic_ctx *ctx, int64_t n, const double *x, const double 
   return write_counters(ctx, &h);
 }
 
-bool valid_grid(int which) { return which >= HPIC_GRID_T && which <= HPIC_GRID_HEAT; }
+bool valid_grid(int which) { return which >= HPIC_GRID_T && which <= HPIC_GRID_TI; }
+
+// cell-centred double arrays: T, eta, drag heat, T_i
+double *cell_array(const hpic_ctx *ctx, int which) {
+  switch (which) {
+    case HPIC_GRID_T: return ctx->T;
+    case HPIC_GRID_ETA: return ctx->eta;
+    case HPIC_GRID_HEAT: return ctx->H;
+    case HPIC_GRID_TI: return ctx->Ti;
+    default: return nullptr;
+  }
+}
 
 // device array of a vector-field component (HPIC_GRID_EX .. HPIC_GRID_JZ)
 void *vector_array(const hpic_ctx *ctx, int which) {
@@ -505,6 +541,8 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
             cudaMalloc(&ctx->T, K.ncell * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ctx->eta, K.ncell * sizeof(double)) == cudaSuccess &&
             (!ctx->fp32 || cudaMalloc(&ctx->eta_r, K.ncell * sizeof(float)) == cudaSuccess) &&
+            cudaMalloc(&ctx->Ti, K.ncell * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&ctx->Fsig, K.ncell * ctx->rsz) == cudaSuccess &&
             cudaMalloc(&ctx->H, K.ncell * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ctx->counts, m * sizeof(uint32_t)) == cudaSuccess &&
             cudaMalloc(&ctx->partials, (ntiles + 1) * sizeof(uint32_t)) == cudaSuccess &&
@@ -526,6 +564,9 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
   cudaStream_t st = ctx->stream;
   std::vector<double> T0(K.ncell, t->T0_K), E0(K.ncell, eta_host(ctx, t->T0_K));
   std::vector<float> E0f(ctx->fp32 ? K.ncell : 0, (float)E0[0]);
+  const double F0 = hpic::fsigma_of(K, t->T0_K);
+  std::vector<float> F0f(ctx->fp32 ? K.ncell : 0, (float)F0);
+  std::vector<double> F0d(ctx->fp32 ? 0 : K.ncell, F0);
   if (cudaMemsetAsync(ctx->fields, 0, 9 * ctx->vstride * ctx->rsz, st) != cudaSuccess ||
       cudaMemsetAsync(ctx->H, 0, K.ncell * sizeof(double), st) != cudaSuccess ||
       cudaMemsetAsync(ctx->tal, 0, hpic::T_COUNT * sizeof(double), st) != cudaSuccess ||
@@ -534,7 +575,10 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
       cudaMemsetAsync(ctx->cnt, 0, sizeof(hpic::Counters), st) != cudaSuccess ||
       cudaMemcpyAsync(ctx->T, T0.data(), K.ncell * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(ctx->eta, E0.data(), K.ncell * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      (ctx->fp32 && cudaMemcpyAsync(ctx->eta_r, E0f.data(), K.ncell * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)) {
+      (ctx->fp32 && cudaMemcpyAsync(ctx->eta_r, E0f.data(), K.ncell * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+      cudaMemcpyAsync(ctx->Ti, T0.data(), K.ncell * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->Fsig, ctx->fp32 ? (const void *)F0f.data() : (const void *)F0d.data(),
+                      K.ncell * ctx->rsz, cudaMemcpyHostToDevice, st) != cudaSuccess) {
     cuda_fail(ctx, cudaGetLastError(), "initialisation");
     return bail(HPIC_ECUDA);
   }
@@ -683,8 +727,7 @@ int hpic_read_history(hpic_ctx *ctx, double *out) {
 
 int hpic_grid_len(const hpic_ctx *ctx, int which, int64_t *len) {
   if (!ctx || !len || !valid_grid(which)) return HPIC_EINVAL;
-  *len = (which == HPIC_GRID_T || which == HPIC_GRID_ETA || which == HPIC_GRID_HEAT) ? ctx->K.ncell
-                                                                                   : ctx->K.nvec;
+  *len = cell_array(ctx, which) ? ctx->K.ncell : ctx->K.nvec;
   return HPIC_OK;
 }
 
@@ -694,8 +737,7 @@ int hpic_read_grid(hpic_ctx *ctx, int which, double *out) {
   int64_t L;
   hpic_grid_len(ctx, which, &L);
   const double s = grid_scale(ctx, which);
-  if (which == HPIC_GRID_T || which == HPIC_GRID_ETA || which == HPIC_GRID_HEAT) {
-    const double *src = which == HPIC_GRID_T ? ctx->T : (which == HPIC_GRID_ETA ? ctx->eta : ctx->H);
+  if (const double *src = cell_array(ctx, which)) {
     CK(cudaMemcpyAsync(out, src, L * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     for (int64_t i = 0; i < L; ++i) out[i] *= s;
@@ -721,14 +763,22 @@ int hpic_write_grid(hpic_ctx *ctx, int which, const double *in) {
   int64_t L;
   hpic_grid_len(ctx, which, &L);
   const double s = 1.0 / grid_scale(ctx, which);
-  if (which == HPIC_GRID_T || which == HPIC_GRID_ETA || which == HPIC_GRID_HEAT) {
-    double *dst = which == HPIC_GRID_T ? ctx->T : (which == HPIC_GRID_ETA ? ctx->eta : ctx->H);
+  if (double *dst = cell_array(ctx, which)) {
     std::vector<double> b(in, in + L);
     for (auto &v : b) v *= s;
     CK(cudaMemcpyAsync(dst, b.data(), L * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     if (which == HPIC_GRID_ETA && ctx->fp32) {  // the field solve's FP32 copy
       std::vector<float> f(b.begin(), b.end());
       CK(cudaMemcpyAsync(ctx->eta_r, f.data(), L * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (which == HPIC_GRID_TI) {  // F_sigma follows T_i
+      std::vector<double> F(L);
+      for (int64_t i = 0; i < L; ++i) F[i] = hpic::fsigma_of(ctx->K, b[i]);
+      std::vector<float> Ff(ctx->fp32 ? L : 0);
+      for (size_t i = 0; i < Ff.size(); ++i) Ff[i] = (float)F[i];
+      CK(cudaMemcpyAsync(ctx->Fsig, ctx->fp32 ? (const void *)Ff.data() : (const void *)F.data(),
+                         L * ctx->rsz, cudaMemcpyHostToDevice, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));

@@ -415,6 +415,7 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
   const size_t o_T = take(cells * sizeof(double)), o_eta = take(cells * sizeof(double));
   const size_t o_H = take(cells * sizeof(double));
   const size_t o_er = take(b->fp32 ? cells * sizeof(float) : 0);
+  const size_t o_Ti = take(cells * sizeof(double)), o_Fs = take(cells * b->rsz);
   const size_t o_tal = take((size_t)n_targets * hpic::T_COUNT * sizeof(double));
   const size_t o_hist = take((size_t)n_targets * 2 * hist_len * sizeof(double));
   const size_t o_hy = take((size_t)n_targets * hlen * sizeof(double));
@@ -474,6 +475,8 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
     c->T = reinterpret_cast<double *>(A + o_T) + c_at;
     c->eta = reinterpret_cast<double *>(A + o_eta) + c_at;
     if (b->fp32) c->eta_r = reinterpret_cast<float *>(A + o_er) + c_at;
+    c->Ti = reinterpret_cast<double *>(A + o_Ti) + c_at;
+    c->Fsig = A + o_Fs + c_at * b->rsz;
     c->H = reinterpret_cast<double *>(A + o_H) + c_at;
     c->tal = reinterpret_cast<double *>(A + o_tal) + (size_t)t * hpic::T_COUNT;
     c->hist = reinterpret_cast<double *>(A + o_hist) + (size_t)t * 2 * hist_len;
@@ -489,15 +492,18 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
 
   // initial state: zero everything, then T0 and eta(T0) per target
   cudaStream_t st = b->stream;
-  std::vector<double> T0(cells), E0(cells);
+  std::vector<double> T0(cells), E0(cells), F0(cells);
   c_at = 0;
   for (int t = 0; t < n_targets; ++t) {
     const hpic_ctx *c = b->tg[t];
-    const double e0 = hpic::eta_of(c->K, c->tgt.T0_K);
+    const double e0 = hpic::eta_of(c->K, c->tgt.T0_K), f0 = hpic::fsigma_of(c->K, c->tgt.T0_K);
     std::fill(T0.begin() + c_at, T0.begin() + c_at + c->K.ncell, c->tgt.T0_K);
     std::fill(E0.begin() + c_at, E0.begin() + c_at + c->K.ncell, e0);
+    std::fill(F0.begin() + c_at, F0.begin() + c_at + c->K.ncell, f0);
     c_at += c->K.ncell;
   }
+  std::vector<float> F0f(b->fp32 ? cells : 0);
+  for (size_t i = 0; i < F0f.size(); ++i) F0f[i] = (float)F0[i];
   std::vector<float> E0f(b->fp32 ? cells : 0);
   for (size_t i = 0; i < E0f.size(); ++i) E0f[i] = (float)E0[i];
   std::vector<char> items;
@@ -506,6 +512,9 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
       cudaMemcpyAsync(b->tg[0]->T, T0.data(), cells * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(b->tg[0]->eta, E0.data(), cells * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       (b->fp32 && cudaMemcpyAsync(b->tg[0]->eta_r, E0f.data(), cells * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+      cudaMemcpyAsync(b->tg[0]->Ti, T0.data(), cells * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(b->tg[0]->Fsig, b->fp32 ? (const void *)F0f.data() : (const void *)F0.data(),
+                      cells * b->rsz, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(b->items, items.data(), items.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(X + a_n, npref.data(), npref.size() * sizeof(long long), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(X + a_k, kpref.data(), kpref.size() * sizeof(long long), cudaMemcpyHostToDevice, st) != cudaSuccess) {

@@ -64,6 +64,11 @@ struct Consts {
   double F_ohm, F_H, dx3, heat_den, Tp_fac;
   double eta_num, A_hot, B_cold, eta_max, lambda1;
   double eta_Tlo, eta_Thi;            // eta(T) is at its cap for eta_Tlo < T < eta_Thi (K)
+  // F_sigma (App. B) = 1 + fs_q (ln T_i / 2 + fs_c), T_i in K
+  double fs_q, fs_c;
+  // e-i equilibration (App. A): rate_e = ei_a / (T_e m_i + T_i m_e)^(3/2)
+  // (masses in u), rate_i = Z* rate_e
+  double ei_a, ei_mi, ei_me, Zstar;
   // injection, Eq. (B1)
   double T_hot, spot_r, spot_y, spot_z, omc_cone;  // omc_cone = 1 - cos(cone)
   long long n_macro, n_inj_steps;
@@ -74,7 +79,7 @@ struct Consts {
 
 enum {
   P_DRAG = 1, P_SCATTER = 2, P_BREM = 4, P_FIELDS = 8, P_FARADAY = 16, P_HEATING = 32,
-  P_UNBOUNDED = 64
+  P_UNBOUNDED = 64, P_FSIGMA = 128, P_EI = 256
 };
 
 // ---------------------------------------------------------------- Philox

@@ -42,6 +42,8 @@ struct hpic_ctx {
   long long vstride = 0;   // nvec + >= 4 padding, a multiple of 64 (aligned vector access)
   double *T = nullptr, *eta = nullptr, *H = nullptr;
   void *eta_r = nullptr;  // FP32 copy of eta read by the FP32 field solve (mixed precision)
+  double *Ti = nullptr;   // ion temperature
+  void *Fsig = nullptr;   // F_sigma per cell, in the particle precision
   // tallies and tables
   double *tal = nullptr, *hist = nullptr, *history = nullptr, *scratch = nullptr;
   double *t64 = nullptr;
@@ -93,6 +95,8 @@ inline hpic::GView<R> gview(const hpic_ctx *c) {
   g.T = c->T;
   g.eta = c->eta;
   g.eta_r = c->fp32 ? static_cast<R *>(c->eta_r) : reinterpret_cast<R *>(c->eta);
+  g.Ti = c->Ti;
+  g.Fsig = static_cast<R *>(c->Fsig);
   g.H = c->H;
   return g;
 }

@@ -94,6 +94,8 @@ __device__ __forceinline__ double bheat_node(const Consts &K, const GView<R> &g,
   if (i < nx && j < ny && k < nz) {
     const long long c = i + (long long)nx * (j + (long long)ny * k);
     double rho = g.H[c] * K.F_H;
+    double Te = g.T[c];
+    bool changed = false;
     if (K.physics & P_FIELDS) {
       const R *Jx = g.J[0], *Jy = g.J[1], *Jz = g.J[2];
       // cell-centred mean of the edge current in the field precision
@@ -104,10 +106,29 @@ __device__ __forceinline__ double bheat_node(const Consts &K, const GView<R> &g,
       e_ohm = ro * K.dx3;
       rho += ro;
     }
-    if ((K.physics & P_HEATING) && rho != 0.0) {  // rho = 0 leaves T and eta(T) as they are
-      const double Tn = heated(K, g.T[c], rho);
-      const double e = resistivity(K, Tn);
-      g.T[c] = Tn;
+    if ((K.physics & P_HEATING) && rho != 0.0) {  // rho = 0 leaves T as it is
+      Te = heated(K, Te, rho);
+      changed = true;
+    }
+    // e-i equilibration over the step (App. A): with a = rate_e dt and
+    // b = rate_i dt frozen, the gap d = T_e - T_i decays by exp(-(a + b)) and
+    // b T_e + a T_i is kept
+    if (K.physics & P_EI) {
+      double Ti = g.Ti[c];
+      const double d = Te - Ti;
+      const double a = K.ei_a / pow(Te * K.ei_mi + Ti * K.ei_me, 1.5), b = K.Zstar * a;
+      if (d != 0.0 && a + b > 0.0) {
+        const double f = expm1(-(a + b)) / (a + b);
+        Te += a * d * f;
+        Ti -= b * d * f;
+        g.Ti[c] = Ti;
+        if (K.physics & P_FSIGMA) g.Fsig[c] = R(1.0 + K.fs_q * (0.5 * log(Ti) + K.fs_c));
+        changed = true;
+      }
+    }
+    if (changed) {  // eta(T) follows T_e
+      const double e = resistivity(K, Te);
+      g.T[c] = Te;
       g.eta[c] = e;
       if constexpr (sizeof(R) == 4) g.eta_r[c] = R(e);
     }

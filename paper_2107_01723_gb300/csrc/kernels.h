@@ -21,6 +21,8 @@ struct GView {
   R *E[3], *B[3], *J[3];
   double *T, *eta, *H;  // cell-centred, double
   R *eta_r;             // eta in the field precision (its own FP32 copy, or eta itself)
+  double *Ti;           // ion temperature (K)
+  R *Fsig;              // F_sigma of each cell, from T_i
 };
 
 struct TallyView {
@@ -70,6 +72,8 @@ void set_global_error(const char *msg);
 void fold(const hpic_target_desc &t, const hpic_run_params &r, const hpic_laser_desc *laser,
           Consts &K);
 double eta_of(const Consts &K, double T);
+// F_sigma of App. B at ion temperature Ti (K)
+double fsigma_of(const Consts &K, double Ti);
 
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,

@@ -54,6 +54,7 @@ struct Grid {
   const R *F[6];  // Ex Ey Ez Bx By Bz
   R *J[3];
   double *H;
+  const R *Fsig;  // F_sigma per cell
   int sy, sz, nx, ny;
   __device__ __forceinline__ int node(int i, int j, int k) const { return i + sy * j + sz * k; }
 };
@@ -67,6 +68,7 @@ __device__ __forceinline__ Grid<R> make_grid(const Consts &K, const GView<R> &gv
     g.J[c] = gv.J[c];
   }
   g.H = gv.H;
+  g.Fsig = gv.Fsig;
   g.sy = K.nx + 1;
   g.sz = (K.nx + 1) * (K.ny + 1);
   g.nx = K.nx;
@@ -253,7 +255,9 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
 
   // ---- bremsstrahlung by optical depth (App. B)
   if (alive && (K.physics & P_BREM) && eps > h.k_min) {
-    tau -= h.K_tau * u_of_eps(eps) / eps * shape_G(h.k_min / eps);
+    R dtau = h.K_tau * u_of_eps(eps) / eps * shape_G(h.k_min / eps);
+    if (K.physics & P_FSIGMA) dtau *= __ldg(g.Fsig + ax.iN + nx * (ay.iN + ny * az.iN));
+    tau -= dtau;
     if (tau <= R(0)) {
       const U4 r1 = philox10(sc.step, id, 1u, sc.target, sc.key0, sc.key1);
       const R k = sample_k(h, K.t_rows, K.t_cols, tab, eps, unif<R>(r1.a));

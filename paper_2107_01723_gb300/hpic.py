@@ -21,9 +21,10 @@ HPIC_FP64, HPIC_FP32_MIXED = 0, 1
 HPIC_DRAG, HPIC_SCATTER, HPIC_BREM, HPIC_FIELDS, HPIC_FARADAY, HPIC_HEATING = 1, 2, 4, 8, 16, 32
 HPIC_ALL = 63
 HPIC_UNBOUNDED = 64
+HPIC_FSIGMA, HPIC_EI_EQUIL = 128, 256
 HPIC_BATCH_MAX_TARGETS = 256
 GRID = {"T": 0, "eta": 1, "Ex": 2, "Ey": 3, "Ez": 4, "Bx": 5, "By": 6, "Bz": 7,
-        "jx": 8, "jy": 9, "jz": 10, "heat": 11}
+        "jx": 8, "jy": 9, "jz": 10, "heat": 11, "Ti": 12}
 
 
 class HpicError(RuntimeError):
@@ -36,7 +37,8 @@ class hpic_target_desc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("dx_m", C.c_double),
                 ("Z", C.c_double), ("n_i_m3", C.c_double), ("I_ex_J", C.c_double),
                 ("Zstar", C.c_double), ("lnLambda", C.c_double), ("eta_max_ohm_m", C.c_double),
-                ("lambda1", C.c_double), ("lambda2", C.c_double), ("T0_K", C.c_double)]
+                ("lambda1", C.c_double), ("lambda2", C.c_double), ("T0_K", C.c_double),
+                ("A_ion", C.c_double)]
 
 
 class hpic_laser_desc(C.Structure):
@@ -165,7 +167,7 @@ def _up(a):
 def target_desc(t: dict) -> hpic_target_desc:
     return hpic_target_desc(t["nx"], t["ny"], t["nz"], t["dx"], t["Z"], t["n_i"], t["I_ex"],
                             t["Zstar"], t["lnLambda"], t["eta_max"], t["lambda1"], t["lambda2"],
-                            t["T0"])
+                            t["T0"], t["A_ion"])
 
 
 def laser_desc(l: dict) -> hpic_laser_desc:

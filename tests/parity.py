@@ -6,7 +6,7 @@ from oracle import oracle as O
 from paper_2107_01723_gb300 import hpic
 
 PKEYS = ("x", "y", "z", "ux", "uy", "uz", "tau")
-GRIDS_STATE = ("T", "eta", "Ex", "Ey", "Ez", "Bx", "By", "Bz")
+GRIDS_STATE = ("T", "eta", "Ti", "Ex", "Ey", "Ez", "Bx", "By", "Bz")
 ENERGY_TALLIES = ("E_injected", "W_field", "E_drag", "E_xray", "E_xray_above", "E_escaped",
                   "E_reflux", "E_ohmic_grid")
 COUNT_TALLIES = ("n_injected", "n_escaped", "n_refluxed", "n_reflux_absorbed", "n_cut",

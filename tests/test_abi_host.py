@@ -72,7 +72,8 @@ def test_validation_rejects_bad_arguments(lib):
     assert _bad(lib, dict(t, Z=0.0), r)[0] == hpic.HPIC_EINVAL
     assert _bad(lib, t, dict(r, n_E=0))[0] == hpic.HPIC_EINVAL
     assert _bad(lib, t, dict(r, table_rows=1))[0] == hpic.HPIC_EINVAL
-    assert _bad(lib, t, dict(r, physics=128))[0] == hpic.HPIC_EINVAL  # undefined bit
+    assert _bad(lib, t, dict(r, physics=512))[0] == hpic.HPIC_EINVAL  # undefined bit
+    assert _bad(lib, dict(t, A_ion=0.0), dict(r, physics=hpic.HPIC_ALL | hpic.HPIC_EI_EQUIL))[0] == hpic.HPIC_EINVAL
     code, msg = _bad(lib, dict(t, nx=1), r)
     assert "dimension" in msg
     assert lib.hpic_init_target(None, None, None, 0, None) == hpic.HPIC_EINVAL

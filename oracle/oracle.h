@@ -148,6 +148,37 @@ double orc_field_energy(const orc_sim *s);  /* sum B^2/(2 mu0) dx^3 (J) */
 double orc_weight(const orc_sim *s);        /* macro-electron weight */
 double orc_a0_of(const orc_sim *s);
 
+/* ---- the three-macro-electron estimate of the loss channels (Sec. III.B) ---- */
+enum {
+  ORC_MODEL_BREM = 1, ORC_MODEL_ION = 2, ORC_MODEL_TNSA = 4, ORC_MODEL_FIELD = 8,
+  ORC_MODEL_ALL = 15
+};
+enum {  /* orc_model_out.E */
+  ORC_MODEL_E_INJ = 0, ORC_MODEL_E_BREM = 1, ORC_MODEL_E_ION = 2, ORC_MODEL_E_TNSA = 3,
+  ORC_MODEL_E_FIELD = 4, ORC_MODEL_E_XRAY_ABOVE = 5, ORC_MODEL_E_ESC = 6
+};
+typedef struct {
+  double Z, n_i, I_ex;            /* solid */
+  double Lx, Ly, Lz;              /* target size (m) */
+  double I0, lambda, eta_l2e;     /* peak intensity (W m^-2), wavelength (m), absorption */
+  double r_fwhm, t_fwhm;          /* envelope widths (m, s) */
+  double mean_fg, mean_sqrt_fg;   /* <fg> and <sqrt(fg)> over the injecting cells */
+  double kappa_esc, kappa_tnsa;   /* reflux constants */
+  double theta_c, eta_avg;        /* current cone half-angle (rad), typical resistivity */
+  double eps_th;                  /* X-ray threshold (J) */
+  double E_stop;                  /* a macro-electron has stopped below this (J) */
+  double rel_step;                /* RK4 step: rel_step eps / S_total long */
+  int32_t mechanisms;             /* ORC_MODEL_* bitmask */
+  int32_t pad;
+} orc_model_in;
+typedef struct {
+  double E[8];                    /* J, indexed by ORC_MODEL_E_* */
+  double N_e, a0;                 /* injected electrons, Eq. (1) */
+  double N_band[3], eps_band[3];  /* warm, emitting, escaping: count, energy per electron (J) */
+  double x_end[3];                /* path length of each macro-electron (m) */
+} orc_model_out;
+void orc_model(const orc_model_in *m, orc_model_out *out);
+
 /* ---- single formulas, for the pins ---- */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_uniform(uint32_t x);

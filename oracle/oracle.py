@@ -1,4 +1,4 @@
-"""ctypes binding of the FP64 CPU oracle (oracle.h, physics.c, sim.c).
+"""ctypes binding of the FP64 CPU oracle (oracle.h, physics.c, sim.c, model.c).
 
 TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the
 benchmark's CPU-baseline leg load this module; the CUDA library never does.
@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
-SOURCES = ["physics.c", "sim.c"]
+SOURCES = ["physics.c", "sim.c", "model.c"]
 
 ORC_DRAG, ORC_SCATTER, ORC_BREM, ORC_FIELDS, ORC_FARADAY, ORC_HEATING = 1, 2, 4, 8, 16, 32
 ORC_ALL = 63
@@ -46,6 +46,22 @@ class Target(C.Structure):
                 ("I_ex", C.c_double), ("Zstar", C.c_double), ("lnLambda", C.c_double),
                 ("eta_max", C.c_double), ("lambda1", C.c_double), ("lambda2", C.c_double),
                 ("T0", C.c_double), ("A_ion", C.c_double)]
+
+
+class ModelIn(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "Z", "n_i", "I_ex", "Lx", "Ly", "Lz", "I0", "lam", "eta_l2e", "r_fwhm", "t_fwhm",
+        "mean_fg", "mean_sqrt_fg", "kappa_esc", "kappa_tnsa", "theta_c", "eta_avg", "eps_th",
+        "E_stop", "rel_step")] + [("mechanisms", C.c_int32), ("pad", C.c_int32)]
+
+
+class ModelOut(C.Structure):
+    _fields_ = [("E", C.c_double * 8), ("N_e", C.c_double), ("a0", C.c_double),
+                ("N_band", C.c_double * 3), ("eps_band", C.c_double * 3), ("x_end", C.c_double * 3)]
+
+
+MODEL_E = ("E_injected", "E_brem", "E_ion", "E_tnsa", "E_field", "E_xray_above", "E_escaped")
+ORC_MODEL_BREM, ORC_MODEL_ION, ORC_MODEL_TNSA, ORC_MODEL_FIELD, ORC_MODEL_ALL = 1, 2, 4, 8, 15
 
 
 class Laser(C.Structure):
@@ -140,6 +156,7 @@ def lib():
         L.orc_ei_rates.argtypes = [tp, C.c_double, C.c_double, C.POINTER(C.c_double),
                                    C.POINTER(C.c_double)]
         L.orc_rotate.argtypes = [dp, C.c_double, C.c_double, dp]
+        L.orc_model.argtypes = [C.POINTER(ModelIn), C.POINTER(ModelOut)]
         L.orc_boris.argtypes = [dp, dp, dp, C.c_double]
     return _lib
 
@@ -346,3 +363,16 @@ def boris(u, E, B, dt: float) -> np.ndarray:
     BB = np.ascontiguousarray(B, dtype=np.float64)
     lib().orc_boris(_dp(uu), _dp(EE), _dp(BB), dt)
     return uu
+
+
+def model(m: dict) -> dict:
+    """The three-macro-electron estimate (Sec. III.B) for one parameter set
+    (keys as ModelIn, wavelength as "lambda")."""
+    d = dict(m)
+    d["lam"] = d.pop("lambda")
+    out = ModelOut()
+    lib().orc_model(C.byref(ModelIn(**d)), C.byref(out))
+    r = {k: out.E[i] for i, k in enumerate(MODEL_E)}
+    r.update(N_e=out.N_e, a0=out.a0, N_band=list(out.N_band), eps_band=list(out.eps_band),
+             x_end=list(out.x_end))
+    return r

@@ -135,3 +135,27 @@ def config4(n_targets=64, seed=1, total_macro=60_000_000, lo=100_000, hi=4_000_0
     lasers = [laser(targets[i], I_Wcm2=float(I[i]), n_macro=n_macro[i]) for i in range(n_targets)]
     return {"targets": targets, "lasers": lasers, "run": run(seed=0, max_history=steps),
             "steps": steps, "I_Wcm2": [float(x) for x in I], "materials": [str(m) for m in mats]}
+
+
+def model_point(Z=79.0, I_Wcm2=1e21, L=(100e-6, 100e-6, 100e-6), n_i=6e28, mechanisms=15) -> dict:
+    """One point of the paper's loss-channel estimate (Sec. III.B): its
+    constants (theta_c = 20 deg, <eta> = 1e-6 Ohm m, 1 MeV threshold,
+    n_i = 6e28 m^-3, I_ex = 11 eV Z) and the injection of Sec. II.B (5 um and
+    40 fs fwhm, <fg> = 0.41, <sqrt(fg)> = 0.61, eta_l2e = 0.3, 1 um light)."""
+    return {"Z": float(Z), "n_i": float(n_i), "I_ex": 11.0 * EV * Z,
+            "Lx": L[0], "Ly": L[1], "Lz": L[2], "I0": I_Wcm2 * 1e4, "lambda": 1e-6,
+            "eta_l2e": 0.3, "r_fwhm": 5e-6, "t_fwhm": 40e-15, "mean_fg": 0.41,
+            "mean_sqrt_fg": 0.61, "kappa_esc": 2.0, "kappa_tnsa": 2.7e-3,
+            "theta_c": math.radians(20.0), "eta_avg": 1e-6, "eps_th": 1.0 * MEV,
+            "E_stop": 1e3 * EV, "rel_step": 0.01, "mechanisms": int(mechanisms)}
+
+
+def model_heatmap(n_I=128, n_Z=92, L=(100e-6, 100e-6, 100e-6)) -> list:
+    """The heatmap grid of the estimate: log-uniform intensity over
+    1e20-1e22 W/cm^2 x Z = 1..n_Z at n_i = 6e28 m^-3, I_ex = 11 eV Z."""
+    pts = []
+    for iz in range(n_Z):
+        for ii in range(n_I):
+            I = 10.0 ** (20.0 + 2.0 * ii / max(n_I - 1, 1))
+            pts.append(model_point(Z=1.0 + iz, I_Wcm2=I, L=L))
+    return pts

@@ -702,3 +702,112 @@ def test_f_sigma_scales_the_optical_depth():
     assert np.all(off > 0)
     assert np.allclose(on, F * off, rtol=1e-9, atol=0)
     assert F.max() - F.min() > 0.02
+
+
+# ---------------------------------------------------------------- three-macro-electron model
+def _model(**kw):
+    base = W.model_point(Z=kw.pop("Z", 79.0), I_Wcm2=kw.pop("I", 1e21),
+                         L=kw.pop("L", (100e-6, 100e-6, 100e-6)), mechanisms=kw.pop("mech", 15))
+    base.update(kw)
+    return base, O.model(base)
+
+
+def test_model_constants_are_the_papers():
+    m = W.model_point()
+    c = GOLD["model_constants"]
+    assert m["theta_c"] == pytest.approx(math.radians(c["theta_c_deg"]))
+    assert m["eta_avg"] == c["eta_avg_ohm_m"] and m["n_i"] == c["n_i_m3"]
+    assert (m["mean_fg"], m["mean_sqrt_fg"]) == (c["mean_fg"], c["mean_sqrt_fg"])
+    assert (m["r_fwhm"], m["t_fwhm"]) == (c["r_fwhm_m"], c["t_fwhm_s"])
+
+
+def test_model_bands_against_quadrature():
+    """Counts and energies of the three macro-electrons are the integrals of
+    the exponential spectrum between 0, the threshold, the escape energy and
+    infinity (numerical quadrature of dN/d eps)."""
+    for I in (1e20, 3e21, 1e22):
+        m, r = _model(I=I)
+        T = r["a0"] * MC2 * m["mean_sqrt_fg"]
+        f = lambda y: r["N_e"] * math.exp(-y)  # dN/dy with y = eps / <eps>
+        esc = m["kappa_esc"] * r["a0"] * MC2
+        edges = [(0.0, min(m["eps_th"], esc)), (m["eps_th"], esc), (esc, np.inf)]
+        for b, (lo, hi) in enumerate(edges):
+            if hi <= lo:
+                assert r["N_band"][b] == 0.0
+                continue
+            n = si.quad(f, lo / T, hi / T, epsabs=0, epsrel=1e-12)[0]
+            e = T * si.quad(lambda y: y * f(y), lo / T, hi / T, epsabs=0, epsrel=1e-12)[0]
+            assert r["N_band"][b] == pytest.approx(n, rel=1e-8)
+            assert r["eps_band"][b] * r["N_band"][b] == pytest.approx(e, rel=1e-8)
+
+
+def test_model_energy_closes():
+    for Z in (6.0, 29.0, 79.0):
+        for I in (1e20, 1e21, 1e22):
+            for L in ((10e-6, 50e-6, 50e-6), (100e-6,) * 3):
+                _, r = _model(Z=Z, I=I, L=L)
+                s = r["E_brem"] + r["E_ion"] + r["E_tnsa"] + r["E_field"] + r["E_escaped"]
+                assert s == pytest.approx(r["E_injected"], rel=1e-12)
+                assert 0 <= r["E_xray_above"] <= r["E_brem"]
+
+
+def test_model_single_channel_closed_forms():
+    """With one channel at a time the escaping macro-electron's energy at
+    x = L_x has a closed form: constant reflux loss, bremsstrahlung loss
+    proportional to gamma (exponential in x), and the field loss
+    F/(x tan(theta_c) + r)^2; the photons above the threshold follow."""
+    Lx = 100e-6
+    # reflux only
+    m, r = _model(mech=O.ORC_MODEL_TNSA, I=1e22)
+    St = 3 * m["kappa_tnsa"] * r["a0"] * MC2 / (3 * Lx)
+    assert r["E_escaped"] == pytest.approx(r["N_band"][2] * (r["eps_band"][2] - St * Lx), rel=1e-10)
+    assert r["x_end"][0] == pytest.approx(r["eps_band"][0] / St, abs=m["E_stop"] / St)
+    # bremsstrahlung only: d gamma/dx = -Kb gamma / mc2
+    m, r = _model(mech=O.ORC_MODEL_BREM, I=1e22)
+    Lrad = math.log(5.6 * math.pi * sc.epsilon_0 * sc.hbar * sc.c / (79 ** (1 / 3) * sc.e ** 2))
+    Kb = sc.e ** 6 * m["n_i"] * 79 ** 2 * Lrad / (12 * math.pi ** 3 * sc.epsilon_0 ** 3 * sc.m_e * sc.c ** 3 * sc.hbar)
+    g0 = 1 + r["eps_band"][2] / MC2
+    gL = g0 * math.exp(-Kb * Lx / MC2)
+    assert r["E_escaped"] == pytest.approx(r["N_band"][2] * (gL - 1) * MC2, rel=1e-8)
+    th = m["eps_th"] / MC2
+    above = si.quad(lambda x: Kb * (g0 * math.exp(-Kb * x / MC2) - th), 0, Lx, epsrel=1e-12)[0]
+    # the escaping electron stays far above the threshold over L_x
+    xray_esc = r["E_xray_above"] - 0.0
+    assert r["N_band"][2] * above <= xray_esc * (1 + 1e-8)
+    # field only
+    m, r = _model(mech=O.ORC_MODEL_FIELD, I=1e22)
+    T = r["a0"] * MC2 * m["mean_sqrt_fg"]
+    rr = m["r_fwhm"] / 2
+    F = sc.e ** 2 * m["eta_avg"] * m["I0"] * m["mean_fg"] * rr ** 2 * m["eta_l2e"] / T
+    tc = math.tan(m["theta_c"])
+    drop = F / tc * (1 / rr - 1 / (Lx * tc + rr))
+    assert r["E_escaped"] == pytest.approx(r["N_band"][2] * (r["eps_band"][2] - drop), rel=1e-9)
+
+
+def test_model_ionisation_range_is_csda():
+    """Ionisation only: the warm and emitting macro-electrons travel their
+    CSDA range, the integral of d eps / S_ion from the stopping energy."""
+    m, r = _model(mech=O.ORC_MODEL_ION, I=1e21)
+    solid = dict(AU, n_i=m["n_i"], I_ex=m["I_ex"])
+    for b in (0, 1):
+        R = si.quad(lambda e: 1 / (O.stop_ion(solid, e)), m["E_stop"], r["eps_band"][b],
+                    epsrel=1e-10, limit=400)[0]
+        assert r["x_end"][b] == pytest.approx(R, rel=2e-3)
+
+
+def test_model_step_convergence():
+    m0, r0 = _model(I=3e21)
+    _, r1 = _model(I=3e21, rel_step=0.0025)
+    for k in ("E_brem", "E_ion", "E_tnsa", "E_field", "E_escaped"):
+        assert r0[k] == pytest.approx(r1[k], rel=1e-6), k
+    # the above-threshold rate jumps from 0 to S_brem(0) at eps_th, as printed:
+    # across the jump the step is first-order accurate
+    assert r0["E_xray_above"] == pytest.approx(r1["E_xray_above"], rel=1e-4)
+
+
+def test_model_dominant_channels_follow_the_paper():
+    for c in GOLD["model_dominant_channel"]["cases"]:
+        Z = W.MATERIALS[c["material"]]["Z"]
+        _, r = _model(Z=Z, I=c["I_Wcm2"])
+        ch = ("E_brem", "E_ion", "E_tnsa", "E_field", "E_escaped")
+        assert max(ch, key=lambda k: r[k]) == c["dominant"], (c, {k: r[k] for k in ch})

@@ -458,9 +458,73 @@ def run_batch(args):
     b.close()
 
 
+def run_model(args):
+    """The paper's loss-channel estimate (Sec. III.B) over its heatmap
+    (intensity x Z), one GPU thread per parameter set, FP64; not the headline
+    line.  value: parameter sets per second with inputs resident on the
+    device; e2e: through hpic_model with host arrays."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2107_01723_gb300 import build as B
+    from paper_2107_01723_gb300 import hpic
+    from paper_2107_01723_gb300 import workloads as W
+    B.build()
+    pts = W.model_heatmap(n_I=args.model_n_I, n_Z=92)
+    n = len(pts)
+    host_in = (hpic.hpic_model_in * n)(*[hpic.model_in(p) for p in pts])
+    nb_in, nb_out = C.sizeof(hpic.hpic_model_in) * n, C.sizeof(hpic.hpic_model_out) * n
+    d_in = torch.empty(nb_in, dtype=torch.uint8, device="cuda")
+    d_out = torch.empty(nb_out, dtype=torch.uint8, device="cuda")
+    d_in.copy_(torch.frombuffer(bytearray(bytes(host_in)), dtype=torch.uint8))
+    stream = torch.cuda.Stream()
+    s = stream.cuda_stream
+    for _ in range(args.warmup):
+        hpic.hpic_model_device(n, d_in.data_ptr(), d_out.data_ptr(), 0, s)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        hpic.hpic_model_device(n, d_in.data_ptr(), d_out.data_ptr(), 0, s)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    out = (hpic.hpic_model_out * n).from_buffer_copy(bytes(d_out.cpu().numpy()))
+    steps = sum(o.steps for o in out)
+    t0 = time.perf_counter()
+    res = hpic.hpic_model(pts, 0, s)
+    wall = time.perf_counter() - t0
+    # the oracle on a sample of the same sets
+    from oracle import oracle as O
+    t1 = time.perf_counter()
+    k = 0
+    while k < n and time.perf_counter() - t1 < 10.0:
+        O.model(pts[(k * 97) % n])
+        k += 1
+    cpu_rate = k / (time.perf_counter() - t1)
+    eta = [r["E_xray_above"] / r["E_injected"] for r in res]
+    line = {"metric": "loss-channel estimate (Sec. III.B): parameter sets per second",
+            "value": n / (ms / 1e3), "unit": "parameter sets/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"heatmap {args.model_n_I} intensities (1e20-1e22 W/cm^2) x Z = 1..92, "
+                                   "100^3 um^3, n_i = 6e28 m^-3, I_ex = 11 eV Z, RK4 rel_step 0.01",
+                       "points": n, "rk4_steps_per_call": steps},
+            "rk4_steps_per_s": steps / (ms / 1e3),
+            "roofline": {"bound": "alu", "note": "FP64 transcendental-bound (log, exp per RK4 stage)"},
+            "e2e": {"value": n / wall, "unit": "parameter sets/s", "h2d_bytes_per_step": nb_in,
+                    "d2h_bytes_per_step": nb_out},
+            "cpu_baseline": {"value": cpu_rate, "unit": "parameter sets/s", "cores": 1,
+                             "kind": "oracle", "sample": f"{k} sets of the heatmap, 10 s"},
+            "eta_e2g": {"min": min(eta), "max": max(eta)}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="headline", choices=["headline", "emission", "batch"])
+    ap.add_argument("--workload", default="headline", choices=["headline", "emission", "batch", "model"])
+    ap.add_argument("--model-n-I", type=int, default=256, help="loss-channel heatmap: intensities")
     ap.add_argument("--emission-n", type=int, default=2 ** 27)
     ap.add_argument("--batch-targets", type=int, default=64,
                     help="batched scan: targets (electrons scale with the count)")
@@ -487,6 +551,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "model":
+        run_model(args)
         return
     if args.impl == "reference":
         # the oracle runs on rank 0 only; other ranks exit without work

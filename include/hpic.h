@@ -348,6 +348,62 @@ int hpic_batch_destroy(hpic_batch *b);
 /* Last error of b, or of the last failed batch creation when b is NULL. */
 const char *hpic_batch_last_error(const hpic_batch *b);
 
+/* ------------------------------------------------------------------------
+ * The paper's three-macro-electron estimate of the loss channels (Sec. III.B),
+ * evaluated for many parameter sets at once, one GPU thread each (the
+ * background heatmap of eta_e->gamma over intensity and Z).  Per set: a0
+ * from Eq. (1), mean energy <eps> = a0 m_e c^2 <sqrt(fg)>, injected count
+ * N_e = I0 <fg> (pi r_fwhm^2/4)(t_fwhm sqrt(ln10/ln2)) eta_l2e / <eps>; the
+ * exponential spectrum is cut at eps_th and eps_esc = kappa_esc a0 m_e c^2
+ * into a warm, an emitting and an escaping macro-electron (band count and
+ * band energy); each is integrated by RK4 in its path length x through
+ * d eps/dx = -(S_brem + S_ion + S_tnsa + S_field(x)), Eqs. (stop_brem),
+ * (stop_ion), (stop_tnsa), (stop_field): the warm and emitting ones until
+ * eps <= E_stop (the remainder counts as ionisation), the escaping one to
+ * x = L_x (the remainder escapes).  Photons above eps_th are counted with
+ * S_brem(eps - eps_th).  Each step is at most rel_step eps / S_total and
+ * rel_step (x + r_fwhm/(2 tan theta_c)) long.  FP64 throughout.
+ * ------------------------------------------------------------------------ */
+enum {
+  HPIC_MODEL_BREM = 1, HPIC_MODEL_ION = 2, HPIC_MODEL_TNSA = 4, HPIC_MODEL_FIELD = 8,
+  HPIC_MODEL_ALL = 15
+};
+enum {  /* hpic_model_out.E */
+  HPIC_MODEL_E_INJ = 0, HPIC_MODEL_E_BREM = 1, HPIC_MODEL_E_ION = 2, HPIC_MODEL_E_TNSA = 3,
+  HPIC_MODEL_E_FIELD = 4, HPIC_MODEL_E_XRAY_ABOVE = 5, HPIC_MODEL_E_ESC = 6
+};
+typedef struct {
+  double Z, n_i_m3, I_ex_J;         /* solid */
+  double Lx_m, Ly_m, Lz_m;          /* target size */
+  double I0_Wm2, lambda_m, eta_l2e; /* laser */
+  double r_fwhm_m, t_fwhm_s;        /* injection envelope widths */
+  double mean_fg, mean_sqrt_fg;     /* envelope means over the injecting cells */
+  double kappa_esc, kappa_tnsa;     /* reflux constants (Sec. II.A) */
+  double theta_c_rad, eta_avg_ohm_m;/* current cone half-angle, typical resistivity */
+  double eps_th_J;                  /* X-ray threshold */
+  double E_stop_J;                  /* a macro-electron has stopped below this */
+  double rel_step;                  /* RK4 step bound, fraction (e.g. 0.01) */
+  int32_t mechanisms;               /* HPIC_MODEL_* bitmask */
+  int32_t pad;
+} hpic_model_in;
+typedef struct {
+  double E[8];                      /* J, indexed by HPIC_MODEL_E_* */
+  double N_e, a0;
+  double N_band[3], eps_band[3];    /* warm, emitting, escaping: count, J per electron */
+  double x_end[3];                  /* path length of each macro-electron (m) */
+  int64_t steps;                    /* RK4 steps taken, all three */
+} hpic_model_out;
+
+/* n parameter sets from host memory in, results to host memory out
+ * (caller-owned; synchronous).  Invalid sets (non-positive rel_step, sizes,
+ * energies or densities) make the call return HPIC_EINVAL before any work. */
+int hpic_model(int64_t n, const hpic_model_in *in, hpic_model_out *out, int device,
+               void *cuda_stream);
+/* The same on device arrays (in, out: n entries each on `device`),
+ * enqueued on cuda_stream; allocates nothing and does not validate. */
+int hpic_model_device(int64_t n, const hpic_model_in *in, hpic_model_out *out, int device,
+                      void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,7 +83,7 @@ static void channels(const model_ctx *c, double eps, double x, double s[5]) {
 static double integrate(const model_ctx *c, double eps0, int escaping, double loss[6]) {
   const orc_model_in *m = c->m;
   double eps = eps0, x = 0.0;
-  for (long it = 0; it < 100000000L; ++it) {
+  for (long it = 0; it < 10000000L; ++it) {
     if (!escaping && eps <= m->E_stop) {
       loss[1] += eps;  /* the remainder is deposited by ionisation */
       return x;
@@ -96,6 +96,10 @@ static double integrate(const model_ctx *c, double eps0, int escaping, double lo
     double k1[5], k2[5], k3[5], k4[5];
     channels(c, eps, x, k1);
     double tot1 = k1[0] + k1[1] + k1[2] + k1[3];
+    if (!(tot1 > 0.0)) {  /* nothing slows it down any more */
+      loss[escaping ? 5 : 1] += eps;
+      return escaping ? m->Lx : x;
+    }
     double h = m->rel_step * eps / tot1;
     if (m->mechanisms & ORC_MODEL_FIELD) {  /* resolve the field's fall-off too */
       double hx = m->rel_step * (x + c->r / c->tan_c);

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libhpic.so")
-SOURCES = ["api.cu", "particles.cu", "grid.cu", "sort_static.cu", "batch_push.cu", "batch.cu"]
+SOURCES = ["api.cu", "particles.cu", "grid.cu", "sort_static.cu", "batch_push.cu", "batch.cu",
+           "model.cu"]
 HEADERS = ["common.cuh", "kernels.h", "ctx.h", "push.cuh", "fields.cuh"]
 # FP32 division and square root in the per-electron kernels to <= 2 ulp
 # (the FP32 path's parity bar is 1e-5; FP64 arithmetic is unaffected)

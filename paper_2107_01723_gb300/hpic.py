@@ -71,6 +71,24 @@ class hpic_batch_tuning(C.Structure):
                 ("use_graph", C.c_int32), ("reserved", C.c_int32), ("ms_per_step", C.c_double)]
 
 
+class hpic_model_in(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "Z", "n_i_m3", "I_ex_J", "Lx_m", "Ly_m", "Lz_m", "I0_Wm2", "lambda_m", "eta_l2e",
+        "r_fwhm_m", "t_fwhm_s", "mean_fg", "mean_sqrt_fg", "kappa_esc", "kappa_tnsa",
+        "theta_c_rad", "eta_avg_ohm_m", "eps_th_J", "E_stop_J", "rel_step")] + [
+        ("mechanisms", C.c_int32), ("pad", C.c_int32)]
+
+
+class hpic_model_out(C.Structure):
+    _fields_ = [("E", C.c_double * 8), ("N_e", C.c_double), ("a0", C.c_double),
+                ("N_band", C.c_double * 3), ("eps_band", C.c_double * 3),
+                ("x_end", C.c_double * 3), ("steps", C.c_int64)]
+
+
+MODEL_E = ("E_injected", "E_brem", "E_ion", "E_tnsa", "E_field", "E_xray_above", "E_escaped")
+HPIC_MODEL_BREM, HPIC_MODEL_ION, HPIC_MODEL_TNSA, HPIC_MODEL_FIELD, HPIC_MODEL_ALL = 1, 2, 4, 8, 15
+
+
 class hpic_tallies(C.Structure):
     _fields_ = [(n, C.c_double) for n in _TALLY_NAMES]
 
@@ -129,6 +147,9 @@ def lib() -> C.CDLL:
         sig["hpic_sort_cells_noalloc"] = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
                                           C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                           C.c_void_p, C.c_int, C.c_void_p]
+        sig["hpic_model"] = [C.c_int64, C.POINTER(hpic_model_in), C.POINTER(hpic_model_out),
+                             C.c_int, vp]
+        sig["hpic_model_device"] = [C.c_int64, vp, vp, C.c_int, vp]
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -317,6 +338,35 @@ def hpic_sort_cells_noalloc(nx: int, ny: int, nz: int, precision: int, n: int, i
 def hpic_destroy(h) -> None:
     if h:
         _check(lib().hpic_destroy(h))
+
+
+# ---- the three-macro-electron estimate (Sec. III.B) ----
+def model_in(m: dict) -> hpic_model_in:
+    return hpic_model_in(m["Z"], m["n_i"], m["I_ex"], m["Lx"], m["Ly"], m["Lz"], m["I0"],
+                         m["lambda"], m["eta_l2e"], m["r_fwhm"], m["t_fwhm"], m["mean_fg"],
+                         m["mean_sqrt_fg"], m["kappa_esc"], m["kappa_tnsa"], m["theta_c"],
+                         m["eta_avg"], m["eps_th"], m["E_stop"], m["rel_step"],
+                         int(m["mechanisms"]), 0)
+
+
+def model_out_dict(o: hpic_model_out) -> dict:
+    r = {k: o.E[i] for i, k in enumerate(MODEL_E)}
+    r.update(N_e=o.N_e, a0=o.a0, N_band=list(o.N_band), eps_band=list(o.eps_band),
+             x_end=list(o.x_end), steps=o.steps)
+    return r
+
+
+def hpic_model(points: list, device: int = 0, stream: int = 0) -> list:
+    n = len(points)
+    src = (hpic_model_in * max(n, 1))(*[model_in(m) for m in points])
+    dst = (hpic_model_out * max(n, 1))()
+    _check(lib().hpic_model(n, src, dst, device, C.c_void_p(stream) if stream else None))
+    return [model_out_dict(dst[i]) for i in range(n)]
+
+
+def hpic_model_device(n: int, in_ptr: int, out_ptr: int, device: int = 0, stream: int = 0) -> None:
+    _check(lib().hpic_model_device(n, C.c_void_p(in_ptr), C.c_void_p(out_ptr), device,
+                                   C.c_void_p(stream) if stream else None))
 
 
 # ---- batches ----

@@ -136,3 +136,23 @@ def test_batch_without_device_is_an_error(lib):
     c = W.config_small()
     code, _ = _bad_batch(lib, [c["target"]] * 2, [c["laser"]] * 2, c["run"])
     assert code == hpic.HPIC_ECUDA
+
+
+def test_model_validation_and_no_device(lib):
+    good = W.model_point()
+    with pytest.raises(hpic.HpicError) as e:
+        hpic.hpic_model([good, dict(good, rel_step=0.0)])
+    assert e.value.code == hpic.HPIC_EINVAL
+    with pytest.raises(hpic.HpicError) as e:
+        hpic.hpic_model([dict(good, mechanisms=hpic.HPIC_MODEL_FIELD)])  # nothing else slows it
+    assert e.value.code == hpic.HPIC_EINVAL
+    assert hpic.hpic_model([]) == []
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return
+    except ImportError:
+        pass
+    with pytest.raises(hpic.HpicError) as e:
+        hpic.hpic_model([good])
+    assert e.value.code == hpic.HPIC_ECUDA

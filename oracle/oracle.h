@@ -79,8 +79,16 @@ typedef struct {
   double spot_y, spot_z; /* disc centre on the x = 0 face (m) */
   double t_inj;       /* injection duration (s) */
   double cone_half;   /* injection cone half-angle (rad) */
-  int64_t n_macro;    /* macro-electrons over the whole injection */
+  int64_t n_macro;    /* flat-top: macro-electrons over the whole injection */
+  int32_t envelope;   /* ORC_ENV_FLAT or ORC_ENV_GAUSS */
+  int32_t per_cell;   /* Gaussian: macro-electrons per injecting cell per step */
+  double r_fwhm, t_fwhm; /* Gaussian: radial and temporal full widths at half maximum */
+  double f_min, g_min;   /* Gaussian: inject where f(r) >= f_min and g(t) >= g_min */
+  int32_t moore_cap;  /* 1: cone half-angle min(cone_half, atan(sqrt(2/(gamma-1)))) */
+  int32_t pad;
 } orc_laser;
+
+enum { ORC_ENV_FLAT = 0, ORC_ENV_GAUSS = 1 };
 
 typedef struct {
   double dt;          /* time step (s) */
@@ -145,7 +153,10 @@ void orc_get_clock(const orc_sim *s, int64_t *step, int64_t *n_injected_ids);
 void orc_set_clock(orc_sim *s, int64_t step, int64_t n_injected_ids);
 double orc_live_energy(const orc_sim *s);   /* sum w * kinetic energy (J) */
 double orc_field_energy(const orc_sim *s);  /* sum B^2/(2 mu0) dx^3 (J) */
-double orc_weight(const orc_sim *s);        /* macro-electron weight */
+double orc_weight(const orc_sim *s);        /* flat-top macro-electron weight */
+/* per-electron weights (real electrons per macro-electron), storage order */
+void orc_get_weights(const orc_sim *s, double *w);
+void orc_set_weights(orc_sim *s, int64_t n, const double *w);
 double orc_a0_of(const orc_sim *s);
 
 /* ---- the three-macro-electron estimate of the loss channels (Sec. III.B) ---- */

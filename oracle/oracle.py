@@ -67,7 +67,10 @@ ORC_MODEL_BREM, ORC_MODEL_ION, ORC_MODEL_TNSA, ORC_MODEL_FIELD, ORC_MODEL_ALL = 
 class Laser(C.Structure):
     _fields_ = [("I0", C.c_double), ("lam", C.c_double), ("eta_l2e", C.c_double),
                 ("spot_r", C.c_double), ("spot_y", C.c_double), ("spot_z", C.c_double),
-                ("t_inj", C.c_double), ("cone_half", C.c_double), ("n_macro", C.c_int64)]
+                ("t_inj", C.c_double), ("cone_half", C.c_double), ("n_macro", C.c_int64),
+                ("envelope", C.c_int32), ("per_cell", C.c_int32), ("r_fwhm", C.c_double),
+                ("t_fwhm", C.c_double), ("f_min", C.c_double), ("g_min", C.c_double),
+                ("moore_cap", C.c_int32), ("pad", C.c_int32)]
 
 
 class Run(C.Structure):
@@ -157,6 +160,8 @@ def lib():
                                    C.POINTER(C.c_double)]
         L.orc_rotate.argtypes = [dp, C.c_double, C.c_double, dp]
         L.orc_model.argtypes = [C.POINTER(ModelIn), C.POINTER(ModelOut)]
+        L.orc_get_weights.argtypes = [C.c_void_p, dp]
+        L.orc_set_weights.argtypes = [C.c_void_p, C.c_int64, dp]
         L.orc_boris.argtypes = [dp, dp, dp, C.c_double]
     return _lib
 
@@ -177,6 +182,20 @@ def make_laser(d: dict) -> Laser:
     d = dict(d)
     d["lam"] = d.pop("lambda")
     return Laser(**d)
+
+
+def weights(sim) -> np.ndarray:
+    """Per-electron weights of an OracleSim, in the order of particles()."""
+    n = sim.n
+    w = np.empty(n)
+    if n:
+        lib().orc_get_weights(sim.h, _dp(w))
+    return w
+
+
+def set_weights(sim, w) -> None:
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    lib().orc_set_weights(sim.h, len(w), _dp(w))
 
 
 def make_run(d: dict) -> Run:

@@ -44,7 +44,7 @@ struct orc_sim {
   double a0, T_hot, w, eps_esc, du_reflux;
   int64_t n_inj_steps;
   int64_t n, cap;
-  double *x, *y, *z, *ux, *uy, *uz, *tau;
+  double *x, *y, *z, *ux, *uy, *uz, *tau, *wt;  /* wt: real electrons per macro */
   uint32_t *id;
   unsigned char *alive;
   int64_t nvec, ncell;
@@ -162,8 +162,8 @@ static void tally_photon(orc_sim *s, double k, double theta, double wph) {
 
 /* ---------------- one electron, one step ---------------- */
 static void kill_with_heat(orc_sim *s, int64_t ip, int64_t cell, double eps) {
-  if (!(s->r.physics & ORC_UNBOUNDED)) s->g[ORC_HEAT][cell] += s->w * eps;
-  s->tal.E_drag += s->w * eps;
+  if (!(s->r.physics & ORC_UNBOUNDED)) s->g[ORC_HEAT][cell] += s->wt[ip] * eps;
+  s->tal.E_drag += s->wt[ip] * eps;
   s->tal.n_cut += 1.0;
   s->alive[ip] = 0;
 }
@@ -171,7 +171,7 @@ static void kill_with_heat(orc_sim *s, int64_t ip, int64_t cell, double eps) {
 static void particle_update(orc_sim *s, int64_t ip) {
   const orc_target *t = &s->t;
   const orc_run *r = &s->r;
-  const double dx = t->dx, dt = r->dt, w = s->w;
+  const double dx = t->dx, dt = r->dt, w = s->wt[ip];
   double X[3] = {s->x[ip] / dx, s->y[ip] / dx, s->z[ip] / dx};
   double u[3] = {s->ux[ip], s->uy[ip], s->uz[ip]};
   double R0[4];
@@ -415,7 +415,7 @@ static void heating(orc_sim *s) {
       }
 }
 
-/* ---------------- injection: Eq. (B1) with flat-top envelopes ---------------- */
+/* ---------------- injection: Eq. (B1) ---------------- */
 static void reserve(orc_sim *s, int64_t need) {
   if (need <= s->cap) return;
   int64_t cap = s->cap ? s->cap : 1024;
@@ -427,12 +427,88 @@ static void reserve(orc_sim *s, int64_t need) {
   s->uy = realloc(s->uy, cap * sizeof(double));
   s->uz = realloc(s->uz, cap * sizeof(double));
   s->tau = realloc(s->tau, cap * sizeof(double));
+  s->wt = realloc(s->wt, cap * sizeof(double));
   s->id = realloc(s->id, cap * sizeof(uint32_t));
   s->alive = realloc(s->alive, cap);
   s->cap = cap;
 }
 
+/* the cone half-angle for an electron of kinetic energy eps: the laser's,
+ * or with the Moore cap (Sec. II.B) the smaller of it and
+ * atan(sqrt(2/(gamma - 1))); returned as 1 - cos(theta) */
+static double cone_omc(const orc_sim *s, double eps) {
+  double th = s->l.cone_half;
+  if (s->l.moore_cap) {
+    double moore = atan(sqrt(2.0 / (eps / MC2)));
+    if (moore < th) th = moore;
+  }
+  return 1.0 - cos(th);
+}
+
+/* Gaussian envelopes of Sec. II.B and App. B: f(r) = exp(-4 ln2 r^2/r_fwhm^2)
+ * at the centre of each face cell, g(t) = exp(-4 ln2 (t - t_pk)^2/t_fwhm^2)
+ * at mid-step t = (s + 1/2) dt with t_pk chosen so that g(0) = g_min; cells
+ * with f >= f_min inject per_cell macro-electrons while g >= g_min, each of
+ * weight N_cell/per_cell, N_cell = I0 f g A dt eta_le / <eps>, with the local
+ * mean energy <eps> = a0 sqrt(f g) m_e c^2 (Eq. (N_cell)) */
+static double g_of(const orc_sim *s, int64_t st) {
+  const orc_laser *l = &s->l;
+  double t_pk = 0.5 * l->t_fwhm * sqrt(log(1.0 / l->g_min) / log(2.0));
+  double t = ((double)st + 0.5) * s->r.dt;
+  double u = (t - t_pk) / l->t_fwhm;
+  return exp(-4.0 * log(2.0) * u * u);
+}
+
+static void inject_gauss(orc_sim *s) {
+  const orc_laser *l = &s->l;
+  const double g = g_of(s, s->step);
+  if (!(g >= l->g_min) || l->per_cell <= 0 || !(s->a0 > 0.0)) return;
+  const double dx = s->t.dx, A = dx * dx;
+  int64_t c = 0;
+  for (int k = 0; k < s->t.nz; ++k)
+    for (int j = 0; j < s->t.ny; ++j) {
+      double yc = (j + 0.5) * dx - l->spot_y, zc = (k + 0.5) * dx - l->spot_z;
+      double f = exp(-4.0 * log(2.0) * (yc * yc + zc * zc) / (l->r_fwhm * l->r_fwhm));
+      if (!(f >= l->f_min)) continue;
+      double mean = s->a0 * sqrt(f * g) * MC2;
+      double N_cell = l->I0 * f * g * A * s->r.dt * l->eta_l2e / mean;
+      double w = N_cell / (double)l->per_cell;
+      reserve(s, s->n + l->per_cell);
+      for (int32_t i = 0; i < l->per_cell; ++i) {
+        uint32_t id = (uint32_t)(s->next_id + c * l->per_cell + i);
+        double R8[4], R9[4];
+        draw(s, id, 8, R8);
+        draw(s, id, 9, R9);
+        double eps = -mean * log(1.0 - R8[2]);
+        double omc = R8[3] * cone_omc(s, eps);
+        double ct = 1.0 - omc, st_ = sqrt(omc * (2.0 - omc)), cph = 2.0 * PI * R9[0];
+        double un = u_of_eps(eps);
+        int64_t q = s->n;
+        s->x[q] = 1e-6 * dx;
+        s->y[q] = (j + R8[0]) * dx;
+        s->z[q] = (k + R8[1]) * dx;
+        s->ux[q] = un * ct;
+        s->uy[q] = un * st_ * cos(cph);
+        s->uz[q] = un * st_ * sin(cph);
+        s->tau[q] = -log(1.0 - R9[1]);
+        s->wt[q] = w;
+        s->id[q] = id;
+        s->alive[q] = 1;
+        s->tal.E_injected += w * eps;
+        s->tal.N_injected += w;
+        s->tal.n_injected += 1.0;
+        s->n += 1;
+      }
+      ++c;
+    }
+  s->next_id += c * l->per_cell;
+}
+
 static void inject(orc_sim *s) {
+  if (s->l.envelope == ORC_ENV_GAUSS) {
+    inject_gauss(s);
+    return;
+  }
   int64_t st = s->step;
   if (st >= s->n_inj_steps || s->l.n_macro <= 0) return;
   int64_t S = s->n_inj_steps, N = s->l.n_macro;
@@ -447,7 +523,7 @@ static void inject(orc_sim *s) {
     double rr = s->l.spot_r * sqrt(R8[0]);
     double ph = 2.0 * PI * R8[1];
     double eps = -s->T_hot * log(1.0 - R8[2]);
-    double omc = R8[3] * (1.0 - cosc);  /* 1 - cos(theta), uniform in solid angle */
+    double omc = R8[3] * (s->l.moore_cap ? cone_omc(s, eps) : 1.0 - cosc);  /* uniform in solid angle */
     double ct = 1.0 - omc;
     double st_ = sqrt(omc * (2.0 - omc));
     double cph = 2.0 * PI * R9[0];
@@ -460,6 +536,7 @@ static void inject(orc_sim *s) {
     s->uy[q] = un * st_ * cos(cph);
     s->uz[q] = un * st_ * sin(cph);
     s->tau[q] = -log(1.0 - R9[1]);
+    s->wt[q] = s->w;
     s->id[q] = id;
     s->alive[q] = 1;
     s->tal.E_injected += s->w * eps;
@@ -496,6 +573,7 @@ void orc_seed(orc_sim *s, int64_t n, double mean_eps) {
     s->uy[q] = un * st * cos(ph);
     s->uz[q] = un * st * sin(ph);
     s->tau[q] = -log(1.0 - R11[2]);
+    s->wt[q] = s->w;
     s->id[q] = id;
     s->alive[q] = 1;
     s->tal.E_injected += s->w * eps;
@@ -543,7 +621,7 @@ orc_sim *orc_create(const orc_target *t, const orc_laser *l, const orc_run *r) {
 void orc_destroy(orc_sim *s) {
   if (!s) return;
   free(s->x); free(s->y); free(s->z); free(s->ux); free(s->uy); free(s->uz);
-  free(s->tau); free(s->id); free(s->alive);
+  free(s->tau); free(s->wt); free(s->id); free(s->alive);
   for (int w = 0; w < 13; ++w) free(s->g[w]);
   free(s->histE); free(s->histN); free(s->history); free(s->table);
   free(s);
@@ -561,7 +639,7 @@ int orc_step(orc_sim *s, int64_t nsteps) {
       if (!s->alive[ip]) continue;
       s->x[m] = s->x[ip]; s->y[m] = s->y[ip]; s->z[m] = s->z[ip];
       s->ux[m] = s->ux[ip]; s->uy[m] = s->uy[ip]; s->uz[m] = s->uz[ip];
-      s->tau[m] = s->tau[ip]; s->id[m] = s->id[ip]; s->alive[m] = 1;
+      s->tau[m] = s->tau[ip]; s->wt[m] = s->wt[ip]; s->id[m] = s->id[ip]; s->alive[m] = 1;
       ++m;
     }
     s->n = m;
@@ -599,6 +677,7 @@ void orc_set_particles(orc_sim *s, int64_t n, const double *x, const double *y,
   memcpy(s->tau, tau, b);
   memcpy(s->id, id, (size_t)n * sizeof(uint32_t));
   memset(s->alive, 1, (size_t)n);
+  for (int64_t i = 0; i < n; ++i) s->wt[i] = s->w;
   s->n = n;
 }
 
@@ -649,7 +728,7 @@ double orc_live_energy(const orc_sim *s) {
   double e = 0.0;
   for (int64_t ip = 0; ip < s->n; ++ip) {
     double u[3] = {s->ux[ip], s->uy[ip], s->uz[ip]};
-    e += s->w * kinetic(u);
+    e += s->wt[ip] * kinetic(u);
   }
   return e;
 }
@@ -662,4 +741,11 @@ double orc_field_energy(const orc_sim *s) {
 }
 
 double orc_weight(const orc_sim *s) { return s->w; }
+
+void orc_get_weights(const orc_sim *s, double *w) { memcpy(w, s->wt, (size_t)s->n * sizeof(double)); }
+
+void orc_set_weights(orc_sim *s, int64_t n, const double *w) {
+  if (n > s->n) n = s->n;
+  memcpy(s->wt, w, (size_t)n * sizeof(double));
+}
 double orc_a0_of(const orc_sim *s) { return s->a0; }

@@ -39,12 +39,31 @@ def target(n=(32, 32, 32), dx=1e-6, material="Au", T0_eV=1.0, eta_max=1e-6,
             "A_ion": m["A"]}
 
 
+ENV_FLAT, ENV_GAUSS = 0, 1
+
+
 def laser(tgt: dict, I_Wcm2=1e20, n_macro=100_000, spot_r=5e-6, t_inj=100e-15,
-          cone_half_deg=30.0, eta_l2e=0.3, lam=1e-6) -> dict:
+          cone_half_deg=30.0, eta_l2e=0.3, lam=1e-6, moore_cap=0) -> dict:
     """Flat-top injection disc centred on the x = 0 face."""
     return {"I0": I_Wcm2 * 1e4, "lambda": lam, "eta_l2e": eta_l2e, "spot_r": spot_r,
             "spot_y": 0.5 * tgt["ny"] * tgt["dx"], "spot_z": 0.5 * tgt["nz"] * tgt["dx"],
-            "t_inj": t_inj, "cone_half": math.radians(cone_half_deg), "n_macro": int(n_macro)}
+            "t_inj": t_inj, "cone_half": math.radians(cone_half_deg), "n_macro": int(n_macro),
+            "envelope": ENV_FLAT, "per_cell": 0, "r_fwhm": 0.0, "t_fwhm": 0.0, "f_min": 0.0,
+            "g_min": 0.0, "moore_cap": int(moore_cap), "pad": 0}
+
+
+def laser_gauss(tgt: dict, I_Wcm2=1e21, per_cell=1226, r_fwhm=5e-6, t_fwhm=40e-15,
+                f_min=0.5, g_min=0.1, cone_half_deg=20.0, moore_cap=1, eta_l2e=0.3,
+                lam=1e-6) -> dict:
+    """The paper's injection (Sec. II.B): Gaussian f(r) of radial FWHM r_fwhm on
+    the x = 0 face and Gaussian g(t) of FWHM t_fwhm, nothing injected where
+    g < 0.1 or into cells with f < 0.5, 1226 macro-electrons per injecting
+    cell per step, cone half-angle min(20 deg, atan(sqrt(2/(gamma - 1))))."""
+    d = laser(tgt, I_Wcm2=I_Wcm2, n_macro=0, spot_r=0.5 * r_fwhm, cone_half_deg=cone_half_deg,
+              eta_l2e=eta_l2e, lam=lam, moore_cap=moore_cap)
+    d.update(envelope=ENV_GAUSS, per_cell=int(per_cell), r_fwhm=r_fwhm, t_fwhm=t_fwhm,
+             f_min=f_min, g_min=g_min, t_inj=t_fwhm * math.sqrt(math.log(1 / g_min) / math.log(2)))
+    return d
 
 
 def run(dt=0.5e-15, seed=0, n_E=100, n_theta=90, E_min=10e3 * EV, E_max=100 * MEV,

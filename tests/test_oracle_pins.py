@@ -811,3 +811,84 @@ def test_model_dominant_channels_follow_the_paper():
         _, r = _model(Z=Z, I=c["I_Wcm2"])
         ch = ("E_brem", "E_ion", "E_tnsa", "E_field", "E_escaped")
         assert max(ch, key=lambda k: r[k]) == c["dominant"], (c, {k: r[k] for k in ch})
+
+
+# ---------------------------------------------------------------- Gaussian injection (Sec. II.B)
+def _gauss_run(per_cell=16, steps=None, physics=0):
+    tgt = W.target(n=(60, 16, 16), dx=0.7e-6)
+    las = W.laser_gauss(tgt, I_Wcm2=1e21, per_cell=per_cell)
+    run = W.run(physics=physics)
+    s = O.OracleSim(tgt, las, run)
+    return tgt, las, run, s
+
+
+def test_gaussian_envelope_means_match_the_paper():
+    """With f >= 0.5 and g >= 0.1 the injecting cells see <fg> = 0.41 and
+    <sqrt(fg)> = 0.61 (Sec. II.B); sqrt(fg) of each electron follows from its
+    weight, N_cell/per_cell = I0 sqrt(fg) A dt eta / (a0 m_e c^2 per_cell)."""
+    tgt, las, run, s = _gauss_run()
+    n_steps = int(round(las["t_inj"] / run["dt"])) + 2
+    s.step(n_steps)
+    w = O.weights(s)
+    unit = las["I0"] * tgt["dx"] ** 2 * run["dt"] * las["eta_l2e"] / (s.a0 * MC2 * las["per_cell"])
+    sq = w / unit
+    g = GOLD["gaussian_envelope_means"]
+    assert np.mean(sq) == pytest.approx(g["mean_sqrt_fg"], abs=0.02)
+    assert np.mean(sq ** 2) == pytest.approx(g["mean_fg"], abs=0.02)
+    assert sq.max() <= 1.0 and sq.min() >= math.sqrt(0.5 * 0.1) - 1e-12
+
+
+def test_gaussian_injection_counts_and_energy():
+    """Per step: per_cell electrons in every face cell whose centre lies within
+    r_fwhm/2 of the spot (f >= 1/2), only while g >= 0.1; the injected energy
+    is the laser energy I0 f g A dt eta_le of those cells (in expectation)."""
+    tgt, las, run, s = _gauss_run(per_cell=64)
+    _, _, _, s_big = _gauss_run(per_cell=3000)
+    dx = tgt["dx"]
+    yc = (np.arange(16) + 0.5) * dx - las["spot_y"]
+    r2 = yc[:, None] ** 2 + yc[None, :] ** 2
+    cells = int(np.sum(r2 <= (las["r_fwhm"] / 2) ** 2 * (1 + 1e-12)))
+    f = np.exp(-4 * math.log(2) * r2 / las["r_fwhm"] ** 2)[r2 <= (las["r_fwhm"] / 2) ** 2]
+    t_pk = 0.5 * las["t_fwhm"] * math.sqrt(math.log(10) / math.log(2))
+    n_inj = 0
+    for st in range(int(2 * t_pk / run["dt"]) + 3):
+        before = s.tallies()
+        s.step(1)
+        t = s.tallies()
+        t_mid = (st + 0.5) * run["dt"]
+        g = math.exp(-4 * math.log(2) * ((t_mid - t_pk) / las["t_fwhm"]) ** 2)
+        dn = t["n_injected"] - before["n_injected"]
+        if g >= 0.1:
+            assert dn == cells * las["per_cell"]
+            if n_inj < 2:  # energy flux, on a 3000-per-cell copy of the first steps
+                b0 = s_big.tallies()["E_injected"]
+                s_big.step(1)
+                want = np.sum(las["I0"] * f * g * dx * dx * run["dt"] * las["eta_l2e"])
+                got = s_big.tallies()["E_injected"] - b0
+                assert got == pytest.approx(want, rel=5 / math.sqrt(cells * 3000))
+            n_inj += 1
+        elif n_inj == 0:
+            s_big.step(1)
+        else:
+            assert dn == 0
+    assert n_inj == pytest.approx(2 * t_pk / run["dt"], abs=1)
+
+
+def test_moore_cone_cap():
+    """Every injected electron lies inside min(20 deg, atan(sqrt(2/(gamma-1))))
+    of +x, uniform in solid angle inside its own cap."""
+    tgt, las, run, s = _gauss_run(per_cell=200)
+    t_pk = 0.5 * las["t_fwhm"] * math.sqrt(math.log(10) / math.log(2))
+    s.step(int(t_pk / run["dt"]))
+    p = s.particles()
+    new = p["x"] == 1e-6 * tgt["dx"]  # injected in the last step, not yet moved
+    p = {k: v[new] for k, v in p.items()}
+    assert len(p["x"]) > 5000
+    un = np.sqrt(p["ux"] ** 2 + p["uy"] ** 2 + p["uz"] ** 2)
+    gam = np.sqrt(1 + un ** 2)
+    cap = np.minimum(math.radians(20), np.arctan(np.sqrt(2 / (gam - 1))))
+    omc = 1 - p["ux"] / un
+    assert np.all(omc <= (1 - np.cos(cap)) * (1 + 1e-9) + 1e-15)
+    frac = omc / (1 - np.cos(cap))
+    assert st.kstest(frac, "uniform").pvalue > 1e-3
+    assert np.mean(cap < math.radians(20)) > 0.05  # the Moore limit binds for hot electrons

@@ -110,9 +110,26 @@ typedef struct {
   double A_ion;         /* ion mass in atomic mass units (e-i equilibration) */
 } hpic_target_desc;
 
-/* Laser and injection, Eq. (1), Eq. (B1), Sec. II.B, with flat-top
- * envelopes: a disc of radius spot_radius_m centred at (0, spot_y, spot_z)
- * for t < t_inj_s. */
+/* Laser and injection, Eq. (1), Eq. (B1), Sec. II.B and App. B.
+ *
+ * HPIC_ENV_FLAT: flat-top envelopes, a disc of radius spot_radius_m centred
+ * at (0, spot_y, spot_z) for t < t_inj_s; n_macro electrons in all, each of
+ * the weight N_real/n_macro of Eq. (B1).
+ *
+ * HPIC_ENV_GAUSS (the paper's own): f(r) = exp(-4 ln2 r^2/r_fwhm^2) at the
+ * centre of each x = 0 face cell (r from the spot centre) and g(t) =
+ * exp(-4 ln2 (t - t_pk)^2/t_fwhm^2) at mid-step t = (s + 1/2) dt, t_pk set so
+ * that g(0) = g_min.  While g >= g_min every face cell with f >= f_min
+ * injects per_cell macro-electrons per step, uniform over the cell's face,
+ * each carrying its own weight N_cell/per_cell with N_cell = I0 f g dx^2 dt
+ * eta_l2e / <eps> and the local mean energy <eps> = a0 sqrt(f g) m_e c^2
+ * (Eq. (N_cell)); spot_radius_m, t_inj_s and n_macro are unused.
+ *
+ * Either way energies are exponential with the (local) mean and directions
+ * uniform in solid angle inside the cone, whose half-angle is, with
+ * moore_cap, the smaller of cone_half_angle_rad and atan(sqrt(2/(gamma-1)))
+ * for each electron (Sec. II.B). */
+enum { HPIC_ENV_FLAT = 0, HPIC_ENV_GAUSS = 1 };
 typedef struct {
   double I0_Wm2;        /* peak intensity, W m^-2 (1e20 W/cm^2 = 1e24) */
   double lambda_m;      /* wavelength */
@@ -122,6 +139,12 @@ typedef struct {
   double t_inj_s;       /* injection window */
   double cone_half_angle_rad; /* uniform in solid angle within this cone */
   int64_t n_macro;      /* macro-electrons over the whole window (< 2^32-1) */
+  int32_t envelope;     /* HPIC_ENV_FLAT or HPIC_ENV_GAUSS */
+  int32_t per_cell;     /* Gaussian: macro-electrons per injecting cell per step */
+  double r_fwhm_m, t_fwhm_s; /* Gaussian: radial and temporal FWHM */
+  double f_min, g_min;  /* Gaussian: inject where f >= f_min and g >= g_min */
+  int32_t moore_cap;    /* 1: Moore-scaling cap on the cone half-angle */
+  int32_t pad;
 } hpic_laser_desc;
 
 typedef struct {
@@ -227,6 +250,15 @@ int hpic_read_particles(hpic_ctx *ctx, double *x, double *y, double *z,
 /* Replace the electron population with n host electrons (same units).
  * Positions must lie in [0, n*dx] on each axis (any finite position with
  * HPIC_UNBOUNDED).  Errors: HPIC_EINVAL, HPIC_ENOMEM. */
+/* Per-electron weights (real electrons per macro-electron) of the live
+ * electrons, in the order hpic_read_particles returns them (same cap / n
+ * semantics).  With the flat-top envelope every weight is the Eq. (B1) one. */
+int hpic_read_weights(hpic_ctx *ctx, double *w, int64_t cap, int64_t *n);
+/* Set the weights of the n electrons last loaded by hpic_load_particles (in
+ * that order); HPIC_ESTATE unless the laser uses the Gaussian envelope (the
+ * flat-top path keeps one weight for all). */
+int hpic_load_weights(hpic_ctx *ctx, int64_t n, const double *w);
+
 int hpic_load_particles(hpic_ctx *ctx, int64_t n, const double *x, const double *y,
                         const double *z, const double *ux, const double *uy,
                         const double *uz, const double *tau, const uint32_t *id);

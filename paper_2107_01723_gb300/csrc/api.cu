@@ -54,6 +54,13 @@ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 int n_rows(const hpic_ctx *c) { return c->run.n_Ebins + 2; }
 long long hist_len(const hpic_ctx *c) { return (long long)n_rows(c) * c->run.n_thbins; }
 
+// electrons the scheduled laser will inject in all
+long long injection_total(const hpic_ctx *c) {
+  if (!c->have_laser) return 0;
+  if (c->K.weighted) return c->K.per_cell * c->K.n_inj_cells * c->K.n_inj_steps;
+  return c->K.n_macro;
+}
+
 int grid_blocks(const hpic_ctx *c, long long work) {
   const long long want = (work + 255) / 256;
   const long long cap = (long long)c->sm_count * 8;
@@ -62,7 +69,7 @@ int grid_blocks(const hpic_ctx *c, long long work) {
 }
 
 size_t particle_bytes(const hpic_ctx *c, long long stride) {
-  return (size_t)stride * (7 * c->rsz + sizeof(uint32_t));
+  return (size_t)stride * (8 * c->rsz + sizeof(uint32_t));  // 7 reals, weight, id
 }
 
 int read_counters(hpic_ctx *ctx, hpic::Counters *h) {
@@ -104,10 +111,10 @@ int reserve(hpic_ctx *ctx, long long need) {
     const size_t so = (size_t)ctx->stride, sn = (size_t)cap;
     char *src = static_cast<char *>(ctx->pbuf[ctx->cur]);
     char *dst = static_cast<char *>(nb[0]);
-    for (int a = 0; a < 7; ++a)
+    for (int a = 0; a < 8; ++a)
       CK(cudaMemcpyAsync(dst + a * sn * ctx->rsz, src + a * so * ctx->rsz, h.n * ctx->rsz,
                          cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(dst + 7 * sn * ctx->rsz, src + 7 * so * ctx->rsz, h.n * sizeof(uint32_t),
+    CK(cudaMemcpyAsync(dst + 8 * sn * ctx->rsz, src + 8 * so * ctx->rsz, h.n * sizeof(uint32_t),
                        cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
   }
@@ -129,6 +136,10 @@ int reserve(hpic_ctx *ctx, long long need) {
 void hpic::fold(const hpic_target_desc &t, const hpic_run_params &r, const hpic_laser_desc *laser,
                 Consts &K) {
   const double dx = t.dx_m, dt = r.dt_s, Z = t.Z, ni = t.n_i_m3;
+  K.weighted = 0;  // set below for the Gaussian envelope; inj_cells is kept
+  K.moore = 0;
+  K.per_cell = K.n_inj_cells = 0;
+  K.g_c = K.t_pk = K.g_min = K.inj_unit = 0.0;
   K.nx = t.nx; K.ny = t.ny; K.nz = t.nz;
   K.nvec = (long long)(t.nx + 1) * (t.ny + 1) * (t.nz + 1);
   K.ncell = (long long)t.nx * t.ny * t.nz;
@@ -225,6 +236,22 @@ void hpic::fold(const hpic_target_desc &t, const hpic_run_params &r, const hpic_
     K.n_macro = l.n_macro;
     long long S = std::llround(l.t_inj_s / dt);
     K.n_inj_steps = S < 1 ? 1 : S;
+    K.moore = l.moore_cap != 0;
+    if (l.envelope == HPIC_ENV_GAUSS) {
+      // App. B: g = exp(-4 ln2 ((s + 1/2) dt - t_pk)^2 / t_fwhm^2), g(0) = g_min
+      K.weighted = 1;
+      K.per_cell = l.per_cell;
+      K.n_inj_cells = (long long)injection_cells(t, l).size();
+      K.g_c = 4.0 * std::log(2.0) * (dt / l.t_fwhm_s) * (dt / l.t_fwhm_s);
+      K.t_pk = 0.5 * l.t_fwhm_s * std::sqrt(std::log(1.0 / l.g_min) / std::log(2.0)) / dt;
+      K.g_min = l.g_min;
+      K.inj_unit = a0 > 0.0 ? l.I0_Wm2 * dx * dx * dt * l.eta_l2e / (a0 * MC2 * l.per_cell) : 0.0;
+      long long s = 0;  // steps while g >= g_min (g rises from g_min, peaks, falls)
+      while (std::exp(-K.g_c * (s + 0.5 - K.t_pk) * (s + 0.5 - K.t_pk)) >= l.g_min) ++s;
+      K.n_inj_steps = s + 1;  // one more: the kernel itself decides on g
+      K.n_macro = 0;
+      w = 1.0;
+    }
   } else {
     K.n_macro = 0;
     K.n_inj_steps = 1;
@@ -262,6 +289,15 @@ const char *hpic::check_laser(const hpic_laser_desc &l, const hpic_target_desc &
       !(l.t_inj_s >= 0) || l.n_macro < 0 || l.n_macro >= 0xFFFFFFFFll ||
       !(l.cone_half_angle_rad >= 0) || l.cone_half_angle_rad > PI)
     return "laser parameters out of range";
+  if ((l.envelope != HPIC_ENV_FLAT && l.envelope != HPIC_ENV_GAUSS) ||
+      (l.moore_cap != 0 && l.moore_cap != 1))
+    return "unknown envelope or Moore flag";
+  if (l.envelope == HPIC_ENV_GAUSS) {
+    if (l.per_cell < 1 || !(l.r_fwhm_m > 0) || !(l.t_fwhm_s > 0) || !(l.f_min > 0 && l.f_min <= 1) ||
+        !(l.g_min > 0 && l.g_min < 1))
+      return "Gaussian envelope parameters out of range";
+    return nullptr;  // only face cells inject: nothing has to fit
+  }
   const double Ly = t.ny * t.dx_m, Lz = t.nz * t.dx_m;
   if (l.spot_y_m - l.spot_radius_m < 0 || l.spot_y_m + l.spot_radius_m > Ly ||
       l.spot_z_m - l.spot_radius_m < 0 || l.spot_z_m + l.spot_radius_m > Lz)
@@ -294,6 +330,21 @@ double hpic::fsigma_of(const Consts &K, double Ti) {
   return 1.0 + K.fs_q * (0.5 * std::log(Ti) + K.fs_c);
 }
 
+// App. B: the x = 0 face cells (k outer, j inner) whose centre has
+// f(r) = exp(-4 ln2 r^2/r_fwhm^2) >= f_min, with sqrt(f)
+std::vector<hpic::InjCell> hpic::injection_cells(const hpic_target_desc &t,
+                                                 const hpic_laser_desc &l) {
+  std::vector<InjCell> out;
+  if (l.envelope != HPIC_ENV_GAUSS) return out;
+  for (int k = 0; k < t.nz; ++k)
+    for (int j = 0; j < t.ny; ++j) {
+      const double y = (j + 0.5) * t.dx_m - l.spot_y_m, z = (k + 0.5) * t.dx_m - l.spot_z_m;
+      const double f = std::exp(-4.0 * std::log(2.0) * (y * y + z * z) / (l.r_fwhm_m * l.r_fwhm_m));
+      if (f >= l.f_min) out.push_back(InjCell{j, k, std::sqrt(f)});
+    }
+  return out;
+}
+
 namespace {
 
 void destroy_all(hpic_ctx *c) {
@@ -308,6 +359,7 @@ void destroy_all(hpic_ctx *c) {
   cudaFree(c->eta_r);
   cudaFree(c->Ti);
   cudaFree(c->Fsig);
+  cudaFree(c->inj_cells);
   cudaFree(c->H);
   cudaFree(c->tal);
   cudaFree(c->hist);
@@ -370,9 +422,10 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
       hpic::launch_bheat<R>(ctx->K, G, tv, gg, ctx->stream);
       ctx->launches += 1;
     }
-    if (ctx->have_laser && ctx->host_step < ctx->K.n_inj_steps && ctx->K.n_macro > 0) {
+    if (ctx->have_laser && ctx->host_step < ctx->K.n_inj_steps && injection_total(ctx) > 0) {
       const long long S = ctx->K.n_inj_steps, N = ctx->K.n_macro, st = ctx->host_step;
-      const long long c = (N * (st + 1)) / S - (N * st) / S;
+      const long long c = ctx->K.weighted ? ctx->K.per_cell * ctx->K.n_inj_cells
+                                          : (N * (st + 1)) / S - (N * st) / S;
       hpic::launch_inject<R>(ctx->K, P(ctx->cur), ctx->cnt, ctx->cap, tv,
                              grid_blocks(ctx, c > 0 ? c : 1), ctx->stream);
       ctx->launches += 1;
@@ -455,7 +508,7 @@ int load_particles_impl(hpic_ctx *ctx, int64_t n, const double *x, const double 
     }
     if (id[i] == hpic::kDead) return fail(ctx, HPIC_EINVAL, "id 0xFFFFFFFF is reserved");
   }
-  const long long extra = ctx->have_laser ? ctx->K.n_macro : 0;
+  const long long extra = injection_total(ctx);
   int rc = reserve(ctx, n + extra);
   if (rc) return rc;
   const hpic::PView<R> P = pview<R>(ctx, ctx->cur);
@@ -469,6 +522,11 @@ int load_particles_impl(hpic_ctx *ctx, int64_t n, const double *x, const double 
     CK(cudaStreamSynchronize(ctx->stream));
   }
   if (n) CK(cudaMemcpyAsync(P.id, id, n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+  if (n && ctx->K.weighted) {  // the envelope's weights come from hpic_load_weights
+    std::vector<R> wd(n, (R)ctx->K.w);
+    CK(cudaMemcpyAsync(P.w, wd.data(), n * sizeof(R), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
   hpic::Counters h;
   rc = read_counters(ctx, &h);
   if (rc) return rc;
@@ -603,12 +661,31 @@ int hpic_inject_electrons(hpic_ctx *ctx, const hpic_laser_desc *l) {
   hpic::Counters h;
   int rc = read_counters(ctx, &h);
   if (rc) return rc;
-  if (h.next_id + l->n_macro >= 0xFFFFFFFFll) return fail(ctx, HPIC_EINVAL, "id space exhausted");
-  rc = reserve(ctx, h.n + l->n_macro);
-  if (rc) return rc;
+  const hpic_laser_desc keep = ctx->laser;
   ctx->laser = *l;
   ctx->have_laser = true;
   fold_constants(ctx);
+  const long long total = injection_total(ctx);
+  std::vector<hpic::InjCell> cells = hpic::injection_cells(ctx->tgt, *l);
+  auto undo = [&](int code, const char *msg) {
+    ctx->laser = keep;
+    ctx->have_laser = false;
+    fold_constants(ctx);
+    return fail(ctx, code, msg);
+  };
+  if (h.next_id + total >= 0xFFFFFFFFll) return undo(HPIC_EINVAL, "id space exhausted");
+  rc = reserve(ctx, h.n + total);
+  if (rc) return undo(rc, ctx->err.c_str());
+  if (!cells.empty()) {
+    if (cudaMalloc(&ctx->inj_cells, cells.size() * sizeof(hpic::InjCell)) != cudaSuccess) {
+      cudaGetLastError();
+      return undo(HPIC_ENOMEM, "injection cell list allocation failed");
+    }
+    CK(cudaMemcpyAsync(ctx->inj_cells, cells.data(), cells.size() * sizeof(hpic::InjCell),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->K.inj_cells = ctx->inj_cells;
+  }
   return HPIC_OK;
 }
 
@@ -621,7 +698,7 @@ int hpic_seed_electrons(hpic_ctx *ctx, int64_t n, double mean_energy_J) {
   int rc = read_counters(ctx, &h);
   if (rc) return rc;
   if (h.next_id + n >= 0xFFFFFFFFll) return fail(ctx, HPIC_EINVAL, "id space exhausted");
-  rc = reserve(ctx, h.n + n + (ctx->have_laser ? ctx->K.n_macro : 0));
+  rc = reserve(ctx, h.n + n + injection_total(ctx));
   if (rc) return rc;
   if (n == 0) return HPIC_OK;
   const int grid = grid_blocks(ctx, n);
@@ -823,6 +900,63 @@ int hpic_read_particles(hpic_ctx *ctx, double *x, double *y, double *z, double *
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   return ctx->fp32 ? read_particles_impl<float>(ctx, x, y, z, ux, uy, uz, tau, id, cap, n)
                    : read_particles_impl<double>(ctx, x, y, z, ux, uy, uz, tau, id, cap, n);
+}
+
+int hpic_read_weights(hpic_ctx *ctx, double *w, int64_t cap, int64_t *n_out) {
+  if (!ctx || !n_out) return fail(ctx, HPIC_EINVAL, "NULL argument");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  hpic::Counters h;
+  int rc = read_counters(ctx, &h);
+  if (rc) return rc;
+  const long long n = h.n;
+  std::vector<uint32_t> ids(n);
+  std::vector<char> wb(n * ctx->rsz);
+  const uint32_t *id_src = ctx->fp32 ? pview<float>(ctx, ctx->cur).id : pview<double>(ctx, ctx->cur).id;
+  const void *w_src = ctx->fp32 ? (const void *)pview<float>(ctx, ctx->cur).w
+                                : (const void *)pview<double>(ctx, ctx->cur).w;
+  if (n) {
+    CK(cudaMemcpyAsync(ids.data(), id_src, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    if (ctx->K.weighted)
+      CK(cudaMemcpyAsync(wb.data(), w_src, n * ctx->rsz, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  long long live = 0;
+  for (long long i = 0; i < n; ++i) live += ids[i] != hpic::kDead;
+  *n_out = live;
+  if (live > cap) return fail(ctx, HPIC_EINVAL, "output capacity below the live particle count");
+  long long m = 0;
+  for (long long i = 0; i < n; ++i) {
+    if (ids[i] == hpic::kDead) continue;
+    double v = ctx->K.w;
+    if (ctx->K.weighted)
+      v = ctx->fp32 ? (double)reinterpret_cast<const float *>(wb.data())[i]
+                    : reinterpret_cast<const double *>(wb.data())[i];
+    if (w) w[m] = v;
+    ++m;
+  }
+  return HPIC_OK;
+}
+
+int hpic_load_weights(hpic_ctx *ctx, int64_t n, const double *w) {
+  if (!ctx || n < 0 || (n > 0 && !w)) return fail(ctx, HPIC_EINVAL, "bad weight arguments");
+  if (!ctx->K.weighted) return fail(ctx, HPIC_ESTATE, "per-electron weights need the Gaussian envelope");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  hpic::Counters h;
+  int rc = read_counters(ctx, &h);
+  if (rc) return rc;
+  if (n > h.n) return fail(ctx, HPIC_EINVAL, "more weights than loaded electrons");
+  for (int64_t i = 0; i < n; ++i)
+    if (!(w[i] > 0) || !std::isfinite(w[i])) return fail(ctx, HPIC_EINVAL, "weights must be positive");
+  if (n == 0) return HPIC_OK;
+  if (ctx->fp32) {
+    std::vector<float> b(w, w + n);
+    CK(cudaMemcpyAsync(pview<float>(ctx, ctx->cur).w, b.data(), n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else {
+    CK(cudaMemcpyAsync(pview<double>(ctx, ctx->cur).w, w, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return HPIC_OK;
 }
 
 int hpic_load_particles(hpic_ctx *ctx, int64_t n, const double *x, const double *y,

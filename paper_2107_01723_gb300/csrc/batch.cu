@@ -106,7 +106,8 @@ hpic::PView<R> pview_all(const hpic_batch *b, int which) {
   v.uy = r + 4 * b->slots;
   v.uz = r + 5 * b->slots;
   v.tau = r + 6 * b->slots;
-  v.id = reinterpret_cast<uint32_t *>(base + 7 * (size_t)b->slots * sizeof(R));
+  v.w = r + 7 * b->slots;
+  v.id = reinterpret_cast<uint32_t *>(base + 8 * (size_t)b->slots * sizeof(R));
   return v;
 }
 
@@ -323,6 +324,9 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
     if (lasers) {
       if (const char *why = hpic::check_laser(lasers[t], targets[t]))
         return bfail(nullptr, HPIC_EINVAL, "laser " + std::to_string(t) + ": " + why);
+      if (lasers[t].envelope != HPIC_ENV_FLAT)
+        return bfail(nullptr, HPIC_EINVAL, "laser " + std::to_string(t) +
+                                               ": batches inject with the flat-top envelope only");
       if (lasers[t].n_macro + spare_slots >= 0xFFFFFFFFll)
         return bfail(nullptr, HPIC_EINVAL, "id space exhausted");
     }
@@ -409,7 +413,7 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
     off = align256(off + bytes);
     return at;
   };
-  const size_t pb = (size_t)slots * (7 * b->rsz + sizeof(uint32_t));
+  const size_t pb = (size_t)slots * (8 * b->rsz + sizeof(uint32_t));
   const size_t o_p0 = take(pb), o_p1 = take(pb);
   const size_t o_eb = take(eb * b->rsz), o_j = take(jv * b->rsz);
   const size_t o_T = take(cells * sizeof(double)), o_eta = take(cells * sizeof(double));

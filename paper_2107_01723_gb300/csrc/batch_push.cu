@@ -244,6 +244,7 @@ k_batch_sort_scatter(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R
     dst.uy[q] = src.uy[ip];
     dst.uz[q] = src.uz[ip];
     dst.tau[q] = src.tau[ip];
+    if (it.K.weighted) dst.w[q] = src.w[ip];
     dst.id[q] = src.id[ip];
   }
 }

@@ -75,6 +75,20 @@ struct Consts {
   // RNG
   uint32_t key0, key1, target_index;
   int physics;
+  // Gaussian injection envelope (App. B): per_cell electrons in each of the
+  // n_inj_cells cells of inj_cells while g = exp(-g_c (s + 1/2 - t_pk)^2) >=
+  // g_min (s in steps); weight inj_unit sqrt(f g), mean energy T_hot sqrt(f g)
+  int weighted;   // electrons carry their own weight
+  int moore;      // Moore-scaling cap on the cone half-angle
+  long long per_cell, n_inj_cells;
+  double g_c, t_pk, g_min, inj_unit;
+  const void *inj_cells;
+};
+
+// one injecting face cell: indices and sqrt(f(r)) at its centre
+struct InjCell {
+  int j, k;
+  double sf;
 };
 
 enum {

@@ -43,6 +43,7 @@ struct hpic_ctx {
   double *T = nullptr, *eta = nullptr, *H = nullptr;
   void *eta_r = nullptr;  // FP32 copy of eta read by the FP32 field solve (mixed precision)
   double *Ti = nullptr;   // ion temperature
+  void *inj_cells = nullptr;  // InjCell list of the Gaussian envelope
   void *Fsig = nullptr;   // F_sigma per cell, in the particle precision
   // tallies and tables
   double *tal = nullptr, *hist = nullptr, *history = nullptr, *scratch = nullptr;
@@ -77,7 +78,8 @@ inline hpic::PView<R> pview(const hpic_ctx *c, int which) {
   v.uy = r + 4 * c->stride;
   v.uz = r + 5 * c->stride;
   v.tau = r + 6 * c->stride;
-  v.id = reinterpret_cast<uint32_t *>(b + 7 * s) + c->poff;
+  v.w = r + 7 * c->stride;
+  v.id = reinterpret_cast<uint32_t *>(b + 8 * s) + c->poff;
   return v;
 }
 

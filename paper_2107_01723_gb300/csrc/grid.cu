@@ -213,6 +213,7 @@ k_sort_scatter(const Consts K, PView<R> src, PView<R> dst, const Counters *cnt,
     dst.uy[q] = src.uy[ip];
     dst.uz[q] = src.uz[ip];
     dst.tau[q] = src.tau[ip];
+    if (K.weighted) dst.w[q] = src.w[ip];
     dst.id[q] = src.id[ip];
   }
 }
@@ -272,7 +273,7 @@ k_live_energy(const Consts K, PView<R> p, const Counters *cnt, double *dst) {
     if (p.id[ip] == kDead) continue;
     const double ux = p.ux[ip], uy = p.uy[ip], uz = p.uz[ip];
     const double u2 = ux * ux + uy * uy + uz * uz;
-    e += K.w * u2 / (1.0 + sqrt(1.0 + u2));
+    e += (K.weighted ? (double)p.w[ip] : K.w) * u2 / (1.0 + sqrt(1.0 + u2));
   }
   const double v[1] = {e};
   const int slot[1] = {0};

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "common.cuh"
 #include "hpic.h"
 
@@ -12,6 +14,7 @@ namespace hpic {
 template <typename R>
 struct PView {
   R *x, *y, *z, *ux, *uy, *uz, *tau;
+  R *w;  // per-electron weight (read only when Consts::weighted)
   uint32_t *id;
 };
 
@@ -74,6 +77,8 @@ void fold(const hpic_target_desc &t, const hpic_run_params &r, const hpic_laser_
 double eta_of(const Consts &K, double T);
 // F_sigma of App. B at ion temperature Ti (K)
 double fsigma_of(const Consts &K, double Ti);
+// the injecting face cells of a Gaussian-envelope laser (empty otherwise)
+std::vector<InjCell> injection_cells(const hpic_target_desc &t, const hpic_laser_desc &l);
 
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,

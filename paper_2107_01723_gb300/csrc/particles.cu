@@ -56,10 +56,51 @@ k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__rest
 // ---------------------------------------------------------------- injection
 // Eq. (B1) with flat-top envelopes: step s < S injects floor((s+1)N/S) -
 // floor(sN/S) electrons (inject_one places each).
+// Gaussian envelope (App. B): per_cell electrons in each injecting face cell
+// while g(t) >= g_min, each of weight inj_unit sqrt(f g) and local mean
+// energy a0 sqrt(f g) m_e c^2; ids run cell by cell in the cells' order.
+template <typename R>
+__device__ void inject_gauss(const Consts &K, PView<R> p, Counters *cnt, long long cap,
+                             TallyView tv, double *smem) {
+  const long long st = cnt->step;
+  const double tm = (double)st + 0.5 - K.t_pk;
+  const double g = exp(-K.g_c * tm * tm);
+  const long long c = g >= K.g_min ? K.per_cell * K.n_inj_cells : 0;
+  const long long n0 = cnt->n, id0 = cnt->next_id;
+  const uint32_t step = (uint32_t)st;
+  const double sg = sqrt(g);
+  const InjCell *cells = static_cast<const InjCell *>(K.inj_cells);
+  double e_inj = 0.0, w_inj = 0.0, n_inj = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < c;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long q = n0 + i;
+    if (q >= cap) {
+      atomicOr(&cnt->flags, 1u);
+      continue;
+    }
+    const InjCell ic = cells[i / K.per_cell];
+    const double sfg = ic.sf * sg;
+    const R w = R(K.inj_unit * sfg);
+    const R eps = inject_cell_one(K, p, q, (uint32_t)(id0 + i), step, ic.j, ic.k, R(K.T_hot * sfg));
+    p.w[q] = w;
+    e_inj += (double)w * (double)eps;
+    w_inj += (double)w;
+    n_inj += 1.0;
+  }
+  const double v[3] = {e_inj, w_inj, n_inj};
+  const int slot[3] = {T_E_INJ, T_N_INJ, T_N_INJECTED};
+  block_flush<3>(v, slot, tv.tal, smem);
+  if (blockIdx.x == 0 && threadIdx.x == 0) cnt->inj_cnt = c;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_inject(const Consts K, PView<R> p, Counters *cnt, long long cap, TallyView tv) {
   __shared__ double smem[3 * 32];
+  if (K.weighted) {
+    inject_gauss(K, p, cnt, cap, tv, smem);
+    return;
+  }
   const long long st = cnt->step;
   if (st >= K.n_inj_steps) return;
   const long long S = K.n_inj_steps, N = K.n_macro;
@@ -118,6 +159,7 @@ k_seed(const Consts K, PView<R> p, Counters *cnt, long long cap, long long count
     p.uy[q] = un * st * cp;
     p.uz[q] = un * st * sp;
     p.tau[q] = -m_log(R(1) - unif<R>(b.c));
+    if (K.weighted) p.w[q] = R(K.w);
     p.id[q] = id;
     e_inj += K.w * (double)eps;
     n_inj += 1.0;

@@ -173,7 +173,7 @@ struct StepCtx {
 template <typename R>
 __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const Grid<R> &g,
                                         const R *__restrict__ tab, const TallyView &tv,
-                                        const StepCtx &sc, uint32_t id, R &X, R &Y, R &Zc,
+                                        const StepCtx &sc, uint32_t id, R w, R &X, R &Y, R &Zc,
                                         R &ux, R &uy, R &uz, R &tau, Acc<R> &acc, R &heat_out,
                                         int &heat_cell) {
   const int nx = K.nx, ny = K.ny, nz = K.nz;
@@ -206,13 +206,13 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     uz = mz + (qx * sy_ - qy * sx) + R(0.5) * Ez;
   }
   R eps = kinetic(ux, uy, uz);
-  acc.W += h.w * (eps0 - eps);
+  acc.W += w * (eps0 - eps);
   R heat = 0;
   bool alive = true;
 
   // ---- tracking cut and ionisation drag, Eq. (5)
   if (eps < h.E_cut) {
-    heat += h.w * eps;
+    heat += w * eps;
     alive = false;
   } else if (K.physics & P_DRAG) {
     const R gam = R(1) + eps;
@@ -224,12 +224,12 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     const R de = h.K_ion / beta * br;
     const R eps1 = eps - de;
     if (eps1 < h.E_cut) {
-      heat += h.w * eps;
+      heat += w * eps;
       alive = false;
     } else {
       const R s = u_of_eps(eps1) / m_sqrt(ux * ux + uy * uy + uz * uz);
       ux *= s; uy *= s; uz *= s;
-      heat += h.w * de;
+      heat += w * de;
       eps = eps1;
     }
   }
@@ -275,7 +275,8 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
       else if (k >= h.tE_max) row = K.n_E + 1;
       else row = min(max(1 + (int)m_floor(h.inv_dlogE * m_log(k / h.tE_min)), 1), K.n_E);
       const int col = min(max((int)m_floor(th * h.th_scale), 0), K.n_th - 1);
-      const double wph = K.w * K.inv_boost;
+      // photon weight: the electron's own, or the shared FP64 weight exactly
+      const double wph = (K.weighted ? (double)w : K.w) * K.inv_boost;
       const double ek = wph * (double)k;
       const int hb = row * K.n_th + col;
       atomicAdd(tv.hist + hb, ek);
@@ -289,7 +290,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
       tau = -m_log(R(1) - unif<R>(r1.d));
       eps -= k * h.inv_boost;
       if (eps < h.E_cut) {
-        heat += h.w * eps;
+        heat += w * eps;
         alive = false;
       } else {
         const R s = u_of_eps(eps) / un;
@@ -317,7 +318,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     if (unbounded || (pos[a] >= R(0) && pos[a] <= L)) continue;
     const R e_out = kinetic(u[0], u[1], u[2]);
     if (e_out >= h.eps_esc) {
-      acc.esc += (double)(h.w * e_out);
+      acc.esc += (double)(w * e_out);
       ++acc.n_esc;
       return false;
     }
@@ -327,7 +328,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     const R un = m_sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     const R un2 = un - h.du_reflux;
     if (un2 <= R(0)) {
-      acc.ref += (double)(h.w * e_out);
+      acc.ref += (double)(w * e_out);
       ++acc.n_refabs;
       return false;
     }
@@ -342,7 +343,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     if (low && d[a] < R(0)) d[a] = -d[a];
     if (!low && d[a] > R(0)) d[a] = -d[a];
     u[0] = un2 * d[0]; u[1] = un2 * d[1]; u[2] = un2 * d[2];
-    acc.ref += (double)(h.w * (e_out - kinetic(u[0], u[1], u[2])));
+    acc.ref += (double)(w * (e_out - kinetic(u[0], u[1], u[2])));
     ++acc.n_ref;
   }
   X = pos[0]; Y = pos[1]; Zc = pos[2];
@@ -479,8 +480,8 @@ __device__ __forceinline__ void frame_component(const Grid<R> &g, int c, const R
 
 // current J += w (u/gamma) S(x) at x^{n+1} for the lanes with dep set
 template <typename R>
-__device__ __forceinline__ void warp_current(const Consts &K, const HotK<R> &h, const Grid<R> &g,
-                                             bool dep, R X, R Y, R Zc, R ux, R uy, R uz) {
+__device__ __forceinline__ void warp_current(const Consts &K, const Grid<R> &g, bool dep, R w,
+                                             R X, R Y, R Zc, R ux, R uy, R uz) {
   const int lane = threadIdx.x & 31;
   Slots<R> wx{}, wy{}, wz{};
   R vx = R(0), vy = R(0), vz = R(0);
@@ -491,9 +492,9 @@ __device__ __forceinline__ void warp_current(const Consts &K, const HotK<R> &h, 
     wx = slots_of(bx);
     wy = slots_of(by);
     wz = slots_of(bz);
-    vx = h.w * ux * ig;
-    vy = h.w * uy * ig;
-    vz = h.w * uz * ig;
+    vx = w * ux * ig;
+    vy = w * uy * ig;
+    vz = w * uz * ig;
     key = (uint32_t)(bx.iN + K.nx * (by.iN + K.ny * bz.iN));
   }
   const uint32_t c = warp_sort32((key << 5) | (uint32_t)lane);
@@ -532,7 +533,7 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
                                           bool in_range, Acc<R> &acc) {
   bool live = false, dep = false;
   uint32_t id = kDead;
-  R X = 0, Y = 0, Zc = 0, ux = 0, uy = 0, uz = 0, tau = 0, heat = 0;
+  R X = 0, Y = 0, Zc = 0, ux = 0, uy = 0, uz = 0, tau = 0, heat = 0, w = h.w;
   int heat_cell = -1;
   if (in_range) {
     id = ld_stream(p.id + ip);
@@ -540,6 +541,7 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
       X = ld_stream(p.x + ip); Y = ld_stream(p.y + ip); Zc = ld_stream(p.z + ip);
       ux = ld_stream(p.ux + ip); uy = ld_stream(p.uy + ip); uz = ld_stream(p.uz + ip);
       tau = ld_stream(p.tau + ip);
+      if (K.weighted) w = ld_stream(p.w + ip);  // uniform over the launch
       if (isfinite(X) && isfinite(Y) && isfinite(Zc) && isfinite(ux) && isfinite(uy) &&
           isfinite(uz) && isfinite(tau)) {
         live = true;
@@ -551,7 +553,7 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
   }
   if (live) {
     ++acc.n_steps;
-    dep = advance(K, h, g, tab, tv, sc, id, X, Y, Zc, ux, uy, uz, tau, acc, heat, heat_cell);
+    dep = advance(K, h, g, tab, tv, sc, id, w, X, Y, Zc, ux, uy, uz, tau, acc, heat, heat_cell);
     if (dep) {
       st_stream(p.x + ip, X); st_stream(p.y + ip, Y); st_stream(p.z + ip, Zc);
       st_stream(p.ux + ip, ux); st_stream(p.uy + ip, uy); st_stream(p.uz + ip, uz);
@@ -562,7 +564,7 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
   }
   if (!(K.physics & P_UNBOUNDED)) {  // uniform over the warp
     warp_heat(g, heat, heat != R(0) ? heat_cell : -1);
-    warp_current(K, h, g, dep, X, Y, Zc, ux, uy, uz);
+    warp_current(K, g, dep, w, X, Y, Zc, ux, uy, uz);
   }
 }
 
@@ -571,6 +573,21 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
 // disc, kinetic energy exponential with mean a0 m_e c^2 (App. B), direction
 // uniform in solid angle inside the cone about +x, fresh optical depth.
 // Returns its kinetic energy (m_e c^2).
+// 1 - cos of the cone half-angle for an electron of kinetic energy eps
+// (m_e c^2): the laser's, or with the Moore cap the smaller of it and
+// atan(sqrt(2/(gamma - 1))), whose 1 - cos is written without cancellation
+// as (2/(gamma + 1)) / (1 + sqrt((gamma - 1)/(gamma + 1)))
+template <typename R>
+__device__ __forceinline__ R cone_omc(const Consts &K, R eps) {
+  R omc = R(K.omc_cone);
+  if (K.moore) {
+    const R gp = R(2) + eps;  // gamma + 1
+    const R m = (R(2) / gp) / (R(1) + m_sqrt(eps / gp));
+    omc = m < omc ? m : omc;
+  }
+  return omc;
+}
+
 template <typename R>
 __device__ __forceinline__ R inject_one(const Consts &K, const PView<R> &p, long long q,
                                         uint32_t id, uint32_t step) {
@@ -580,7 +597,7 @@ __device__ __forceinline__ R inject_one(const Consts &K, const PView<R> &p, long
   R sp, cp;
   m_sincos2pi(unif<R>(r8.b), &sp, &cp);
   const R eps = -R(K.T_hot) * m_log(R(1) - unif<R>(r8.c));
-  const R omc = unif<R>(r8.d) * R(K.omc_cone);  // 1 - cos(theta)
+  const R omc = unif<R>(r8.d) * cone_omc(K, eps);  // 1 - cos(theta)
   const R ct = R(1) - omc;
   const R stt = m_sqrt(omc * (R(2) - omc));
   R sc, cc;
@@ -589,6 +606,33 @@ __device__ __forceinline__ R inject_one(const Consts &K, const PView<R> &p, long
   p.x[q] = R(1e-6);
   p.y[q] = R(K.spot_y) + rr * cp;
   p.z[q] = R(K.spot_z) + rr * sp;
+  p.ux[q] = un * ct;
+  p.uy[q] = un * stt * cc;
+  p.uz[q] = un * stt * sc;
+  p.tau[q] = -m_log(R(1) - unif<R>(r9.b));
+  p.id[q] = id;
+  return eps;
+}
+
+// One electron of the Gaussian envelope (App. B) in face cell (j, k): uniform
+// over the cell's face at x = 1e-6 cells, kinetic energy exponential with the
+// local mean `mean` (m_e c^2), direction uniform in the (capped) cone; the
+// caller stores its weight.  Returns its kinetic energy.
+template <typename R>
+__device__ __forceinline__ R inject_cell_one(const Consts &K, const PView<R> &p, long long q,
+                                             uint32_t id, uint32_t step, int j, int k, R mean) {
+  const U4 r8 = philox10(step, id, 8u, K.target_index, K.key0, K.key1);
+  const U4 r9 = philox10(step, id, 9u, K.target_index, K.key0, K.key1);
+  const R eps = -mean * m_log(R(1) - unif<R>(r8.c));
+  const R omc = unif<R>(r8.d) * cone_omc(K, eps);
+  const R ct = R(1) - omc;
+  const R stt = m_sqrt(omc * (R(2) - omc));
+  R sc, cc;
+  m_sincos2pi(unif<R>(r9.a), &sc, &cc);
+  const R un = u_of_eps(eps);
+  p.x[q] = R(1e-6);
+  p.y[q] = R(j) + unif<R>(r8.a);
+  p.z[q] = R(k) + unif<R>(r8.b);
   p.ux[q] = un * ct;
   p.uy[q] = un * stt * cc;
   p.uz[q] = un * stt * sc;

@@ -82,6 +82,7 @@ hpic::PView<R> view_of(void *const a[8]) {
   v.uz = static_cast<R *>(a[5]);
   v.tau = static_cast<R *>(a[6]);
   v.id = static_cast<uint32_t *>(a[7]);
+  v.w = nullptr;  // weights are not part of this entry point
   return v;
 }
 

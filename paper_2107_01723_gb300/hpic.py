@@ -22,6 +22,7 @@ HPIC_DRAG, HPIC_SCATTER, HPIC_BREM, HPIC_FIELDS, HPIC_FARADAY, HPIC_HEATING = 1,
 HPIC_ALL = 63
 HPIC_UNBOUNDED = 64
 HPIC_FSIGMA, HPIC_EI_EQUIL = 128, 256
+HPIC_ENV_FLAT, HPIC_ENV_GAUSS = 0, 1
 HPIC_BATCH_MAX_TARGETS = 256
 GRID = {"T": 0, "eta": 1, "Ex": 2, "Ey": 3, "Ez": 4, "Bx": 5, "By": 6, "Bz": 7,
         "jx": 8, "jy": 9, "jz": 10, "heat": 11, "Ti": 12}
@@ -45,7 +46,9 @@ class hpic_laser_desc(C.Structure):
     _fields_ = [("I0_Wm2", C.c_double), ("lambda_m", C.c_double), ("eta_l2e", C.c_double),
                 ("spot_radius_m", C.c_double), ("spot_y_m", C.c_double), ("spot_z_m", C.c_double),
                 ("t_inj_s", C.c_double), ("cone_half_angle_rad", C.c_double),
-                ("n_macro", C.c_int64)]
+                ("n_macro", C.c_int64), ("envelope", C.c_int32), ("per_cell", C.c_int32),
+                ("r_fwhm_m", C.c_double), ("t_fwhm_s", C.c_double), ("f_min", C.c_double),
+                ("g_min", C.c_double), ("moore_cap", C.c_int32), ("pad", C.c_int32)]
 
 
 class hpic_run_params(C.Structure):
@@ -125,6 +128,8 @@ def lib() -> C.CDLL:
             "hpic_count_particles": [vp, _I64P],
             "hpic_read_particles": [vp] + [_DP] * 7 + [_UP, C.c_int64, _I64P],
             "hpic_load_particles": [vp, C.c_int64] + [_DP] * 7 + [_UP],
+            "hpic_read_weights": [vp, _DP, C.c_int64, _I64P],
+            "hpic_load_weights": [vp, C.c_int64, _DP],
             "hpic_get_clock": [vp, _I64P, _I64P],
             "hpic_set_clock": [vp, C.c_int64, C.c_int64],
             "hpic_profile": [vp, C.c_int],
@@ -193,7 +198,10 @@ def target_desc(t: dict) -> hpic_target_desc:
 
 def laser_desc(l: dict) -> hpic_laser_desc:
     return hpic_laser_desc(l["I0"], l["lambda"], l["eta_l2e"], l["spot_r"], l["spot_y"],
-                           l["spot_z"], l["t_inj"], l["cone_half"], int(l["n_macro"]))
+                           l["spot_z"], l["t_inj"], l["cone_half"], int(l["n_macro"]),
+                           int(l.get("envelope", 0)), int(l.get("per_cell", 0)),
+                           l.get("r_fwhm", 0.0), l.get("t_fwhm", 0.0), l.get("f_min", 0.0),
+                           l.get("g_min", 0.0), int(l.get("moore_cap", 0)), 0)
 
 
 def run_params(r: dict, precision: int = HPIC_FP64, sort_interval: int = 0) -> hpic_run_params:
@@ -294,6 +302,19 @@ def hpic_load_particles(h, p: dict) -> None:
     arrs = [np.ascontiguousarray(p[k], dtype=np.float64) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")]
     ids = np.ascontiguousarray(p["id"], dtype=np.uint32)
     _check(lib().hpic_load_particles(h, len(ids), *[_dp(a) for a in arrs], _up(ids)), h)
+
+
+def hpic_read_weights(h) -> np.ndarray:
+    n = C.c_int64()
+    cnt = hpic_count_particles(h)
+    out = np.empty(max(cnt, 1))
+    _check(lib().hpic_read_weights(h, _dp(out), cnt, C.byref(n)), h)
+    return out[:n.value]
+
+
+def hpic_load_weights(h, w) -> None:
+    a = np.ascontiguousarray(w, dtype=np.float64)
+    _check(lib().hpic_load_weights(h, len(a), _dp(a)), h)
 
 
 def hpic_get_clock(h):
@@ -470,6 +491,12 @@ class Target:
 
     def set_particles(self, p: dict) -> None:
         hpic_load_particles(self.h, p)
+
+    def weights(self) -> np.ndarray:
+        return hpic_read_weights(self.h)
+
+    def set_weights(self, w) -> None:
+        hpic_load_weights(self.h, w)
 
     def clock(self):
         return hpic_get_clock(self.h)

@@ -17,6 +17,8 @@ def gpu_from_oracle(osim: O.OracleSim, cfg: dict, precision: int, sort_interval:
     g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=precision,
                  sort_interval=sort_interval)
     g.set_particles(osim.particles())
+    if cfg["laser"].get("envelope", 0) == 1:  # per-electron weights
+        g.set_weights(O.weights(osim))
     for k in GRIDS_STATE:
         g.set_grid(k, osim.grid(k))
     step, nid = osim.clock()

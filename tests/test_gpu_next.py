@@ -111,3 +111,76 @@ def test_equilibration_alone_conserves_fp64():
     inv = t["Zstar"] * Te + Ti
     assert np.allclose(t["Zstar"] * g.grid("T") + g.grid("Ti"), inv, rtol=1e-13, atol=0)
     g.close()
+
+
+# ---------------------------------------------------------------- Gaussian injection envelope
+def gauss_cfg(per_cell=60, seed=4, physics=hpic.HPIC_ALL):
+    t = W.target(n=(16, 12, 12), dx=0.7e-6)
+    las = W.laser_gauss(t, I_Wcm2=1e21, per_cell=per_cell)
+    return {"target": t, "laser": las, "run": W.run(seed=seed, physics=physics, max_history=40)}
+
+
+def assert_weights_close(g, o, tol):
+    gp, ow = g.particles(), O.weights(o)
+    op = o.particles()
+    gi, oi = np.argsort(gp["id"]), np.argsort(op["id"])
+    assert np.array_equal(gp["id"][gi], op["id"][oi])
+    gw = g.weights()[gi]
+    np.testing.assert_allclose(gw, ow[oi], rtol=tol, atol=0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gaussian_injection_first_steps(prec):
+    """Steps 0 and 1 of the paper's envelope: per-cell electrons with their own
+    weights and local mean energies, Moore-capped cones, then the first push."""
+    cfg = gauss_cfg()
+    prec_id, tol, abs_frac = PREC[prec]
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec_id)
+    for _ in range(2):
+        o.step(1)
+        g.step(1)
+        dx = cfg["target"]["dx"]
+        assert_particles_close(g.particles(), o.particles(), tol, dx)
+        assert_weights_close(g, o, tol)
+        ot = o.tallies()
+        assert_tallies_close(g.tallies(), ot, tol, abs_frac * ot["E_injected"])
+    assert o.tallies()["n_injected"] > 0
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gaussian_single_step_from_state(prec):
+    """One full step from the oracle's state 12 steps into the envelope
+    (electrons of many weights moving, fields and heating on)."""
+    cfg = gauss_cfg(per_cell=40, seed=8)
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    o.step(12)
+    prec_id, tol, abs_frac = PREC[prec]
+    g = gpu_from_oracle(o, cfg, prec_id)
+    ot0 = o.tallies()
+    o.step(1)
+    g.step(1)
+    dx = cfg["target"]["dx"]
+    assert_particles_close(g.particles(), o.particles(), tol, dx)
+    assert_weights_close(g, o, tol)
+    for f in ("j", "E", "B"):
+        assert_vector_close(g.grid, o.grid, f, tol)
+    assert_cell_scalars_close(g, o, tol)
+    ot = tally_delta(o.tallies(), ot0)
+    assert_tallies_close(g.tallies(), ot, tol, abs_frac * ot0["E_live"])
+    g.close()
+
+
+def test_gaussian_run_tracks_oracle_fp64():
+    cfg = gauss_cfg(per_cell=30, seed=12)
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=hpic.HPIC_FP64, sort_interval=5)
+    o.step(30)
+    g.step(30)
+    dx = cfg["target"]["dx"]
+    assert_particles_close(g.particles(), o.particles(), 1e-9, dx)
+    assert_weights_close(g, o, 1e-12)
+    ot = o.tallies()
+    assert_tallies_close(g.tallies(), ot, 1e-9, 1e-9 * ot["E_injected"])
+    g.close()

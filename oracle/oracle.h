@@ -56,6 +56,12 @@ enum {
   ORC_HEAT = 11, ORC_TI = 12
 };
 
+/* one more element sharing every cell with the target's own (a compound
+ * solid, App. A), at its own ion density */
+typedef struct {
+  double Z, n_i, I_ex, Zstar, A_ion;
+} orc_solid;
+
 typedef struct {
   int32_t nx, ny, nz;
   double dx;          /* cell side (m) */
@@ -69,6 +75,9 @@ typedef struct {
   double lambda2;     /* resistivity multiplier */
   double T0;          /* initial background temperature, electrons and ions (K) */
   double A_ion;       /* ion mass in atomic mass units (e-i equilibration) */
+  int32_t n_extra;    /* further elements of a compound (0..3) */
+  int32_t pad;
+  orc_solid extra[3];
 } orc_target;
 
 typedef struct {
@@ -194,10 +203,14 @@ void orc_model(const orc_model_in *m, orc_model_out *out);
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_uniform(uint32_t x);
 double orc_a0(double I0_Wm2, double lambda_m);
+/* A compound's stopping powers, cross sections, scatter variances and
+ * heat capacities combine its elements as documented in physics.c. */
 double orc_stop_ion(const orc_target *t, double eps_k);   /* J/m */
 double orc_stop_brem(const orc_target *t, double eps_k);  /* J/m, Eq. (4) */
 double orc_dsigma_dk(const orc_target *t, double eps_k, double k); /* m^2/J */
-double orc_sigma_tot(const orc_target *t, double k_min, double eps_k); /* m^2 */
+double orc_sigma_tot(const orc_target *t, double k_min, double eps_k); /* m^2, per target ion */
+/* sum over the elements of n_i sigma_tot (1/m): the emission rate per length */
+double orc_brem_rate(const orc_target *t, double k_min, double eps_k);
 void orc_brem_table(const orc_target *t, double k_min, double E_max, int rows,
                     int cols, double *v);
 double orc_brem_sample(const double *v, int rows, int cols, double k_min,
@@ -205,6 +218,9 @@ double orc_brem_sample(const double *v, int rows, int cols, double k_min,
 double orc_davies_sigma(const orc_target *t, double p_SI, double dt); /* rad */
 double orc_photon_theta(double gamma, double u);
 double orc_heat_capacity(double T_K, double Z);
+/* the temperature rise of Eq. (A7) for a deposited energy density rho
+ * (J/m^3); a compound uses sum Z n_i and the n_e-weighted mean of 1/C */
+double orc_temperature_rise(const orc_target *t, double T_K, double rho);
 double orc_resistivity(const orc_target *t, double T_K);
 /* F_sigma of the bremsstrahlung cross section at ion temperature T_i (K) */
 double orc_f_sigma(const orc_target *t, double Ti_K);

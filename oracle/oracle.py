@@ -40,12 +40,17 @@ def build(force: bool = False) -> str:
     return LIB_PATH
 
 
+class Solid(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("Z", "n_i", "I_ex", "Zstar", "A_ion")]
+
+
 class Target(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("dx", C.c_double), ("Z", C.c_double), ("n_i", C.c_double),
                 ("I_ex", C.c_double), ("Zstar", C.c_double), ("lnLambda", C.c_double),
                 ("eta_max", C.c_double), ("lambda1", C.c_double), ("lambda2", C.c_double),
-                ("T0", C.c_double), ("A_ion", C.c_double)]
+                ("T0", C.c_double), ("A_ion", C.c_double), ("n_extra", C.c_int32),
+                ("pad", C.c_int32), ("extra", Solid * 3)]
 
 
 class ModelIn(C.Structure):
@@ -152,6 +157,8 @@ def lib():
         L.orc_photon_theta.argtypes = [C.c_double, C.c_double]
         L.orc_heat_capacity.restype = C.c_double
         L.orc_heat_capacity.argtypes = [C.c_double, C.c_double]
+        L.orc_temperature_rise.restype = C.c_double
+        L.orc_temperature_rise.argtypes = [tp, C.c_double, C.c_double]
         L.orc_resistivity.restype = C.c_double
         L.orc_resistivity.argtypes = [tp, C.c_double]
         L.orc_f_sigma.restype = C.c_double
@@ -175,7 +182,13 @@ def _up(a: np.ndarray):
 
 
 def make_target(d: dict) -> Target:
-    return Target(**d)
+    d = dict(d)
+    extra = d.pop("extra", [])
+    t = Target(**d)
+    t.n_extra = len(extra)
+    for i, e in enumerate(extra):
+        t.extra[i] = Solid(e["Z"], e["n_i"], e["I_ex"], e["Zstar"], e["A_ion"])
+    return t
 
 
 def make_laser(d: dict) -> Laser:
@@ -353,6 +366,10 @@ def photon_theta(gamma: float, u: float) -> float:
 
 def heat_capacity(T_K: float, Z: float) -> float:
     return lib().orc_heat_capacity(T_K, Z)
+
+
+def temperature_rise(target: dict, T_K: float, rho: float) -> float:
+    return lib().orc_temperature_rise(C.byref(make_target(target)), T_K, rho)
 
 
 def resistivity(target: dict, T_K: float) -> float:

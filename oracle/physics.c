@@ -69,11 +69,37 @@ double orc_a0(double I0_Wm2, double lambda_m) {
   return 8.5e-6 * sqrt(I0_Wm2 * lambda_m * lambda_m);
 }
 
+/* ---------------- compounds ----------------
+ * App. A: several elements may share every cell (a compound solid such as
+ * plastic).  The paper prints the rule for the heating only: n_e = Z n_i is
+ * replaced by the sum over the elements and 1/C by its n_e-weighted mean, so
+ * that two overlapping solids of one material behave as the single solid.
+ * For the rest the readings are the usual mixture rules: ionisation
+ * stopping powers and bremsstrahlung rates (n_i sigma) add (Bragg's rule),
+ * Davies scatter variances add, and the resistivity of Eqs. (A4)-(A6) takes
+ * the free-electron density sum Z* n_i, the e-i collision density sum
+ * Z*^2 n_i and the total ion density for the ion-sphere radius. */
+static int n_solids(const orc_target *t) { return 1 + t->n_extra; }
+
+/* element s of the target as a single-element target */
+static orc_target solid(const orc_target *t, int s) {
+  orc_target o = *t;
+  o.n_extra = 0;
+  if (s > 0) {
+    o.Z = t->extra[s - 1].Z;
+    o.n_i = t->extra[s - 1].n_i;
+    o.I_ex = t->extra[s - 1].I_ex;
+    o.Zstar = t->extra[s - 1].Zstar;
+    o.A_ion = t->extra[s - 1].A_ion;
+  }
+  return o;
+}
+
 /* ---------------- stopping powers ---------------- */
 /* Eq. (5), Sec. III.B: continuous ionisation stopping power (J/m) for an
  * electron of kinetic energy eps_k.  The bracket is held at >= 0 (it is
  * positive for every energy above the tracking cut). */
-double orc_stop_ion(const orc_target *t, double eps_k) {
+static double stop_ion_1(const orc_target *t, double eps_k) {
   double mc2 = M_E * C_L * C_L;
   double gamma = 1.0 + eps_k / mc2;
   double beta2 = 1.0 - 1.0 / (gamma * gamma);
@@ -85,6 +111,15 @@ double orc_stop_ion(const orc_target *t, double eps_k) {
   return pref * bracket;
 }
 
+double orc_stop_ion(const orc_target *t, double eps_k) {
+  double s = stop_ion_1(t, eps_k);
+  for (int q = 1; q < n_solids(t); ++q) {
+    orc_target o = solid(t, q);
+    s += stop_ion_1(&o, eps_k);
+  }
+  return s;
+}
+
 /* the screening logarithm of Eq. (4) */
 static double brem_log(double Z) {
   return log(5.6 * PI * EPS0 * HBAR * C_L / (cbrt(Z) * Q_E * Q_E));
@@ -92,10 +127,19 @@ static double brem_log(double Z) {
 
 /* Eq. (4), Sec. III.B: bremsstrahlung stopping power over all photon
  * energies (J/m). */
-double orc_stop_brem(const orc_target *t, double eps_k) {
+static double stop_brem_1(const orc_target *t, double eps_k) {
   double gamma = 1.0 + eps_k / (M_E * C_L * C_L);
   return gamma * pow(Q_E, 6) * t->n_i * t->Z * t->Z * brem_log(t->Z) /
          (12.0 * PI * PI * PI * pow(EPS0, 3) * M_E * pow(C_L, 3) * HBAR);
+}
+
+double orc_stop_brem(const orc_target *t, double eps_k) {
+  double s = stop_brem_1(t, eps_k);
+  for (int q = 1; q < n_solids(t); ++q) {
+    orc_target o = solid(t, q);
+    s += stop_brem_1(&o, eps_k);
+  }
+  return s;
 }
 
 /* ---------------- bremsstrahlung cross section ----------------
@@ -121,10 +165,17 @@ static double shape_G(double u0, double u) {
   return (4.0 / 3.0) * (log(u / u0) - (u - u0)) + 0.5 * (u * u - u0 * u0);
 }
 
-/* total cross section for photons k_min <= k <= eps_k (m^2) */
+/* total cross section for photons k_min <= k <= eps_k (m^2, per ion of the
+ * target's own element; a compound's is its emission rate over that n_i) */
 double orc_sigma_tot(const orc_target *t, double k_min, double eps_k) {
   if (eps_k <= k_min) return 0.0;
   return brem_C(t, eps_k) * shape_G(k_min / eps_k, 1.0);
+}
+
+/* emission rate per unit length, the sum of n_i sigma_tot over the elements
+ * (the photon spectrum's shape s(k/eps)/k is the same for every element) */
+double orc_brem_rate(const orc_target *t, double k_min, double eps_k) {
+  return t->n_i * orc_sigma_tot(t, k_min, eps_k);
 }
 
 /* Inverse-CDF table.  Row i is the electron energy
@@ -195,12 +246,20 @@ double orc_photon_theta(double gamma, double u) {
 /* ---------------- elastic scatter ---------------- */
 /* Eq. (B4), App. B (Davies): rms polar deflection over dt for momentum p
  * (SI).  The logarithm is held at >= 0. */
-double orc_davies_sigma(const orc_target *t, double p, double dt) {
+static double davies_var_1(const orc_target *t, double p, double dt) {
   double gamma = sqrt(1.0 + (p / (M_E * C_L)) * (p / (M_E * C_L)));
   double lg = log(4.0 * EPS0 * H_PL * p / (cbrt(t->Z) * M_E * Q_E * Q_E));
   if (lg < 0.0) lg = 0.0;
-  double var = t->Z * t->Z * pow(Q_E, 4) * t->n_i * gamma * M_E /
-               (2.0 * PI * EPS0 * EPS0 * p * p * p) * lg * dt;
+  return t->Z * t->Z * pow(Q_E, 4) * t->n_i * gamma * M_E /
+         (2.0 * PI * EPS0 * EPS0 * p * p * p) * lg * dt;
+}
+
+double orc_davies_sigma(const orc_target *t, double p, double dt) {
+  double var = davies_var_1(t, p, dt);
+  for (int q = 1; q < n_solids(t); ++q) {
+    orc_target o = solid(t, q);
+    var += davies_var_1(&o, p, dt);
+  }
   return sqrt(var);
 }
 
@@ -211,22 +270,42 @@ double orc_heat_capacity(double T_K, double Z) {
   return 0.3 + 1.2 * Tp * (2.2 + Tp) / ((1.1 + Tp) * (1.1 + Tp));
 }
 
+/* Eq. (A7): dT = rho / (Z n_i C k_B); a compound replaces Z n_i by the sum
+ * of n_e = Z n_i over its elements and 1/C by its n_e-weighted mean */
+double orc_temperature_rise(const orc_target *t, double T_K, double rho) {
+  if (t->n_extra == 0) return rho / (t->Z * t->n_i * orc_heat_capacity(T_K, t->Z) * K_B);
+  double ne = 0.0, inv_c = 0.0;
+  for (int q = 0; q < n_solids(t); ++q) {
+    orc_target o = solid(t, q);
+    double n = o.Z * o.n_i;
+    ne += n;
+    inv_c += n / orc_heat_capacity(T_K, o.Z);
+  }
+  return rho * (inv_c / ne) / (ne * K_B);
+}
+
 /* Eqs. (A4)-(A6), App. A: reduced Lee-More resistivity.  tauA is the larger
  * of the hot (A5) and cold (A6) limits; the cold limit is dropped when
  * lambda1 = 0; the result is multiplied by lambda2 and capped at eta_max. */
 double orc_resistivity(const orc_target *t, double T_K) {
   double kT = K_B * T_K;
+  double ne = 0.0, nz2 = 0.0, ni = 0.0;  /* sum Z* n_i, sum Z*^2 n_i, sum n_i */
+  for (int q = 0; q < n_solids(t); ++q) {
+    orc_target o = solid(t, q);
+    ne += o.Zstar * o.n_i;
+    nz2 += o.Zstar * o.Zstar * o.n_i;
+    ni += o.n_i;
+  }
   double tau_hot = 128.0 * PI * EPS0 * EPS0 / (3.0 * pow(Q_E, 4)) *
-                   sqrt(M_E / (2.0 * PI)) * pow(kT, 1.5) /
-                   (t->Zstar * t->Zstar * t->n_i * t->lnLambda);
+                   sqrt(M_E / (2.0 * PI)) * pow(kT, 1.5) / (nz2 * t->lnLambda);
   double tau = tau_hot;
   if (t->lambda1 > 0.0) {
-    double R0 = cbrt(3.0 / (4.0 * PI * t->n_i));
+    double R0 = cbrt(3.0 / (4.0 * PI * ni));
     double vbar = sqrt(3.0 * kT / M_E);
     double tau_cold = R0 / vbar * t->lambda1;
     if (tau_cold > tau) tau = tau_cold;
   }
-  double eta = t->lambda2 * M_E / (t->Zstar * t->n_i * Q_E * Q_E * tau);
+  double eta = t->lambda2 * M_E / (ne * Q_E * Q_E * tau);
   if (eta > t->eta_max) eta = t->eta_max;
   return eta;
 }

@@ -231,9 +231,9 @@ static void particle_update(orc_sim *s, int64_t ip) {
   if ((r->physics & ORC_BREM) && eps > r->k_min) {
     double gam = 1.0 + eps / MC2;
     double beta = sqrt(1.0 - 1.0 / (gam * gam));
-    double sig = orc_sigma_tot(t, r->k_min, eps);
-    if (r->physics & ORC_FSIGMA) sig *= orc_f_sigma(t, s->g[ORC_TI][cell]);
-    s->tau[ip] -= t->n_i * r->brem_boost * sig * beta * C_L * dt;
+    double rate = orc_brem_rate(t, r->k_min, eps);  /* sum n_i sigma (1/m) */
+    if (r->physics & ORC_FSIGMA) rate *= orc_f_sigma(t, s->g[ORC_TI][cell]);
+    s->tau[ip] -= r->brem_boost * rate * beta * C_L * dt;
     if (s->tau[ip] <= 0.0) {
       double R1[4];
       draw(s, s->id[ip], 1, R1);
@@ -395,10 +395,7 @@ static void heating(orc_sim *s) {
           s->tal.E_ohmic_grid += rho_ohm * V;
           rho += rho_ohm;
         }
-        if (s->r.physics & ORC_HEATING) {
-          double C = orc_heat_capacity(T[c], s->t.Z);
-          T[c] += rho / (s->t.Z * s->t.n_i * C * K_B);
-        }
+        if (s->r.physics & ORC_HEATING) T[c] += orc_temperature_rise(&s->t, T[c], rho);
         /* e-i equilibration over the step, rates frozen at the temperatures
          * after the heating: d = T_e - T_i decays as exp(-(a + b) dt) and
          * b T_e + a T_i is kept (a = rate_e, b = rate_i) */

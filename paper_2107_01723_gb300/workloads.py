@@ -26,6 +26,9 @@ MATERIALS = {
     "Al": {"Z": 13.0, "n_i": 6.03e28, "Zstar": 3.0, "A": 26.982},
     "Cu": {"Z": 29.0, "n_i": 8.49e28, "Zstar": 1.0, "A": 63.546},
     "Au": {"Z": 79.0, "n_i": 5.9e28, "Zstar": 1.0, "A": 196.967},
+    # the elements of CH plastic (1.05 g/cm^3: 4.86e28 m^-3 of each)
+    "C": {"Z": 6.0, "n_i": 4.86e28, "Zstar": 1.0, "A": 12.011},
+    "H": {"Z": 1.0, "n_i": 4.86e28, "Zstar": 1.0, "A": 1.008},
 }
 
 
@@ -36,7 +39,29 @@ def target(n=(32, 32, 32), dx=1e-6, material="Au", T0_eV=1.0, eta_max=1e-6,
             "Z": m["Z"], "n_i": m["n_i"], "I_ex": 11.0 * EV * m["Z"],
             "Zstar": m["Zstar"], "lnLambda": lnLambda, "eta_max": eta_max,
             "lambda1": lambda1, "lambda2": lambda2, "T0": T0_eV * KELVIN_PER_EV,
-            "A_ion": m["A"]}
+            "A_ion": m["A"], "n_extra": 0, "pad": 0, "extra": []}
+
+
+def element(material: str, n_i=None) -> dict:
+    """One element of a compound (App. A) at its ion density (m^-3)."""
+    m = MATERIALS[material]
+    return {"Z": m["Z"], "n_i": float(m["n_i"] if n_i is None else n_i), "I_ex": 11.0 * EV * m["Z"],
+            "Zstar": m["Zstar"], "A_ion": m["A"]}
+
+
+def compound(parts, n=(32, 32, 32), dx=1e-6, T0_eV=1.0, eta_max=1e-6, lnLambda=2.0,
+             lambda1=0.0, lambda2=1.0) -> dict:
+    """A compound solid filling the box: parts = [(material, n_i or None), ...];
+    the first is the target's own element, the rest (up to three) share
+    every cell with it."""
+    mat0, n0 = parts[0]
+    t = target(n=n, dx=dx, material=mat0, T0_eV=T0_eV, eta_max=eta_max, lnLambda=lnLambda,
+               lambda1=lambda1, lambda2=lambda2)
+    if n0 is not None:
+        t["n_i"] = float(n0)
+    t["extra"] = [element(m, ni) for m, ni in parts[1:]]
+    t["n_extra"] = len(t["extra"])
+    return t
 
 
 ENV_FLAT, ENV_GAUSS = 0, 1

@@ -892,3 +892,51 @@ def test_moore_cone_cap():
     frac = omc / (1 - np.cos(cap))
     assert st.kstest(frac, "uniform").pvalue > 1e-3
     assert np.mean(cap < math.radians(20)) > 0.05  # the Moore limit binds for hot electrons
+
+
+# ---------------------------------------------------------------- compound solids (App. A)
+def test_two_overlapping_solids_behave_as_one():
+    """App. A: two overlapping solids of one material behave as the single
+    solid: gold at n_i against gold at n_i/2 plus gold at n_i/2, 25 steps of
+    the whole method (drag, scatter, emission, fields, heating)."""
+    assert "same material" in GOLD["compound_same_material"]["statement"]
+    cfg = W.config_small(n=(8, 7, 9), n_macro=1500, steps=25, I_Wcm2=1e21, spot_r=2e-6)
+    one = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    half = cfg["target"]["n_i"] / 2
+    two_t = W.compound([("Au", half), ("Au", half)], n=(8, 7, 9))
+    two = O.OracleSim(two_t, cfg["laser"], cfg["run"])
+    one.step(25)
+    two.step(25)
+    p1, p2 = one.particles(), two.particles()
+    assert np.array_equal(p1["id"], p2["id"])
+    for k in ("x", "y", "z", "ux", "uy", "uz", "tau"):
+        np.testing.assert_allclose(p2[k], p1[k], rtol=1e-12, atol=1e-18, err_msg=k)
+    for k in ("T", "eta", "Ex", "Bz", "jx", "heat"):
+        a, b = one.grid(k), two.grid(k)
+        assert np.max(np.abs(a - b)) <= 1e-12 * max(np.abs(a).max(), 1e-300), k
+    t1, t2 = one.tallies(), two.tallies()
+    for k in ("E_injected", "E_drag", "E_xray", "W_field", "E_live", "n_emitted"):
+        assert t2[k] == pytest.approx(t1[k], rel=1e-12), k
+    assert t1["n_emitted"] > 0
+
+
+def test_compound_mixture_rules():
+    """CH plastic: ionisation stopping and bremsstrahlung stopping are the sums
+    over the elements (Bragg's rule), the scatter variance likewise; the
+    temperature rise uses sum Z n_i and the n_e-weighted mean of 1/C, whose
+    cold and hot limits are 1/0.3 and 1/1.5."""
+    ch = W.compound([("C", None), ("H", None)])
+    c = dict(W.target(material="C"), n_i=ch["n_i"])
+    h = dict(W.target(material="H"), n_i=ch["extra"][0]["n_i"])
+    for eps in (0.05 * MEV, 1 * MEV, 30 * MEV):
+        assert O.stop_ion(ch, eps) == pytest.approx(O.stop_ion(c, eps) + O.stop_ion(h, eps), rel=1e-14)
+        assert O.stop_brem(ch, eps) == pytest.approx(O.stop_brem(c, eps) + O.stop_brem(h, eps), rel=1e-14)
+        p = math.sqrt((eps / MC2) * (eps / MC2 + 2)) * sc.m_e * sc.c
+        s2 = O.davies_sigma(c, p, 1e-15) ** 2 + O.davies_sigma(h, p, 1e-15) ** 2
+        assert O.davies_sigma(ch, p, 1e-15) ** 2 == pytest.approx(s2, rel=1e-13)
+    ne = 6 * ch["n_i"] + 1 * ch["extra"][0]["n_i"]
+    rho = 1e9
+    cold = O.temperature_rise(ch, 1e-3, rho)
+    assert cold == pytest.approx(rho / (ne * sc.k * 0.3), rel=1e-6)
+    hot = O.temperature_rise(ch, 1e12, rho)
+    assert hot == pytest.approx(rho / (ne * sc.k * 1.5), rel=1e-3)

@@ -94,7 +94,19 @@ enum {
   HPIC_GRID_TI = 12    /* ion temperature (K), cell-centred */
 };
 
-/* One target: a uniform single-element solid filling the box (App. A). */
+/* One more element sharing every cell of a compound target (App. A). */
+typedef struct {
+  double Z, n_i_m3, I_ex_J, Zstar, A_ion;
+} hpic_solid;
+
+/* One target: a uniform solid filling the box (App. A): one element, or a
+ * compound of it and up to three more (n_extra; e.g. CH plastic).  For a
+ * compound the heating of Eq. (A7) uses n_e = sum Z n_i and the n_e-weighted
+ * mean of 1/C (the paper's rule); the ionisation and bremsstrahlung stopping
+ * powers and the emission rate add over the elements, the Davies scatter
+ * variances add, and eta of Eqs. (A4)-(A6) takes sum Z* n_i, sum Z*^2 n_i and
+ * the total ion density.  Compounds do not combine with HPIC_FSIGMA or
+ * HPIC_EI_EQUIL. */
 typedef struct {
   int32_t nx, ny, nz;   /* cells, each >= 2 */
   double dx_m;          /* cell side; must exceed c * dt */
@@ -108,6 +120,9 @@ typedef struct {
   double lambda2;       /* multiplier on eta (App. A) */
   double T0_K;          /* initial background temperature (electrons and ions) */
   double A_ion;         /* ion mass in atomic mass units (e-i equilibration) */
+  int32_t n_extra;      /* further elements of a compound, 0..3 */
+  int32_t pad;
+  hpic_solid extra[3];
 } hpic_target_desc;
 
 /* Laser and injection, Eq. (1), Eq. (B1), Sec. II.B and App. B.

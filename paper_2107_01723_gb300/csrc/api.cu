@@ -148,16 +148,34 @@ void hpic::fold(const hpic_target_desc &t, const hpic_run_params &r, const hpic_
   K.ntk = (t.nz + 3) / 4;
   K.nkeys = (long long)K.nti * K.ntj * K.ntk * 64;
   K.cdt_dx = CL * dt / dx;
-  // Eq. (5): S v dt = Z n_i e^4 dt / (4 pi eps0^2 m_e v) [bracket]
-  K.K_ion = Z * ni * std::pow(QE, 4) * dt / (4.0 * PI * EPS0 * EPS0 * ME * CL) / MC2;
-  K.L_I = std::log(MC2 / t.I_ex_J);
-  // Eq. (B4) with p = m_e c u
-  K.K_sc = Z * Z * std::pow(QE, 4) * ni * dt / (2.0 * PI * EPS0 * EPS0 * ME * ME * std::pow(CL, 3));
-  K.K_lg = 4.0 * EPS0 * HPL * CL / (std::cbrt(Z) * QE * QE);
-  // Eq. (4) per unit gamma; sigma_tot n_i v dt = boost Kb c dt/mc2 * (u/eps) G(u0)
-  const double Lrad = std::log(5.6 * PI * EPS0 * HBAR * CL / (std::cbrt(Z) * QE * QE));
-  const double Kb = std::pow(QE, 6) * ni * Z * Z * Lrad /
-                    (12.0 * PI * PI * PI * std::pow(EPS0, 3) * ME * std::pow(CL, 3) * HBAR);
+  // per element s (0: the target's own, then the compound's extra ones)
+  K.n_solids = 1 + t.n_extra;
+  double Kb = 0.0, ne_tot = 0.0, nz1 = 0.0, nz2 = 0.0, ni_tot = 0.0;
+  for (int s = 0; s < 4; ++s) {
+    K.K_ion[s] = K.L_I[s] = K.K_sc[s] = K.K_lg[s] = K.ne_frac[s] = K.Tp_fac_s[s] = 0.0;
+  }
+  for (int s = 0; s < K.n_solids; ++s) {
+    const double Zs = s ? t.extra[s - 1].Z : Z, ns = s ? t.extra[s - 1].n_i_m3 : ni;
+    const double Is = s ? t.extra[s - 1].I_ex_J : t.I_ex_J, Zss = s ? t.extra[s - 1].Zstar : t.Zstar;
+    // Eq. (5): S v dt = Z n_i e^4 dt / (4 pi eps0^2 m_e v) [bracket]
+    K.K_ion[s] = Zs * ns * std::pow(QE, 4) * dt / (4.0 * PI * EPS0 * EPS0 * ME * CL) / MC2;
+    K.L_I[s] = std::log(MC2 / Is);
+    // Eq. (B4) with p = m_e c u
+    K.K_sc[s] = Zs * Zs * std::pow(QE, 4) * ns * dt / (2.0 * PI * EPS0 * EPS0 * ME * ME * std::pow(CL, 3));
+    K.K_lg[s] = 4.0 * EPS0 * HPL * CL / (std::cbrt(Zs) * QE * QE);
+    // Eq. (4) per unit gamma; the elements' emission rates add
+    const double Lrad = std::log(5.6 * PI * EPS0 * HBAR * CL / (std::cbrt(Zs) * QE * QE));
+    Kb += std::pow(QE, 6) * ns * Zs * Zs * Lrad /
+          (12.0 * PI * PI * PI * std::pow(EPS0, 3) * ME * std::pow(CL, 3) * HBAR);
+    K.ne_frac[s] = Zs * ns;  // normalised below
+    K.Tp_fac_s[s] = (KB / QE) * std::pow(Zs, -4.0 / 3.0);
+    ne_tot += Zs * ns;
+    nz1 += Zss * ns;
+    nz2 += Zss * Zss * ns;
+    ni_tot += ns;
+  }
+  for (int s = 0; s < K.n_solids; ++s) K.ne_frac[s] /= ne_tot;
+  // sigma_tot n_i v dt = boost Kb c dt/mc2 * (u/eps) G(u0)
   K.K_tau = r.brem_boost * Kb * CL * dt / MC2;
   K.k_min = r.k_min_J / MC2;
   K.boost = r.brem_boost;
@@ -181,12 +199,16 @@ void hpic::fold(const hpic_target_desc &t, const hpic_run_params &r, const hpic_
   K.F_ohm = std::pow(QE * CL / (dx * dx * dx), 2) * dt;
   K.F_H = MC2 / (dx * dx * dx);
   K.dx3 = dx * dx * dx;
-  K.heat_den = Z * ni * KB;
+  K.heat_den = K.n_solids == 1 ? Z * ni * KB : ne_tot * KB;
   K.Tp_fac = (KB / QE) * std::pow(Z, -4.0 / 3.0);
-  K.eta_num = t.lambda2 * ME / (t.Zstar * ni * QE * QE);
+  // Eqs. (A4)-(A6); a compound's free-electron density sum Z* n_i, e-i
+  // collision density sum Z*^2 n_i and total ion density
+  K.eta_num = K.n_solids == 1 ? t.lambda2 * ME / (t.Zstar * ni * QE * QE)
+                              : t.lambda2 * ME / (nz1 * QE * QE);
   K.A_hot = 128.0 * PI * EPS0 * EPS0 / (3.0 * std::pow(QE, 4)) * std::sqrt(ME / (2.0 * PI)) /
-            (t.Zstar * t.Zstar * ni * t.lnLambda);
-  K.B_cold = std::cbrt(3.0 / (4.0 * PI * ni)) * t.lambda1 * std::sqrt(ME / 3.0);
+            ((K.n_solids == 1 ? t.Zstar * t.Zstar * ni : nz2) * t.lnLambda);
+  K.B_cold = std::cbrt(3.0 / (4.0 * PI * (K.n_solids == 1 ? ni : ni_tot))) * t.lambda1 *
+             std::sqrt(ME / 3.0);
   K.eta_max = t.eta_max_ohm_m;
   K.lambda1 = t.lambda1;
   // eta = eta_max exactly while tau <= eta_num/eta_max: tau_hot = A_hot (k T)^1.5
@@ -274,6 +296,13 @@ const char *hpic::check_target(const hpic_target_desc &t, const hpic_run_params 
     return "material parameters must be positive";
   if (r.precision != HPIC_FP64 && r.precision != HPIC_FP32_MIXED) return "unknown precision";
   if ((r.physics & HPIC_EI_EQUIL) && !(t.A_ion > 0)) return "e-i equilibration needs A_ion > 0";
+  if (t.n_extra < 0 || t.n_extra > 3) return "a compound has at most three further elements";
+  for (int s = 0; s < t.n_extra; ++s)
+    if (!(t.extra[s].Z > 0) || !(t.extra[s].n_i_m3 > 0) || !(t.extra[s].I_ex_J > 0) ||
+        !(t.extra[s].Zstar > 0))
+      return "compound element parameters must be positive";
+  if (t.n_extra > 0 && (r.physics & (HPIC_FSIGMA | HPIC_EI_EQUIL)))
+    return "F_sigma and e-i equilibration are defined for single-element targets only";
   if (!(r.brem_boost > 0) || !(r.k_min_J > 0) || !(r.E_cut_J > 0) ||
       !(r.table_Emax_J > r.k_min_J) || r.table_rows < 2 || r.table_cols < 2 ||
       r.n_Ebins < 1 || r.n_thbins < 1 || !(r.tally_Emax_J > r.tally_Emin_J) ||

@@ -42,10 +42,14 @@ struct Consts {
   long long nkeys;         // nti*ntj*ntk*64 sort keys (the dead bin is nkeys)
   double cdt_dx;           // c dt / dx: cells per step at v = c
   double w;                // macro-electron weight (real electrons)
-  // drag, Eq. (5): d_eps = K_ion/beta * bracket
-  double K_ion, L_I;       // L_I = ln(m_e c^2 / I_ex)
-  // scatter, Eq. (B4): sigma^2 = K_sc gamma/u^3 ln(K_lg u)
-  double K_sc, K_lg;
+  // per element of the solid (a compound has up to kMaxSolids):
+  // drag, Eq. (5): d_eps = sum K_ion/beta * bracket, L_I = ln(m_e c^2 / I_ex);
+  // scatter, Eq. (B4): sigma^2 = sum K_sc gamma/u^3 ln(K_lg u)
+  int n_solids;
+  double K_ion[4], L_I[4], K_sc[4], K_lg[4];
+  // heating of a compound, Eq. (A7): 1/C averaged with the weights ne_frac
+  // (n_e of each element over the total), T' = T Tp_fac_s
+  double ne_frac[4], Tp_fac_s[4];
   // bremsstrahlung optical depth: d_tau = K_tau u/eps G(k_min/eps)
   double K_tau, k_min, boost, inv_boost;
   // cut and reflux (Sec. II.A)

@@ -54,9 +54,21 @@ __device__ __forceinline__ void efield_node(const Consts &K, const GView<R> &g, 
 // C = 0.3 + 1.2 T'(2.2 + T')/(1.1 + T')^2, T' = (k_B T/e) Z^(-4/3), brought
 // over one denominator (one FP64 division per cell)
 __device__ __forceinline__ double heated(const Consts &K, double T, double rho) {
-  const double tp = T * K.Tp_fac, D = 1.1 + tp;
-  const double D2 = D * D;
-  return T + rho * D2 / (K.heat_den * (0.3 * D2 + 1.2 * tp * (2.2 + tp)));
+  if (K.n_solids == 1) {
+    const double tp = T * K.Tp_fac, D = 1.1 + tp;
+    const double D2 = D * D;
+    return T + rho * D2 / (K.heat_den * (0.3 * D2 + 1.2 * tp * (2.2 + tp)));
+  }
+  // a compound: heat_den = k_B sum Z n_i, 1/C averaged with the n_e weights
+  double inv_c = 0.0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (s >= K.n_solids) break;
+    const double tp = T * K.Tp_fac_s[s], D = 1.1 + tp;
+    const double D2 = D * D;
+    inv_c += K.ne_frac[s] * D2 / (0.3 * D2 + 1.2 * tp * (2.2 + tp));
+  }
+  return T + rho * inv_c / K.heat_den;
 }
 
 // reduced Lee-More resistivity, Eqs. (A4)-(A6), capped; inside the band

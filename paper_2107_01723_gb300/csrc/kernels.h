@@ -38,7 +38,8 @@ struct TallyView {
 // host so that no double->float conversion runs per electron)
 template <typename R>
 struct HotK {
-  R w, cdt, E_cut, K_ion, L_I, K_sc, K_lg, K_tau, k_min, inv_boost;
+  R w, cdt, E_cut, K_tau, k_min, inv_boost;
+  R K_ion[4], L_I[4], K_sc[4], K_lg[4];  // per element (Consts::n_solids used)
   R eps_esc, du_reflux, sigma_dtheta, tE_min, tE_max, inv_dlogE, th_scale, t_inv_dlog;
 };
 
@@ -49,10 +50,12 @@ inline HotK<R> make_hot(const Consts &K) {
   h.w = R(K.w);
   h.cdt = R(K.cdt_dx);
   h.E_cut = R(K.E_cut);
-  h.K_ion = R(K.K_ion);
-  h.L_I = R(K.L_I);
-  h.K_sc = R(K.K_sc);
-  h.K_lg = R(K.K_lg);
+  for (int s = 0; s < 4; ++s) {
+    h.K_ion[s] = R(K.K_ion[s]);
+    h.L_I[s] = R(K.L_I[s]);
+    h.K_sc[s] = R(K.K_sc[s]);
+    h.K_lg[s] = R(K.K_lg[s]);
+  }
   h.K_tau = R(K.K_tau);
   h.k_min = R(K.k_min);
   h.inv_boost = R(K.inv_boost);

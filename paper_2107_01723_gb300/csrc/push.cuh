@@ -218,10 +218,16 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     const R gam = R(1) + eps;
     const R beta = u_of_eps(eps) / gam;
     const R ig = R(1) / gam;
-    R br = m_flog(eps) + h.L_I + R(0.5) * m_flog(gam + R(1)) + R(0.909) * ig * ig -
-           R(0.818) * ig - R(0.246);
-    br = br < R(0) ? R(0) : br;
-    const R de = h.K_ion / beta * br;
+    const R le = m_flog(eps), lh = R(0.5) * m_flog(gam + R(1));
+    const R a2 = R(0.909) * ig * ig, a1 = R(0.818) * ig;
+    R de = R(0);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {  // the elements' stopping powers add
+      if (s >= K.n_solids) break;  // constant indices: no local-memory copy
+      R br = le + h.L_I[s] + lh + a2 - a1 - R(0.246);
+      br = br < R(0) ? R(0) : br;
+      de += h.K_ion[s] / beta * br;
+    }
     const R eps1 = eps - de;
     if (eps1 < h.E_cut) {
       heat += w * eps;
@@ -239,9 +245,15 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     const U4 r0 = philox10(sc.step, id, 0u, sc.target, sc.key0, sc.key1);
     const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
     const R gam = m_sqrt(R(1) + un * un);
-    R lg = m_flog(h.K_lg * un);
-    lg = lg < R(0) ? R(0) : lg;
-    const R sig = m_sqrt(h.K_sc * gam / (un * un * un) * lg);
+    R var = R(0);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {  // the elements' variances add
+      if (s >= K.n_solids) break;
+      R lg = m_flog(h.K_lg[s] * un);
+      lg = lg < R(0) ? R(0) : lg;
+      var += h.K_sc[s] * gam / (un * un * un) * lg;
+    }
+    const R sig = m_sqrt(var);
     R s1, c1, s2, c2, st, ct;
     m_sincos2pi(unif<R>(r0.b), &s1, &c1);
     const R gauss = m_sqrt(R(-2) * m_log(unif<R>(r0.a))) * c1;

@@ -34,12 +34,17 @@ class HpicError(RuntimeError):
         self.code = code
 
 
+class hpic_solid(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("Z", "n_i_m3", "I_ex_J", "Zstar", "A_ion")]
+
+
 class hpic_target_desc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("dx_m", C.c_double),
                 ("Z", C.c_double), ("n_i_m3", C.c_double), ("I_ex_J", C.c_double),
                 ("Zstar", C.c_double), ("lnLambda", C.c_double), ("eta_max_ohm_m", C.c_double),
                 ("lambda1", C.c_double), ("lambda2", C.c_double), ("T0_K", C.c_double),
-                ("A_ion", C.c_double)]
+                ("A_ion", C.c_double), ("n_extra", C.c_int32), ("pad", C.c_int32),
+                ("extra", hpic_solid * 3)]
 
 
 class hpic_laser_desc(C.Structure):
@@ -191,9 +196,14 @@ def _up(a):
 
 # ---- structs from the workload dicts (SI units) ----
 def target_desc(t: dict) -> hpic_target_desc:
-    return hpic_target_desc(t["nx"], t["ny"], t["nz"], t["dx"], t["Z"], t["n_i"], t["I_ex"],
-                            t["Zstar"], t["lnLambda"], t["eta_max"], t["lambda1"], t["lambda2"],
-                            t["T0"], t["A_ion"])
+    d = hpic_target_desc(t["nx"], t["ny"], t["nz"], t["dx"], t["Z"], t["n_i"], t["I_ex"],
+                         t["Zstar"], t["lnLambda"], t["eta_max"], t["lambda1"], t["lambda2"],
+                         t["T0"], t["A_ion"])
+    extra = t.get("extra", [])
+    d.n_extra = len(extra)
+    for i, e in enumerate(extra):
+        d.extra[i] = hpic_solid(e["Z"], e["n_i"], e["I_ex"], e["Zstar"], e["A_ion"])
+    return d
 
 
 def laser_desc(l: dict) -> hpic_laser_desc:

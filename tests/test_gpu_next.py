@@ -184,3 +184,79 @@ def test_gaussian_run_tracks_oracle_fp64():
     ot = o.tallies()
     assert_tallies_close(g.tallies(), ot, 1e-9, 1e-9 * ot["E_injected"])
     g.close()
+
+
+# ---------------------------------------------------------------- compounds, Lee-More fit
+def ch_cfg(seed=6, n=(10, 9, 12), **tkw):
+    t = W.compound([("C", None), ("H", None)], n=n, **tkw)
+    las = W.laser(t, I_Wcm2=1e21, n_macro=5000, spot_r=3e-6, t_inj=20e-15)
+    return {"target": t, "laser": las, "run": W.run(seed=seed, max_history=40)}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_compound_single_step(prec):
+    """CH plastic: summed stopping powers, scatter variances and emission
+    rates, the n_e-weighted heat capacity and the compound resistivity, one
+    step from the oracle's state 20 steps in."""
+    cfg = ch_cfg()
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    o.step(20)
+    prec_id, tol, abs_frac = PREC[prec]
+    g = gpu_from_oracle(o, cfg, prec_id)
+    ot0 = o.tallies()
+    o.step(1)
+    g.step(1)
+    dx = cfg["target"]["dx"]
+    assert_particles_close(g.particles(), o.particles(), tol, dx)
+    for f in ("j", "E", "B"):
+        assert_vector_close(g.grid, o.grid, f, tol)
+    assert_cell_scalars_close(g, o, tol)
+    ot = tally_delta(o.tallies(), ot0)
+    assert_tallies_close(g.tallies(), ot, tol, abs_frac * ot0["E_live"])
+    g.close()
+
+
+def test_compound_run_tracks_oracle_fp64():
+    cfg = ch_cfg(seed=13)
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=hpic.HPIC_FP64, sort_interval=10)
+    o.step(35)
+    g.step(35)
+    assert_particles_close(g.particles(), o.particles(), 1e-9, cfg["target"]["dx"])
+    assert_cell_scalars_close(g, o, 1e-9)
+    ot = o.tallies()
+    assert_tallies_close(g.tallies(), ot, 1e-9, 1e-9 * ot["E_injected"])
+    g.close()
+
+
+def test_two_overlapping_golds_equal_one_gold_on_gpu():
+    """The paper's compound property on the CUDA path: gold at n_i and gold at
+    n_i/2 twice give the same run (FP64, 20 steps)."""
+    cfg = W.config_small(n=(8, 7, 9), n_macro=1500, steps=20, I_Wcm2=1e21, spot_r=2e-6)
+    half = cfg["target"]["n_i"] / 2
+    two_t = W.compound([("Au", half), ("Au", half)], n=(8, 7, 9))
+    a = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=hpic.HPIC_FP64)
+    b = hpic.Sim(two_t, cfg["laser"], cfg["run"], precision=hpic.HPIC_FP64)
+    a.step(20)
+    b.step(20)
+    assert_particles_close(b.particles(), a.particles(), 1e-11, cfg["target"]["dx"])
+    assert_cell_scalars_close(b, a, 1e-11)
+    a.close()
+    b.close()
+
+
+def test_lee_more_fit_run_tracks_oracle_fp64():
+    """The paper's reduced Lee-More fit (lambda1 = 7, lambda2 = 3.5) with the
+    cap lifted, so that eta moves between its cold and hot limits."""
+    t = W.target(n=(10, 9, 12), T0_eV=5.0, lambda1=7.0, lambda2=3.5, eta_max=1e-3)
+    las = W.laser(t, I_Wcm2=1e21, n_macro=5000, spot_r=3e-6, t_inj=20e-15)
+    run = W.run(seed=21, max_history=40)
+    o = O.OracleSim(t, las, run)
+    g = hpic.Sim(t, las, run, precision=hpic.HPIC_FP64, sort_interval=10)
+    o.step(30)
+    g.step(30)
+    assert_particles_close(g.particles(), o.particles(), 1e-9, t["dx"])
+    assert_cell_scalars_close(g, o, 1e-9)
+    eta = o.grid("eta")
+    assert eta.max() > 1.01 * eta.min()  # eta(T) has moved off its initial value
+    g.close()

@@ -314,6 +314,20 @@ int hpic_sort_cells_noalloc(int32_t nx, int32_t ny, int32_t nz, int32_t precisio
                             const void *const in_soa[8], void *const out_soa[8],
                             int64_t *n_live_dev, int device, void *cuda_stream);
 
+/* Checkpoint and resume.  hpic_save writes the whole state of ctx (target,
+ * run and laser descriptions, clock, every particle slot with weights, all
+ * grids, tallies, histograms and history) to the file `path` (created or
+ * truncated; HPIC_EINVAL if it cannot be written).  hpic_load creates a new
+ * context on `device` / cuda_stream from such a file, as hpic_init_target and
+ * hpic_inject_electrons would, then restores the state; stepping it continues
+ * the saved run (random numbers are keyed on the saved clock and ids).  The
+ * file is raw host memory of this ABI's structs (little-endian, natural
+ * alignment); a file that is not a checkpoint, or is truncated, gives
+ * HPIC_EINVAL with nothing created.  Works on batch targets too (the loaded
+ * context is a single one). */
+int hpic_save(hpic_ctx *ctx, const char *path);
+int hpic_load(hpic_ctx **out, const char *path, int device, void *cuda_stream);
+
 int hpic_destroy(hpic_ctx *ctx);
 /* Last error of ctx, or of the last failed creation when ctx is NULL. */
 const char *hpic_last_error(const hpic_ctx *ctx);

@@ -1064,6 +1064,131 @@ int hpic_launch_count(const hpic_ctx *ctx, int64_t *launches) {
   return HPIC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+constexpr char kCkptMagic[8] = {'H', 'P', 'I', 'C', 'C', 'K', 'P', '1'};
+
+// a device array of `bytes` to the file (through host memory)
+int save_dev(hpic_ctx *ctx, FILE *f, const void *dev, size_t bytes) {
+  std::vector<char> b(bytes);
+  if (bytes) {
+    CK(cudaMemcpyAsync(b.data(), dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (bytes && fwrite(b.data(), 1, bytes, f) != bytes) return fail(ctx, HPIC_EINVAL, "checkpoint write failed");
+  return HPIC_OK;
+}
+
+int load_dev(hpic_ctx *ctx, FILE *f, void *dev, size_t bytes) {
+  std::vector<char> b(bytes);
+  if (bytes && fread(b.data(), 1, bytes, f) != bytes) return fail(ctx, HPIC_EINVAL, "checkpoint truncated");
+  if (bytes) {
+    CK(cudaMemcpyAsync(dev, b.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return HPIC_OK;
+}
+
+// the state arrays of a context in file order: particle slots [0, n) of the
+// current buffer (7 reals, weight, id), then the grids, tallies, histograms
+// and history; `fn` is save_dev or load_dev
+template <typename Fn>
+int each_array(hpic_ctx *ctx, FILE *f, long long n, Fn fn) {
+  char *b = static_cast<char *>(ctx->pbuf[ctx->cur]);
+  const size_t rs = ctx->rsz, st = (size_t)ctx->stride * rs;
+  int rc = HPIC_OK;
+  for (int a = 0; a < 8 && !rc; ++a) rc = fn(ctx, f, b + a * st + ctx->poff * rs, n * rs);
+  if (!rc) rc = fn(ctx, f, reinterpret_cast<uint32_t *>(b + 8 * st) + ctx->poff, n * sizeof(uint32_t));
+  const size_t nv = ctx->vstride * rs, nc = ctx->K.ncell * sizeof(double);
+  if (!rc) rc = fn(ctx, f, ctx->fields, 6 * nv);
+  if (!rc) rc = fn(ctx, f, ctx->jfield, 3 * nv);
+  if (!rc) rc = fn(ctx, f, ctx->T, nc);
+  if (!rc) rc = fn(ctx, f, ctx->eta, nc);
+  if (!rc) rc = fn(ctx, f, ctx->H, nc);
+  if (!rc) rc = fn(ctx, f, ctx->Ti, nc);
+  if (!rc) rc = fn(ctx, f, ctx->Fsig, ctx->K.ncell * rs);
+  if (!rc && ctx->fp32) rc = fn(ctx, f, ctx->eta_r, ctx->K.ncell * sizeof(float));
+  if (!rc) rc = fn(ctx, f, ctx->tal, hpic::T_COUNT * sizeof(double));
+  if (!rc) rc = fn(ctx, f, ctx->hist, 2 * hist_len(ctx) * sizeof(double));
+  if (!rc) rc = fn(ctx, f, ctx->history, (ctx->run.max_history > 0 ? ctx->run.max_history : 1) * sizeof(double));
+  return rc;
+}
+
+struct CkptHeader {
+  char magic[8];
+  hpic_target_desc tgt;
+  hpic_run_params run;
+  hpic_laser_desc laser;
+  int32_t have_laser, pad;
+  long long host_step;
+  hpic::Counters cnt;
+};
+
+}  // namespace
+
+extern "C" {
+
+int hpic_save(hpic_ctx *ctx, const char *path) {
+  if (!ctx || !path) return fail(ctx, HPIC_EINVAL, "NULL argument");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, 8);
+  h.tgt = ctx->tgt;
+  h.run = ctx->run;
+  h.laser = ctx->laser;
+  h.have_laser = ctx->have_laser;
+  h.host_step = ctx->host_step;
+  int rc = read_counters(ctx, &h.cnt);
+  if (rc) return rc;
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return fail(ctx, HPIC_EINVAL, std::string("cannot write ") + path);
+  rc = fwrite(&h, sizeof(h), 1, f) == 1 ? HPIC_OK : fail(ctx, HPIC_EINVAL, "checkpoint write failed");
+  if (!rc) rc = each_array(ctx, f, h.cnt.n, save_dev);
+  if (std::fclose(f) != 0 && !rc) rc = fail(ctx, HPIC_EINVAL, "checkpoint write failed");
+  return rc;
+}
+
+int hpic_load(hpic_ctx **out, const char *path, int device, void *cuda_stream) {
+  if (!out || !path) return fail(nullptr, HPIC_EINVAL, "NULL argument");
+  *out = nullptr;
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return fail(nullptr, HPIC_EINVAL, std::string("cannot read ") + path);
+  CkptHeader h{};
+  if (fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.cnt.n < 0) {
+    std::fclose(f);
+    return fail(nullptr, HPIC_EINVAL, "not a checkpoint of this library");
+  }
+  hpic_ctx *ctx = nullptr;
+  int rc = hpic_init_target(&ctx, &h.tgt, &h.run, device, cuda_stream);
+  if (!rc && h.have_laser) {
+    rc = hpic_inject_electrons(ctx, &h.laser);
+    if (rc) g_create_error = ctx->err;
+  }
+  if (!rc) {
+    rc = reserve(ctx, h.cnt.n + injection_total(ctx));
+    if (rc) g_create_error = ctx->err;
+  }
+  if (!rc) {
+    rc = each_array(ctx, f, h.cnt.n, load_dev);
+    if (!rc) rc = write_counters(ctx, &h.cnt);
+    ctx->host_step = h.host_step;
+    if (rc) g_create_error = ctx->err;
+  }
+  std::fclose(f);
+  if (rc) {
+    if (ctx) {
+      cudaStreamSynchronize(ctx->stream);
+      destroy_all(ctx);
+      delete ctx;
+    }
+    return rc;
+  }
+  *out = ctx;
+  return HPIC_OK;
+}
+
 int hpic_destroy(hpic_ctx *ctx) {
   if (!ctx) return HPIC_EINVAL;
   if (ctx->owner) return refuse_batch_target(ctx);

@@ -134,6 +134,8 @@ def lib() -> C.CDLL:
             "hpic_read_particles": [vp] + [_DP] * 7 + [_UP, C.c_int64, _I64P],
             "hpic_load_particles": [vp, C.c_int64] + [_DP] * 7 + [_UP],
             "hpic_read_weights": [vp, _DP, C.c_int64, _I64P],
+            "hpic_save": [vp, C.c_char_p],
+            "hpic_load": [C.POINTER(vp), C.c_char_p, C.c_int, vp],
             "hpic_load_weights": [vp, C.c_int64, _DP],
             "hpic_get_clock": [vp, _I64P, _I64P],
             "hpic_set_clock": [vp, C.c_int64, C.c_int64],
@@ -325,6 +327,17 @@ def hpic_read_weights(h) -> np.ndarray:
 def hpic_load_weights(h, w) -> None:
     a = np.ascontiguousarray(w, dtype=np.float64)
     _check(lib().hpic_load_weights(h, len(a), _dp(a)), h)
+
+
+def hpic_save(h, path: str) -> None:
+    _check(lib().hpic_save(h, os.fsencode(path)), h)
+
+
+def hpic_load(path: str, device: int = 0, stream: int = 0) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().hpic_load(C.byref(h), os.fsencode(path), device,
+                           C.c_void_p(stream) if stream else None))
+    return h
 
 
 def hpic_get_clock(h):
@@ -541,6 +554,18 @@ class Sim(Target):
 
     def seed(self, n: int, mean_energy_J: float) -> None:
         hpic_seed_electrons(self.h, n, mean_energy_J)
+
+    def save(self, path: str) -> None:
+        hpic_save(self.h, path)
+
+    @classmethod
+    def load(cls, path: str, target: dict, run: dict, device: int = 0, stream: int = 0) -> "Sim":
+        """A context restored from a checkpoint (target and run: the dicts the
+        saved run was made from, kept for the reads' shapes)."""
+        s = cls.__new__(cls)
+        Target.__init__(s, None, target, run)
+        s.h = hpic_load(path, device, stream)
+        return s
 
     def sort(self) -> None:
         hpic_sort(self.h)

@@ -156,3 +156,15 @@ def test_model_validation_and_no_device(lib):
     with pytest.raises(hpic.HpicError) as e:
         hpic.hpic_model([good])
     assert e.value.code == hpic.HPIC_ECUDA
+
+
+def test_checkpoint_load_rejects_bad_files(lib, tmp_path):
+    with pytest.raises(hpic.HpicError) as e:
+        hpic.hpic_load(str(tmp_path / "missing.ckpt"))
+    assert e.value.code == hpic.HPIC_EINVAL
+    junk = tmp_path / "junk.ckpt"
+    junk.write_bytes(b"not a checkpoint at all" * 10)
+    with pytest.raises(hpic.HpicError) as e:
+        hpic.hpic_load(str(junk))
+    assert e.value.code == hpic.HPIC_EINVAL
+    assert "checkpoint" in lib.hpic_last_error(None).decode()

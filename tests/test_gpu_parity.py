@@ -273,3 +273,29 @@ def test_emission_benchmark_mode(prec):
     assert ghE.shape == (202, 180)
     g.close()
     g2.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_checkpoint_resume_continues_the_run(prec, tmp_path):
+    """Save after 25 steps, restore into a new context, and step both 15 more:
+    the resumed run is the original (same draws; only atomic order may differ)."""
+    cfg = small_cfg(n_macro=4000, seed=17)
+    prec_id, tol, _ = PREC[prec]
+    a = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec_id, sort_interval=10)
+    a.step(25)
+    path = str(tmp_path / "run.ckpt")
+    a.save(path)
+    b = hpic.Sim.load(path, cfg["target"], cfg["run"])
+    assert b.clock() == a.clock() and b.n == a.n
+    assert b.tallies()["E_injected"] == a.tallies()["E_injected"]
+    a.step(15)
+    b.step(15)
+    rtol = 1e-12 if prec == "fp64" else 1e-5
+    assert_particles_close(b.particles(), a.particles(), rtol, cfg["target"]["dx"])
+    for k in ("T", "eta"):
+        assert np.allclose(b.grid(k), a.grid(k), rtol=rtol, atol=0)
+    ta, tb = a.tallies(), b.tallies()
+    for k in ("E_injected", "E_drag", "E_xray", "n_emitted", "particle_steps"):
+        assert tb[k] == pytest.approx(ta[k], rel=rtol), k
+    a.close()
+    b.close()

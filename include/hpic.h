@@ -354,7 +354,7 @@ const char *hpic_last_error(const hpic_ctx *ctx);
 #define HPIC_BATCH_MAX_TARGETS 256
 
 typedef struct {
-  int32_t blocks_per_sm;   /* persistent particle-kernel blocks per SM (1..3; FP64 1..2) */
+  int32_t blocks_per_sm;   /* persistent particle-kernel blocks per SM (1..5; FP64 1..2) */
   int32_t sort_interval;   /* steps between cell sorts (0: never) */
   int32_t use_graph;       /* replay captured CUDA graphs (1) or launch directly (0) */
   int32_t reserved;
@@ -388,7 +388,8 @@ int hpic_batch_get_tuning(const hpic_batch *b, hpic_batch_tuning *out);
 int hpic_batch_set_tuning(hpic_batch *b, const hpic_batch_tuning *in);
 
 /* Autotuner: from a snapshot of the whole batch state, time trial_steps
- * steps (>= 1) for every candidate (blocks_per_sm x sort_interval in
+ * steps (>= 1, rounded up to a multiple of 40) for every candidate
+ * (blocks_per_sm 2..5 in FP32, 1..2 in FP64, x sort_interval in
  * {5, 10, 20, 40}, graphs on), restore the snapshot after each trial, and
  * keep the fastest.  The simulation is left exactly where it was.  Needs
  * device memory for one copy of the batch state; the result is written to

@@ -436,7 +436,8 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
       }
       CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
     }
-    hpic::launch_push<R>(ctx->K, P(ctx->cur), G, tab, ctx->cnt, tv, gp, ctx->stream);
+    hpic::launch_push<R>(ctx->K, P(ctx->cur), G, tab, ctx->cnt, tv,
+                         ctx->sm_count * hpic::push_blocks_per_sm<R>(), ctx->stream);
     ctx->launches += 1;
     if (ctx->prof) {
       CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));

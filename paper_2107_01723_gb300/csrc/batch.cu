@@ -92,7 +92,8 @@ int grid_for(const hpic_batch *b, long long work) {
   return (int)(g < 1 ? 1 : g);
 }
 
-int max_blocks_per_sm(const hpic_batch *b) { return b->fp32 ? 3 : 2; }
+int max_blocks_per_sm(const hpic_batch *b) { return b->fp32 ? 5 : 2; }
+int min_blocks_per_sm(const hpic_batch *b) { return b->fp32 ? 2 : 1; }
 
 template <typename R>
 hpic::PView<R> pview_all(const hpic_batch *b, int which) {
@@ -604,7 +605,7 @@ int hpic_batch_autotune(hpic_batch *b, int32_t trial_steps, hpic_batch_tuning *o
       cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     rc = bcuda(b, cudaGetLastError(), "autotune setup");
   }
-  for (int bps = 1; rc == HPIC_OK && bps <= max_blocks_per_sm(b); ++bps) {
+  for (int bps = min_blocks_per_sm(b); rc == HPIC_OK && bps <= max_blocks_per_sm(b); ++bps) {
     for (int s = 0; rc == HPIC_OK && s < 4; ++s) {
       rc = restore();
       if (rc) break;

@@ -58,8 +58,8 @@ __device__ __forceinline__ void flush_acc(const Acc<R> &acc, double *dst) {
 }
 
 // MINB = the blocks per SM the launch asks for: the register budget follows
-// (3: 80 registers, the FP32 state then spills a little; 2: 128; 1: 255), and
-// the autotuner picks among the variants by timing them
+// (5: 48 registers, 4: 64, 3: 80, 2: 128, 1: 255; the FP32 state spills a
+// little below 64), and the autotuner picks among the variants by timing them
 template <typename R, int MINB>
 __global__ void __launch_bounds__(256, MINB)
 k_batch_push(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
@@ -266,14 +266,20 @@ void launch_batch_push(const BatchItem<R> *items, BatchDev d, PView<R> p, const 
                        int sm_count, int blocks_per_sm, cudaStream_t st) {
   const size_t sm = (size_t)d.n * kAccN * sizeof(double) + (d.n + 1) * sizeof(long long);
   const int grid = sm_count * blocks_per_sm;
-  if (blocks_per_sm <= 1) {
-    k_batch_push<R, 1><<<grid, 256, sm, st>>>(items, d, p, table);
-  } else if constexpr (sizeof(R) == 8) {  // FP64: at most two blocks per SM
-    k_batch_push<R, 2><<<grid, 256, sm, st>>>(items, d, p, table);
-  } else if (blocks_per_sm == 2) {
-    k_batch_push<R, 2><<<grid, 256, sm, st>>>(items, d, p, table);
-  } else {
-    k_batch_push<R, 3><<<grid, 256, sm, st>>>(items, d, p, table);
+  if constexpr (sizeof(R) == 8) {  // FP64: one or two blocks per SM
+    if (blocks_per_sm <= 1)
+      k_batch_push<R, 1><<<grid, 256, sm, st>>>(items, d, p, table);
+    else
+      k_batch_push<R, 2><<<grid, 256, sm, st>>>(items, d, p, table);
+  } else {  // FP32: two to five (one runs the two-block code)
+    if (blocks_per_sm <= 2)
+      k_batch_push<R, 2><<<grid, 256, sm, st>>>(items, d, p, table);
+    else if (blocks_per_sm == 3)
+      k_batch_push<R, 3><<<grid, 256, sm, st>>>(items, d, p, table);
+    else if (blocks_per_sm == 4)
+      k_batch_push<R, 4><<<grid, 256, sm, st>>>(items, d, p, table);
+    else
+      k_batch_push<R, 5><<<grid, 256, sm, st>>>(items, d, p, table);
   }
 }
 

@@ -83,6 +83,11 @@ double fsigma_of(const Consts &K, double Ti);
 // the injecting face cells of a Gaussian-envelope laser (empty otherwise)
 std::vector<InjCell> injection_cells(const hpic_target_desc &t, const hpic_laser_desc &l);
 
+// resident 256-thread blocks per SM of the single-target particle kernel; it
+// is launched as one persistent wave of sm_count times this many blocks
+template <typename R>
+constexpr int push_blocks_per_sm() { return sizeof(R) == 4 ? 5 : 2; }
+
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
                  TallyView tv, int grid, cudaStream_t st);

@@ -365,11 +365,15 @@ typedef struct {
  * run parameters `run` (time step, precision, physics, tallies, table; the
  * run's sort_interval is the initial tuning).  lasers[t] schedules target t's
  * injection as hpic_inject_electrons does (lasers may be NULL: no injection).
- * Work goes to cuda_stream, or to a stream the batch creates if NULL (a
- * captured graph needs a stream other than the legacy default). */
+ * target_index[t] is target t's fourth Philox counter word (NULL: the run's
+ * target_index + t); a scan sharded over several batches keeps each target's
+ * random numbers by passing its global index.  Work goes to cuda_stream, or
+ * to a stream the batch creates if NULL (a captured graph needs a stream
+ * other than the legacy default). */
 int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc *targets,
                     const hpic_laser_desc *lasers, const hpic_run_params *run,
-                    int64_t spare_slots, int device, void *cuda_stream);
+                    const uint32_t *target_index, int64_t spare_slots, int device,
+                    void *cuda_stream);
 
 /* Borrow target t's context.  On it the read/write calls work as on a
  * single context (hpic_read_tallies, hpic_read_hist, hpic_read_history,

@@ -312,7 +312,8 @@ extern "C" {
 
 int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc *targets,
                     const hpic_laser_desc *lasers, const hpic_run_params *run,
-                    int64_t spare_slots, int device, void *cuda_stream) {
+                    const uint32_t *target_index, int64_t spare_slots, int device,
+                    void *cuda_stream) {
   if (!out) return bfail(nullptr, HPIC_EINVAL, "out is NULL");
   *out = nullptr;
   if (!targets || !run) return bfail(nullptr, HPIC_EINVAL, "targets or run params NULL");
@@ -332,7 +333,7 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
         return bfail(nullptr, HPIC_EINVAL, "id space exhausted");
     }
   }
-  if ((long long)run->target_index + n_targets > 0xFFFFFFFFll)
+  if (!target_index && (long long)run->target_index + n_targets > 0xFFFFFFFFll)
     return bfail(nullptr, HPIC_EINVAL, "target_index + n_targets exceeds 32 bits");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -377,7 +378,7 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
     c->stream = b->stream;
     c->tgt = targets[t];
     c->run = *run;
-    c->run.target_index = run->target_index + (uint32_t)t;
+    c->run.target_index = target_index ? target_index[t] : run->target_index + (uint32_t)t;
     c->have_laser = lasers != nullptr;
     if (lasers) c->laser = lasers[t];
     c->fp32 = b->fp32;

@@ -145,7 +145,7 @@ def lib() -> C.CDLL:
             "hpic_destroy": [vp],
             "hpic_batch_init": [C.POINTER(vp), C.c_int32, C.POINTER(hpic_target_desc),
                                 C.POINTER(hpic_laser_desc), C.POINTER(hpic_run_params),
-                                C.c_int64, C.c_int, vp],
+                                C.POINTER(C.c_uint32), C.c_int64, C.c_int, vp],
             "hpic_batch_target": [vp, C.c_int32, C.POINTER(vp)],
             "hpic_batch_step": [vp, C.c_int64],
             "hpic_batch_get_tuning": [vp, C.POINTER(hpic_batch_tuning)],
@@ -416,13 +416,14 @@ def hpic_model_device(n: int, in_ptr: int, out_ptr: int, device: int = 0, stream
 # ---- batches ----
 def hpic_batch_init(targets: list, lasers: list | None, run: dict, precision: int = HPIC_FP64,
                     spare_slots: int = 0, device: int = 0, stream: int = 0,
-                    sort_interval: int = 0) -> C.c_void_p:
+                    sort_interval: int = 0, target_index=None) -> C.c_void_p:
     n = len(targets)
     T = (hpic_target_desc * n)(*[target_desc(t) for t in targets])
     Lz = (hpic_laser_desc * n)(*[laser_desc(l) for l in lasers]) if lasers is not None else None
+    ti = (C.c_uint32 * n)(*[int(v) for v in target_index]) if target_index is not None else None
     r = run_params(run, precision, sort_interval)
     b = C.c_void_p()
-    _bcheck(lib().hpic_batch_init(C.byref(b), n, T, Lz, C.byref(r), spare_slots, device,
+    _bcheck(lib().hpic_batch_init(C.byref(b), n, T, Lz, C.byref(r), ti, spare_slots, device,
                                   C.c_void_p(stream) if stream else None))
     return b
 
@@ -576,13 +577,14 @@ class Batch:
 
     def __init__(self, targets: list, lasers: list | None, run: dict,
                  precision: int = HPIC_FP64, spare_slots: int = 0, device: int = 0,
-                 stream: int = 0, sort_interval: int = 0):
+                 stream: int = 0, sort_interval: int = 0, target_index=None):
         self.run = dict(run)
         self.b = hpic_batch_init(targets, lasers, run, precision, spare_slots, device, stream,
-                                 sort_interval)
+                                 sort_interval, target_index)
+        ti = (list(target_index) if target_index is not None else
+              [int(run.get("target_index", 0)) + t for t in range(len(targets))])
         self.targets = [Target(hpic_batch_target(self.b, t), targets[t],
-                               dict(run, target_index=int(run.get("target_index", 0)) + t))
-                        for t in range(len(targets))]
+                               dict(run, target_index=ti[t])) for t in range(len(targets))]
 
     def __len__(self) -> int:
         return len(self.targets)

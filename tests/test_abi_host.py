@@ -106,7 +106,7 @@ def _bad_batch(lib, targets, lasers, run, spare=0):
     T = (hpic.hpic_target_desc * max(n, 1))(*[hpic.target_desc(t) for t in targets])
     L = (hpic.hpic_laser_desc * max(n, 1))(*[hpic.laser_desc(l) for l in lasers]) if lasers else None
     r = hpic.run_params(run)
-    code = lib.hpic_batch_init(C.byref(b), n, T, L, C.byref(r), spare, 0, None)
+    code = lib.hpic_batch_init(C.byref(b), n, T, L, C.byref(r), None, spare, 0, None)
     assert not b.value
     return code, lib.hpic_batch_last_error(None).decode()
 

@@ -168,3 +168,11 @@ def test_checkpoint_load_rejects_bad_files(lib, tmp_path):
         hpic.hpic_load(str(junk))
     assert e.value.code == hpic.HPIC_EINVAL
     assert "checkpoint" in lib.hpic_last_error(None).decode()
+
+
+def test_batch_refuses_the_gaussian_envelope(lib):
+    c = W.config_small()
+    t = c["target"]
+    g = W.laser_gauss(t, per_cell=10)
+    code, msg = _bad_batch(lib, [t, t], [c["laser"], g], c["run"])
+    assert code == hpic.HPIC_EINVAL and "flat-top" in msg

@@ -193,3 +193,40 @@ def test_batched_scan_full_size():
         S = lasers[t]["t_inj"] / run["dt"]
         assert T["n_injected"] == (lasers[t]["n_macro"] * 60) // int(round(S)), t
     b.close()
+
+
+def test_batch_with_background_physics_and_compounds_fp64():
+    """A batch mixing a CH-plastic compound, aluminium and gold, then a batch
+    with F_sigma and e-i equilibration on single-element targets: every
+    target against its own oracle run (20 steps, FP64)."""
+    ch = W.compound([("C", None), ("H", None)], n=(7, 9, 8))
+    al = W.target(n=(9, 8, 7), material="Al")
+    au = W.target(n=(6, 8, 9), material="Au")
+    for targets, physics in (([ch, al, au], hpic.HPIC_ALL),
+                             ([al, au], hpic.HPIC_ALL | hpic.HPIC_FSIGMA | hpic.HPIC_EI_EQUIL)):
+        lasers = [W.laser(t, I_Wcm2=5e20, n_macro=900, spot_r=2e-6, t_inj=10e-15) for t in targets]
+        run = W.run(seed=7, physics=physics, max_history=20)
+        b = hpic.Batch(targets, lasers, run, precision=hpic.HPIC_FP64, sort_interval=5)
+        b.step(20)
+        for t in range(len(targets)):
+            o = O.OracleSim(targets[t], lasers[t], dict(run, target_index=t))
+            o.step(20)
+            assert_targets_close(b.target(t), o, 1e-9, targets[t]["dx"], 1e-9)
+            if physics & hpic.HPIC_EI_EQUIL:
+                np.testing.assert_allclose(b.target(t).grid("Ti"), o.grid("Ti"), rtol=1e-9, atol=0)
+        b.close()
+
+
+def test_batch_target_index_override():
+    """A batch built from targets 1 and 0 of a scan with their global indices
+    draws what the whole scan draws for them."""
+    targets, lasers, run = uneven_batch(seed=9)
+    whole = hpic.Batch(targets, lasers, run, precision=hpic.HPIC_FP64, sort_interval=5)
+    part = hpic.Batch([targets[2], targets[0]], [lasers[2], lasers[0]], run,
+                      precision=hpic.HPIC_FP64, sort_interval=5, target_index=[2, 0])
+    whole.step(15)
+    part.step(15)
+    for mine, glob in ((0, 2), (1, 0)):
+        assert_targets_close(part.target(mine), whole.target(glob), 1e-9, targets[glob]["dx"], 1e-9)
+    whole.close()
+    part.close()

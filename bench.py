@@ -38,7 +38,7 @@ WORKLOAD = ("128^3 cells x 1 um Au (Z=79, n_i=5.9e28 m^-3, T0=1 eV), 1e7 e- inje
 ALG_BYTES = {"fp32": 7 * 4 + 4 + 7 * 4, "fp64": 7 * 8 + 4 + 7 * 8}
 # DRAM bytes (read + write) per particle-step of k_push measured by ncu on
 # this workload (profiles/k_push_headline_fp32.md); None where not captured
-NCU_DRAM_BYTES_PER_PSTEP = {"fp32": 54.9, "fp64": None}
+NCU_DRAM_BYTES_PER_PSTEP = {"fp32": 57.0, "fp64": None}
 SORT_INTERVAL = 10  # measured: 10 beats 20 (k_push 0.99 vs 1.04 ms, step 1.17 vs 1.20 ms)
 
 

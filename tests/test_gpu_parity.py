@@ -299,3 +299,73 @@ def test_checkpoint_resume_continues_the_run(prec, tmp_path):
         assert tb[k] == pytest.approx(ta[k], rel=rtol), k
     a.close()
     b.close()
+
+
+def test_config1_single_step_after_warmup():
+    """Config 1 (32^3 gold, 1e5 electrons at 1e20 W/cm^2): one step after 10
+    warm-up steps, every electron and grid element against the oracle."""
+    cfg = W.config1()
+    for prec in ("fp64", "fp32"):
+        o2 = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+        o2.step(10)
+        one_step_compare(o2, cfg, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_config1_full_run_statistics(prec):
+    """The whole config 1 (200 steps): CE(>1 MeV), the energy-budget fractions
+    and the photon histogram's marginals agree with the oracle's run within 1 %
+    (the trajectories decorrelate in their last bits through atomic order)."""
+    cfg = W.config1()
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=PREC[prec][0], sort_interval=10)
+    o.step(cfg["steps"])
+    g.step(cfg["steps"])
+    ot, gt = o.tallies(), g.tallies()
+    assert gt["n_injected"] == ot["n_injected"] == 100_000
+    for k in ("E_live", "W_field", "E_drag", "E_xray", "E_escaped", "E_reflux", "E_xray_above"):
+        assert gt[k] / gt["E_injected"] == pytest.approx(ot[k] / ot["E_injected"], abs=0.01), k
+    ce_o = ot["E_xray_above"] / (ot["E_injected"] / cfg["laser"]["eta_l2e"])
+    ce_g = gt["E_xray_above"] / (gt["E_injected"] / cfg["laser"]["eta_l2e"])
+    assert ce_g == pytest.approx(ce_o, rel=0.01)
+    (gE, gN), (oE, oN) = g.hist(), o.hist()
+    for a, b in ((gE.sum(axis=1), oE.sum(axis=1)), (gE.sum(axis=0), oE.sum(axis=0))):
+        assert np.abs(a - b).sum() <= 0.01 * b.sum()
+    g.close()
+
+
+def test_nonfinite_electron_is_detected_and_removed():
+    """A NaN momentum loaded into one slot is counted by the step's
+    non-finite tally, that electron is dropped, and the rest step on."""
+    cfg = small_cfg(n_macro=0)
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=hpic.HPIC_FP32_MIXED)
+    n = 64
+    p = {"x": np.full(n, 3e-6), "y": np.full(n, 3e-6), "z": np.full(n, 3e-6),
+         "ux": np.full(n, 2.0), "uy": np.zeros(n), "uz": np.zeros(n), "tau": np.ones(n),
+         "id": np.arange(n, dtype=np.uint32)}
+    p["ux"][17] = np.nan
+    g.set_particles(p)
+    g.step(1)
+    with pytest.raises(hpic.HpicError) as e:
+        g.tallies()
+    assert e.value.code == hpic.HPIC_ENONFINITE
+    t = hpic.hpic_read_tallies(g.h, allow_nonfinite=True)
+    assert t["n_nonfinite"] == 1
+    assert g.n == n - 1 and 17 not in g.particles()["id"]
+    g.close()
+
+
+def test_oversized_request_is_refused_before_any_allocation():
+    """Seeding 1e12 electrons overruns the 32-bit id space: HPIC_EINVAL from the
+    host check, before any device allocation, and the context still steps its
+    existing state.  (A real device-memory exhaustion is not provoked on the
+    shared GPUs.)"""
+    cfg = small_cfg(n_macro=0)
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=hpic.HPIC_FP32_MIXED)
+    g.seed(1000, 1e6 * 1.602176634e-19)
+    with pytest.raises(hpic.HpicError) as e:
+        g.seed(10 ** 12, 1e6 * 1.602176634e-19)
+    assert e.value.code == hpic.HPIC_EINVAL
+    g.step(3)
+    assert 0 < g.n <= 1000 and g.tallies()["particle_steps"] > 0
+    g.close()

@@ -134,6 +134,8 @@ __device__ __forceinline__ float m_flog(float x) { return __logf(x); }
 __device__ __forceinline__ double m_flog(double x) { return log(x); }
 __device__ __forceinline__ float m_exp(float x) { return expf(x); }
 __device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }

@@ -224,19 +224,22 @@ __global__ void k_sort_finish(Counters *cnt, const uint32_t *offsets, long long 
 }
 
 // ---------------------------------------------------------------- photon table
-// Row i: eps_i = k_min (E_max/k_min)^(i/(rows-1)); column j: the v with
-// CDF(k_min (eps_i/k_min)^v) = j/(cols-1), where CDF is the normalised
-// integral of s(u)/u, s(u) = (4/3)(1-u) + u^2, from u0 = k_min/eps to u.
-// Solved by Newton's method on y = ln u (dG/dy = s(e^y)) inside a bracket.
+// Row i: eps_i = k_min (E_max/k_min)^(i/(rows-1)); column j: the photon
+// energy k with CDF(k/eps_i) = j/(cols-1), where CDF is the normalised
+// integral of s(u)/u, s(u) = (4/3)(1-u) + u^2, from u0 = k_min/eps to u,
+// stored as the log-ratio w = ln(eps_i/k) / ln(eps_i/k_min) (the sampler
+// subtracts k from eps through it without cancellation).  Solved by
+// Newton's method on y = ln u (dG/dy = s(e^y)) inside a bracket.
 __global__ void k_table(int rows, int cols, double k_min, double E_max, double *t64, float *t32) {
   const long long nt = (long long)rows * cols;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nt;
        q += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(q / cols), j = (int)(q - (long long)i * cols);
     const double r = (double)j / (double)(cols - 1);
-    double v;
+    // w = ln(eps/k) / ln(eps/k_min): 1 at k = k_min, 0 at k = eps
+    double w;
     if (i == 0 || j == 0 || j == cols - 1) {
-      v = (i == 0) ? r : (j == 0 ? 0.0 : 1.0);
+      w = (i == 0) ? 1.0 - r : (j == 0 ? 1.0 : 0.0);
     } else {
       const double lu0 = ((double)i / (double)(rows - 1)) * -log(E_max / k_min);  // ln u0 < 0
       const double u0 = exp(lu0);
@@ -254,10 +257,10 @@ __global__ void k_table(int rows, int cols, double k_min, double E_max, double *
         if (fabs(yn - y) < 1e-16 * fabs(lu0)) { y = yn; break; }
         y = yn;
       }
-      v = 1.0 - y / lu0;
+      w = y / lu0;  // y = ln(k/eps)
     }
-    t64[q] = v;
-    t32[q] = (float)v;
+    t64[q] = w;
+    t32[q] = (float)w;
   }
 }
 

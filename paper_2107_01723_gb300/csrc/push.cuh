@@ -110,26 +110,32 @@ __device__ __forceinline__ R shape_G(R u0) {
   return R(4.0 / 3.0) * (-m_flog(u0) - (R(1) - u0)) + R(0.5) * (R(1) - u0 * u0);
 }
 
-// photon energy from the inverse-CDF table (rows: ln eps, columns: r)
+// Photon energy from the inverse-CDF table (rows: ln eps, columns: the
+// uniform deviate).  The table holds w = ln(eps/k) / ln(eps/k_min), and the
+// sampler returns ln(eps/k) = w ln(eps/k_min) >= 0: the caller forms k =
+// eps e^{-x} and the electron's remainder with expm1, so a photon that takes
+// nearly all of eps leaves a remainder as accurate as eps itself (k_min
+// e^{v ln(eps/k_min)} subtracted from eps loses the digits of k in FP32).
+// The column and its fraction come from the deviate's 23 bits m in integers,
+// (m + 1/2) 2^-23 (cols-1) = (2m+1)(cols-1) 2^-24, exact in either precision.
 template <typename R>
-__device__ __forceinline__ R sample_k(const HotK<R> &h, int rows, int cols,
-                                      const R *__restrict__ tab, R eps, R r) {
+__device__ __forceinline__ R sample_log_ratio(const HotK<R> &h, int rows, int cols,
+                                              const R *__restrict__ tab, R eps, uint32_t bits) {
   const R lr = m_log(eps / h.k_min);
   R L = lr * h.t_inv_dlog;
   int i = (int)m_floor(L);
   i = min(max(i, 0), rows - 2);
   R f = L - R(i);
   f = f < R(0) ? R(0) : (f > R(1) ? R(1) : f);
-  const R cpos = r * R(cols - 1);
-  int j = (int)m_floor(cpos);
-  j = min(max(j, 0), cols - 2);
-  const R g = cpos - R(j);
+  const unsigned long long cpos =
+      (unsigned long long)(2u * (bits >> 9) + 1u) * (unsigned long long)(cols - 1);
+  const int j = (int)(cpos >> 24);  // <= cols - 2 since 2m+1 < 2^24
+  const R g = R((uint32_t)(cpos & 0xFFFFFFull)) * R(1.0 / 16777216.0);
   const R *t0 = tab + i * cols + j;
   const R *t1 = t0 + cols;
   const R va = __ldg(t0) * (R(1) - g) + __ldg(t0 + 1) * g;
   const R vb = __ldg(t1) * (R(1) - g) + __ldg(t1 + 1) * g;
-  const R v = va * (R(1) - f) + vb * f;
-  return h.k_min * m_exp(v * lr);
+  return (va * (R(1) - f) + vb * f) * lr;
 }
 
 // photon polar angle: theta = t/gamma, t ~ t/(1+t^2)^2 truncated at theta = pi
@@ -272,7 +278,8 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     tau -= dtau;
     if (tau <= R(0)) {
       const U4 r1 = philox10(sc.step, id, 1u, sc.target, sc.key0, sc.key1);
-      const R k = sample_k(h, K.t_rows, K.t_cols, tab, eps, unif<R>(r1.a));
+      const R xk = sample_log_ratio(h, K.t_rows, K.t_cols, tab, eps, r1.a);
+      const R k = eps * m_exp(-xk);
       const R thg = photon_theta(R(1) + eps, unif<R>(r1.b));
       const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
       R dx = ux / un, dy = uy / un, dz = uz / un;
@@ -300,7 +307,8 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
       }
       ++acc.n_emit;
       tau = -m_log(R(1) - unif<R>(r1.d));
-      eps -= k * h.inv_boost;
+      // eps - k/boost = eps ((1 - 1/boost) + (1 - e^{-x})/boost)
+      eps *= (R(1) - h.inv_boost) - h.inv_boost * m_expm1(-xk);
       if (eps < h.E_cut) {
         heat += w * eps;
         alive = false;

@@ -130,6 +130,15 @@ def config5(n_electrons=2 ** 27, steps=1000) -> dict:
             "n_electrons": int(n_electrons), "mean_energy": 10.0 * MEV, "steps": steps}
 
 
+def config3() -> dict:
+    """Thick-target long run: 500 x 256 x 256 cells of 1 um gold (500 um thick
+    along x), 1e8 electrons injected over 100 fs at 1e22 W/cm^2 (a0 = 85),
+    reflux on all faces, 100 ps (200,000 steps)."""
+    t = target(n=(500, 256, 256))
+    return {"target": t, "laser": laser(t, I_Wcm2=1e22, n_macro=100_000_000),
+            "run": run(seed=0, max_history=200_000), "steps": 200_000}
+
+
 def config2() -> dict:
     """128^3 cells of 1 um gold, 1e7 electrons over 100 fs at 1e21 W/cm^2, 10 ps."""
     t = target(n=(128, 128, 128))

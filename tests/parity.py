@@ -75,3 +75,57 @@ def assert_tallies_close(gt: dict, ot: dict, tol: float, abs_tol: float, exact_c
     for k in COUNT_TALLIES:
         if exact_counts:
             assert gt[k] == ot[k], (k, gt[k], ot[k])
+
+
+def heat_cells(p: dict, dx: float, shape, fp32: bool) -> np.ndarray:
+    """Cell of x^n that receives each electron's drag heat (the clamped floor of
+    its position in cells), taken in the precision the position is held in."""
+    idx = []
+    for k, n in zip("xyz", shape):
+        X = np.asarray(p[k]) / dx
+        if fp32:  # the kernel's own FP32 coordinate, recovered exactly
+            X = X.astype(np.float32)
+        idx.append(np.clip(np.floor(X), 0, n - 1).astype(np.int64))
+    return idx[0] + shape[0] * (idx[1] + shape[1] * idx[2])
+
+
+def heat_with_cell_swaps(cfg: dict, state: dict, clock, gp: dict, op: dict,
+                         o_heat: np.ndarray, fp32: bool, limit: int = 64):
+    """The oracle's drag heat of one step, with the heat of every electron whose
+    cell the kernel took differently moved to the kernel's cell.
+
+    The drag heat goes to the cell holding x^n, a decision by floor(x/dx): an
+    FP32 coordinate within rounding of a cell face can land on the other side
+    than the FP64 one.  `gp`, `op` are the kernel's and the oracle's electrons
+    at the start of the step, `state` and `clock` the oracle's grids and clock
+    there.  The heat of each swapped electron comes from the oracle stepping
+    that electron alone in the same fields.  Returns the corrected heat and
+    the cells involved (whose T and eta then differ by that electron's heat)."""
+    t = cfg["target"]
+    shape, dx = (t["nx"], t["ny"], t["nz"]), t["dx"]
+    gp, op = by_id(gp), by_id(op)
+    assert np.array_equal(gp["id"], op["id"])
+    cg, co = heat_cells(gp, dx, shape, fp32), heat_cells(op, dx, shape, False)
+    swapped = np.nonzero(cg != co)[0]
+    assert swapped.size <= limit, f"{swapped.size} electrons change heat cell"
+    heat = o_heat.copy()
+    touched = np.unique(np.concatenate([cg[swapped], co[swapped]]))
+    todo = list(swapped)
+    while todo:  # electrons stepped together must sit in distinct oracle cells
+        batch, seen, rest = [], set(), []
+        for i in todo:
+            (rest if co[i] in seen else batch).append(i)
+            seen.add(co[i])
+        s = O.OracleSim(t, cfg["laser"], cfg["run"])
+        for k in GRIDS_STATE:
+            s.set_grid(k, state[k])
+        s.set_particles({k: v[batch] for k, v in op.items()})
+        s.set_clock(*clock)
+        s.reset_tallies()
+        s.step(1)
+        h = s.grid("heat")[co[batch]]
+        del s
+        np.add.at(heat, co[batch], -h)
+        np.add.at(heat, cg[batch], h)
+        todo = rest
+    return heat, touched

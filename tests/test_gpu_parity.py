@@ -18,7 +18,7 @@ from paper_2107_01723_gb300 import workloads as W
 
 from parity import (GRIDS_STATE, assert_field_close, assert_particles_close,
                     assert_tallies_close, assert_vector_close, by_id, gpu_from_oracle,
-                    tally_delta)
+                    heat_with_cell_swaps, tally_delta)
 
 
 def assert_grids_close(g, o, tol):
@@ -124,6 +124,35 @@ def test_edge_cases_fp64():
     assert ot["n_cut"] >= 1 and ot["n_escaped"] >= 1 and ot["n_emitted"] >= 1
     assert_tallies_close(gt, ot, 1e-12, 1e-25)
     g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("boost", [1.0, 4.0])
+def test_hard_photon_remainders(prec, boost):
+    """Electrons of 50-300 m_e c^2 at zero optical depth all emit in one step.
+    A photon that takes nearly all of the electron's energy leaves a small
+    remainder, which must still meet the per-element bar: the kernel forms it
+    from ln(eps/k) with expm1 instead of subtracting two nearly equal numbers
+    (App. B; photon energies from the inverse-CDF table, Sec. II.B boost)."""
+    cfg = small_cfg(n=(8, 8, 8), n_macro=0, brem_boost=boost)
+    rng = np.random.default_rng(17)
+    n = 32768
+    L = 8 * cfg["target"]["dx"]
+    eps = rng.uniform(50.0, 300.0, n)
+    d = rng.normal(size=(n, 3))
+    d *= (np.sqrt(eps * (eps + 2.0)) / np.linalg.norm(d, axis=1))[:, None]
+    p = {"x": rng.uniform(0.25, 0.75, n) * L, "y": rng.uniform(0.25, 0.75, n) * L,
+         "z": rng.uniform(0.25, 0.75, n) * L, "ux": d[:, 0], "uy": d[:, 1], "uz": d[:, 2],
+         "tau": np.zeros(n), "id": np.arange(n, dtype=np.uint32)}
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    o.set_particles(p)
+    o.step(0)
+    one_step_compare(o, cfg, prec)
+    assert o.tallies()["n_emitted"] == n
+    q = by_id(o.particles())
+    left = np.sqrt(1.0 + q["ux"] ** 2 + q["uy"] ** 2 + q["uz"] ** 2) - 1.0
+    if boost == 1.0:  # the hard tail the test is about is populated
+        assert np.count_nonzero(left < 0.05 * eps[q["id"]]) > 100
 
 
 def test_empty_population_steps():
@@ -244,6 +273,60 @@ def test_full_size_headline(prec):
     hE, hN = g.hist()
     assert hE.sum() == pytest.approx(t["E_xray"], rel=1e-9)
     assert hN.sum() == pytest.approx(t["n_emitted"] * w / cfg["run"]["brem_boost"], rel=1e-9)
+    assert g.history().sum() == pytest.approx(t["E_xray_above"], rel=1e-9)
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_thick_target(prec):
+    """Config 3, the thick-target run: 500 x 256 x 256 cells of gold, 1e8
+    electrons at 1e22 W/cm^2.  The oracle computes the first two steps itself
+    (5e5 electrons injected and pushed on the full grid) and every electron
+    and grid element is compared; in FP32 the run then completes the 200-step
+    injection and is checked for its electron count, bookkeeping, energy
+    closure and current."""
+    cfg = W.config3()
+    prec_id, tol, abs_frac = PREC[prec]
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec_id, sort_interval=10)
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    g.step(1)
+    o.step(1)
+    gp1, op1, clock1 = g.particles(), o.particles(), o.clock()
+    state1 = {k: o.grid(k) for k in GRIDS_STATE}
+    g.step(1)
+    o.step(1)
+    dx = cfg["target"]["dx"]
+    assert_particles_close(g.particles(), o.particles(), tol, dx)
+    for f in ("j", "E", "B"):
+        assert_vector_close(g.grid, o.grid, f, tol)
+    # drag heat by cell, with electrons whose FP32 position sits across a
+    # cell face from the FP64 one counted in the kernel's cell
+    heat, swapped = heat_with_cell_swaps(cfg, state1, clock1, gp1, op1, o.grid("heat"),
+                                         prec == "fp32")
+    del state1
+    assert_field_close(g.grid("heat"), heat, tol, "heat", np.abs(o.grid("heat")).max())
+    for k in ("T", "eta"):
+        rel = np.abs(g.grid(k) - o.grid(k)) / np.abs(o.grid(k))
+        rel[swapped] = 0.0
+        assert rel.max() <= tol, (k, rel.max())
+    ot = o.tallies()
+    assert_tallies_close(g.tallies(), ot, tol, abs_frac * ot["E_injected"])
+    del o
+    if prec == "fp64":
+        g.close()
+        return
+    g.step(248)
+    t = g.tallies()
+    assert t["n_injected"] == 100_000_000
+    rhs = t["E_live"] + t["W_field"] + t["E_drag"] + t["E_xray"] + t["E_escaped"] + t["E_reflux"]
+    assert abs(t["E_injected"] - rhs) / t["E_injected"] < 1e-4
+    live = t["n_injected"] - t["n_cut"] - t["n_escaped"] - t["n_reflux_absorbed"]
+    assert g.n == live
+    P = g.particles()
+    gam = np.sqrt(1 + P["ux"] ** 2 + P["uy"] ** 2 + P["uz"] ** 2)
+    w = t["N_injected"] / t["n_injected"]
+    want = -1.602176634e-19 * 299792458.0 * w * np.sum(P["ux"] / gam) / dx ** 3
+    assert g.grid("jx").sum() == pytest.approx(want, rel=1e-4, abs=1e-6 * abs(want) + 1.0)
     assert g.history().sum() == pytest.approx(t["E_xray_above"], rel=1e-9)
     g.close()
 

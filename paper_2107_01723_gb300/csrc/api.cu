@@ -620,6 +620,10 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
   };
   if (cudaSetDevice(device) != cudaSuccess) { cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice"); return bail(HPIC_ECUDA); }
   cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (const cudaError_t e = hpic::prepare_push(); e != cudaSuccess) {
+    cuda_fail(ctx, e, "push kernel shared memory");
+    return bail(HPIC_ECUDA);
+  }
   fold_constants(ctx);
   const hpic::Consts &K = ctx->K;
   ctx->vstride = round_up(K.nvec + 4, 64);

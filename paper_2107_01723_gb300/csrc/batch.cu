@@ -355,6 +355,10 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
     g_batch_error = m;
     return code;
   };
+  if (const cudaError_t e = hpic::prepare_batch_push(); e != cudaSuccess) {
+    bcuda(b, e, "batch push kernel shared memory");
+    return bail(HPIC_ECUDA);
+  }
   if (cuda_stream) {
     b->stream = static_cast<cudaStream_t>(cuda_stream);
   } else {

@@ -65,7 +65,10 @@ __global__ void __launch_bounds__(256, MINB)
 k_batch_push(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
              const R *__restrict__ tab) {
   __shared__ BatchItem<R> wc[kBatchWarps];  // each warp's current target
-  extern __shared__ double tal_s[];         // n x kAccN sums, then the task prefix
+  // the warps' deposit stages, then n x kAccN tally sums, then the task prefix
+  extern __shared__ __align__(16) double dyn[];
+  R *stage = reinterpret_cast<R *>(dyn) + (threadIdx.x >> 5) * dep_words<R>();
+  double *tal_s = dyn + kBatchWarps * dep_words<R>() * sizeof(R) / sizeof(double);
   long long *wpref_s = reinterpret_cast<long long *>(tal_s + d.n * kAccN);
   for (int i = threadIdx.x; i < d.n * kAccN; i += blockDim.x) tal_s[i] = 0.0;
   for (int t = threadIdx.x; t <= d.n; t += blockDim.x) wpref_s[t] = d.wpref[t];
@@ -106,7 +109,7 @@ k_batch_push(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
     sc.target = it.K.target_index;
     const long long local = (w - wpref_s[t]) * 32 + lane;
     push_warp(it.K, it.h, make_grid(it.K, it.g), tab, it.tv, sc, p, it.off + local,
-              local < wstate[warp][1], acc);
+              local < wstate[warp][1], acc, stage);
   }
   if (t >= 0) flush_acc(acc, tal_s + t * kAccN);
   __syncthreads();
@@ -262,9 +265,32 @@ void launch_batch_plan(const BatchItem<R> *items, BatchDev d, cudaStream_t st) {
 }
 
 template <typename R>
+constexpr size_t batch_stage_bytes() { return (size_t)kBatchWarps * dep_words<R>() * sizeof(R); }
+
+// dynamic shared memory of the push for up to the maximum number of targets
+template <typename R>
+constexpr size_t batch_push_smem_max() {
+  return batch_stage_bytes<R>() + (size_t)HPIC_BATCH_MAX_TARGETS * kAccN * sizeof(double) +
+         (HPIC_BATCH_MAX_TARGETS + 1) * sizeof(long long);
+}
+
+cudaError_t prepare_batch_push() {
+  const int f = (int)batch_push_smem_max<float>(), d = (int)batch_push_smem_max<double>();
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_batch_push<float, 2>, a, f);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_push<float, 3>, a, f);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_push<float, 4>, a, f);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_push<float, 5>, a, f);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_push<double, 1>, a, d);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_push<double, 2>, a, d);
+  return e;
+}
+
+template <typename R>
 void launch_batch_push(const BatchItem<R> *items, BatchDev d, PView<R> p, const R *table,
                        int sm_count, int blocks_per_sm, cudaStream_t st) {
-  const size_t sm = (size_t)d.n * kAccN * sizeof(double) + (d.n + 1) * sizeof(long long);
+  const size_t sm = batch_stage_bytes<R>() + (size_t)d.n * kAccN * sizeof(double) +
+                    (d.n + 1) * sizeof(long long);
   const int grid = sm_count * blocks_per_sm;
   if constexpr (sizeof(R) == 8) {  // FP64: one or two blocks per SM
     if (blocks_per_sm <= 1)

@@ -88,6 +88,10 @@ std::vector<InjCell> injection_cells(const hpic_target_desc &t, const hpic_laser
 template <typename R>
 constexpr int push_blocks_per_sm() { return sizeof(R) == 4 ? 5 : 2; }
 
+// allow the push kernels their shared-memory deposit stages (above the
+// default 48 KB for FP64 and the batch); once per device, before any launch
+cudaError_t prepare_push();
+cudaError_t prepare_batch_push();
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
                  TallyView tv, int grid, cudaStream_t st);

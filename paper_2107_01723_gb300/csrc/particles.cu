@@ -31,6 +31,8 @@ __global__ void __launch_bounds__(256, push_blocks_per_sm<R>())
 k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__restrict__ tab,
        Counters *cnt, TallyView tv) {
   __shared__ double red[kAccN * 32];
+  extern __shared__ __align__(16) unsigned char dyn[];  // the warps' deposit stages
+  R *stage = reinterpret_cast<R *>(dyn) + (threadIdx.x >> 5) * dep_words<R>();
   const long long n = cnt->n;
   StepCtx sc;
   sc.step_ll = cnt->step;
@@ -47,7 +49,7 @@ k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__rest
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); base < n;
        base += stride)
-    push_warp(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc);
+    push_warp(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc, stage);
 
   double v[kAccN];
   acc.values(v);
@@ -204,9 +206,21 @@ __global__ void k_advance(Counters *cnt, long long cap) {
 // ---------------------------------------------------------------- launchers
 
 template <typename R>
+constexpr size_t push_stage_bytes() { return 8 * dep_words<R>() * sizeof(R); }
+
+cudaError_t prepare_push() {
+  cudaError_t e = cudaFuncSetAttribute(k_push<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)push_stage_bytes<float>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_push<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)push_stage_bytes<double>());
+  return e;
+}
+
+template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
                  TallyView tv, int grid, cudaStream_t st) {
-  k_push<R><<<grid, 256, 0, st>>>(K, make_hot<R>(K), p, g, table, cnt, tv);
+  k_push<R><<<grid, 256, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv);
 }
 
 template <typename R>

@@ -42,12 +42,6 @@ __device__ __forceinline__ void ld_pair(const R *G, int q, R &v0, R &v1) {
   v1 = __ldg(G + q + 1);
 }
 
-template <typename R>
-__device__ __forceinline__ void red_pair(R *G, int q, R v0, R v1) {
-  atomicAdd(G + q, v0);
-  atomicAdd(G + q + 1, v1);
-}
-
 // the grid as the push kernel sees it; node (i, j, k) lives at i + sy*j + sz*k
 template <typename R>
 struct Grid {
@@ -91,17 +85,6 @@ __device__ __forceinline__ R trilerp(const Grid<R> &g, int c, int b, R fx, R fy,
   const R e0 = e00 * (R(1) - fy) + e10 * fy;
   const R e1 = e01 * (R(1) - fy) + e11 * fy;
   return e0 * (R(1) - fz) + e1 * fz;
-}
-
-template <typename R>
-__device__ __forceinline__ void spread(const Grid<R> &g, int c, int b, R fx, R fy, R fz, R v) {
-  const R gx = R(1) - fx, gy = R(1) - fy, gz = R(1) - fz;
-  const R v0 = v * gz, v1 = v * fz;
-  R *G = g.J[c];
-  red_pair(G, b, v0 * gy * gx, v0 * gy * fx);
-  red_pair(G, b + g.sy, v0 * fy * gx, v0 * fy * fx);
-  red_pair(G, b + g.sz, v1 * gy * gx, v1 * gy * fx);
-  red_pair(G, b + g.sz + g.sy, v1 * fy * gx, v1 * fy * fx);
 }
 
 // G(u0) = integral_{u0}^{1} s(u)/u du for s(u) = (4/3)(1-u) + u^2
@@ -166,6 +149,66 @@ struct Acc {
     v[11] = n_steps; v[12] = n_nf;
   }
 };
+
+// Escape or reflux at each face the move crossed, in the order x, y, z
+// (Sec. II.A).  Rare, so kept out of line.
+template <typename R>
+struct Crossing {
+  R pos[3], u[3];
+  double esc, ref;
+  int n_esc, n_ref, n_refabs;
+  bool alive;
+};
+
+template <typename R>
+__device__ __noinline__ Crossing<R> cross_faces(R eps_esc, R du_reflux, R sigma_dtheta,
+                                                uint32_t step, uint32_t target, uint32_t key0,
+                                                uint32_t key1, uint32_t id, R w, int nx, int ny,
+                                                int nz, R p0, R p1, R p2, R u0, R u1, R u2) {
+  Crossing<R> c;
+  c.pos[0] = p0; c.pos[1] = p1; c.pos[2] = p2;
+  c.u[0] = u0; c.u[1] = u1; c.u[2] = u2;
+  c.esc = 0.0; c.ref = 0.0; c.n_esc = 0; c.n_ref = 0; c.n_refabs = 0; c.alive = true;
+  R *pos = c.pos, *u = c.u;
+  const int nn[3] = {nx, ny, nz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const R L = R(nn[a]);
+    if (pos[a] >= R(0) && pos[a] <= L) continue;
+    const R e_out = kinetic(u[0], u[1], u[2]);
+    if (e_out >= eps_esc) {
+      c.esc += (double)(w * e_out);
+      ++c.n_esc;
+      c.alive = false;
+      return c;
+    }
+    const bool low = pos[a] < R(0);
+    pos[a] = low ? -pos[a] : R(2) * L - pos[a];
+    u[a] = -u[a];
+    const R un = m_sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const R un2 = un - du_reflux;
+    if (un2 <= R(0)) {
+      c.ref += (double)(w * e_out);
+      ++c.n_refabs;
+      c.alive = false;
+      return c;
+    }
+    const U4 r2 = philox10(step, id, 2u + a, target, key0, key1);
+    const R xi = sigma_dtheta * (unif<R>(r2.a) - R(0.5));
+    R st, ct, sp, cp;
+    m_sincos(xi, &st, &ct);
+    m_sincos2pi(unif<R>(r2.b), &sp, &cp);
+    const R inv = R(1) / un;
+    R d[3] = {u[0] * inv, u[1] * inv, u[2] * inv};
+    rotate(d[0], d[1], d[2], ct, st, cp, sp);
+    if (low && d[a] < R(0)) d[a] = -d[a];
+    if (!low && d[a] > R(0)) d[a] = -d[a];
+    u[0] = un2 * d[0]; u[1] = un2 * d[1]; u[2] = un2 * d[2];
+    c.ref += (double)(w * (e_out - kinetic(u[0], u[1], u[2])));
+    ++c.n_ref;
+  }
+  return c;
+}
 
 struct StepCtx {
   uint32_t step, key0, key1, target;
@@ -327,60 +370,59 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     return false;
   }
 
-  // ---- move, then escape or reflux at each face crossed (x, y, z)
+  // ---- move, then escape or reflux at each face crossed (out of line: rare)
   R ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
   R pos[3] = {X + ux * ig * h.cdt, Y + uy * ig * h.cdt, Zc + uz * ig * h.cdt};
-  R u[3] = {ux, uy, uz};
-  const int nn[3] = {nx, ny, nz};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const R L = R(nn[a]);
-    if (unbounded || (pos[a] >= R(0) && pos[a] <= L)) continue;
-    const R e_out = kinetic(u[0], u[1], u[2]);
-    if (e_out >= h.eps_esc) {
-      acc.esc += (double)(w * e_out);
-      ++acc.n_esc;
-      return false;
-    }
-    const bool low = pos[a] < R(0);
-    pos[a] = low ? -pos[a] : R(2) * L - pos[a];
-    u[a] = -u[a];
-    const R un = m_sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const R un2 = un - h.du_reflux;
-    if (un2 <= R(0)) {
-      acc.ref += (double)(w * e_out);
-      ++acc.n_refabs;
-      return false;
-    }
-    const U4 r2 = philox10(sc.step, id, 2u + a, sc.target, sc.key0, sc.key1);
-    const R xi = h.sigma_dtheta * (unif<R>(r2.a) - R(0.5));
-    R st, ct, sp, cp;
-    m_sincos(xi, &st, &ct);
-    m_sincos2pi(unif<R>(r2.b), &sp, &cp);
-    const R inv = R(1) / un;
-    R d[3] = {u[0] * inv, u[1] * inv, u[2] * inv};
-    rotate(d[0], d[1], d[2], ct, st, cp, sp);
-    if (low && d[a] < R(0)) d[a] = -d[a];
-    if (!low && d[a] > R(0)) d[a] = -d[a];
-    u[0] = un2 * d[0]; u[1] = un2 * d[1]; u[2] = un2 * d[2];
-    acc.ref += (double)(w * (e_out - kinetic(u[0], u[1], u[2])));
-    ++acc.n_ref;
+  if (!unbounded && !(pos[0] >= R(0) && pos[0] <= R(nx) && pos[1] >= R(0) && pos[1] <= R(ny) &&
+                      pos[2] >= R(0) && pos[2] <= R(nz))) {
+    const Crossing<R> c = cross_faces<R>(h.eps_esc, h.du_reflux, h.sigma_dtheta, sc.step,
+                                         sc.target, sc.key0, sc.key1, id, w, nx, ny, nz,
+                                         pos[0], pos[1], pos[2], ux, uy, uz);
+    acc.esc += c.esc;
+    acc.ref += c.ref;
+    acc.n_esc += c.n_esc;
+    acc.n_ref += c.n_ref;
+    acc.n_refabs += c.n_refabs;
+    if (!c.alive) return false;
+    pos[0] = c.pos[0]; pos[1] = c.pos[1]; pos[2] = c.pos[2];
+    ux = c.u[0]; uy = c.u[1]; uz = c.u[2];
   }
   X = pos[0]; Y = pos[1]; Zc = pos[2];
-  ux = u[0]; uy = u[1]; uz = u[2];
 
   return true;  // the caller's warp deposits the current at x^{n+1}
 }
 
 // ---------------------------------------------------------------- warp deposits
-// A warp's 32 electrons can sit in one cell (just after a cell sort) or in a
-// dozen (many steps later).  Atomics from one instruction that hit the same
-// address serialise in L2, so each warp first sorts its (cell, lane) keys
-// with a 32-wide bitonic network in registers, moves every electron's
-// deposit inputs to its sorted lane, sums each cell's contributions with a
-// segmented shuffle reduction and lets the first lane of each cell issue
-// the atomics: within one instruction every address is distinct.
-constexpr uint32_t kNoCell = (1u << 27) - 1u;  // key of a lane with nothing to deposit
+// A warp adds its electrons' current and drag heat to the grid in one pass
+// through a shared-memory stage.  The warp first sorts its electrons by the
+// cell of x^{n+1} (a 32-wide bitonic network on (cell, lane) keys), and each
+// lane writes its electron as the row of its sorted position: 25 values, per
+// current component c the 8 corners of its own lattice (axis c
+// half-staggered, the other two node-centred) times w v_c / c, then the drag
+// heat.  Each lane then walks one column down the 32 rows, summing while the
+// rows stay in one cell and adding the sum to the grid with one reduction
+// when the cell changes: a cell's electrons cost one reduction per node,
+// not one per electron, and within one reduction instruction the lanes
+// target distinct addresses.
+//
+// Node of a corner: with nk the node index of the cell of x^{n+1}, the
+// corner (a, b, e) of component c of an electron whose axis-c staggered
+// index is i_c - 1 + off (off = 0 or 1) is nk + a + sy b + sz e - (1 - off)
+// stride_c; the walker keeps one sum per value of off.
+constexpr int kDepCols = 25;               // 3 x 8 corners, heat
+constexpr uint32_t kNoKey = 0xFFFFFFFFu;   // row with nothing to deposit
+constexpr uint32_t kNoCell = (1u << 27) - 1u;  // sort key of such a row (cells < 2^27 - 1)
+constexpr unsigned kFull = 0xffffffffu;
+
+// column stride in elements: 16-byte column reads by 8 lanes fall in 8
+// distinct 4-bank groups (stride = 16 bytes mod 128)
+template <typename R>
+__host__ __device__ constexpr int dep_stride() { return (32 * (int)sizeof(R) + 16) / (int)sizeof(R); }
+// elements of one warp's stage: the columns, then 32 row indices
+template <typename R>
+__host__ __device__ constexpr int dep_words() {
+  return kDepCols * dep_stride<R>() + 32 * 4 / (int)sizeof(R);
+}
 
 // ascending sort of one 32-bit value per lane across the warp
 __device__ __forceinline__ uint32_t warp_sort32(uint32_t c) {
@@ -397,143 +439,120 @@ __device__ __forceinline__ uint32_t warp_sort32(uint32_t c) {
   return c;
 }
 
-struct Runs {
-  bool head;  // first lane of its run
-  int end;    // last lane of the run
-};
-
-// runs of equal keys in lane order (the keys are sorted)
-__device__ __forceinline__ Runs runs_of(uint32_t key) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-  Runs r;
-  r.head = lane == 0 || prev != key;
-  const unsigned heads = __ballot_sync(0xffffffffu, r.head);
-  const unsigned after = heads & ~((2u << lane) - 1u);  // heads after this lane
-  r.end = after ? __ffs(after) - 2 : 31;
-  return r;
-}
-
-// sum of v over [lane, end]; at a head lane, the whole run
 template <typename R>
-__device__ __forceinline__ R seg_sum(R v, int end) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const R y = __shfl_down_sync(0xffffffffu, v, off);
-    if (lane + off <= end) v += y;
+struct Vec16;  // the rows one 16-byte shared load covers
+template <>
+struct Vec16<float> {
+  static constexpr int n = 4;
+  __device__ __forceinline__ static void load(const float *p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
   }
-  return v;
-}
-
-// drag heat into the cell of x^n (heat_cell < 0: nothing to add)
-template <typename R>
-__device__ __forceinline__ void warp_heat(const Grid<R> &g, R heat, int heat_cell) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t key = heat_cell >= 0 ? (uint32_t)heat_cell : kNoCell;
-  const uint32_t c = warp_sort32((key << 5) | (uint32_t)lane);
-  const uint32_t skey = c >> 5;
-  const R v = __shfl_sync(0xffffffffu, heat, (int)(c & 31u));
-  const Runs r = runs_of(skey);
-  const R s = seg_sum(v, r.end);
-  if (r.head && skey != kNoCell && s != R(0)) atomicAdd(g.H + skey, (double)s);
-}
-
-// Per-axis weights of one electron on the 3 nodes iN-1, iN, iN+1: the
-// node-centred lattice uses slots 1, 2; the half-staggered one slots off,
-// off+1 with off = iS - iN + 1.
-template <typename R>
-struct Slots {
-  R n1, n2, s0, s1, s2;
+};
+template <>
+struct Vec16<double> {
+  static constexpr int n = 2;
+  __device__ __forceinline__ static void load(const double *p, double (&v)[2]) {
+    const double2 q = *reinterpret_cast<const double2 *>(p);
+    v[0] = q.x; v[1] = q.y;
+  }
 };
 
+// current J += w (u/gamma) S(x^{n+1}) of the lanes with dep set, and drag
+// heat into the cell heat_cell of x^n (heat == 0: nothing); buf is this
+// warp's stage.  Every lane of the warp must call it.
 template <typename R>
-__device__ __forceinline__ Slots<R> slots_of(const Axis<R> &a) {
-  Slots<R> w;
-  w.n1 = R(1) - a.fN;
-  w.n2 = a.fN;
-  const int off = a.iS - a.iN + 1;  // 0 or 1
-  w.s0 = off == 0 ? R(1) - a.fS : R(0);
-  w.s1 = off == 0 ? a.fS : R(1) - a.fS;
-  w.s2 = off == 0 ? R(0) : a.fS;
-  return w;
-}
-
-template <typename R>
-__device__ __forceinline__ Slots<R> shfl_slots(const Slots<R> &w, int src) {
-  Slots<R> o;
-  o.n1 = __shfl_sync(0xffffffffu, w.n1, src);
-  o.n2 = __shfl_sync(0xffffffffu, w.n2, src);
-  o.s0 = __shfl_sync(0xffffffffu, w.s0, src);
-  o.s1 = __shfl_sync(0xffffffffu, w.s1, src);
-  o.s2 = __shfl_sync(0xffffffffu, w.s2, src);
-  return o;
-}
-
-template <typename R>
-__device__ __forceinline__ R slot_n(const Slots<R> &w, int c) { return c == 1 ? w.n1 : w.n2; }
-template <typename R>
-__device__ __forceinline__ R slot_s(const Slots<R> &w, int c) {
-  return c == 0 ? w.s0 : (c == 1 ? w.s1 : w.s2);
-}
-
-// one current component over its 12-node frame, staggered along axis SA
-template <typename R, int SA>
-__device__ __forceinline__ void frame_component(const Grid<R> &g, int c, const Runs &r,
-                                                bool valid, int i, int j, int k,
-                                                const Slots<R> &wx, const Slots<R> &wy,
-                                                const Slots<R> &wz, R v) {
-#pragma unroll
-  for (int cz = (SA == 2 ? 0 : 1); cz < 3; ++cz)
-#pragma unroll
-    for (int cy = (SA == 1 ? 0 : 1); cy < 3; ++cy)
-#pragma unroll
-      for (int cx = (SA == 0 ? 0 : 1); cx < 3; ++cx) {
-        const R w = (SA == 0 ? slot_s(wx, cx) : slot_n(wx, cx)) *
-                    (SA == 1 ? slot_s(wy, cy) : slot_n(wy, cy)) *
-                    (SA == 2 ? slot_s(wz, cz) : slot_n(wz, cz));
-        const R s = seg_sum(v * w, r.end);
-        if (r.head && valid && s != R(0))
-          atomicAdd(g.J[c] + g.node(i - 1 + cx, j - 1 + cy, k - 1 + cz), s);
-      }
-}
-
-// current J += w (u/gamma) S(x) at x^{n+1} for the lanes with dep set
-template <typename R>
-__device__ __forceinline__ void warp_current(const Consts &K, const Grid<R> &g, bool dep, R w,
-                                             R X, R Y, R Zc, R ux, R uy, R uz) {
+__device__ __forceinline__ void warp_deposit(const Consts &K, const Grid<R> &g, R *__restrict__ buf,
+                                             bool dep, R w, R X, R Y, R Zc, R ux, R uy, R uz,
+                                             R heat, int heat_cell) {
+  constexpr int S = dep_stride<R>();
   const int lane = threadIdx.x & 31;
-  Slots<R> wx{}, wy{}, wz{};
-  R vx = R(0), vy = R(0), vz = R(0);
-  uint32_t key = kNoCell;
+
+  // ---- this lane's electron, written as row `row` of the cell order
+  if (!dep) { X = R(0); Y = R(0); Zc = R(0); }  // finite weights, zero values
+  const Axis<R> ax = axis_weights(X, K.nx), ay = axis_weights(Y, K.ny), az = axis_weights(Zc, K.nz);
+  R v[3] = {R(0), R(0), R(0)};
+  uint32_t nk = kNoKey, ck = kNoCell;
   if (dep) {
     const R ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
-    const Axis<R> bx = axis_weights(X, K.nx), by = axis_weights(Y, K.ny), bz = axis_weights(Zc, K.nz);
-    wx = slots_of(bx);
-    wy = slots_of(by);
-    wz = slots_of(bz);
-    vx = w * ux * ig;
-    vy = w * uy * ig;
-    vz = w * uz * ig;
-    key = (uint32_t)(bx.iN + K.nx * (by.iN + K.ny * bz.iN));
+    v[0] = w * ux * ig;
+    v[1] = w * uy * ig;
+    v[2] = w * uz * ig;
+    nk = (uint32_t)g.node(ax.iN, ay.iN, az.iN);
+    ck = (uint32_t)(ax.iN + K.nx * (ay.iN + K.ny * az.iN));
   }
-  const uint32_t c = warp_sort32((key << 5) | (uint32_t)lane);
-  const uint32_t skey = c >> 5;
-  const int src = (int)(c & 31u);
-  wx = shfl_slots(wx, src);
-  wy = shfl_slots(wy, src);
-  wz = shfl_slots(wz, src);
-  vx = __shfl_sync(0xffffffffu, vx, src);
-  vy = __shfl_sync(0xffffffffu, vy, src);
-  vz = __shfl_sync(0xffffffffu, vz, src);
-  const Runs r = runs_of(skey);
-  const bool valid = skey != kNoCell;
-  const int kk = (int)(skey / (uint32_t)(K.nx * K.ny));
-  const int rem = (int)skey - kk * K.nx * K.ny;
-  const int jj = rem / K.nx, ii = rem - jj * K.nx;
-  frame_component<R, 0>(g, 0, r, valid, ii, jj, kk, wx, wy, wz, vx);
-  frame_component<R, 1>(g, 1, r, valid, ii, jj, kk, wx, wy, wz, vy);
-  frame_component<R, 2>(g, 2, r, valid, ii, jj, kk, wx, wy, wz, vz);
+  const int offs = (ax.iS - ax.iN + 1) | ((ay.iS - ay.iN + 1) << 1) | ((az.iS - az.iN + 1) << 2);
+  const uint32_t hk = (heat != R(0) && heat_cell >= 0) ? (uint32_t)heat_cell : kNoKey;
+  // lane p learns which electron is p-th in cell order (src) and tells it
+  const int src = (int)(warp_sort32((ck << 5) | (uint32_t)lane) & 31u);
+  uint32_t *rowof = reinterpret_cast<uint32_t *>(buf + kDepCols * S);
+  rowof[src] = (uint32_t)lane;
+  __syncwarp();
+  const int row = (int)rowof[lane];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R fx = c == 0 ? ax.fS : ax.fN, fy = c == 1 ? ay.fS : ay.fN, fz = c == 2 ? az.fS : az.fN;
+    const R z0 = v[c] * (R(1) - fz), z1 = v[c] * fz;
+    const R yz[4] = {z0 * (R(1) - fy), z0 * fy, z1 * (R(1) - fy), z1 * fy};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      buf[(8 * c + 2 * q) * S + row] = yz[q] * (R(1) - fx);
+      buf[(8 * c + 2 * q + 1) * S + row] = yz[q] * fx;
+    }
+  }
+  buf[24 * S + row] = heat;
+  // from here on lane p speaks for row p
+  const uint32_t pnk = __shfl_sync(kFull, nk, src), phk = __shfl_sync(kFull, hk, src);
+  const int poffs = __shfl_sync(kFull, offs, src);
+
+  // ---- run ends (bit r: row r is the last of its cell) and stagger offsets
+  const uint32_t nk1 = __shfl_down_sync(kFull, pnk, 1), hk1 = __shfl_down_sync(kFull, phk, 1);
+  const uint32_t endc = __ballot_sync(kFull, lane == 31 || nk1 != pnk);
+  const uint32_t endh = __ballot_sync(kFull, lane == 31 || hk1 != phk);
+  const uint32_t offx = __ballot_sync(kFull, poffs & 1);
+  const uint32_t offy = __ballot_sync(kFull, poffs & 2);
+  const uint32_t offz = __ballot_sync(kFull, poffs & 4);
+  __syncwarp();
+
+  // ---- column `lane`: lanes 0-23 the current corners, 24 the heat
+  const int c = lane >> 3;
+  const uint32_t offm = c == 0 ? offx : (c == 1 ? offy : (c == 2 ? offz : 0u));
+  const uint32_t mine = lane < 24 ? endc : (lane == 24 ? endh : 0u);
+  const uint32_t any = endc | endh;
+  R *J = c == 0 ? g.J[0] : (c == 1 ? g.J[1] : g.J[2]);
+  const int o1 = (lane & 1) + g.sy * ((lane >> 1) & 1) + g.sz * ((lane >> 2) & 1);
+  const int sc = c == 0 ? 1 : (c == 1 ? g.sy : g.sz);
+  const R *col = buf + (lane < kDepCols ? lane : kDepCols - 1) * S;
+  R s0 = R(0), s1 = R(0);  // rows with off = 0, off = 1
+  constexpr int V = Vec16<R>::n;
+#pragma unroll 1
+  for (int r0 = 0; r0 < 32; r0 += V) {
+    R x[V];
+    Vec16<R>::load(col + r0, x);
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const int r = r0 + q;
+      if (offm & (1u << r)) s1 += x[q]; else s0 += x[q];
+      if (any & (1u << r)) {  // warp-uniform
+        const uint32_t kc = __shfl_sync(kFull, pnk, r);
+        const uint32_t kh = __shfl_sync(kFull, phk, r);
+        if (mine & (1u << r)) {
+          if (lane < 24) {
+            if (kc != kNoKey) {
+              const long long q1 = (long long)kc + o1;
+              if (s1 != R(0)) atomicAdd(J + q1, s1);
+              if (s0 != R(0)) atomicAdd(J + (q1 - sc), s0);
+            }
+          } else if (kh != kNoKey && s0 != R(0)) {
+            atomicAdd(g.H + kh, (double)s0);
+          }
+          s0 = R(0);
+          s1 = R(0);
+        }
+      }
+    }
+  }
+  __syncwarp();  // the stage is rewritten by the warp's next electrons
 }
 
 // ---------------------------------------------------------------- one warp's step
@@ -545,12 +564,14 @@ __device__ __forceinline__ void st_stream(R *p, R v) { __stcs(p, v); }
 
 // The 32 lanes of a warp advance the electrons in slots ip (one per lane;
 // in_range false: nothing there) through the step, then deposit their
-// current and drag heat together.  Every lane of the warp must call it.
+// current and drag heat together through the warp's shared-memory stage
+// (dep_words<R>() elements, 16-byte aligned).  Every lane of the warp must
+// call it.
 template <typename R>
 __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, const Grid<R> &g,
                                           const R *__restrict__ tab, const TallyView &tv,
                                           const StepCtx &sc, const PView<R> &p, long long ip,
-                                          bool in_range, Acc<R> &acc) {
+                                          bool in_range, Acc<R> &acc, R *__restrict__ stage) {
   bool live = false, dep = false;
   uint32_t id = kDead;
   R X = 0, Y = 0, Zc = 0, ux = 0, uy = 0, uz = 0, tau = 0, heat = 0, w = h.w;
@@ -582,10 +603,8 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
       p.id[ip] = kDead;
     }
   }
-  if (!(K.physics & P_UNBOUNDED)) {  // uniform over the warp
-    warp_heat(g, heat, heat != R(0) ? heat_cell : -1);
-    warp_current(K, g, dep, w, X, Y, Zc, ux, uy, uz);
-  }
+  if (!(K.physics & P_UNBOUNDED))  // uniform over the warp
+    warp_deposit(K, g, stage, dep, w, X, Y, Zc, ux, uy, uz, heat, heat_cell);
 }
 
 // ---------------------------------------------------------------- injection

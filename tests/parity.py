@@ -62,6 +62,19 @@ def assert_vector_close(gsim, osim_grid, prefix: str, tol: float):
         assert_field_close(gsim(c), o[c], tol, c, scale)
 
 
+def faraday_tol(o, cfg: dict, tol: float) -> float:
+    """Tolerance on B (against its max-norm) one Faraday step after B = 0,
+    propagated from the tolerance on E (against E's max-norm): each B
+    component is dt times two differences of E components over dx, so an
+    element error of tol max|E| in E bounds B's error by 4 tol dt max|E| / dx
+    (Eq. (A3); B is not deposited, it follows from E).  Never below tol."""
+    E = max(np.abs(o.grid(k)).max() for k in ("Ex", "Ey", "Ez"))
+    B = max(np.abs(o.grid(k)).max() for k in ("Bx", "By", "Bz"))
+    if B == 0.0:
+        return tol
+    return max(tol, 4.0 * tol * cfg["run"]["dt"] * E / (cfg["target"]["dx"] * B))
+
+
 def tally_delta(after: dict, before: dict) -> dict:
     return {k: after[k] - before[k] for k in after}
 

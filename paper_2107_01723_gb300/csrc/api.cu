@@ -211,6 +211,8 @@ void hpic::fold(const hpic_target_desc &t, const hpic_run_params &r, const hpic_
              std::sqrt(ME / 3.0);
   K.eta_max = t.eta_max_ohm_m;
   K.lambda1 = t.lambda1;
+  K.eta_hot_c = K.eta_num / K.A_hot;
+  K.eta_cold_c = t.lambda1 > 0.0 ? K.eta_num / K.B_cold : 0.0;
   // eta = eta_max exactly while tau <= eta_num/eta_max: tau_hot = A_hot (k T)^1.5
   // grows with T, tau_cold = B_cold/sqrt(k T) falls; the band is narrowed by a
   // relative 1e-6 so that inside it the full formula is capped with room to spare

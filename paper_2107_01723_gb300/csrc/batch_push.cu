@@ -52,6 +52,7 @@ __device__ __forceinline__ void flush_acc(const Acc<R> &acc, double *dst) {
   acc.values(v);
 #pragma unroll
   for (int q = 0; q < kAccN; ++q) {
+    if (!__any_sync(0xffffffffu, v[q] != 0.0)) continue;  // rare events: mostly none
     const double s = warp_sum(v[q]);
     if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(dst + q, s);
   }

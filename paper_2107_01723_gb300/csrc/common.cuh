@@ -67,6 +67,7 @@ struct Consts {
   // heating, Eqs. (A4)-(A8), SI
   double F_ohm, F_H, dx3, heat_den, Tp_fac;
   double eta_num, A_hot, B_cold, eta_max, lambda1;
+  double eta_hot_c, eta_cold_c;  // eta_num / A_hot, eta_num / B_cold (0 without lambda1)
   double eta_Tlo, eta_Thi;            // eta(T) is at its cap for eta_Tlo < T < eta_Thi (K)
   // F_sigma (App. B) = 1 + fs_q (ln T_i / 2 + fs_c), T_i in K
   double fs_q, fs_c;

@@ -72,16 +72,18 @@ __device__ __forceinline__ double heated(const Consts &K, double T, double rho) 
 }
 
 // reduced Lee-More resistivity, Eqs. (A4)-(A6), capped; inside the band
-// where the cap holds, the cap itself (no square root or division)
+// where the cap holds, the cap itself.  eta_num / max(tau_hot, tau_cold) is
+// the smaller of eta_num/(A_hot (kT)^1.5) and eta_num sqrt(kT)/B_cold, both
+// formed from one reciprocal square root (no FP64 division)
 __device__ __forceinline__ double resistivity(const Consts &K, double T) {
   if (T > K.eta_Tlo && T < K.eta_Thi) return K.eta_max;
   const double kT = 1.380649e-23 * T;
-  double tau = K.A_hot * kT * sqrt(kT);
+  const double r = rsqrt(kT);
+  double eta = K.eta_hot_c * (r * r * r);
   if (K.lambda1 > 0.0) {
-    const double tc = K.B_cold / sqrt(kT);
-    tau = tc > tau ? tc : tau;
+    const double ec = K.eta_cold_c * (kT * r);
+    eta = ec < eta ? ec : eta;
   }
-  const double eta = K.eta_num / tau;
   return eta < K.eta_max ? eta : K.eta_max;
 }
 

@@ -102,10 +102,10 @@ __device__ __forceinline__ R shape_G(R u0) {
 // The column and its fraction come from the deviate's 23 bits m in integers,
 // (m + 1/2) 2^-23 (cols-1) = (2m+1)(cols-1) 2^-24, exact in either precision.
 template <typename R>
-__device__ __forceinline__ R sample_log_ratio(const HotK<R> &h, int rows, int cols,
+__device__ __forceinline__ R sample_log_ratio(R k_min, R t_inv_dlog, int rows, int cols,
                                               const R *__restrict__ tab, R eps, uint32_t bits) {
-  const R lr = m_log(eps / h.k_min);
-  R L = lr * h.t_inv_dlog;
+  const R lr = m_log(eps / k_min);
+  R L = lr * t_inv_dlog;
   int i = (int)m_floor(L);
   i = min(max(i, 0), rows - 2);
   R f = L - R(i);
@@ -215,6 +215,78 @@ struct StepCtx {
   long long step_ll;
 };
 
+// What the emission of one photon needs besides the electron (App. B);
+// filled only on that rare path.
+template <typename R>
+struct EmitIn {
+  const R *tab;
+  double *hist, *history;
+  double w_shared, inv_boost_d, ce_thr;
+  long long max_history;
+  int t_rows, t_cols, n_E, n_th, weighted;
+  R k_min, t_inv_dlog, tE_min, tE_max, inv_dlogE, th_scale, inv_boost, E_cut;
+};
+
+template <typename R>
+struct EmitOut {
+  R eps, ux, uy, uz, tau, heat;
+  double x, xa;
+  bool alive;
+};
+
+// One photon at zero optical depth: energy from the table, polar angle about
+// the electron, energy x angle tallies, fresh optical depth, and the
+// electron's remainder (cut below E_cut).  Rare, so kept out of line.
+template <typename R>
+__device__ __noinline__ EmitOut<R> emit_photon(const EmitIn<R> e, StepCtx sc, uint32_t id, R w,
+                                               R eps, R ux, R uy, R uz) {
+  EmitOut<R> o;
+  o.x = 0.0;
+  o.xa = 0.0;
+  o.heat = R(0);
+  o.alive = true;
+  const U4 r1 = philox10(sc.step, id, 1u, sc.target, sc.key0, sc.key1);
+  const R xk = sample_log_ratio(e.k_min, e.t_inv_dlog, e.t_rows, e.t_cols, e.tab, eps, r1.a);
+  const R k = eps * m_exp(-xk);
+  const R thg = photon_theta(R(1) + eps, unif<R>(r1.b));
+  const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
+  R dx = ux / un, dy = uy / un, dz = uz / un;
+  R st, ct, sp, cp;
+  m_sincos(thg, &st, &ct);
+  m_sincos2pi(unif<R>(r1.c), &sp, &cp);
+  rotate(dx, dy, dz, ct, st, cp, sp);
+  const R th = m_atan2(m_sqrt(dy * dy + dz * dz), dx);  // polar angle from +x
+  // photon tally: energy row (underflow, log bins, overflow) x polar bin
+  int row;
+  if (k < e.tE_min) row = 0;
+  else if (k >= e.tE_max) row = e.n_E + 1;
+  else row = min(max(1 + (int)m_floor(e.inv_dlogE * m_log(k / e.tE_min)), 1), e.n_E);
+  const int col = min(max((int)m_floor(th * e.th_scale), 0), e.n_th - 1);
+  // photon weight: the electron's own, or the shared FP64 weight exactly
+  const double wph = (e.weighted ? (double)w : e.w_shared) * e.inv_boost_d;
+  const double ek = wph * (double)k;
+  const int hb = row * e.n_th + col;
+  atomicAdd(e.hist + hb, ek);
+  atomicAdd(e.hist + (e.n_E + 2) * e.n_th + hb, wph);
+  o.x = ek;
+  if ((double)k >= e.ce_thr) {
+    o.xa = ek;
+    if (sc.step_ll < e.max_history) atomicAdd(e.history + sc.step_ll, ek);
+  }
+  o.tau = -m_log(R(1) - unif<R>(r1.d));
+  // eps - k/boost = eps ((1 - 1/boost) + (1 - e^{-x})/boost)
+  eps *= (R(1) - e.inv_boost) - e.inv_boost * m_expm1(-xk);
+  if (eps < e.E_cut) {
+    o.heat = w * eps;
+    o.alive = false;
+  } else {
+    const R s = u_of_eps(eps) / un;
+    ux *= s; uy *= s; uz *= s;
+  }
+  o.eps = eps; o.ux = ux; o.uy = uy; o.uz = uz;
+  return o;
+}
+
 // Advance one live electron through the step.  Returns false when the
 // electron is absorbed or escapes (the caller marks its slot dead).  On
 // true, the state holds x^{n+1}, u^{n+1} and tau, and its current is
@@ -320,45 +392,24 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     if (K.physics & P_FSIGMA) dtau *= __ldg(g.Fsig + ax.iN + nx * (ay.iN + ny * az.iN));
     tau -= dtau;
     if (tau <= R(0)) {
-      const U4 r1 = philox10(sc.step, id, 1u, sc.target, sc.key0, sc.key1);
-      const R xk = sample_log_ratio(h, K.t_rows, K.t_cols, tab, eps, r1.a);
-      const R k = eps * m_exp(-xk);
-      const R thg = photon_theta(R(1) + eps, unif<R>(r1.b));
-      const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
-      R dx = ux / un, dy = uy / un, dz = uz / un;
-      R st, ct, sp, cp;
-      m_sincos(thg, &st, &ct);
-      m_sincos2pi(unif<R>(r1.c), &sp, &cp);
-      rotate(dx, dy, dz, ct, st, cp, sp);
-      const R th = m_atan2(m_sqrt(dy * dy + dz * dz), dx);  // polar angle from +x
-      // photon tally: energy row (underflow, log bins, overflow) x polar bin
-      int row;
-      if (k < h.tE_min) row = 0;
-      else if (k >= h.tE_max) row = K.n_E + 1;
-      else row = min(max(1 + (int)m_floor(h.inv_dlogE * m_log(k / h.tE_min)), 1), K.n_E);
-      const int col = min(max((int)m_floor(th * h.th_scale), 0), K.n_th - 1);
-      // photon weight: the electron's own, or the shared FP64 weight exactly
-      const double wph = (K.weighted ? (double)w : K.w) * K.inv_boost;
-      const double ek = wph * (double)k;
-      const int hb = row * K.n_th + col;
-      atomicAdd(tv.hist + hb, ek);
-      atomicAdd(tv.hist + (K.n_E + 2) * K.n_th + hb, wph);
-      acc.x += ek;
-      if ((double)k >= K.ce_thr) {
-        acc.xa += ek;
-        if (sc.step_ll < K.max_history) atomicAdd(tv.history + sc.step_ll, ek);
-      }
+      EmitIn<R> e;
+      e.tab = tab; e.hist = tv.hist; e.history = tv.history;
+      e.w_shared = K.w; e.inv_boost_d = K.inv_boost; e.ce_thr = K.ce_thr;
+      e.max_history = K.max_history;
+      e.t_rows = K.t_rows; e.t_cols = K.t_cols; e.n_E = K.n_E; e.n_th = K.n_th;
+      e.weighted = K.weighted;
+      e.k_min = h.k_min; e.t_inv_dlog = h.t_inv_dlog; e.tE_min = h.tE_min; e.tE_max = h.tE_max;
+      e.inv_dlogE = h.inv_dlogE; e.th_scale = h.th_scale; e.inv_boost = h.inv_boost;
+      e.E_cut = h.E_cut;
+      const EmitOut<R> o = emit_photon<R>(e, sc, id, w, eps, ux, uy, uz);
+      acc.x += o.x;
+      acc.xa += o.xa;
       ++acc.n_emit;
-      tau = -m_log(R(1) - unif<R>(r1.d));
-      // eps - k/boost = eps ((1 - 1/boost) + (1 - e^{-x})/boost)
-      eps *= (R(1) - h.inv_boost) - h.inv_boost * m_expm1(-xk);
-      if (eps < h.E_cut) {
-        heat += w * eps;
-        alive = false;
-      } else {
-        const R s = u_of_eps(eps) / un;
-        ux *= s; uy *= s; uz *= s;
-      }
+      tau = o.tau;
+      eps = o.eps;
+      ux = o.ux; uy = o.uy; uz = o.uz;
+      heat += o.heat;
+      alive = o.alive;
     }
   }
 
@@ -418,11 +469,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // distinct 4-bank groups (stride = 16 bytes mod 128)
 template <typename R>
 __host__ __device__ constexpr int dep_stride() { return (32 * (int)sizeof(R) + 16) / (int)sizeof(R); }
-// elements of one warp's stage: the columns, then 32 row indices
+// elements of one warp's stage: the columns, then 32 slots (the row index
+// of each electron, later the heat sum of each run)
 template <typename R>
-__host__ __device__ constexpr int dep_words() {
-  return kDepCols * dep_stride<R>() + 32 * 4 / (int)sizeof(R);
-}
+__host__ __device__ constexpr int dep_words() { return kDepCols * dep_stride<R>() + 32; }
 
 // ascending sort of one 32-bit value per lane across the warp
 __device__ __forceinline__ uint32_t warp_sort32(uint32_t c) {
@@ -523,6 +573,7 @@ __device__ __forceinline__ void warp_deposit(const Consts &K, const Grid<R> &g, 
   const int o1 = (lane & 1) + g.sy * ((lane >> 1) & 1) + g.sz * ((lane >> 2) & 1);
   const int sc = c == 0 ? 1 : (c == 1 ? g.sy : g.sz);
   const R *col = buf + (lane < kDepCols ? lane : kDepCols - 1) * S;
+  R *hsum = buf + kDepCols * S;  // the row indices there have been read
   R s0 = R(0), s1 = R(0);  // rows with off = 0, off = 1
   constexpr int V = Vec16<R>::n;
 #pragma unroll 1
@@ -535,7 +586,6 @@ __device__ __forceinline__ void warp_deposit(const Consts &K, const Grid<R> &g, 
       if (offm & (1u << r)) s1 += x[q]; else s0 += x[q];
       if (any & (1u << r)) {  // warp-uniform
         const uint32_t kc = __shfl_sync(kFull, pnk, r);
-        const uint32_t kh = __shfl_sync(kFull, phk, r);
         if (mine & (1u << r)) {
           if (lane < 24) {
             if (kc != kNoKey) {
@@ -543,14 +593,21 @@ __device__ __forceinline__ void warp_deposit(const Consts &K, const Grid<R> &g, 
               if (s1 != R(0)) atomicAdd(J + q1, s1);
               if (s0 != R(0)) atomicAdd(J + (q1 - sc), s0);
             }
-          } else if (kh != kNoKey && s0 != R(0)) {
-            atomicAdd(g.H + kh, (double)s0);
+          } else {
+            hsum[r] = s0;  // the heat of the run ending at row r
           }
           s0 = R(0);
           s1 = R(0);
         }
       }
     }
+  }
+  __syncwarp();
+  // lane p adds the heat run ending at row p (one FP64 conversion per warp,
+  // not one per row in the walk)
+  if ((endh >> lane) & 1u) {
+    const R hv = hsum[lane];
+    if (phk != kNoKey && hv != R(0)) atomicAdd(g.H + phk, (double)hv);
   }
   __syncwarp();  // the stage is rewritten by the warp's next electrons
 }

@@ -38,7 +38,11 @@ WORKLOAD = ("128^3 cells x 1 um Au (Z=79, n_i=5.9e28 m^-3, T0=1 eV), 1e7 e- inje
 ALG_BYTES = {"fp32": 7 * 4 + 4 + 7 * 4, "fp64": 7 * 8 + 4 + 7 * 8}
 # DRAM bytes (read + write) per particle-step of k_push measured by ncu on
 # this workload (profiles/k_push_headline_fp32.md); None where not captured
-NCU_DRAM_BYTES_PER_PSTEP = {"fp32": 57.0, "fp64": None}
+NCU_DRAM_BYTES_PER_PSTEP = {"fp32": 57.1, "fp64": None}
+# the same for k_batch_push, captured on the first 16 targets of the scan
+# (profiles/k_batch_push_batched_scan16_fp32.md): the traffic is the
+# electron state streamed once, so it scales with the particle-steps
+NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": 65.1, "fp64": None}
 SORT_INTERVAL = 10  # measured: 10 beats 20 (k_push 0.99 vs 1.04 ms, step 1.17 vs 1.20 ms)
 
 
@@ -472,7 +476,11 @@ def run_batch(args):
                        "live_electrons_at_start": live, "tuning": tune,
                        "graphs": "step and sort replayed from captured CUDA graphs"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                         "frac": achieved / pk["hbm_gbs"],
+                         "traffic": (NCU_BATCH_DRAM_BYTES_PER_PSTEP[prec_name] * kp / kl
+                                     if NCU_BATCH_DRAM_BYTES_PER_PSTEP[prec_name] else None),
+                         "traffic_unit": "bytes per launch (ncu dram read+write on 16 targets, "
+                                         "scaled by particle-steps)",
                          "kernel": "k_batch_push", "kernel_ms_avg": km / kl,
                          "measured_over": f"{kl} direct launches after the timed window",
                          "peak_source": pk["source"]},

@@ -71,6 +71,27 @@ __device__ __forceinline__ double heated(const Consts &K, double T, double rho) 
   return T + rho * inv_c / K.heat_den;
 }
 
+// The FP32-mixed path: the increment rho / (n k_B C(T)) of the same
+// expression in FP32 (relative error ~1e-7 of the increment); T itself
+// accumulates in FP64
+__device__ __forceinline__ float heat_increment_f32(const Consts &K, double T, float rho) {
+  const float Tf = (float)T;
+  if (K.n_solids == 1) {
+    const float tp = Tf * (float)K.Tp_fac, D = 1.1f + tp;
+    const float D2 = D * D;
+    return rho * D2 / ((float)K.heat_den * (0.3f * D2 + 1.2f * tp * (2.2f + tp)));
+  }
+  float inv_c = 0.0f;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (s >= K.n_solids) break;
+    const float tp = Tf * (float)K.Tp_fac_s[s], D = 1.1f + tp;
+    const float D2 = D * D;
+    inv_c += (float)K.ne_frac[s] * D2 / (0.3f * D2 + 1.2f * tp * (2.2f + tp));
+  }
+  return rho * inv_c / (float)K.heat_den;
+}
+
 // reduced Lee-More resistivity, Eqs. (A4)-(A6), capped; inside the band
 // where the cap holds, the cap itself.  eta_num / max(tau_hot, tau_cold) is
 // the smaller of eta_num/(A_hot (kT)^1.5) and eta_num sqrt(kT)/B_cold, both
@@ -107,22 +128,38 @@ __device__ __forceinline__ double bheat_node(const Consts &K, const GView<R> &g,
   }
   if (i < nx && j < ny && k < nz) {
     const long long c = i + (long long)nx * (j + (long long)ny * k);
-    double rho = g.H[c] * K.F_H;
-    double Te = g.T[c];
-    bool changed = false;
+    const double Hc = g.H[c];
+    R jb2 = R(0);
     if (K.physics & P_FIELDS) {
       const R *Jx = g.J[0], *Jy = g.J[1], *Jz = g.J[2];
       // cell-centred mean of the edge current in the field precision
       const R jbx = R(0.25) * (Jx[q] + Jx[q + sy] + Jx[q + sz] + Jx[q + sy + sz]);
       const R jby = R(0.25) * (Jy[q] + Jy[q + 1] + Jy[q + sz] + Jy[q + 1 + sz]);
       const R jbz = R(0.25) * (Jz[q] + Jz[q + 1] + Jz[q + sy] + Jz[q + 1 + sy]);
-      const double ro = g.eta[c] * K.F_ohm * (double)(jbx * jbx + jby * jby + jbz * jbz);
+      jb2 = jbx * jbx + jby * jby + jbz * jbz;
+    }
+    // a cell without drag heat or current keeps T and eta (and adds no
+    // Ohmic energy) unless e-i equilibration moves it
+    if (Hc == 0.0 && jb2 == R(0) && !(K.physics & P_EI)) return e_ohm;
+    double Te = g.T[c];
+    bool changed = false;
+    if constexpr (sizeof(R) == 4) {
+      const float ro = g.eta_r[c] * (float)K.F_ohm * jb2;
+      const float rho = (float)(Hc * K.F_H) + ro;
+      e_ohm = (double)ro * K.dx3;
+      if ((K.physics & P_HEATING) && rho != 0.0f) {  // rho = 0 leaves T as it is
+        Te += (double)heat_increment_f32(K, Te, rho);
+        changed = true;
+      }
+    } else {
+      double rho = Hc * K.F_H;
+      const double ro = g.eta[c] * K.F_ohm * (double)jb2;
       e_ohm = ro * K.dx3;
       rho += ro;
-    }
-    if ((K.physics & P_HEATING) && rho != 0.0) {  // rho = 0 leaves T as it is
-      Te = heated(K, Te, rho);
-      changed = true;
+      if ((K.physics & P_HEATING) && rho != 0.0) {  // rho = 0 leaves T as it is
+        Te = heated(K, Te, rho);
+        changed = true;
+      }
     }
     // e-i equilibration over the step (App. A): with a = rate_e dt and
     // b = rate_i dt frozen, the gap d = T_e - T_i decays by exp(-(a + b)) and

@@ -445,12 +445,12 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
 
 // ---------------------------------------------------------------- warp deposits
 // A warp adds its electrons' current and drag heat to the grid in one pass
-// through a shared-memory stage.  The warp first sorts its electrons by the
-// cell of x^{n+1} (a 32-wide bitonic network on (cell, lane) keys), and each
-// lane writes its electron as the row of its sorted position: 25 values, per
-// current component c the 8 corners of its own lattice (axis c
-// half-staggered, the other two node-centred) times w v_c / c, then the drag
-// heat.  Each lane then walks one column down the 32 rows, summing while the
+// through a shared-memory stage.  The warp first groups its electrons by the
+// cell of x^{n+1} (lanes with equal cells found by one match instruction),
+// and each lane writes its electron as the row of its place in that
+// grouping: 25 values, per current component c the 8 corners of its own
+// lattice (axis c half-staggered, the other two node-centred) times
+// w v_c / c, then the drag heat.  Each lane then walks one column down the 32 rows, summing while the
 // rows stay in one cell and adding the sum to the grid with one reduction
 // when the cell changes: a cell's electrons cost one reduction per node,
 // not one per electron, and within one reduction instruction the lanes
@@ -462,7 +462,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
 // stride_c; the walker keeps one sum per value of off.
 constexpr int kDepCols = 25;               // 3 x 8 corners, heat
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;   // row with nothing to deposit
-constexpr uint32_t kNoCell = (1u << 27) - 1u;  // sort key of such a row (cells < 2^27 - 1)
+constexpr uint32_t kNoCell = (1u << 27) - 1u;  // cell key of such a row (cells < 2^27 - 1)
 constexpr unsigned kFull = 0xffffffffu;
 
 // column stride in elements: 16-byte column reads by 8 lanes fall in 8
@@ -473,21 +473,6 @@ __host__ __device__ constexpr int dep_stride() { return (32 * (int)sizeof(R) + 1
 // of each electron, later the heat sum of each run)
 template <typename R>
 __host__ __device__ constexpr int dep_words() { return kDepCols * dep_stride<R>() + 32; }
-
-// ascending sort of one 32-bit value per lane across the warp
-__device__ __forceinline__ uint32_t warp_sort32(uint32_t c) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const uint32_t o = __shfl_xor_sync(0xffffffffu, c, j);
-      const bool keep_min = ((lane & k) == 0) == ((lane & j) == 0);
-      c = keep_min ? min(c, o) : max(c, o);
-    }
-  }
-  return c;
-}
 
 template <typename R>
 struct Vec16;  // the rows one 16-byte shared load covers
@@ -533,12 +518,24 @@ __device__ __forceinline__ void warp_deposit(const Consts &K, const Grid<R> &g, 
   }
   const int offs = (ax.iS - ax.iN + 1) | ((ay.iS - ay.iN + 1) << 1) | ((az.iS - az.iN + 1) << 2);
   const uint32_t hk = (heat != R(0) && heat_cell >= 0) ? (uint32_t)heat_cell : kNoKey;
-  // lane p learns which electron is p-th in cell order (src) and tells it
-  const int src = (int)(warp_sort32((ck << 5) | (uint32_t)lane) & 31u);
-  uint32_t *rowof = reinterpret_cast<uint32_t *>(buf + kDepCols * S);
-  rowof[src] = (uint32_t)lane;
+  // rows grouped by cell: the lanes sharing a cell take consecutive rows, the
+  // groups in the order of their first lanes (offsets: a prefix sum of the
+  // group sizes over the groups' first lanes); lane p then learns which
+  // electron holds row p (src)
+  const unsigned same = __match_any_sync(kFull, ck);
+  const int lead = __ffs((int)same) - 1;
+  const int size_here = lane == lead ? __popc(same) : 0;
+  int incl = size_here;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int row = __shfl_sync(kFull, incl - size_here, lead) + __popc(same & ((1u << lane) - 1u));
+  uint32_t *srcof = reinterpret_cast<uint32_t *>(buf + kDepCols * S);
+  srcof[row] = (uint32_t)lane;
   __syncwarp();
-  const int row = (int)rowof[lane];
+  const int src = (int)srcof[lane];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const R fx = c == 0 ? ax.fS : ax.fN, fy = c == 1 ? ay.fS : ay.fN, fz = c == 2 ? az.fS : az.fN;
@@ -573,7 +570,7 @@ __device__ __forceinline__ void warp_deposit(const Consts &K, const Grid<R> &g, 
   const int o1 = (lane & 1) + g.sy * ((lane >> 1) & 1) + g.sz * ((lane >> 2) & 1);
   const int sc = c == 0 ? 1 : (c == 1 ? g.sy : g.sz);
   const R *col = buf + (lane < kDepCols ? lane : kDepCols - 1) * S;
-  R *hsum = buf + kDepCols * S;  // the row indices there have been read
+  R *hsum = buf + kDepCols * S;  // the lane indices there have been read
   R s0 = R(0), s1 = R(0);  // rows with off = 0, off = 1
   constexpr int V = Vec16<R>::n;
 #pragma unroll 1

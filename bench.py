@@ -42,7 +42,7 @@ NCU_DRAM_BYTES_PER_PSTEP = {"fp32": 57.1, "fp64": None}
 # the same for k_batch_push, captured on the first 16 targets of the scan
 # (profiles/k_batch_push_batched_scan16_fp32.md): the traffic is the
 # electron state streamed once, so it scales with the particle-steps
-NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": 65.1, "fp64": None}
+NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": 64.7, "fp64": None}
 SORT_INTERVAL = 10  # measured: 10 beats 20 (k_push 0.99 vs 1.04 ms, step 1.17 vs 1.20 ms)
 
 

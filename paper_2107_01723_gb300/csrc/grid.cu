@@ -11,14 +11,14 @@
 namespace hpic {
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_efield(const Consts K, GView<R> g) {
+__global__ void __launch_bounds__(256, 6) k_efield(const Consts K, GView<R> g) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < K.nvec;
        q += (long long)gridDim.x * blockDim.x)
     efield_node(K, g, q);
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_bheat(const Consts K, GView<R> g, TallyView tv) {
+__global__ void __launch_bounds__(256, 6) k_bheat(const Consts K, GView<R> g, TallyView tv) {
   __shared__ double smem[32];
   double e_ohm = 0.0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < K.nvec;

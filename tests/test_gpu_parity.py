@@ -96,6 +96,58 @@ def test_injection_from_empty(prec):
     one_step_compare(o, cfg, prec)  # step 0: nothing moves, 150 electrons injected
 
 
+def deposit_pattern(kind: str, n: int, nc: int, rng) -> np.ndarray:
+    """Cell (i, j, k) of each electron, in slot order, for the layouts the
+    warp-level deposit must handle: a whole warp in one cell, every lane in
+    its own cell, two cells interleaved lane by lane, runs of random length,
+    and random cells."""
+    if kind == "one_cell":
+        c = np.tile([[3, 3, 3]], (n, 1))
+    elif kind == "all_distinct":
+        c = np.stack([np.arange(n) % nc, (np.arange(n) // nc) % nc, (np.arange(n) // nc ** 2) % nc], 1)
+    elif kind == "interleaved":
+        c = np.where((np.arange(n) % 2)[:, None] == 0, [[2, 3, 4]], [[2, 4, 4]])
+    elif kind == "runs":
+        cells, left = [], n
+        while left > 0:
+            m = int(min(left, rng.integers(1, 12)))
+            cells += [rng.integers(1, nc - 1, 3)] * m
+            left -= m
+        c = np.array(cells)
+    else:
+        c = rng.integers(0, nc, (n, 3))
+    return np.asarray(c, dtype=float)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", ["one_cell", "all_distinct", "interleaved", "runs", "random"])
+def test_deposit_layouts(prec, kind):
+    """j_h and the drag heat of one step for electrons laid out in slots so
+    that a warp holds one cell, 32 cells, two cells alternating, runs of
+    random length or random cells; positions inside a cell on both sides of
+    its centre (both offsets of each staggered lattice); some electrons at
+    zero energy so that they are cut and leave only heat (j_h, Eq. (A2);
+    drag heat, Eq. (5))."""
+    cfg = small_cfg(n=(8, 8, 8), n_macro=0)
+    rng = np.random.default_rng({"one_cell": 1, "all_distinct": 2, "interleaved": 3,
+                                 "runs": 4, "random": 5}[kind])
+    n = 4096 + 17  # ragged last warp
+    dx = cfg["target"]["dx"]
+    cell = deposit_pattern(kind, n, 8, rng)
+    pos = (cell + rng.uniform(0.02, 0.98, (n, 3))) * dx
+    eps = rng.uniform(0.2, 40.0, n)
+    eps[rng.random(n) < 0.05] = 1e-6  # below the 1 keV cut
+    d = rng.normal(size=(n, 3))
+    d *= (np.sqrt(eps * (eps + 2.0)) / np.linalg.norm(d, axis=1))[:, None]
+    p = {"x": pos[:, 0], "y": pos[:, 1], "z": pos[:, 2], "ux": d[:, 0], "uy": d[:, 1],
+         "uz": d[:, 2], "tau": rng.uniform(1.0, 5.0, n), "id": np.arange(n, dtype=np.uint32)}
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    o.set_particles(p)
+    o.step(0)
+    one_step_compare(o, cfg, prec)
+    assert o.tallies()["n_cut"] > 0
+
+
 def test_edge_cases_fp64():
     """Walls, the cut, zero optical depth and escape, in one step."""
     cfg = small_cfg(n=(6, 5, 7), n_macro=0, spot_r=1e-6)

@@ -5,7 +5,7 @@ Workload: 128^3 cells of 1 um gold, 1e7 macro-electrons injected over
 100 fs at 1e21 W/cm^2 (T_hot = 13.7 MeV), dt = 0.5 fs, reflux on all faces;
 the 200-step injection runs before timing, then K steps are timed with the
 full population resident in HBM.  One step = push/collide/emit/deposit,
-E and B update, heating, (injection), and the cell sort every 10 steps.
+E and B update, heating, (injection), and the cell sort every 5 steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
     python bench.py --impl reference ...   # the FP64 CPU oracle, timed alone
@@ -43,7 +43,7 @@ NCU_DRAM_BYTES_PER_PSTEP = {"fp32": 57.1, "fp64": None}
 # (profiles/k_batch_push_batched_scan16_fp32.md): the traffic is the
 # electron state streamed once, so it scales with the particle-steps
 NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": 64.7, "fp64": None}
-SORT_INTERVAL = 10  # measured: 10 beats 20 (k_push 0.99 vs 1.04 ms, step 1.17 vs 1.20 ms)
+SORT_INTERVAL = 5  # measured, default bench: 5 / 10 / 20 / 40 give 9.64 / 9.45 / 8.99 / 8.20e9 particle-steps/s
 
 
 def peaks() -> dict:

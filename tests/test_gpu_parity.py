@@ -276,7 +276,7 @@ def test_load_rejects_outside_positions():
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_full_size_headline(prec):
     """128^3 gold, 1e7 electrons at 1e21 W/cm^2 (the headline workload) in the
-    launch configuration the benchmark times (cell sort every 10 steps).
+    launch configuration the benchmark times (cell sort every 5 steps).
 
     (1) The oracle computes the first two steps itself -- 5e4 electrons
     injected at step 0 and pushed at step 1 through the full 128^3 grid, plus
@@ -285,7 +285,7 @@ def test_full_size_headline(prec):
     energy closure, total current, div B, heating, tally consistency."""
     cfg = W.config2()
     prec_id, tol, abs_frac = PREC[prec]
-    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec_id, sort_interval=10)
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec_id, sort_interval=5)
     o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
     g.step(2)
     o.step(2)

@@ -399,6 +399,7 @@ void destroy_all(hpic_ctx *c) {
   cudaFree(c->t64);
   cudaFree(c->t32);
   cudaFree(c->cnt);
+  cudaFree(c->xfer);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
 }
 
@@ -486,6 +487,31 @@ int sort_impl(hpic_ctx *ctx) {
   return HPIC_OK;
 }
 
+// device scratch of at least `bytes` for the host transfers
+int xfer_reserve(hpic_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->xfer_bytes) return HPIC_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  cudaFree(ctx->xfer);
+  ctx->xfer = nullptr;
+  ctx->xfer_bytes = 0;
+  const size_t want = (bytes + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
+  if (cudaMalloc(&ctx->xfer, want) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, HPIC_ENOMEM, "transfer scratch allocation failed");
+  }
+  ctx->xfer_bytes = want;
+  return HPIC_OK;
+}
+
+int xfer_grid(const hpic_ctx *ctx, long long n) {
+  const long long want = (n + 255) / 256, cap = 8LL * ctx->sm_count;
+  return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+// The live electrons in storage order.  On the device: the live slots are
+// counted per chunk and scanned, then each array is compacted and
+// converted to double (positions back to metres) into the transfer scratch
+// and copied to the caller's array; the ids likewise.
 template <typename R>
 int read_particles_impl(hpic_ctx *ctx, double *x, double *y, double *z, double *ux, double *uy,
                         double *uz, double *tau, uint32_t *id, int64_t cap, int64_t *n_out) {
@@ -493,71 +519,101 @@ int read_particles_impl(hpic_ctx *ctx, double *x, double *y, double *z, double *
   int rc = read_counters(ctx, &h);
   if (rc) return rc;
   const long long n = h.n;
-  std::vector<R> a[7];
-  std::vector<uint32_t> ids(n);
+  const long long nb = hpic::xfer_chunks(n);
+  const size_t cc_bytes = (size_t)(nb + 1) * sizeof(uint32_t);
+  const size_t data_off = (cc_bytes + 255) & ~(size_t)255;
+  rc = xfer_reserve(ctx, data_off + (size_t)(n > 0 ? n : 1) * sizeof(double));
+  if (rc) return rc;
+  uint32_t *cc = static_cast<uint32_t *>(ctx->xfer);
+  void *data = static_cast<char *>(ctx->xfer) + data_off;
   const hpic::PView<R> P = pview<R>(ctx, ctx->cur);
-  R *src[7] = {P.x, P.y, P.z, P.ux, P.uy, P.uz, P.tau};
-  for (int q = 0; q < 7; ++q) {
-    a[q].resize(n);
-    if (n) CK(cudaMemcpyAsync(a[q].data(), src[q], n * sizeof(R), cudaMemcpyDeviceToHost, ctx->stream));
-  }
-  if (n) CK(cudaMemcpyAsync(ids.data(), P.id, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  hpic::launch_live_scan(P.id, n, cc, ctx->stream);
+  uint32_t live32 = 0;
+  CK(cudaMemcpyAsync(&live32, cc + nb, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  long long live = 0;
-  for (long long i = 0; i < n; ++i) live += ids[i] != hpic::kDead;
+  const long long live = live32;
   *n_out = live;
   if (live > cap) return fail(ctx, HPIC_EINVAL, "output capacity below the live particle count");
   const double dx = ctx->tgt.dx_m;
-  long long m = 0;
-  for (long long i = 0; i < n; ++i) {
-    if (ids[i] == hpic::kDead) continue;
-    if (x) x[m] = (double)a[0][i] * dx;
-    if (y) y[m] = (double)a[1][i] * dx;
-    if (z) z[m] = (double)a[2][i] * dx;
-    if (ux) ux[m] = (double)a[3][i];
-    if (uy) uy[m] = (double)a[4][i];
-    if (uz) uz[m] = (double)a[5][i];
-    if (tau) tau[m] = (double)a[6][i];
-    if (id) id[m] = ids[i];
-    ++m;
+  const R *src[7] = {P.x, P.y, P.z, P.ux, P.uy, P.uz, P.tau};
+  double *dst[7] = {x, y, z, ux, uy, uz, tau};
+  for (int q = 0; q < 7; ++q) {
+    if (!dst[q] || live == 0) continue;
+    hpic::launch_compact<R, double>(src[q], P.id, n, cc, q < 3 ? dx : 1.0,
+                                    static_cast<double *>(data), ctx->stream);
+    CK(cudaMemcpyAsync(dst[q], data, live * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
   }
+  if (id && live > 0) {
+    hpic::launch_compact<uint32_t, uint32_t>(P.id, P.id, n, cc, 1.0,
+                                             static_cast<uint32_t *>(data), ctx->stream);
+    CK(cudaMemcpyAsync(id, data, live * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  CK(cudaGetLastError());
   return HPIC_OK;
 }
 
+// Replace the population with n host electrons.  Every array is copied to
+// the transfer scratch as it is; a first pass checks the positions and ids
+// on the device (nothing is written to the state unless all pass), a second
+// converts each array into the particle storage.
 template <typename R>
 int load_particles_impl(hpic_ctx *ctx, int64_t n, const double *x, const double *y,
                         const double *z, const double *ux, const double *uy, const double *uz,
                         const double *tau, const uint32_t *id) {
   const double dx = ctx->tgt.dx_m;
   const int nn[3] = {ctx->tgt.nx, ctx->tgt.ny, ctx->tgt.nz};
-  const double *pos[3] = {x, y, z};
-  const bool unbounded = (ctx->K.physics & hpic::P_UNBOUNDED) != 0;
-  for (int64_t i = 0; i < n; ++i) {
+  const int unbounded = (ctx->K.physics & hpic::P_UNBOUNDED) != 0;
+  const size_t data_off = 256;  // the error count first
+  int rc = xfer_reserve(ctx, data_off + (size_t)(n > 0 ? n : 1) * sizeof(double));
+  if (rc) return rc;
+  unsigned *bad = static_cast<unsigned *>(ctx->xfer);
+  double *data = reinterpret_cast<double *>(static_cast<char *>(ctx->xfer) + data_off);
+  const int grid = xfer_grid(ctx, n);
+  CK(cudaMemsetAsync(bad, 0, sizeof(unsigned), ctx->stream));
+  const double *src[7] = {x, y, z, ux, uy, uz, tau};
+  if (n > 0) {
     for (int a = 0; a < 3; ++a) {
-      const double X = pos[a][i] / dx;
-      if (unbounded ? !std::isfinite(X) : !(X >= 0.0 && X <= (double)nn[a]))
-        return fail(ctx, HPIC_EINVAL, "particle position outside the target");
+      CK(cudaMemcpyAsync(data, src[a], n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      hpic::launch_load_convert<R>(data, n, 1.0, static_cast<R *>(nullptr), 1, dx, (double)nn[a],
+                                   unbounded, bad, grid, ctx->stream);
     }
-    if (id[i] == hpic::kDead) return fail(ctx, HPIC_EINVAL, "id 0xFFFFFFFF is reserved");
+    CK(cudaMemcpyAsync(data, id, n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+    hpic::launch_check_ids(reinterpret_cast<const uint32_t *>(data), n, bad, grid, ctx->stream);
+  }
+  unsigned nbad = 0;
+  CK(cudaMemcpyAsync(&nbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
+  if (nbad) {
+    // the host's own reading of the first offence, for the message
+    for (int64_t i = 0; i < n; ++i) {
+      if (id[i] == hpic::kDead) return fail(ctx, HPIC_EINVAL, "id 0xFFFFFFFF is reserved");
+      for (int a = 0; a < 3; ++a) {
+        const double X = src[a][i] / dx;
+        if (unbounded ? !std::isfinite(X) : !(X >= 0.0 && X <= (double)nn[a]))
+          return fail(ctx, HPIC_EINVAL, "particle position outside the target");
+      }
+    }
+    return fail(ctx, HPIC_EINVAL, "particle position outside the target");
   }
   const long long extra = injection_total(ctx);
-  int rc = reserve(ctx, n + extra);
+  rc = reserve(ctx, n + extra);
   if (rc) return rc;
   const hpic::PView<R> P = pview<R>(ctx, ctx->cur);
   R *dst[7] = {P.x, P.y, P.z, P.ux, P.uy, P.uz, P.tau};
-  const double *src[7] = {x, y, z, ux, uy, uz, tau};
-  std::vector<R> buf(n);
-  for (int q = 0; q < 7; ++q) {
-    const double s = q < 3 ? 1.0 / dx : 1.0;
-    for (int64_t i = 0; i < n; ++i) buf[i] = (R)(src[q][i] * s);
-    if (n) CK(cudaMemcpyAsync(dst[q], buf.data(), n * sizeof(R), cudaMemcpyHostToDevice, ctx->stream));
+  if (n > 0) {
+    CK(cudaMemcpyAsync(P.id, id, n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+    for (int q = 0; q < 7; ++q) {
+      CK(cudaMemcpyAsync(data, src[q], n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      hpic::launch_load_convert<R>(data, n, q < 3 ? 1.0 / dx : 1.0, dst[q], 0, dx, 0.0, unbounded,
+                                   bad, grid, ctx->stream);
+    }
+    if (ctx->K.weighted)  // the envelope's weights come from hpic_load_weights
+      hpic::launch_fill<R>(P.w, n, (R)ctx->K.w, grid, ctx->stream);
     CK(cudaStreamSynchronize(ctx->stream));
-  }
-  if (n) CK(cudaMemcpyAsync(P.id, id, n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
-  if (n && ctx->K.weighted) {  // the envelope's weights come from hpic_load_weights
-    std::vector<R> wd(n, (R)ctx->K.w);
-    CK(cudaMemcpyAsync(P.w, wd.data(), n * sizeof(R), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaGetLastError());
   }
   hpic::Counters h;
   rc = read_counters(ctx, &h);
@@ -918,14 +974,17 @@ int hpic_count_particles(hpic_ctx *ctx, int64_t *n) {
   hpic::Counters h;
   int rc = read_counters(ctx, &h);
   if (rc) return rc;
-  std::vector<uint32_t> ids(h.n);
+  // the live slots counted on the device (the chunk counts of the transfers)
+  const long long nb = hpic::xfer_chunks(h.n);
+  rc = xfer_reserve(ctx, (size_t)(nb + 1) * sizeof(uint32_t));
+  if (rc) return rc;
+  uint32_t *cc = static_cast<uint32_t *>(ctx->xfer);
   const uint32_t *src = ctx->fp32 ? pview<float>(ctx, ctx->cur).id : pview<double>(ctx, ctx->cur).id;
-  if (h.n) {
-    CK(cudaMemcpyAsync(ids.data(), src, h.n * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-  }
-  long long live = 0;
-  for (uint32_t v : ids) live += v != hpic::kDead;
+  hpic::launch_live_scan(src, h.n, cc, ctx->stream);
+  uint32_t live = 0;
+  CK(cudaMemcpyAsync(&live, cc + nb, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
   *n = live;
   return HPIC_OK;
 }

@@ -284,7 +284,10 @@ void destroy_batch(hpic_batch *b) {
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   cudaFree(b->arena);
   cudaFree(b->aux);
-  for (hpic_ctx *c : b->tg) delete c;
+  for (hpic_ctx *c : b->tg) {
+    cudaFree(c->xfer);
+    delete c;
+  }
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
 }

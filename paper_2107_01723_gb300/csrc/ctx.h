@@ -36,6 +36,10 @@ struct hpic_ctx {
   uint32_t *keys = nullptr;
   uint32_t *counts = nullptr;
   uint32_t *partials = nullptr;
+  // device scratch of the host transfers (read/load of the electron state),
+  // grown on demand; owned by this context (also a borrowed batch target)
+  void *xfer = nullptr;
+  size_t xfer_bytes = 0;
   // grid
   void *fields = nullptr;  // E[3], B[3] of R, each nvec long, vstride apart
   void *jfield = nullptr;  // J[3], vstride apart (just after B in a single context)

@@ -8,6 +8,8 @@
 //   k_table  : inverse-CDF bremsstrahlung table from the closed-form CDF
 #include "fields.cuh"
 
+#include <type_traits>
+
 namespace hpic {
 
 template <typename R>
@@ -359,6 +361,161 @@ void launch_field_energy(const Consts &K, GView<R> g, double *dst, int grid, cud
   k_field_energy<R><<<grid, 256, 0, st>>>(K, g, dst);
 }
 
+// ---------------------------------------------------------------- host transfers
+// Reading the electrons out: the live slots in storage order, converted to
+// double with a scale, compacted on the device so that one copy per array
+// crosses to the host.  Slots go in chunks of kXferChunk (256 threads x 8
+// consecutive slots): the live count of each chunk, an exclusive scan of the
+// chunk counts, then each array written at the compacted positions.
+constexpr int kXferChunk = 2048;
+
+__global__ void __launch_bounds__(256) k_live_counts(const uint32_t *id, long long n,
+                                                     uint32_t *cc) {
+  __shared__ uint32_t ws[8];
+  const long long base = (long long)blockIdx.x * kXferChunk + threadIdx.x * 8;
+  uint32_t c = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) c += (base + k < n && id[base + k] != kDead) ? 1u : 0u;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < 8; ++w) t += ws[w];
+    cc[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of cc[0, nb) in one block; the total goes to cc[nb]
+__global__ void __launch_bounds__(1024) k_scan_chunks(uint32_t *cc, long long nb) {
+  __shared__ uint32_t part[1024];
+  const long long per = (nb + 1023) / 1024;
+  const long long b0 = threadIdx.x * per, b1 = b0 + per < nb ? b0 + per : nb;
+  uint32_t s = 0;
+  for (long long b = b0; b < b1; ++b) s += cc[b];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the slice sums
+    const uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  for (long long b = b0; b < b1; ++b) {
+    const uint32_t c = cc[b];
+    cc[b] = run;
+    run += c;
+  }
+  if (threadIdx.x == 1023) cc[nb] = part[1023];
+}
+
+// out[rank] = src[i] * scale (converted to O) for the live slots i of this
+// block's chunk, rank = the slot's place among the live slots
+template <typename T, typename O>
+__global__ void __launch_bounds__(256) k_compact(const T *src, const uint32_t *id, long long n,
+                                                 const uint32_t *cc, double scale, O *out) {
+  __shared__ uint32_t ws[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long base = (long long)blockIdx.x * kXferChunk + threadIdx.x * 8;
+  uint32_t live = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (base + k < n && id[base + k] != kDead) live |= 1u << k;
+  const uint32_t c = __popc(live);
+  uint32_t incl = c;  // inclusive scan over the warp, then over the warps
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) ws[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int w = 0; w < warp; ++w) before += ws[w];
+  long long pos = (long long)cc[blockIdx.x] + before + incl - c;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (live & (1u << k)) {
+      if constexpr (std::is_floating_point<T>::value)
+        out[pos++] = (O)((double)src[base + k] * scale);
+      else
+        out[pos++] = (O)src[base + k];
+    }
+}
+
+// Loading electrons in: dst[i] = (R)(src[i] * scale); with check set, also
+// count positions outside [0, hi] after division by dx (any non-finite
+// value with unbounded), the test the host made before
+template <typename R>
+__global__ void __launch_bounds__(256) k_load_convert(const double *src, long long n,
+                                                      double scale, R *dst, int check,
+                                                      double dx, double hi, int unbounded,
+                                                      unsigned *bad) {
+  unsigned b = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = src[i];
+    if (check) {
+      const double X = v / dx;
+      b += (unbounded ? !isfinite(X) : !(X >= 0.0 && X <= hi)) ? 1u : 0u;
+    }
+    if (dst) dst[i] = (R)(v * scale);
+  }
+  if (check && b) atomicAdd(bad, b);
+}
+
+__global__ void __launch_bounds__(256) k_check_ids(const uint32_t *id, long long n,
+                                                   unsigned *bad) {
+  unsigned b = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b += id[i] == kDead ? 1u : 0u;
+  if (b) atomicAdd(bad, b);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_fill(R *dst, long long n, R v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = v;
+}
+
+long long xfer_chunks(long long n) { return (n + kXferChunk - 1) / kXferChunk; }
+
+void launch_live_scan(const uint32_t *id, long long n, uint32_t *cc, cudaStream_t st) {
+  const long long nb = xfer_chunks(n);
+  if (nb > 0) k_live_counts<<<(unsigned)nb, 256, 0, st>>>(id, n, cc);
+  k_scan_chunks<<<1, 1024, 0, st>>>(cc, nb);
+}
+
+template <typename T, typename O>
+void launch_compact(const T *src, const uint32_t *id, long long n, const uint32_t *cc,
+                    double scale, O *out, cudaStream_t st) {
+  const long long nb = xfer_chunks(n);
+  if (nb > 0) k_compact<T, O><<<(unsigned)nb, 256, 0, st>>>(src, id, n, cc, scale, out);
+}
+
+template <typename R>
+void launch_load_convert(const double *src, long long n, double scale, R *dst, int check,
+                         double dx, double hi, int unbounded, unsigned *bad, int grid,
+                         cudaStream_t st) {
+  k_load_convert<R><<<grid, 256, 0, st>>>(src, n, scale, dst, check, dx, hi, unbounded, bad);
+}
+
+void launch_check_ids(const uint32_t *id, long long n, unsigned *bad, int grid, cudaStream_t st) {
+  k_check_ids<<<grid, 256, 0, st>>>(id, n, bad);
+}
+
+template <typename R>
+void launch_fill(R *dst, long long n, R v, int grid, cudaStream_t st) {
+  k_fill<R><<<grid, 256, 0, st>>>(dst, n, v);
+}
+
+template void launch_compact<uint32_t, uint32_t>(const uint32_t *, const uint32_t *, long long,
+                                                 const uint32_t *, double, uint32_t *,
+                                                 cudaStream_t);
+
 #define HPIC_INST(R)                                                                          \
   template void launch_efield<R>(const Consts &, GView<R>, int, cudaStream_t);                \
   template void launch_bheat<R>(const Consts &, GView<R>, TallyView, int, cudaStream_t);      \
@@ -368,7 +525,12 @@ void launch_field_energy(const Consts &K, GView<R> g, double *dst, int grid, cud
                                       cudaStream_t);                                          \
   template void launch_field_energy<R>(const Consts &, GView<R>, double *, int, cudaStream_t); \
   template void launch_batch_efield<R>(const BatchItem<R> *, BatchDev, int, cudaStream_t);     \
-  template void launch_batch_bheat<R>(const BatchItem<R> *, BatchDev, int, cudaStream_t);
+  template void launch_batch_bheat<R>(const BatchItem<R> *, BatchDev, int, cudaStream_t);     \
+  template void launch_compact<R, double>(const R *, const uint32_t *, long long,             \
+                                          const uint32_t *, double, double *, cudaStream_t);  \
+  template void launch_load_convert<R>(const double *, long long, double, R *, int, double,   \
+                                       double, int, unsigned *, int, cudaStream_t);           \
+  template void launch_fill<R>(R *, long long, R, int, cudaStream_t);
 HPIC_INST(float)
 HPIC_INST(double)
 #undef HPIC_INST

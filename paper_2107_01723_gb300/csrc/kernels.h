@@ -88,6 +88,21 @@ std::vector<InjCell> injection_cells(const hpic_target_desc &t, const hpic_laser
 template <typename R>
 constexpr int push_blocks_per_sm() { return sizeof(R) == 4 ? 5 : 2; }
 
+// host transfers of the electron state (the C-ABI's read and load calls):
+// live-slot compaction in storage order and FP64 <-> R conversion on the device
+long long xfer_chunks(long long n);  // chunk counts needed: xfer_chunks(n) + 1
+void launch_live_scan(const uint32_t *id, long long n, uint32_t *cc, cudaStream_t st);
+template <typename T, typename O>
+void launch_compact(const T *src, const uint32_t *id, long long n, const uint32_t *cc,
+                    double scale, O *out, cudaStream_t st);
+template <typename R>
+void launch_load_convert(const double *src, long long n, double scale, R *dst, int check,
+                         double dx, double hi, int unbounded, unsigned *bad, int grid,
+                         cudaStream_t st);
+void launch_check_ids(const uint32_t *id, long long n, unsigned *bad, int grid, cudaStream_t st);
+template <typename R>
+void launch_fill(R *dst, long long n, R v, int grid, cudaStream_t st);
+
 // allow the push kernels their shared-memory deposit stages (above the
 // default 48 KB for FP64 and the batch); once per device, before any launch
 cudaError_t prepare_push();

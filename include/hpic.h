@@ -258,13 +258,21 @@ int hpic_write_grid(hpic_ctx *ctx, int which, const double *host_in);
 int hpic_count_particles(hpic_ctx *ctx, int64_t *n);
 /* Copy live electrons out in storage order: positions (m), u = p/(m_e c),
  * remaining optical depth tau, id.  Fails with HPIC_EINVAL if cap is less
- * than the live count; *n receives the count. */
+ * than the live count; *n receives the count.  Any of the output pointers
+ * may be NULL (that array is skipped).  The compaction and the conversion
+ * to double run on the device in a scratch buffer the context owns (grown
+ * to 8 bytes per electron slot, freed by hpic_destroy or
+ * hpic_batch_destroy); HPIC_ENOMEM if it cannot be allocated.  This call
+ * and hpic_load_particles / hpic_count_particles synchronise the stream. */
 int hpic_read_particles(hpic_ctx *ctx, double *x, double *y, double *z,
                         double *ux, double *uy, double *uz, double *tau,
                         uint32_t *id, int64_t cap, int64_t *n);
 /* Replace the electron population with n host electrons (same units).
  * Positions must lie in [0, n*dx] on each axis (any finite position with
- * HPIC_UNBOUNDED).  Errors: HPIC_EINVAL, HPIC_ENOMEM. */
+ * HPIC_UNBOUNDED).  The arrays are checked on the device before anything is
+ * written, so on HPIC_EINVAL the population is unchanged; the upload uses
+ * the context's transfer scratch (see hpic_read_particles).  Errors:
+ * HPIC_EINVAL, HPIC_ENOMEM. */
 /* Per-electron weights (real electrons per macro-electron) of the live
  * electrons, in the order hpic_read_particles returns them (same cap / n
  * semantics).  With the flat-top envelope every weight is the Eq. (B1) one. */

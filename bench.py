@@ -242,7 +242,8 @@ def run_gpu(args, world, rank, local):
         sim.set_grid(k, v)
     sim.set_clock(*snap_clock)
     host = snap_p
-    nbytes_state = len(host["id"]) * (7 * (4 if args.precision == "fp32" else 8) + 4)
+    # the C-ABI moves FP64 arrays (and u32 ids) across; conversion is on the device
+    nbytes_state = len(host["id"]) * (7 * 8 + 4)
     torch.cuda.synchronize()
     barrier(world)
     w0 = time.perf_counter()
@@ -258,8 +259,7 @@ def run_gpu(args, world, rank, local):
     tally_bytes = 19 * 8
     e2e = {"value": e_ps_sum / wall_max, "unit": UNIT,
            "h2d_bytes_per_step": nbytes_state / args.steps,
-           "d2h_bytes_per_step": (len(back["id"]) * (7 * (4 if args.precision == "fp32" else 8) + 4)
-                                  + 2 * tally_bytes) / args.steps,
+           "d2h_bytes_per_step": (len(back["id"]) * (7 * 8 + 4) + 2 * tally_bytes) / args.steps,
            "what": ("hpic_load_particles from host arrays + hpic_step(K) + hpic_read_tallies + "
                     "hpic_read_particles to host, wall clock, over the timed steps again "
                     "(grids and clock of their start restored untimed)")}

@@ -450,11 +450,11 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
 // and each lane writes its electron as the row of its place in that
 // grouping: 25 values, per current component c the 8 corners of its own
 // lattice (axis c half-staggered, the other two node-centred) times
-// w v_c / c, then the drag heat.  Each lane then walks one column down the 32 rows, summing while the
-// rows stay in one cell and adding the sum to the grid with one reduction
-// when the cell changes: a cell's electrons cost one reduction per node,
-// not one per electron, and within one reduction instruction the lanes
-// target distinct addresses.
+// w v_c / c, then the drag heat.  Each lane then walks one column down the
+// 32 rows, summing while the rows stay in one cell and adding the sum to the
+// grid with one reduction when the cell changes: a cell's electrons cost one
+// reduction per node, not one per electron, and within one reduction
+// instruction the lanes target distinct addresses.
 //
 // Node of a corner: with nk the node index of the cell of x^{n+1}, the
 // corner (a, b, e) of component c of an electron whose axis-c staggered
@@ -469,8 +469,8 @@ constexpr unsigned kFull = 0xffffffffu;
 // distinct 4-bank groups (stride = 16 bytes mod 128)
 template <typename R>
 __host__ __device__ constexpr int dep_stride() { return (32 * (int)sizeof(R) + 16) / (int)sizeof(R); }
-// elements of one warp's stage: the columns, then 32 slots (the row index
-// of each electron, later the heat sum of each run)
+// elements of one warp's stage: the columns, then 32 slots (the lane that
+// holds each row, later the heat sum of the run ending at each row)
 template <typename R>
 __host__ __device__ constexpr int dep_words() { return kDepCols * dep_stride<R>() + 32; }
 
@@ -503,7 +503,7 @@ __device__ __forceinline__ void warp_deposit(const Consts &K, const Grid<R> &g, 
   constexpr int S = dep_stride<R>();
   const int lane = threadIdx.x & 31;
 
-  // ---- this lane's electron, written as row `row` of the cell order
+  // ---- this lane's electron, written as row `row` of the cell grouping
   if (!dep) { X = R(0); Y = R(0); Zc = R(0); }  // finite weights, zero values
   const Axis<R> ax = axis_weights(X, K.nx), ay = axis_weights(Y, K.ny), az = axis_weights(Zc, K.nz);
   R v[3] = {R(0), R(0), R(0)};

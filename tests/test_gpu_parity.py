@@ -273,6 +273,49 @@ def test_load_rejects_outside_positions():
     g.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_load_checks_before_writing(prec):
+    """A load whose last electron lies outside the target (or carries the
+    reserved id) is refused and leaves the population as it was; a valid
+    load of 10,001 electrons (ragged against the transfer chunks) reads back
+    exactly (FP64) or to FP32 rounding, in storage order, with dead slots
+    skipped."""
+    cfg = small_cfg(n=(9, 7, 8), n_macro=0)
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=PREC[prec][0])
+    rng = np.random.default_rng(21)
+    n = 10_001
+    dx = cfg["target"]["dx"]
+    L = np.array([9, 7, 8]) * dx
+    p = {"x": rng.uniform(0, 1, n) * L[0], "y": rng.uniform(0, 1, n) * L[1],
+         "z": rng.uniform(0, 1, n) * L[2], "ux": rng.normal(0, 3, n), "uy": rng.normal(0, 3, n),
+         "uz": rng.normal(0, 3, n), "tau": rng.uniform(0.1, 5, n),
+         "id": rng.permutation(n).astype(np.uint32) + 7}
+    g.set_particles(p)
+    before = g.particles()
+    tol = 0.0 if prec == "fp64" else 1e-7
+    for k in ("x", "y", "z", "ux", "uy", "uz", "tau"):
+        np.testing.assert_allclose(before[k], p[k], rtol=tol, atol=tol * (dx if k in "xyz" else 1.0))
+    assert np.array_equal(before["id"], p["id"])
+    for bad in ("z", "id"):
+        q = {k: v.copy() for k, v in p.items()}
+        if bad == "z":
+            q["z"][-1] = L[2] * (1 + 1e-9)
+        else:
+            q["id"][-1] = 0xFFFFFFFF
+        with pytest.raises(hpic.HpicError) as e:
+            g.set_particles(q)
+        assert e.value.code == hpic.HPIC_EINVAL
+        after = g.particles()
+        for k in before:
+            assert np.array_equal(after[k], before[k]), (bad, k)
+    # one step: some electrons leave through the walls or stay; the read
+    # skips no live one and returns only ids that were loaded
+    g.step(1)
+    assert g.n == len(g.particles()["id"])
+    assert np.isin(g.particles()["id"], p["id"]).all()
+    g.close()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_full_size_headline(prec):
     """128^3 gold, 1e7 electrons at 1e21 W/cm^2 (the headline workload) in the

@@ -278,8 +278,8 @@ def test_load_checks_before_writing(prec):
     """A load whose last electron lies outside the target (or carries the
     reserved id) is refused and leaves the population as it was; a valid
     load of 10,001 electrons (ragged against the transfer chunks) reads back
-    exactly (FP64) or to FP32 rounding, in storage order, with dead slots
-    skipped."""
+    in storage order to the rounding of the unit conversion (positions are
+    held in cells: x/dx and back) or of FP32, with dead slots skipped."""
     cfg = small_cfg(n=(9, 7, 8), n_macro=0)
     g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=PREC[prec][0])
     rng = np.random.default_rng(21)
@@ -292,7 +292,7 @@ def test_load_checks_before_writing(prec):
          "id": rng.permutation(n).astype(np.uint32) + 7}
     g.set_particles(p)
     before = g.particles()
-    tol = 0.0 if prec == "fp64" else 1e-7
+    tol = 1e-15 if prec == "fp64" else 1e-7
     for k in ("x", "y", "z", "ux", "uy", "uz", "tau"):
         np.testing.assert_allclose(before[k], p[k], rtol=tol, atol=tol * (dx if k in "xyz" else 1.0))
     assert np.array_equal(before["id"], p["id"])

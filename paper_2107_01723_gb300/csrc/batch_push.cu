@@ -110,7 +110,7 @@ k_batch_push(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
     sc.target = it.K.target_index;
     const long long local = (w - wpref_s[t]) * 32 + lane;
     push_warp(it.K, it.h, make_grid(it.K, it.g), tab, it.tv, sc, p, it.off + local,
-              local < wstate[warp][1], acc, stage);
+              local < wstate[warp][1], acc, tal_s + t * kAccN, stage);
   }
   if (t >= 0) flush_acc(acc, tal_s + t * kAccN);
   __syncthreads();

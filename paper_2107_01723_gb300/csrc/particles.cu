@@ -31,6 +31,9 @@ __global__ void __launch_bounds__(256, push_blocks_per_sm<R>())
 k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__restrict__ tab,
        Counters *cnt, TallyView tv) {
   __shared__ double red[kAccN * 32];
+  __shared__ double rare[kAccN];  // the rare tally sums of the block
+  if (threadIdx.x < kAccN) rare[threadIdx.x] = 0.0;
+  __syncthreads();
   extern __shared__ __align__(16) unsigned char dyn[];  // the warps' deposit stages
   R *stage = reinterpret_cast<R *>(dyn) + (threadIdx.x >> 5) * dep_words<R>();
   const long long n = cnt->n;
@@ -49,11 +52,13 @@ k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__rest
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); base < n;
        base += stride)
-    push_warp(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc, stage);
+    push_warp(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc, rare, stage);
 
   double v[kAccN];
   acc.values(v);
-  block_flush<kAccN>(v, kAccSlot, tv.tal, red);
+  block_flush<kAccN>(v, kAccSlot, tv.tal, red);  // synchronises the block
+  if (threadIdx.x < kAccN && rare[threadIdx.x] != 0.0)
+    atomicAdd(tv.tal + kAccSlot[threadIdx.x], rare[threadIdx.x]);
 }
 
 // ---------------------------------------------------------------- injection

@@ -137,16 +137,21 @@ __device__ constexpr int kAccSlot[kAccN] = {
     T_W_FIELD, T_E_DRAG, T_E_ESC, T_E_REFLUX, T_E_XRAY, T_E_XRAY_ABOVE, T_N_ESC,
     T_N_REFLUX, T_N_REFLUX_ABS, T_N_CUT, T_N_EMIT, T_PSTEPS, T_N_NONFINITE};
 
+// the frequent sums stay in registers; the rare ones (escape, reflux,
+// photons, non-finite electrons) go straight into a shared-memory array of
+// kAccN doubles indexed like kAccSlot, so they hold no registers
+enum AccIndex { A_W = 0, A_DRAG, A_ESC, A_REF, A_X, A_XA, A_N_ESC, A_N_REF, A_N_REFABS, A_N_CUT,
+                A_N_EMIT, A_N_STEPS, A_N_NF };
+
 template <typename R>
 struct Acc {
   R W = 0, drag = 0;
-  double esc = 0, ref = 0, x = 0, xa = 0;
-  int n_esc = 0, n_ref = 0, n_refabs = 0, n_cut = 0, n_emit = 0, n_steps = 0, n_nf = 0;
-  // in the order of kAccSlot
+  int n_cut = 0, n_steps = 0;
+  // in the order of kAccSlot (the rare slots are zero here)
   __device__ __forceinline__ void values(double (&v)[kAccN]) const {
-    v[0] = (double)W; v[1] = (double)drag; v[2] = esc; v[3] = ref; v[4] = x; v[5] = xa;
-    v[6] = n_esc; v[7] = n_ref; v[8] = n_refabs; v[9] = n_cut; v[10] = n_emit;
-    v[11] = n_steps; v[12] = n_nf;
+#pragma unroll
+    for (int q = 0; q < kAccN; ++q) v[q] = 0.0;
+    v[A_W] = (double)W; v[A_DRAG] = (double)drag; v[A_N_CUT] = n_cut; v[A_N_STEPS] = n_steps;
   }
 };
 
@@ -295,7 +300,8 @@ template <typename R>
 __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const Grid<R> &g,
                                         const R *__restrict__ tab, const TallyView &tv,
                                         const StepCtx &sc, uint32_t id, R w, R &X, R &Y, R &Zc,
-                                        R &ux, R &uy, R &uz, R &tau, Acc<R> &acc, R &heat_out,
+                                        R &ux, R &uy, R &uz, R &tau, Acc<R> &acc, double *rare,
+                                        R &heat_out,
                                         int &heat_cell) {
   const int nx = K.nx, ny = K.ny, nz = K.nz;
 
@@ -402,9 +408,9 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
       e.inv_dlogE = h.inv_dlogE; e.th_scale = h.th_scale; e.inv_boost = h.inv_boost;
       e.E_cut = h.E_cut;
       const EmitOut<R> o = emit_photon<R>(e, sc, id, w, eps, ux, uy, uz);
-      acc.x += o.x;
-      acc.xa += o.xa;
-      ++acc.n_emit;
+      atomicAdd(rare + A_X, o.x);
+      if (o.xa != 0.0) atomicAdd(rare + A_XA, o.xa);
+      atomicAdd(rare + A_N_EMIT, 1.0);
       tau = o.tau;
       eps = o.eps;
       ux = o.ux; uy = o.uy; uz = o.uz;
@@ -429,11 +435,11 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     const Crossing<R> c = cross_faces<R>(h.eps_esc, h.du_reflux, h.sigma_dtheta, sc.step,
                                          sc.target, sc.key0, sc.key1, id, w, nx, ny, nz,
                                          pos[0], pos[1], pos[2], ux, uy, uz);
-    acc.esc += c.esc;
-    acc.ref += c.ref;
-    acc.n_esc += c.n_esc;
-    acc.n_ref += c.n_ref;
-    acc.n_refabs += c.n_refabs;
+    if (c.esc != 0.0) atomicAdd(rare + A_ESC, c.esc);
+    if (c.ref != 0.0) atomicAdd(rare + A_REF, c.ref);
+    if (c.n_esc) atomicAdd(rare + A_N_ESC, (double)c.n_esc);
+    if (c.n_ref) atomicAdd(rare + A_N_REF, (double)c.n_ref);
+    if (c.n_refabs) atomicAdd(rare + A_N_REFABS, (double)c.n_refabs);
     if (!c.alive) return false;
     pos[0] = c.pos[0]; pos[1] = c.pos[1]; pos[2] = c.pos[2];
     ux = c.u[0]; uy = c.u[1]; uz = c.u[2];
@@ -625,7 +631,8 @@ template <typename R>
 __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, const Grid<R> &g,
                                           const R *__restrict__ tab, const TallyView &tv,
                                           const StepCtx &sc, const PView<R> &p, long long ip,
-                                          bool in_range, Acc<R> &acc, R *__restrict__ stage) {
+                                          bool in_range, Acc<R> &acc, double *rare,
+                                          R *__restrict__ stage) {
   bool live = false, dep = false;
   uint32_t id = kDead;
   R X = 0, Y = 0, Zc = 0, ux = 0, uy = 0, uz = 0, tau = 0, heat = 0, w = h.w;
@@ -642,13 +649,13 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
         live = true;
       } else {
         p.id[ip] = kDead;
-        ++acc.n_nf;
+        atomicAdd(rare + A_N_NF, 1.0);
       }
     }
   }
   if (live) {
     ++acc.n_steps;
-    dep = advance(K, h, g, tab, tv, sc, id, w, X, Y, Zc, ux, uy, uz, tau, acc, heat, heat_cell);
+    dep = advance(K, h, g, tab, tv, sc, id, w, X, Y, Zc, ux, uy, uz, tau, acc, rare, heat, heat_cell);
     if (dep) {
       st_stream(p.x + ip, X); st_stream(p.y + ip, Y); st_stream(p.z + ip, Zc);
       st_stream(p.ux + ip, ux); st_stream(p.uy + ip, uy); st_stream(p.uz + ip, uz);

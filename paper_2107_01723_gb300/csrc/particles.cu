@@ -24,9 +24,9 @@ namespace hpic {
 
 template <typename R>
 // FP32: five 256-thread blocks per SM (48 registers, a few spills to L1),
-// launched as one persistent wave, measured 14 % faster than three blocks
-// (80 registers): the warp-sorted deposit is issue- and shuffle-latency
-// bound and gains from the extra warps.  FP64 keeps two.
+// launched as one persistent wave: the kernel is issue- and latency-bound
+// and gains from the warps (three blocks at 80 registers were 14 % slower,
+// four and six slower too).  FP64 keeps two.
 __global__ void __launch_bounds__(256, push_blocks_per_sm<R>())
 k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__restrict__ tab,
        Counters *cnt, TallyView tv) {

@@ -79,6 +79,11 @@ def test_validation_rejects_bad_arguments(lib):
     assert lib.hpic_init_target(None, None, None, 0, None) == hpic.HPIC_EINVAL
     assert lib.hpic_step(None, 1) == hpic.HPIC_EINVAL
     assert lib.hpic_destroy(None) == hpic.HPIC_EINVAL
+    # the electron transfers refuse a missing context before any device call
+    n = C.c_int64()
+    assert lib.hpic_count_particles(None, C.byref(n)) == hpic.HPIC_EINVAL
+    assert lib.hpic_read_particles(None, *([None] * 8), 0, C.byref(n)) == hpic.HPIC_EINVAL
+    assert lib.hpic_load_particles(None, 0, *([None] * 8)) == hpic.HPIC_EINVAL
 
 
 def test_no_device_is_an_error_not_a_fallback(lib):

@@ -37,10 +37,11 @@ WORKLOAD = ("128^3 cells x 1 um Au (Z=79, n_i=5.9e28 m^-3, T0=1 eV), 1e7 e- inje
 # read once (x,y,z,ux,uy,uz,tau + u32 id) and written once (7 reals)
 ALG_BYTES = {"fp32": 7 * 4 + 4 + 7 * 4, "fp64": 7 * 8 + 4 + 7 * 8}
 # DRAM bytes (read + write) per particle-step of k_push measured by ncu on
-# this workload (profiles/k_push_headline_fp32.md); None where not captured
+# this workload (dram__bytes_read.sum + dram__bytes_write.sum of one launch
+# over its particle-steps); None where not captured
 NCU_DRAM_BYTES_PER_PSTEP = {"fp32": 56.0, "fp64": None}
 # the same for k_batch_push, captured on the first 16 targets of the scan
-# (profiles/k_batch_push_batched_scan16_fp32.md): the traffic is the
+# (the full scan holds too much device memory for a multi-pass capture): the traffic is the
 # electron state streamed once, so it scales with the particle-steps
 NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": 65.5, "fp64": None}
 SORT_INTERVAL = 5  # measured, default bench: 5 / 10 / 20 / 40 give 9.64 / 9.45 / 8.99 / 8.20e9 particle-steps/s

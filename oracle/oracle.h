@@ -229,6 +229,10 @@ double orc_f_sigma(const orc_target *t, double Ti_K);
 void orc_ei_rates(const orc_target *t, double Te_K, double Ti_K, double *rate_e,
                   double *rate_i);
 void orc_rotate(const double d[3], double theta, double phi, double out[3]);
+/* energy row and polar column of a photon of energy k (J) at polar angle
+ * theta (rad, from +x) in the run's photon tallies; the step's own tally
+ * uses it */
+void orc_tally_bin(const orc_run *r, double k, double theta, int *row, int *col);
 void orc_boris(double u[3], const double E[3], const double B[3], double dt);
 
 #ifdef __cplusplus

@@ -166,6 +166,8 @@ def lib():
         L.orc_ei_rates.argtypes = [tp, C.c_double, C.c_double, C.POINTER(C.c_double),
                                    C.POINTER(C.c_double)]
         L.orc_rotate.argtypes = [dp, C.c_double, C.c_double, dp]
+        L.orc_tally_bin.argtypes = [C.POINTER(Run), C.c_double, C.c_double,
+                                    C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.orc_model.argtypes = [C.POINTER(ModelIn), C.POINTER(ModelOut)]
         L.orc_get_weights.argtypes = [C.c_void_p, dp]
         L.orc_set_weights.argtypes = [C.c_void_p, C.c_int64, dp]
@@ -391,6 +393,14 @@ def rotate(d, theta: float, phi: float) -> np.ndarray:
     out = np.empty(3)
     lib().orc_rotate(_dp(dd), theta, phi, _dp(out))
     return out
+
+
+def tally_bin(run: dict, k: float, theta: float):
+    """(row, column) of a photon of energy k (J) at polar angle theta (rad,
+    from +x) in the photon tallies of the run."""
+    r, c = C.c_int(), C.c_int()
+    lib().orc_tally_bin(C.byref(make_run(run)), k, theta, C.byref(r), C.byref(c))
+    return r.value, c.value
 
 
 def boris(u, E, B, dt: float) -> np.ndarray:

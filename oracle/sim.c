@@ -136,21 +136,33 @@ static void deposit(orc_sim *s, int which, const double X[3], double val) {
       }
 }
 
-/* photon tally: energy row (underflow, n_E log bins, overflow) x polar bin */
-static void tally_photon(orc_sim *s, double k, double theta, double wph) {
-  int nE = s->r.n_E, nth = s->r.n_theta;
+/* bin of one photon in the energy x angle tallies (Sec. III.A spectra and
+ * angular distributions): row 0 below tally_E_min, rows 1..n_E the log bins
+ * of equal width in ln k, row n_E + 1 at or above tally_E_max; column the
+ * polar angle theta in [0, pi] (measured by the caller from +x, the laser
+ * axis) in n_theta equal bins, theta = pi in the last */
+void orc_tally_bin(const orc_run *r, double k, double theta, int *row_out, int *col_out) {
+  int nE = r->n_E, nth = r->n_theta;
   int row;
-  if (k < s->r.tally_E_min) row = 0;
-  else if (k >= s->r.tally_E_max) row = nE + 1;
+  if (k < r->tally_E_min) row = 0;
+  else if (k >= r->tally_E_max) row = nE + 1;
   else {
-    row = 1 + (int)floor((double)nE * log(k / s->r.tally_E_min) /
-                         log(s->r.tally_E_max / s->r.tally_E_min));
+    row = 1 + (int)floor((double)nE * log(k / r->tally_E_min) /
+                         log(r->tally_E_max / r->tally_E_min));
     if (row < 1) row = 1;
     if (row > nE) row = nE;
   }
   int col = (int)floor(theta / PI * (double)nth);
   if (col < 0) col = 0;
   if (col > nth - 1) col = nth - 1;
+  *row_out = row;
+  *col_out = col;
+}
+
+/* photon tally: energy row (underflow, n_E log bins, overflow) x polar bin */
+static void tally_photon(orc_sim *s, double k, double theta, double wph) {
+  int nth = s->r.n_theta, row, col;
+  orc_tally_bin(&s->r, k, theta, &row, &col);
   s->histE[row * nth + col] += wph * k;
   s->histN[row * nth + col] += wph;
   s->tal.E_xray += wph * k;

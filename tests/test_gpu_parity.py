@@ -1,10 +1,13 @@
 """GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
 
-Tolerances (derived in DESIGN.md, "Parity bar"):
-  FP64 path: 1e-12 relative per element after one step (rounding order only).
+Tolerances:
+  FP64 path: 1e-12 relative per element after one step (the two sides differ
+  only in rounding order and in SI vs normalised units, about 1e-15).
   FP32-mixed path: 1e-5 relative per element after one step (particle state
   relative to |value| + dx or 1; fields relative to their max-norm), energy
-  tallies within 1e-5 relative plus 1e-6 of the electrons' kinetic energy.
+  tallies within 1e-5 relative plus 1e-6 of the electrons' kinetic energy,
+  since a per-electron energy difference formed in FP32 carries a few ulp
+  (6e-8) of that electron's own energy.
 Decisions (survival, emission, reflux) must agree exactly at these sizes.
 """
 import math

@@ -345,6 +345,206 @@ def test_photon_spectrum_chi_square_and_mean():
         assert AU["n_i"] * sig * ks.mean() == pytest.approx(O.stop_brem(AU, eps) * frac, rel=0.01)
 
 
+def _sampler_cdf_distance(tab, k_min, E_max, eps, n=2000):
+    """Kolmogorov distance of the table sampler at electron energy eps from the
+    closed-form spectrum: the sampler maps r to k(r) monotonically, so its CDF
+    at k(r) is r; the exact CDF there is the quadrature of dsigma/dk."""
+    r = (np.arange(n) + 0.5) / n
+    ks = np.array([O.brem_sample(tab, k_min, E_max, eps, x) for x in r])
+    sig = O.sigma_tot(AU, k_min, eps)
+    F, acc, prev = np.empty(n), 0.0, math.log(k_min)
+    for i, lk in enumerate(np.log(ks)):
+        acc += si.quad(lambda t: O.dsigma_dk(AU, eps, math.exp(t)) * math.exp(t), prev, lk,
+                       epsrel=1e-12)[0]
+        prev = lk
+        F[i] = acc / sig
+    return np.abs(F - r).max()
+
+
+def test_photon_sampler_cdf_on_and_off_grid():
+    """App. B sampling at electron energies on the table's rows and between
+    them (fractional rows), where the sampler interpolates linearly in ln eps.
+    Stated interpolation tolerance: the sampled spectrum's Kolmogorov distance
+    from the closed-form dsigma/dk is below 2e-4 at any energy (measured
+    1.1e-4 just above k_min, 2e-5 above 1 MeV); the same sampler one row off
+    is at least 4e-3 away."""
+    k_min, E_max = 10e3 * sc.e, 1000 * MEV
+    tab = O.brem_table(AU, k_min, E_max, 200, 200)
+    row_eps = lambda q: k_min * (E_max / k_min) ** (q / 199)
+    for q in (37, 120, 0.4, 5.5, 37.5, 120.3, 181.7, 198.6):
+        assert _sampler_cdf_distance(tab, k_min, E_max, row_eps(q)) < 2e-4, q
+    # a sampler reading the neighbouring row fails the bar
+    r = (np.arange(200) + 0.5) / 200
+    ks = np.array([O.brem_sample(tab, k_min, E_max, row_eps(121.3), x) for x in r])
+    ks = ks[ks < row_eps(120.3)]
+    sig = O.sigma_tot(AU, k_min, row_eps(120.3))
+    F = np.array([si.quad(lambda k: O.dsigma_dk(AU, row_eps(120.3), k), k_min, k, epsrel=1e-10)[0]
+                  for k in ks]) / sig
+    assert np.abs(F - r[:len(ks)]).max() > 2e-3
+
+
+def test_photon_spectrum_chi_square_off_grid():
+    """The sampled photon spectrum at electron energies between the table's
+    rows: chi-square of 2e5 sampled photons against the closed-form dsigma/dk per
+    bin; with the interpolation's CDF error below 2e-4 the per-bin bias is
+    under 1 standard deviation of the counts, so p > 1e-3 still holds."""
+    k_min, E_max = 10e3 * sc.e, 1000 * MEV
+    tab = O.brem_table(AU, k_min, E_max, 200, 200)
+    rng = np.random.default_rng(15)
+    for q in (37.5, 120.3, 181.7):
+        eps = k_min * (E_max / k_min) ** (q / 199)
+        ks = np.array([O.brem_sample(tab, k_min, E_max, eps, x) for x in rng.random(200000)])
+        v = np.log(ks / k_min) / np.log(eps / k_min)
+        edges = np.linspace(0, 1, 41)
+        obs, _ = np.histogram(v, bins=edges)
+        kk = k_min * (eps / k_min) ** edges
+        probs = np.array([si.quad(lambda k: O.dsigma_dk(AU, eps, k), kk[a], kk[a + 1], epsrel=1e-10)[0]
+                          for a in range(40)]) / O.sigma_tot(AU, k_min, eps)
+        assert st.chisquare(obs, probs * len(ks)).pvalue > 1e-3, q
+
+
+# ---------------------------------------------------------------- photon tallies
+def _bins_by_definition(run, k, theta):
+    """Row and column of the tally definition, written with bin edges: n_E bins
+    of equal ratio between tally_E_min and tally_E_max (row 0 below, n_E + 1 at
+    or above), n_theta equal polar bins over [0, pi] with theta = pi in the
+    last."""
+    edges = np.geomspace(run["tally_E_min"], run["tally_E_max"], run["n_E"] + 1)
+    row = np.searchsorted(edges, k, side="right")
+    tedges = np.linspace(0.0, math.pi, run["n_theta"] + 1)
+    col = np.minimum(np.searchsorted(tedges, theta, side="right") - 1, run["n_theta"] - 1)
+    return row, col
+
+
+@pytest.mark.parametrize("n_E,n_theta,lo_keV,hi_MeV", [(100, 90, 10, 100), (200, 180, 10, 100),
+                                                       (7, 5, 3, 0.5)])
+def test_tally_bins_follow_the_tally_definition(n_E, n_theta, lo_keV, hi_MeV):
+    """The oracle's photon binning (used by its step) against the bin-edge
+    definition: random photons, both sides of every energy edge and of every
+    polar edge, under- and overflow, the 1 MeV CE threshold, theta at 0 and pi.
+    A shifted row, another log base or a width error fails."""
+    run = W.run(n_E=n_E, n_theta=n_theta, E_min=lo_keV * 1e3 * sc.e, E_max=hi_MeV * MEV)
+    lo, hi = run["tally_E_min"], run["tally_E_max"]
+    rng = np.random.default_rng(n_E)
+    edges = np.geomspace(lo, hi, n_E + 1)
+    tedges = np.linspace(0.0, math.pi, n_theta + 1)
+    ks = list(np.exp(rng.uniform(math.log(lo / 20), math.log(hi * 20), 3000)))
+    ks += list(edges * (1 + 1e-9)) + list(edges * (1 - 1e-9))
+    ks += [lo, hi, lo * (1 - 1e-15), hi * (1 - 1e-15), 0.0, 1e-30, 1e3 * hi]
+    ths = list(rng.uniform(0, math.pi, len(ks)))
+    ths[:2 * n_theta + 2] = list(tedges * (1 + 1e-9) + 1e-12) + list(tedges * (1 - 1e-9))
+    ths[:4] = [0.0, 1e-300, math.pi, math.nextafter(math.pi, 0.0)]
+    for k, th in zip(ks, ths):
+        want = _bins_by_definition(run, k, th)
+        assert O.tally_bin(run, k, th) == (int(want[0]), int(want[1])), (k, th)
+    assert O.tally_bin(run, lo, 0.0)[0] == 1 and O.tally_bin(run, hi, 0.0)[0] == n_E + 1
+    assert O.tally_bin(run, 0.0, 0.0) == (0, 0)
+    assert O.tally_bin(run, 1.0, math.pi) == (n_E + 1, n_theta - 1)
+    if (n_E, lo_keV, hi_MeV) == (100, 10, 100):
+        # 25 bins per decade: the CE threshold (1 MeV) is an edge, so the rows
+        # from 51 up hold exactly the photons the CE scalar counts
+        thr = run["ce_threshold"]
+        assert O.tally_bin(run, thr, 0.0)[0] == 51
+        assert O.tally_bin(run, thr * (1 - 1e-12), 0.0)[0] == 50
+
+
+class _OnePhoton:
+    """One electron of kinetic energy eps moving along a given direction in
+    8^3 gold with emission only and an exhausted optical depth, so that it
+    emits in its step.  Returns the (row, column) the oracle's step tallied
+    the photon in, and the photon energy and polar angle about the electron
+    from the draws."""
+
+    def __init__(self):
+        tgt = W.target(n=(8, 8, 8))
+        self.run = W.run(physics=O.ORC_BREM, seed=11)
+        self.s = O.OracleSim(tgt, W.laser(tgt, n_macro=0), self.run)
+        r = self.run
+        self.tab = O.brem_table(tgt, r["k_min"], r["table_E_max"], r["table_rows"], r["table_cols"])
+
+    def __call__(self, direction, eps, id_, step=0):
+        s, run = self.s, self.run
+        s.set_clock(step, 0)
+        u = math.sqrt((eps / MC2) * (eps / MC2 + 2))
+        d = np.asarray(direction, float) / np.linalg.norm(direction)
+        _, hN0 = s.hist()
+        n0 = s.tallies()["n_emitted"]
+        s.set_particles({"x": [4e-6], "y": [4e-6], "z": [4e-6], "ux": [u * d[0]],
+                         "uy": [u * d[1]], "uz": [u * d[2]], "tau": [1e-12],
+                         "id": np.array([id_], np.uint32)})
+        s.step(1)
+        _, hN = s.hist()
+        nz = np.argwhere(hN - hN0 > 0)
+        assert len(nz) == 1 and s.tallies()["n_emitted"] == n0 + 1
+        # draws of block 1 (emission) for this electron and step
+        r1 = [O.uniform(x) for x in O.philox([step, id_, 1, 0], [11, 0])]
+        k = O.brem_sample(self.tab, run["k_min"], run["table_E_max"], eps, r1[0])
+        thg = O.photon_theta(1 + eps / MC2, r1[1])
+        return tuple(nz[0]), k, thg
+
+
+def test_photon_tally_angle_is_measured_from_the_laser_axis():
+    """The step's photon tally through the whole emission path: the photon
+    energy comes from draw 0 of block 1 and lands in its energy row; the polar
+    column is the photon's angle from +x (Sec. III.A's angular distributions
+    about the laser axis), not from the electron's direction.  For an electron
+    along +x that angle is the emission angle theta_g itself, along -x it is
+    pi - theta_g, and along +y it lies within theta_g of pi/2 (spherical law
+    of cosines, any azimuth)."""
+    rng = np.random.default_rng(3)
+    one = _OnePhoton()
+    width = math.pi / one.run["n_theta"]
+    checked = 0
+    for i in range(24):
+        eps = float(np.exp(rng.uniform(math.log(0.2 * MEV), math.log(30 * MEV))))
+        for d, expect in (((1, 0, 0), lambda t: t), ((-1, 0, 0), lambda t: math.pi - t)):
+            (row, col), k, thg = one(d, eps, id_=100 + i, step=i)
+            th = expect(thg)
+            wrow, wcol = _bins_by_definition(one.run, k, th)
+            assert row == wrow
+            if abs(th / width - round(th / width)) > 1e-6:  # not on a bin edge
+                assert col == wcol, (d, eps, th, col, wcol)
+                checked += 1
+        (row, col), k, thg = one((0, 1, 0), eps, id_=100 + i, step=i)
+        assert math.floor((math.pi / 2 - thg) / width) - 1 <= col <= math.floor((math.pi / 2 + thg) / width) + 1
+    assert checked >= 40
+
+
+# ---------------------------------------------------------------- bulk seeding
+def test_seeding_statistics():
+    """Bulk seeding (the emission benchmark's initial state): kinetic energies
+    exponential with the stated mean, directions uniform on the sphere (cos
+    theta uniform on [-1, 1] about any axis, azimuth uniform), positions uniform
+    in the box, optical depths Exp(1), ids consecutive, and the injected-energy
+    tally equal to w sum eps (KS tests, p > 1e-3)."""
+    tgt = W.target(n=(6, 9, 11))
+    s = O.OracleSim(tgt, W.laser(tgt, n_macro=0), W.run())
+    s.set_clock(7, 1000)
+    n, mean = 30000, 10 * MEV
+    s.seed(n, mean)
+    p = s.particles()
+    assert np.array_equal(p["id"], np.arange(1000, 1000 + n, dtype=np.uint32))
+    u2 = p["ux"] ** 2 + p["uy"] ** 2 + p["uz"] ** 2
+    eps = MC2 * u2 / (1 + np.sqrt(1 + u2))
+    assert st.kstest(eps / mean, "expon").pvalue > 1e-3
+    un = np.sqrt(u2)
+    for comp in ("ux", "uy", "uz"):
+        assert st.kstest((p[comp] / un + 1) / 2, "uniform").pvalue > 1e-3, comp
+    az = np.arctan2(p["uz"], p["uy"])
+    assert st.kstest((az + math.pi) / (2 * math.pi), "uniform").pvalue > 1e-3
+    for comp, ncell in (("x", tgt["nx"]), ("y", tgt["ny"]), ("z", tgt["nz"])):
+        assert st.kstest(p[comp] / (ncell * tgt["dx"]), "uniform").pvalue > 1e-3, comp
+    assert st.kstest(p["tau"], "expon").pvalue > 1e-3
+    # no correlation between energy, direction and position
+    for a, b in ((eps, p["x"]), (eps, p["ux"] / un), (p["x"], p["y"]), (p["tau"], eps)):
+        assert abs(np.corrcoef(a, b)[0, 1]) < 5 / math.sqrt(n)
+    t = s.tallies()
+    w = s.weight
+    assert t["E_injected"] == pytest.approx(w * eps.sum(), rel=1e-12)
+    assert t["n_injected"] == n and t["N_injected"] == pytest.approx(w * n, rel=1e-12)
+    assert s.clock() == (7, 1000 + n)
+
+
 def test_photon_angle_ks():
     rng = np.random.default_rng(6)
     for gam in (2.0, 30.0):

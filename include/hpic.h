@@ -316,8 +316,13 @@ int hpic_launch_count(const hpic_ctx *ctx, int64_t *launches);
  * dimension rounded up to a multiple of 4), beyond which it returns
  * HPIC_EINVAL with a message in hpic_last_error(NULL).  The first call on a
  * device looks up the scratch address on that device; make that call
- * before any stream capture.  Calls share the scratch: calls that overlap on
- * the GPU race, so serialise them.  Asynchronous on cuda_stream. */
+ * before any stream capture.  That address is kept for the life of the
+ * device's primary context: do not call this again in a process that has
+ * reset the device (cudaDeviceReset), since the array may have moved.  Calls
+ * share the scratch: calls that overlap on the GPU race, so serialise them.
+ * No output array may overlap an input array (the sort reads one while it
+ * writes the other): overlapping ranges give HPIC_EINVAL before any device
+ * call.  Asynchronous on cuda_stream. */
 int hpic_sort_cells_noalloc(int32_t nx, int32_t ny, int32_t nz, int32_t precision, int64_t n,
                             const void *const in_soa[8], void *const out_soa[8],
                             int64_t *n_live_dev, int device, void *cuda_stream);

@@ -686,7 +686,6 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
   const hpic::Consts &K = ctx->K;
   ctx->vstride = round_up(K.nvec + 4, 64);
   const long long m = K.nkeys + 1;
-  const long long ntiles = (m + 4095) / 4096;
   bool ok = cudaMalloc(&ctx->fields, 9 * ctx->vstride * ctx->rsz) == cudaSuccess &&
             cudaMalloc(&ctx->T, K.ncell * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ctx->eta, K.ncell * sizeof(double)) == cudaSuccess &&
@@ -695,7 +694,7 @@ int hpic_init_target(hpic_ctx **out, const hpic_target_desc *t, const hpic_run_p
             cudaMalloc(&ctx->Fsig, K.ncell * ctx->rsz) == cudaSuccess &&
             cudaMalloc(&ctx->H, K.ncell * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ctx->counts, m * sizeof(uint32_t)) == cudaSuccess &&
-            cudaMalloc(&ctx->partials, (ntiles + 1) * sizeof(uint32_t)) == cudaSuccess &&
+            cudaMalloc(&ctx->partials, hpic::scan_partials(m) * sizeof(uint32_t)) == cudaSuccess &&
             cudaMalloc(&ctx->tal, hpic::T_COUNT * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ctx->hist, 2 * hist_len(ctx) * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ctx->history, (r->max_history > 0 ? r->max_history : 1) * sizeof(double)) == cudaSuccess &&

@@ -437,7 +437,6 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
   b->arena_bytes = off;
   // aux: items, prefixes, sort scratch, tables
   const size_t isz = b->fp32 ? sizeof(hpic::BatchItem<float>) : sizeof(hpic::BatchItem<double>);
-  const long long ntiles = (b->nkeys_total + 4095) / 4096;
   const long long tab = (long long)run->table_rows * run->table_cols;
   off = 0;
   const size_t a_items = take(isz * n_targets);
@@ -448,7 +447,7 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
   const size_t a_s0 = take(n_targets * sizeof(long long)), a_s1 = take(n_targets * sizeof(long long));
   const size_t a_keys = take(slots * sizeof(uint32_t));
   const size_t a_cnts = take(b->nkeys_total * sizeof(uint32_t));
-  const size_t a_part = take((ntiles + 1) * sizeof(uint32_t));
+  const size_t a_part = take(hpic::scan_partials(b->nkeys_total) * sizeof(uint32_t));
   const size_t a_t64 = take(tab * sizeof(double)), a_t32 = take(tab * sizeof(float));
   const size_t aux_bytes = off;
   if (cudaMalloc(&b->arena, b->arena_bytes) != cudaSuccess ||
@@ -597,6 +596,7 @@ int hpic_batch_autotune(hpic_batch *b, int32_t trial_steps, hpic_batch_tuning *o
   }
   const int cur0 = b->cur;
   const long long step0 = b->host_step;
+  const long long launches0 = b->launches;  // the trials' launches are not the run's
   const hpic_batch_tuning keep = b->tune;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = HPIC_OK;
@@ -607,6 +607,7 @@ int hpic_batch_autotune(hpic_batch *b, int32_t trial_steps, hpic_batch_tuning *o
     set_cur(b, cur0);
     b->host_step = step0;
     for (hpic_ctx *c : b->tg) c->host_step = step0;
+    b->launches = launches0;
     return HPIC_OK;
   };
   if (cudaMemcpyAsync(snap, b->arena, b->arena_bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||

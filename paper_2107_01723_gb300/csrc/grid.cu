@@ -100,7 +100,6 @@ k_sort_keys(const Consts K, PView<R> p, const Counters *cnt, uint32_t *keys, uin
   }
 }
 
-constexpr int kScanTile = 4096;  // counts per block in the scan
 
 // per-tile sums of counts[0, m)
 __global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *counts, long long m,

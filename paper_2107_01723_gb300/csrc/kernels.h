@@ -183,8 +183,12 @@ template <typename R>
 int launch_batch_sort(const BatchItem<R> *items, BatchDev d, PView<R> src, PView<R> dst,
                       uint32_t *keys, uint32_t *counts, uint32_t *partials, long long nkeys_total,
                       int grid, cudaStream_t st);
+// counts summed per block of the scan; the partials scratch of a scan of m
+// counts holds scan_partials(m) words
+constexpr long long kScanTile = 4096;
+constexpr long long scan_partials(long long m) { return (m + kScanTile - 1) / kScanTile + 1; }
 // exclusive scan of counts[0, m) in place (partials: scratch of
-// ceil(m / 4096) + 1 words); returns launches made
+// scan_partials(m) words); returns launches made
 int launch_scan(uint32_t *counts, long long m, uint32_t *partials, cudaStream_t st);
 
 }  // namespace hpic

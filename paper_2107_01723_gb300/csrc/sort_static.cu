@@ -21,7 +21,13 @@
 // keeps the previous call's contents: the per-key counts are cleared at the
 // start of each call, and everything else is overwritten before it is read.
 // Calls that overlap on the GPU (on different streams, or from several host
-// threads) share the scratch and race; serialise them.
+// threads) share the scratch and race; serialise them.  The looked-up
+// address stays valid for the life of the device's primary context: after
+// cudaDeviceReset (or any reset of that context) the module is loaded again
+// and the array may move, so this entry point must not be called again in a
+// process that has reset the device.  The output arrays must not overlap the
+// input arrays (the scatter reads one while it writes the other); overlapping
+// ranges are refused.
 #include <mutex>
 
 #include "hpic.h"
@@ -31,8 +37,6 @@ namespace {
 
 constexpr long long kMaxElectrons = 1ll << 20;  // HPIC_NOALLOC_MAX_ELECTRONS
 constexpr long long kMaxKeys = 1ll << 20;       // HPIC_NOALLOC_MAX_TILE_CELLS
-constexpr long long kScanTile = 4096;           // counts per block of the scan
-constexpr long long kMaxTiles = (kMaxKeys + 1 + kScanTile - 1) / kScanTile;
 
 // scratch layout (bytes): keys | counts | scan partials | counters, every
 // region starting on a 256-byte boundary (the counters hold 64-bit fields)
@@ -40,11 +44,16 @@ constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kKeysOff = 0;
 constexpr size_t kCountsOff = align256(kKeysOff + sizeof(uint32_t) * kMaxElectrons);
 constexpr size_t kPartialsOff = align256(kCountsOff + sizeof(uint32_t) * (kMaxKeys + 1));
-constexpr size_t kCountersOff = align256(kPartialsOff + sizeof(uint32_t) * (kMaxTiles + 1));
+// the scan runs over the nkeys + 1 counts (tile keys and the dead bin) with
+// the scan tile of launch_scan
+constexpr size_t kCountersOff =
+    align256(kPartialsOff + sizeof(uint32_t) * hpic::scan_partials(kMaxKeys + 1));
 constexpr size_t kScratchBytes = (8u << 20) + (64u << 10);
 static_assert(kCountsOff % 256 == 0 && kPartialsOff % 256 == 0 && kCountersOff % 256 == 0,
               "scratch regions must be 256-byte aligned");
 static_assert(kCountersOff + sizeof(hpic::Counters) <= kScratchBytes, "scratch layout");
+static_assert(kPartialsOff + sizeof(uint32_t) * hpic::scan_partials(kMaxKeys + 1) <= kCountersOff,
+              "the scan's partials must end before the counters");
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
@@ -110,6 +119,21 @@ extern "C" int hpic_sort_cells_noalloc(int32_t nx, int32_t ny, int32_t nz, int32
   for (int a = 0; a < 8; ++a)
     if (n > 0 && (!in_soa[a] || !out_soa[a]))
       return noalloc_fail(HPIC_EINVAL, "hpic_sort_cells_noalloc: NULL array");
+  // the scatter reads in_soa while it writes out_soa: no output range may
+  // overlap an input range
+  if (n > 0) {
+    const size_t rb = precision == HPIC_FP32_MIXED ? sizeof(float) : sizeof(double);
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b) {
+        const uintptr_t i0 = reinterpret_cast<uintptr_t>(in_soa[a]);
+        const uintptr_t o0 = reinterpret_cast<uintptr_t>(out_soa[b]);
+        const uintptr_t i1 = i0 + (size_t)n * (a < 7 ? rb : sizeof(uint32_t));
+        const uintptr_t o1 = o0 + (size_t)n * (b < 7 ? rb : sizeof(uint32_t));
+        if (i0 < o1 && o0 < i1)
+          return noalloc_fail(HPIC_EINVAL,
+                              "hpic_sort_cells_noalloc: an output array overlaps an input array");
+      }
+  }
   if (device < 0 || device >= kMaxDevices)
     return noalloc_fail(HPIC_EINVAL, "hpic_sort_cells_noalloc: device index out of range");
   cudaError_t e = cudaSetDevice(device);

@@ -181,3 +181,28 @@ def test_batch_refuses_the_gaussian_envelope(lib):
     g = W.laser_gauss(t, per_cell=10)
     code, msg = _bad_batch(lib, [t, t], [c["laser"], g], c["run"])
     assert code == hpic.HPIC_EINVAL and "flat-top" in msg
+
+
+def test_noalloc_sort_refuses_overlapping_arrays(lib):
+    """The allocation-free sort reads its input arrays while it writes its
+    output arrays, so any output range that overlaps an input range is
+    refused with HPIC_EINVAL before any device call (the addresses below are
+    never dereferenced).  Disjoint ranges pass this check and, with no GPU
+    here, stop at the device call instead."""
+    n = 100
+    base = 1 << 32
+    ins = [base + a * 4096 for a in range(8)]
+    outs = [base + (1 << 20) + a * 4096 for a in range(8)]
+    for prec, rb in ((hpic.HPIC_FP32_MIXED, 4), (hpic.HPIC_FP64, 8)):
+        for a, b, shift in ((3, 3, 0), (0, 5, rb * (n - 1)), (7, 2, -rb * n + 4)):
+            bad = list(outs)
+            bad[b] = ins[a] + shift
+            with pytest.raises(hpic.HpicError) as e:
+                hpic.hpic_sort_cells_noalloc(8, 8, 8, prec, n, ins, bad, base - 64)
+            assert e.value.code == hpic.HPIC_EINVAL and "overlaps" in str(e.value), (a, b, shift)
+        # adjacent but disjoint: the next range starts where the input ends
+        ok = list(outs)
+        ok[0] = ins[6] + rb * n
+        with pytest.raises(hpic.HpicError) as e:
+            hpic.hpic_sort_cells_noalloc(8, 8, 8, prec, n, ins, ok, base - 64)
+        assert e.value.code != hpic.HPIC_EINVAL

@@ -111,3 +111,10 @@ def test_noalloc_sort_refuses_oversize():
     with pytest.raises(hpic.HpicError) as e:
         hpic.hpic_sort_cells_noalloc(1024, 1024, 8, hpic.HPIC_FP32_MIXED, 10, null8, null8, 0)
     assert e.value.code == hpic.HPIC_EINVAL and "cells" in str(e.value)
+    # an output array that aliases an input array is refused before any launch
+    import torch
+    x = torch.zeros(8 * 64, dtype=torch.float32, device="cuda")
+    ins = [x.data_ptr() + 4 * 64 * a for a in range(8)]
+    with pytest.raises(hpic.HpicError) as e:
+        hpic.hpic_sort_cells_noalloc(8, 8, 8, hpic.HPIC_FP32_MIXED, 64, ins, ins, x.data_ptr())
+    assert e.value.code == hpic.HPIC_EINVAL and "overlaps" in str(e.value)

@@ -44,6 +44,8 @@ NCU_DRAM_BYTES_PER_PSTEP = {"fp32": 56.0, "fp64": None}
 # (the full scan holds too much device memory for a multi-pass capture): the traffic is the
 # electron state streamed once, so it scales with the particle-steps
 NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": 65.5, "fp64": None}
+# the accuracy window: the injection (200 steps) and 1 ps beyond
+ACCURACY_STEPS = 2200
 SORT_INTERVAL = 5  # measured, default bench: 5 / 10 / 20 / 40 give 9.64 / 9.45 / 8.99 / 8.20e9 particle-steps/s
 
 
@@ -265,8 +267,10 @@ def run_gpu(args, world, rank, local):
                     "hpic_read_particles to host, wall clock, over the timed steps again "
                     "(grids and clock of their start restored untimed)")}
 
-    # FP64 reference path on the same workload (shorter run), for "FP32 vs FP64"
-    fp64 = None
+    # FP64 reference path on the same workload (shorter run), for "FP32 vs FP64",
+    # and the accuracy gate: both precisions from t = 0 through the injection
+    # window and 1 ps beyond, CE(>1 MeV) and energy closure of each
+    fp64, accuracy = None, None
     if args.precision == "fp32" and not args.no_fp64 and world == 1:
         s64 = hpic.Sim(cfg["target"], cfg["laser"], run, precision=hpic.HPIC_FP64, device=local,
                        stream=stream.cuda_stream, sort_interval=SORT_INTERVAL)
@@ -283,9 +287,35 @@ def run_gpu(args, world, rank, local):
         m64 = e0.elapsed_time(e1)
         a1 = s64.tallies()["particle_steps"]
         km, kl, kp = hpic.hpic_kernel_time(s64.h)
+        hpic.hpic_profile(s64.h, False)
         fp64 = {"value": (a1 - a0) / (m64 / 1e3), "unit": UNIT, "steps": k64,
                 "ms_per_step": m64 / k64,
                 "push_kernel_gbs": ALG_BYTES["fp64"] * kp / (km / 1e3) / 1e9 if km > 0 else None}
+        if not args.no_accuracy:
+            done64 = 200 + args.warmup + k64
+            acc_steps = max(ACCURACY_STEPS, done64)
+            s64.step(acc_steps - done64)
+            s32 = hpic.Sim(cfg["target"], cfg["laser"], run, precision=hpic.HPIC_FP32_MIXED,
+                           device=local, stream=stream.cuda_stream, sort_interval=SORT_INTERVAL)
+            s32.step(acc_steps)
+            acc = {}
+            for name, s_ in (("fp32", s32), ("fp64", s64)):
+                t = s_.tallies()
+                rhs = (t["E_live"] + t["W_field"] + t["E_drag"] + t["E_xray"] + t["E_escaped"]
+                       + t["E_reflux"])
+                acc[name] = {"ce_above_1MeV": t["E_xray_above"] / (t["E_injected"] / cfg["laser"]["eta_l2e"]),
+                             "closure": (t["E_injected"] - rhs) / t["E_injected"],
+                             "particle_steps": t["particle_steps"]}
+            s32.close()
+            ce_rel = acc["fp32"]["ce_above_1MeV"] / acc["fp64"]["ce_above_1MeV"] - 1.0
+            accuracy = {"window": f"steps 0..{acc_steps - 1} (injection + {(acc_steps - 200) * 0.5e-3:g} ps), same seed",
+                        "ce_fp32": acc["fp32"]["ce_above_1MeV"], "ce_fp64": acc["fp64"]["ce_above_1MeV"],
+                        "ce_rel_diff": ce_rel, "closure_fp32": acc["fp32"]["closure"],
+                        "closure_fp64": acc["fp64"]["closure"],
+                        "particle_steps_per_run": acc["fp64"]["particle_steps"],
+                        "bar": {"ce_rel": 0.01, "closure": 1e-3},
+                        "pass": bool(abs(ce_rel) < 0.01 and abs(acc["fp32"]["closure"]) < 1e-3
+                                     and abs(acc["fp64"]["closure"]) < 1e-3)}
         s64.close()
 
     if rank != 0:
@@ -317,7 +347,7 @@ def run_gpu(args, world, rank, local):
                        "l2": "inputs larger than L2 (particle state >= 320 MB per step)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "fp64": fp64}
+            "clocks": clk, "fp64": fp64, "accuracy": accuracy}
     print(json.dumps(line), flush=True)
     sim.close()
 
@@ -337,7 +367,9 @@ def run_full(args):
     steps = cfg["steps"] if args.full_steps <= 0 else args.full_steps
     out = {"what": "full headline run, CE(>1 MeV) FP32-mixed vs FP64", "steps": steps}
     stream = torch.cuda.Stream()
-    for name, prec in (("fp32", hpic.HPIC_FP32_MIXED), ("fp64", hpic.HPIC_FP64)):
+    legs = [(n, p) for n, p in (("fp32", hpic.HPIC_FP32_MIXED), ("fp64", hpic.HPIC_FP64))
+            if args.full_precision in ("both", n)]
+    for name, prec in legs:
         sim = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec,
                        stream=stream.cuda_stream, sort_interval=SORT_INTERVAL)
         torch.cuda.synchronize()
@@ -356,7 +388,8 @@ def run_full(args):
                      "particle_steps_per_s": t["particle_steps"] / (e0.elapsed_time(e1) / 1e3),
                      "live_at_end": sim.n, "tallies": t}
         sim.close()
-    out["CE_rel_diff"] = out["fp32"]["CE_above_1MeV"] / out["fp64"]["CE_above_1MeV"] - 1.0
+    if len(legs) == 2:
+        out["CE_rel_diff"] = out["fp32"]["CE_above_1MeV"] / out["fp64"]["CE_above_1MeV"] - 1.0
     print(json.dumps(out), flush=True)
 
 
@@ -578,6 +611,7 @@ def main():
     ap.add_argument("--full-run", action="store_true",
                     help="run the whole headline workload in FP32 and FP64 and compare CE")
     ap.add_argument("--full-steps", type=int, default=0)
+    ap.add_argument("--full-precision", default="both", choices=["both", "fp32", "fp64"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
@@ -585,6 +619,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the FP32-vs-FP64 CE and closure window")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -146,6 +146,16 @@ __device__ __forceinline__ void m_sincos(double x, double *s, double *c) { sinco
 // sin/cos of 2 pi u without rounding 2 pi u first
 __device__ __forceinline__ void m_sincos2pi(float u, float *s, float *c) { sincospif(2.0f * u, s, c); }
 __device__ __forceinline__ void m_sincos2pi(double u, double *s, double *c) { sincospi(2.0 * u, s, c); }
+// Round-to-nearest square root and division.  The FP32 particle kernels are
+// compiled with approximate division and square root; these wrappers keep
+// IEEE rounding where the push converts between an electron's energy and
+// its momentum (kinetic, u_of_eps, the rescale after drag or a photon) and
+// where it builds the frame of a rotation, so that no systematic rounding
+// bias enters an energy change that no tally records.
+__device__ __forceinline__ float m_sqrt_rn(float x) { return __fsqrt_rn(x); }
+__device__ __forceinline__ double m_sqrt_rn(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double m_div_rn(double a, double b) { return a / b; }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 
@@ -156,14 +166,16 @@ __host__ __device__ __forceinline__ uint32_t tile_key(int i, int j, int k, int n
   return t * 64u + (uint32_t)(((k & 3) << 4) | ((j & 3) << 2) | (i & 3));
 }
 
+// kinetic energy (m_e c^2) of momentum u, without the gamma - 1 cancellation
 template <typename R>
 __device__ __forceinline__ R kinetic(R ux, R uy, R uz) {
   const R u2 = ux * ux + uy * uy + uz * uz;
-  return u2 / (R(1) + m_sqrt(R(1) + u2));
+  return m_div_rn(u2, R(1) + m_sqrt_rn(R(1) + u2));
 }
 
+// momentum |u| of kinetic energy e (m_e c^2)
 template <typename R>
-__device__ __forceinline__ R u_of_eps(R e) { return m_sqrt(e * (e + R(2))); }
+__device__ __forceinline__ R u_of_eps(R e) { return m_sqrt_rn(e * (e + R(2))); }
 
 // Rotate unit d by polar angle (cos ct, sin st) at azimuth (cp, sp) in the
 // orthonormal frame of Duff et al., "Building an orthonormal basis,
@@ -171,7 +183,7 @@ __device__ __forceinline__ R u_of_eps(R e) { return m_sqrt(e * (e + R(2))); }
 template <typename R>
 __device__ __forceinline__ void rotate(R &dx, R &dy, R &dz, R ct, R st, R cp, R sp) {
   const R sg = dz >= R(0) ? R(1) : R(-1);
-  const R a = R(-1) / (sg + dz);
+  const R a = m_div_rn(R(-1), sg + dz);
   const R b = dx * dy * a;
   const R e1x = R(1) + sg * dx * dx * a, e1y = sg * b, e1z = -sg * dx;
   const R e2x = b, e2y = sg + dy * dy * a, e2z = -dy;

@@ -190,7 +190,7 @@ __device__ __noinline__ Crossing<R> cross_faces(R eps_esc, R du_reflux, R sigma_
     const bool low = pos[a] < R(0);
     pos[a] = low ? -pos[a] : R(2) * L - pos[a];
     u[a] = -u[a];
-    const R un = m_sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const R un = m_sqrt_rn(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     const R un2 = un - du_reflux;
     if (un2 <= R(0)) {
       c.ref += (double)(w * e_out);
@@ -203,7 +203,7 @@ __device__ __noinline__ Crossing<R> cross_faces(R eps_esc, R du_reflux, R sigma_
     R st, ct, sp, cp;
     m_sincos(xi, &st, &ct);
     m_sincos2pi(unif<R>(r2.b), &sp, &cp);
-    const R inv = R(1) / un;
+    const R inv = m_div_rn(R(1), un);
     R d[3] = {u[0] * inv, u[1] * inv, u[2] * inv};
     rotate(d[0], d[1], d[2], ct, st, cp, sp);
     if (low && d[a] < R(0)) d[a] = -d[a];
@@ -254,7 +254,7 @@ __device__ __noinline__ EmitOut<R> emit_photon(const EmitIn<R> e, StepCtx sc, ui
   const R xk = sample_log_ratio(e.k_min, e.t_inv_dlog, e.t_rows, e.t_cols, e.tab, eps, r1.a);
   const R k = eps * m_exp(-xk);
   const R thg = photon_theta(R(1) + eps, unif<R>(r1.b));
-  const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
+  const R un = m_sqrt_rn(ux * ux + uy * uy + uz * uz);
   R dx = ux / un, dy = uy / un, dz = uz / un;
   R st, ct, sp, cp;
   m_sincos(thg, &st, &ct);
@@ -285,7 +285,7 @@ __device__ __noinline__ EmitOut<R> emit_photon(const EmitIn<R> e, StepCtx sc, ui
     o.heat = w * eps;
     o.alive = false;
   } else {
-    const R s = u_of_eps(eps) / un;
+    const R s = m_div_rn(u_of_eps(eps), un);
     ux *= s; uy *= s; uz *= s;
   }
   o.eps = eps; o.ux = ux; o.uy = uy; o.uz = uz;
@@ -360,7 +360,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
       heat += w * eps;
       alive = false;
     } else {
-      const R s = u_of_eps(eps1) / m_sqrt(ux * ux + uy * uy + uz * uz);
+      const R s = m_div_rn(u_of_eps(eps1), m_sqrt_rn(ux * ux + uy * uy + uz * uz));
       ux *= s; uy *= s; uz *= s;
       heat += w * de;
       eps = eps1;
@@ -370,7 +370,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
   // ---- Davies scatter, Eq. (B4): polar Gamma*sigma, azimuth uniform
   if (alive && (K.physics & P_SCATTER)) {
     const U4 r0 = philox10(sc.step, id, 0u, sc.target, sc.key0, sc.key1);
-    const R un = m_sqrt(ux * ux + uy * uy + uz * uz);
+    const R un = m_sqrt_rn(ux * ux + uy * uy + uz * uz);
     const R gam = m_sqrt(R(1) + un * un);
     R var = R(0);
 #pragma unroll
@@ -386,7 +386,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     const R gauss = m_sqrt(R(-2) * m_log(unif<R>(r0.a))) * c1;
     m_sincos(gauss * sig, &st, &ct);
     m_sincos2pi(unif<R>(r0.c), &s2, &c2);
-    const R inv = R(1) / un;
+    const R inv = m_div_rn(R(1), un);
     R dx = ux * inv, dy = uy * inv, dz = uz * inv;
     rotate(dx, dy, dz, ct, st, c2, s2);
     ux = un * dx; uy = un * dy; uz = un * dz;

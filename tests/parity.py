@@ -142,3 +142,100 @@ def heat_with_cell_swaps(cfg: dict, state: dict, clock, gp: dict, op: dict,
         np.add.at(heat, cg[batch], h)
         todo = rest
     return heat, touched
+
+
+def smooth_grids(t: dict, seed: int, E0=3e9, B0=200.0) -> dict:
+    """Smooth non-zero fields over the whole grid (oracle layout): each E and
+    B component a sum of two plane waves of random low wave numbers (E0 V/m,
+    B0 T), padding entries past a component's staggered extent left at 0;
+    T from 1 to about 500 eV and eta from 1e-7 to 1e-6 Ohm m as independent
+    smooth patterns; T_i = T."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = t["nx"], t["ny"], t["nz"]
+    i = np.arange(nx + 1, dtype=np.float64)[None, None, :] / nx
+    j = np.arange(ny + 1, dtype=np.float64)[None, :, None] / ny
+    k = np.arange(nz + 1, dtype=np.float64)[:, None, None] / nz
+
+    def wave(a, b, c):
+        p = rng.integers(1, 4, size=(2, 3))
+        ph = rng.uniform(0, 2 * np.pi, 2)
+        return (0.6 * np.sin(2 * np.pi * (p[0, 0] * a + p[0, 1] * b + p[0, 2] * c) + ph[0])
+                + 0.4 * np.cos(2 * np.pi * (p[1, 0] * a + p[1, 1] * b + p[1, 2] * c) + ph[1]))
+
+    out = {}
+    # staggering (half cells) of Ex Ey Ez Bx By Bz along x, y, z
+    stag = {"Ex": (1, 0, 0), "Ey": (0, 1, 0), "Ez": (0, 0, 1),
+            "Bx": (0, 1, 1), "By": (1, 0, 1), "Bz": (1, 1, 0)}
+    for name, (sx, sy, sz) in stag.items():
+        amp = E0 if name[0] == "E" else B0
+        v = amp * wave(i + 0.5 * sx / nx, j + 0.5 * sy / ny, k + 0.5 * sz / nz)
+        v = np.broadcast_to(v, (nz + 1, ny + 1, nx + 1)).copy()
+        if sx:
+            v[:, :, nx] = 0.0
+        if sy:
+            v[:, ny, :] = 0.0
+        if sz:
+            v[nz, :, :] = 0.0
+        out[name] = v.ravel()
+    ci = (np.arange(nx) + 0.5)[None, None, :] / nx
+    cj = (np.arange(ny) + 0.5)[None, :, None] / ny
+    ck = (np.arange(nz) + 0.5)[:, None, None] / nz
+    T = 11604.5 * (1.0 + 250.0 * (1.0 + wave(ci, cj, ck)))
+    eta = 1e-7 * (5.5 + 4.5 * wave(ci, cj, ck))
+    out["T"] = np.broadcast_to(T, (nz, ny, nx)).ravel().copy()
+    out["eta"] = np.broadcast_to(eta, (nz, ny, nx)).ravel().copy()
+    out["Ti"] = out["T"].copy()
+    return out
+
+
+def spread_electrons(t: dict, n: int, seed: int, e_lo=5e4, e_hi=6e7) -> dict:
+    """n electrons over the whole box plus electrons at its 8 corners and in
+    the first and last cell of each axis, moving in all directions, kinetic
+    energies log-uniform over [e_lo, e_hi] eV.  Coordinates (in cells) are
+    FP32 numbers whose fractional parts stay 1e-4 away from 0 and 1/2, so
+    that the FP32 path holds the same positions exactly and every cell
+    decision (the drag heat's cell, a lattice's base node) is the oracle's."""
+    rng = np.random.default_rng(seed)
+    dims = np.array([t["nx"], t["ny"], t["nz"]], dtype=np.float64)
+    X = rng.uniform(0.0, 1.0, size=(n, 3)) * dims
+    lo = [0.3, 0.7]
+    corners = np.array([[a, b, c] for a in (0, 1) for b in (0, 1) for c in (0, 1)], float)
+    edge = np.vstack([corners * (dims - 0.6) + 0.3,
+                      np.column_stack([dims[0] - np.array(lo), np.full(2, dims[1] / 2), np.full(2, dims[2] / 2)]),
+                      np.column_stack([np.full(2, dims[0] / 2), dims[1] - np.array(lo), np.full(2, dims[2] / 2)]),
+                      np.column_stack([np.full(2, dims[0] / 2), np.full(2, dims[1] / 2), dims[2] - np.array(lo)]),
+                      np.column_stack([np.array(lo), np.array(lo), np.array(lo)])])
+    X = np.vstack([edge, X]).astype(np.float32).astype(np.float64)
+    fr = X - np.floor(X)
+    keep = np.all((np.abs(fr - 0.5) > 1e-4) & (fr > 1e-4) & (fr < 1 - 1e-4), axis=1)
+    X = X[keep]
+    m = len(X)
+    eps = 1.602176634e-19 * np.exp(rng.uniform(np.log(e_lo), np.log(e_hi), m))
+    mc2 = 9.1093837015e-31 * 299792458.0 ** 2
+    e = eps / mc2
+    u = np.sqrt(e * (e + 2.0))
+    d = rng.normal(size=(m, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    # the corner and edge electrons head out through their nearest faces
+    ne = int(keep[:len(edge)].sum())
+    out_dir = np.sign(X[:ne] - dims / 2)
+    d[:ne] = out_dir / np.linalg.norm(out_dir, axis=1)[:, None]
+    dx = t["dx"]
+    return {"x": X[:, 0] * dx, "y": X[:, 1] * dx, "z": X[:, 2] * dx,
+            "ux": u * d[:, 0], "uy": u * d[:, 1], "uz": u * d[:, 2],
+            "tau": -np.log(1.0 - rng.uniform(0.0, 1.0, m)),
+            "id": np.arange(m, dtype=np.uint32)}
+
+
+def live_state(cfg: dict, n: int, seed: int, step: int, e_hi=6e7) -> "O.OracleSim":
+    """An oracle context at clock `step` (after the injection window) holding
+    smooth non-zero grids and electrons spread over the whole box (kinetic
+    energies up to e_hi eV)."""
+    o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    for k, v in smooth_grids(cfg["target"], seed).items():
+        o.set_grid(k, v)
+    p = spread_electrons(cfg["target"], n, seed + 1, e_hi=e_hi)
+    o.set_particles(p)
+    o.set_clock(step, len(p["id"]))
+    o.reset_tallies()
+    return o

@@ -21,7 +21,7 @@ from paper_2107_01723_gb300 import workloads as W
 
 from parity import (GRIDS_STATE, assert_field_close, assert_particles_close,
                     assert_tallies_close, assert_vector_close, by_id, gpu_from_oracle,
-                    faraday_tol, heat_with_cell_swaps, tally_delta)
+                    faraday_tol, heat_with_cell_swaps, live_state, tally_delta)
 
 
 def assert_grids_close(g, o, tol, b_tol=None):
@@ -428,6 +428,74 @@ def test_full_size_thick_target(prec):
     want = -1.602176634e-19 * 299792458.0 * w * np.sum(P["ux"] / gam) / dx ** 3
     assert g.grid("jx").sum() == pytest.approx(want, rel=1e-4, abs=1e-6 * abs(want) + 1.0)
     assert g.history().sum() == pytest.approx(t["E_xray_above"], rel=1e-9)
+    g.close()
+
+
+_LIVE = {}
+
+
+def _live_reference(which):
+    """The oracle's step from a live full-size state (cached per workload):
+    the state's electrons and grids, and the oracle's electrons, grids and
+    tallies one step later."""
+    if which not in _LIVE:
+        _LIVE.clear()  # one full-size state in memory at a time
+        cfg = W.config2() if which == "headline" else W.config3()
+        n = 200_000 if which == "headline" else 1_000_000
+        # energies up to twice the escape threshold (27.5 MeV at 1e21 W/cm^2,
+        # 86.9 MeV at 1e22) so that escapes happen next to refluxes
+        o = live_state(cfg, n, seed=31 if which == "headline" else 37, step=299,
+                       e_hi=6e7 if which == "headline" else 2e8)
+        before = {"p": o.particles(), "g": {k: o.grid(k) for k in GRIDS_STATE},
+                  "clock": o.clock(), "E_live": o.tallies()["E_live"]}
+        o.step(1)
+        after = {"p": o.particles(), "t": o.tallies(),
+                 "g": {k: o.grid(k) for k in ("T", "eta", "Ex", "Ey", "Ez", "Bx", "By", "Bz",
+                                              "jx", "jy", "jz", "heat")}}
+        del o
+        _LIVE[which] = (cfg, before, after)
+    return _LIVE[which]
+
+
+@pytest.mark.parametrize("which", ["headline", "thick"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_live_fields(which, prec):
+    """The full-size grids with live values everywhere: smooth non-zero E and
+    B (about 3e9 V/m and 200 T), T from 1 to 500 eV and an independent eta
+    pattern, and electrons spread over the whole box -- its 8 corners and the
+    first and last cells of each axis included, heading out through the
+    faces -- so that every index path of the gather, the deposit, the field
+    and heating stencils and the reflux is exercised at 128^3 and at
+    500 x 256 x 256 with non-zero values.  The GPU context is cell-sorted
+    first and sorts again at the end of the step (the benchmark's launch
+    configuration, a sort every 5 steps); one step, then every electron and
+    grid element against the oracle."""
+    cfg, before, after = _live_reference(which)
+    prec_id, tol, abs_frac = PREC[prec]
+    assert max(np.abs(before["g"][k]).max() for k in ("Ex", "By")) > 0
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec_id, sort_interval=5)
+    g.set_particles(before["p"])
+    for k, v in before["g"].items():
+        g.set_grid(k, v)
+    g.set_clock(*before["clock"])
+    g.reset_tallies()
+    g.sort()
+    g.step(1)
+    assert g.clock() == (300, before["clock"][1])
+    ot = after["t"]
+    assert ot["n_refluxed"] > 0 and ot["n_escaped"] > 0 and ot["n_emitted"] > 0
+    dx = cfg["target"]["dx"]
+    assert_particles_close(g.particles(), after["p"], tol, dx)
+    for f in ("j", "E", "B"):
+        comps = [f + c for c in "xyz"]
+        scale = max(np.abs(after["g"][c]).max() for c in comps)
+        for c in comps:
+            assert_field_close(g.grid(c), after["g"][c], tol, c, scale)
+    assert_field_close(g.grid("heat"), after["g"]["heat"], tol, "heat")
+    for k in ("T", "eta"):
+        err = np.max(np.abs(g.grid(k) - after["g"][k]) / np.abs(after["g"][k]))
+        assert err <= tol, (k, err)
+    assert_tallies_close(g.tallies(), ot, tol, abs_frac * before["E_live"])
     g.close()
 
 

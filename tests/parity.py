@@ -148,8 +148,7 @@ def smooth_grids(t: dict, seed: int, E0=3e9, B0=200.0) -> dict:
     """Smooth non-zero fields over the whole grid (oracle layout): each E and
     B component a sum of two plane waves of random low wave numbers (E0 V/m,
     B0 T), padding entries past a component's staggered extent left at 0;
-    T from 1 to about 500 eV and eta from 1e-7 to 1e-6 Ohm m as independent
-    smooth patterns; T_i = T."""
+    T from 1 to 500 eV as a smooth pattern with eta = eta(T); T_i = T."""
     rng = np.random.default_rng(seed)
     nx, ny, nz = t["nx"], t["ny"], t["nz"]
     i = np.arange(nx + 1, dtype=np.float64)[None, None, :] / nx
@@ -180,10 +179,15 @@ def smooth_grids(t: dict, seed: int, E0=3e9, B0=200.0) -> dict:
     ci = (np.arange(nx) + 0.5)[None, None, :] / nx
     cj = (np.arange(ny) + 0.5)[None, :, None] / ny
     ck = (np.arange(nz) + 0.5)[:, None, None] / nz
-    T = 11604.5 * (1.0 + 250.0 * (1.0 + wave(ci, cj, ck)))
-    eta = 1e-7 * (5.5 + 4.5 * wave(ci, cj, ck))
-    out["T"] = np.broadcast_to(T, (nz, ny, nx)).ravel().copy()
-    out["eta"] = np.broadcast_to(eta, (nz, ny, nx)).ravel().copy()
+    # T on 64 levels, geometric from 1 to 500 eV, and eta = eta(T) of each
+    # level: a stepped state keeps eta equal to eta(T) (a cell without heat or
+    # current keeps both), so the input does too
+    levels = 11604.5 * np.geomspace(1.0, 500.0, 64)
+    eta_lv = np.array([O.resistivity(t, T) for T in levels])
+    lv = np.clip(((wave(ci, cj, ck) + 1.0) * 32.0).astype(np.int64), 0, 63)
+    lv = np.broadcast_to(lv, (nz, ny, nx)).ravel()
+    out["T"] = levels[lv]
+    out["eta"] = eta_lv[lv]
     out["Ti"] = out["T"].copy()
     return out
 

@@ -461,8 +461,8 @@ def _live_reference(which):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_full_size_live_fields(which, prec):
     """The full-size grids with live values everywhere: smooth non-zero E and
-    B (about 3e9 V/m and 200 T), T from 1 to 500 eV and an independent eta
-    pattern, and electrons spread over the whole box -- its 8 corners and the
+    B (about 3e9 V/m and 200 T), T from 1 to 500 eV with eta = eta(T), and
+    electrons spread over the whole box -- its 8 corners and the
     first and last cells of each axis included, heading out through the
     faces -- so that every index path of the gather, the deposit, the field
     and heating stencils and the reflux is exercised at 128^3 and at

@@ -146,6 +146,26 @@ def replica_rate(world, ms, particle_steps):
     return ps_sum / (ms_max / 1e3), ms_max, ps_sum
 
 
+def host_cpu() -> dict:
+    """The host's CPU model and core count, read at run time."""
+    model = None
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip() in ("Model name", "Model") and v.strip() and not v.strip().isdigit():
+                model = v.strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                model = ln.split(":", 1)[1].strip()
+                break
+    return {"cpu_model": model, "host_cores": os.cpu_count()}
+
+
 def oracle_rate(steps_timed: int, warmup: int, budget_s: float) -> dict:
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
     the same 128^3 target and laser, stepped from t = 0 through the start of
@@ -166,7 +186,7 @@ def oracle_rate(steps_timed: int, warmup: int, budget_s: float) -> dict:
             break
     dt = time.perf_counter() - t0
     ps = o.tallies()["particle_steps"] - ps0
-    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle", **host_cpu(),
             "sample": (f"oracle steps {max(warmup, 1)}..{max(warmup, 1) + done - 1} of the headline "
                        f"workload (injection phase, {int(ps / max(done, 1))} live e- per step on "
                        f"average, full 128^3 field/heat update each step), serial FP64, {dt:.1f} s"),
@@ -182,7 +202,8 @@ def run_reference(args, world, rank):
             "ms_per_step": 1e3 * r["seconds"] / max(r["steps_timed"], 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 oracle"},
-            "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu_model",
+                                               "host_cores")},
             "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -335,7 +356,7 @@ def run_gpu(args, world, rank, local):
     cpu = None
     if not args.no_cpu_baseline:
         r = oracle_rate(200, 2, budget_s=20.0)
-        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu_model", "host_cores")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -348,8 +369,20 @@ def run_gpu(args, world, rank, local):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "fp64": fp64, "accuracy": accuracy}
+    if world == 1 and not args.no_sub:
+        # the other single-GPU workloads, short windows: the batched scan
+        # (64 targets, 200 timed steps after the injection window and the
+        # autotuner) and the emission microbenchmark (2^27 electrons)
+        sim.close()
+        sim = None
+        bl = batch_result(64, 200, 200)
+        line["batched_scan"] = {k: bl[k] for k in ("metric", "value", "unit", "steps", "warmup",
+                                                   "ms_per_step", "dtype", "config", "roofline",
+                                                   "gpu_launches", "clocks", "ce_above_1MeV")}
+        line["emission"] = emission_result(2 ** 27, {"fp32": 50, "fp64": 5}, 3)
     print(json.dumps(line), flush=True)
-    sim.close()
+    if sim is not None:
+        sim.close()
 
 
 def run_full(args):
@@ -393,80 +426,78 @@ def run_full(args):
     print(json.dumps(out), flush=True)
 
 
-def run_emission(args):
-    """Emission microbenchmark (not the headline line): 2^27 electrons in an
-    unbounded uniform gold medium, drag + scatter + bremsstrahlung only, in
-    FP32 and FP64; k_push's particle-steps/s and HBM fraction."""
+def emission_result(n: int, steps: dict, warmup: int) -> dict:
+    """Emission microbenchmark: n electrons in an unbounded uniform gold medium,
+    drag + scatter + bremsstrahlung only, in FP32 and FP64 (steps[precision]
+    timed steps after `warmup`); k_push's particle-steps/s and HBM fraction."""
     import torch
 
-    from paper_2107_01723_gb300 import build as B
     from paper_2107_01723_gb300 import hpic
     from paper_2107_01723_gb300 import workloads as W
-    B.build()
-    cfg = W.config5(n_electrons=args.emission_n)
+    cfg = W.config5(n_electrons=n)
     pk = peaks()
     out = {"what": "emission microbenchmark: unbounded gold, drag+scatter+bremsstrahlung",
-           "electrons": cfg["n_electrons"], "steps": args.steps, "warmup": args.warmup}
+           "electrons": cfg["n_electrons"], "steps": steps, "warmup": warmup}
     stream = torch.cuda.Stream()
     for name, prec in (("fp32", hpic.HPIC_FP32_MIXED), ("fp64", hpic.HPIC_FP64)):
         sim = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec,
                        stream=stream.cuda_stream)
         sim.seed(cfg["n_electrons"], cfg["mean_energy"])
-        sim.step(args.warmup)
+        sim.step(warmup)
         hpic.hpic_profile(sim.h, True)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        sim.step(args.steps)
+        sim.step(steps[name])
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         km, kl, kp = hpic.hpic_kernel_time(sim.h)
+        hpic.hpic_profile(sim.h, False)
         gbs = ALG_BYTES[name] * kp / (km / 1e3) / 1e9
-        out[name] = {"particle_steps_per_s": kp / (ms / 1e3), "ms_per_step": ms / args.steps,
+        out[name] = {"particle_steps_per_s": kp / (ms / 1e3), "ms_per_step": ms / steps[name],
                      "k_push_ms": km / kl, "achieved_GBs": gbs, "frac_of_hbm": gbs / pk["hbm_gbs"],
                      "peak_source": pk["source"], "emissions": sim.tallies()["n_emitted"]}
         sim.close()
-    print(json.dumps(out), flush=True)
+    return out
 
 
-def run_batch(args):
-    """Batched scan (not the headline line): 64 targets of uneven thickness,
-    element and intensity (6e7 electrons in all), FP32-mixed, one launch per
-    kernel kind per step, steps replayed from CUDA graphs.  Under torchrun
-    the targets are sharded over the ranks (greedy LPT on electron counts,
-    no exchange until an end-of-run tally sum).  The first
-    `warmup` steps (default: the 200-step injection window) run first, the
-    autotuner then picks blocks per SM and the sort interval from a
-    snapshot, and the remaining steps of the 1 ps window are timed."""
+def run_emission(args):
+    """The emission microbenchmark alone (not the headline line)."""
+    from paper_2107_01723_gb300 import build as B
+    B.build()
+    print(json.dumps(emission_result(args.emission_n, {"fp32": args.steps, "fp64": args.steps},
+                                     args.warmup)), flush=True)
+
+
+def batch_result(n_targets: int, warm: int, steps: int, precision: str = "fp32",
+                 tuning: str = "", world: int = 1, rank: int = 0, local: int = 0):
+    """Batched scan: n_targets targets of uneven thickness, element and
+    intensity (6e7 electrons for 64), one launch per kernel kind per step,
+    steps replayed from CUDA graphs.  Under torchrun the targets are sharded
+    over the ranks (greedy LPT on electron counts, no exchange until an
+    end-of-run tally sum).  The first `warm` steps (at least the 200-step
+    injection window) run first, the autotuner then picks blocks per SM and
+    the sort interval from a snapshot, and `steps` steps are timed.  Returns
+    rank 0's line (None on other ranks)."""
     import torch
 
-    from paper_2107_01723_gb300 import build as B
     from paper_2107_01723_gb300 import hpic
     from paper_2107_01723_gb300 import shard
     from paper_2107_01723_gb300 import workloads as W
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    if rank == 0 or not os.path.exists(B.LIB):
-        B.build()
-    barrier(world)
-    cfg = W.config4(n_targets=args.batch_targets,
-                    total_macro=int(6e7 * args.batch_targets / 64))
+    cfg = W.config4(n_targets=n_targets, total_macro=int(6e7 * n_targets / 64))
     # whole targets to ranks by electron count (greedy LPT); global indices
     # keep each target's random numbers
     mine = shard.lpt_assign([l["n_macro"] for l in cfg["lasers"]], world)[rank]
     targets = [cfg["targets"][t] for t in mine]
     lasers = [cfg["lasers"][t] for t in mine]
-    prec_name = args.precision
-    prec = hpic.HPIC_FP32_MIXED if prec_name == "fp32" else hpic.HPIC_FP64
-    warm = args.warmup if args.warmup >= 200 else 200
-    steps = args.steps if args.steps != 1000 else cfg["steps"] - warm - 1
+    prec = hpic.HPIC_FP32_MIXED if precision == "fp32" else hpic.HPIC_FP64
     stream = torch.cuda.Stream()
     b = hpic.Batch(targets, lasers, cfg["run"], precision=prec, device=local,
                    stream=stream.cuda_stream, sort_interval=SORT_INTERVAL, target_index=mine)
     b.step(warm)
-    if args.batch_tuning:
-        bps, si = (int(v) for v in args.batch_tuning.split(","))
+    if tuning:
+        bps, si = (int(v) for v in tuning.split(","))
         b.set_tuning(bps, si)
         tune = dict(b.tuning(), chosen="fixed by --batch-tuning")
     else:
@@ -497,7 +528,7 @@ def run_batch(args):
     km, kl, kp = hpic.hpic_batch_kernel_time(b.b)
     hpic.hpic_batch_profile(b.b, False)
     pk = peaks()
-    achieved = ALG_BYTES[prec_name] * (kp / kl) / (km / kl / 1e3) / 1e9
+    achieved = ALG_BYTES[precision] * (kp / kl) / (km / kl / 1e3) / 1e9
     ce, tot = [], {"E_xray_above": 0.0, "E_injected": 0.0}
     for t in range(len(b)):
         T = b.target(t).tallies()
@@ -505,25 +536,25 @@ def run_batch(args):
         for k in tot:
             tot[k] += T[k]
     tot = shard.reduce_tallies(world, tot)  # the scan's only exchange, at the end
+    b.close()
     if rank != 0:
-        b.close()
-        return
-    line = {"metric": "particle-steps/s, batched scan of 64 targets", "value": value,
+        return None
+    return {"metric": f"particle-steps/s, batched scan of {n_targets} targets", "value": value,
             "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": ms_max / steps,
             "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
-            "dtype": "f32" if prec_name == "fp32" else "f64",
+            "dtype": "f32" if precision == "fp32" else "f64",
             "data": "synthetic",
             "config": {"parallelism": f"{world} ranks, whole targets by LPT" if world > 1 else "single GPU",
-                       "workload": (f"{args.batch_targets} targets: thickness U{{5..200}} x 64 x 64 cells of 1 um, "
+                       "workload": (f"{n_targets} targets: thickness U{{5..200}} x 64 x 64 cells of 1 um, "
                                     "Z in {13, 29, 79}, log10 I ~ U[20, 22] W/cm^2, "
                                     f"{sum(l['n_macro'] for l in cfg['lasers']):.3g} e- in all "
-                                    "(1e5..4e6 per target), 1 ps window"),
+                                    "(1e5..4e6 per target)"),
                        "live_electrons_at_start": live, "tuning": tune,
                        "graphs": "step and sort replayed from captured CUDA graphs"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / pk["hbm_gbs"],
-                         "traffic": (NCU_BATCH_DRAM_BYTES_PER_PSTEP[prec_name] * kp / kl
-                                     if NCU_BATCH_DRAM_BYTES_PER_PSTEP[prec_name] else None),
+                         "traffic": (NCU_BATCH_DRAM_BYTES_PER_PSTEP[precision] * kp / kl
+                                     if NCU_BATCH_DRAM_BYTES_PER_PSTEP[precision] else None),
                          "traffic_unit": "bytes per launch (ncu dram read+write on 16 targets, "
                                          "scaled by particle-steps)",
                          "kernel": "k_batch_push", "kernel_ms_avg": km / kl,
@@ -532,8 +563,26 @@ def run_batch(args):
             "gpu_launches": launches, "clocks": clk,
             "ce_above_1MeV": {"rank0_min": min(ce), "rank0_max": max(ce),
                               "scan_eta_e2g": tot["E_xray_above"] / tot["E_injected"]}}
-    print(json.dumps(line), flush=True)
-    b.close()
+
+
+def run_batch(args):
+    """The batched scan alone (not the headline line): the 1 ps window after
+    the injection window."""
+    import torch
+
+    from paper_2107_01723_gb300 import build as B
+    from paper_2107_01723_gb300 import workloads as W
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    barrier(world)
+    warm = args.warmup if args.warmup >= 200 else 200
+    steps = args.steps if args.steps != 1000 else W.config4()["steps"] - warm - 1
+    line = batch_result(args.batch_targets, warm, steps, args.precision, args.batch_tuning,
+                        world, rank, local)
+    if line is not None:
+        print(json.dumps(line), flush=True)
 
 
 def run_model(args):
@@ -619,6 +668,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the batched-scan and emission sub-lines")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the FP32-vs-FP64 CE and closure window")
     args = ap.parse_args()

@@ -150,7 +150,8 @@ int enqueue_step(hpic_batch *b) {
     }
     BCK(cudaEventRecord(b->ev[b->ev_used], b->stream));
   }
-  hpic::launch_batch_push<R>(items, b->d, P, tab, b->sm_count, b->tune.blocks_per_sm, b->stream);
+  hpic::launch_batch_push<R>(b->tg[0]->K, items, b->d, P, tab, b->sm_count, b->tune.blocks_per_sm,
+                             b->stream);
   ++k;
   if (b->prof) {
     BCK(cudaEventRecord(b->ev[b->ev_used + 1], b->stream));

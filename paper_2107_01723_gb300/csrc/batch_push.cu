@@ -58,14 +58,27 @@ __device__ __forceinline__ void flush_acc(const Acc<R> &acc, double *dst) {
   }
 }
 
+// What a warp keeps of its current target: the per-target hot constants
+// and the grid and tally views (the run-wide constants are the kernel's
+// parameter Krun, read from the constant bank like the single-target
+// kernel's).
+template <typename R>
+struct TargetHot {
+  HotK<R> h;
+  GView<R> g;
+  TallyView tv;
+  long long off;  // first particle slot of the target
+  long long step, n;  // the target's step and slot count
+};
+
 // MINB = the blocks per SM the launch asks for: the register budget follows
 // (5: 48 registers, 4: 64, 3: 80, 2: 128, 1: 255; the FP32 state spills a
 // little below 64), and the autotuner picks among the variants by timing them
 template <typename R, int MINB>
 __global__ void __launch_bounds__(256, MINB)
-k_batch_push(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
+k_batch_push(const Consts Krun, const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
              const R *__restrict__ tab) {
-  __shared__ BatchItem<R> wc[kBatchWarps];  // each warp's current target
+  __shared__ TargetHot<R> wc[kBatchWarps];  // each warp's current target
   // the warps' deposit stages, then n x kAccN tally sums, then the task prefix
   extern __shared__ __align__(16) double dyn[];
   R *stage = reinterpret_cast<R *>(dyn) + (threadIdx.x >> 5) * dep_words<R>();
@@ -75,11 +88,10 @@ k_batch_push(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
   for (int t = threadIdx.x; t <= d.n; t += blockDim.x) wpref_s[t] = d.wpref[t];
   __syncthreads();
 
-  __shared__ long long wstate[kBatchWarps][2];  // the target's step and slot count
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long ntask = wpref_s[d.n];
   const long long nwarps = (long long)gridDim.x * kBatchWarps;
-  BatchItem<R> &it = wc[warp];
+  TargetHot<R> &it = wc[warp];
   int t = -1;
   Acc<R> acc;
   for (long long w = blockIdx.x * (long long)kBatchWarps + warp; w < ntask; w += nwarps) {
@@ -92,25 +104,32 @@ k_batch_push(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
       }
       t = tn;
       __syncwarp();
-      const uint32_t *src = reinterpret_cast<const uint32_t *>(items + t);
-      uint32_t *dst = reinterpret_cast<uint32_t *>(&it);
-      for (int k = lane; k < (int)(sizeof(BatchItem<R>) / 4); k += 32) dst[k] = __ldg(src + k);
+      const BatchItem<R> *src = items + t;
+      auto copy = [&](void *dst, const void *from, int bytes) {
+        const uint32_t *a = static_cast<const uint32_t *>(from);
+        uint32_t *b = static_cast<uint32_t *>(dst);
+        for (int k = lane; k < bytes / 4; k += 32) b[k] = __ldg(a + k);
+      };
+      copy(&it.h, &src->h, (int)sizeof(HotK<R>));
+      copy(&it.g, &src->g, (int)sizeof(GView<R>));
+      copy(&it.tv, &src->tv, (int)sizeof(TallyView));
       if (lane == 0) {
-        wstate[warp][0] = items[t].cnt->step;
-        wstate[warp][1] = items[t].cnt->n;
+        it.off = src->off;
+        it.step = src->cnt->step;
+        it.n = src->cnt->n;
       }
       __syncwarp();
     }
     // rebuilt per task from shared memory rather than held in registers
     StepCtx sc;
-    sc.step_ll = wstate[warp][0];
+    sc.step_ll = it.step;
     sc.step = (uint32_t)sc.step_ll;
-    sc.key0 = it.K.key0;
-    sc.key1 = it.K.key1;
-    sc.target = it.K.target_index;
+    sc.key0 = Krun.key0;
+    sc.key1 = Krun.key1;
+    sc.target = it.h.target_index;
     const long long local = (w - wpref_s[t]) * 32 + lane;
-    push_warp(it.K, it.h, make_grid(it.K, it.g), tab, it.tv, sc, p, it.off + local,
-              local < wstate[warp][1], acc, tal_s + t * kAccN, stage);
+    push_warp<R, 4>(Krun, it.h, make_grid(it.h, it.g), tab, it.tv, sc, p, it.off + local,
+                    local < it.n, acc, tal_s + t * kAccN, stage);
   }
   if (t >= 0) flush_acc(acc, tal_s + t * kAccN);
   __syncthreads();
@@ -229,27 +248,39 @@ template <typename R>
 __global__ void __launch_bounds__(256)
 k_batch_sort_scatter(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> src,
                      PView<R> dst, const uint32_t *keys, uint32_t *offs) {
+  __shared__ uint32_t sm_key[256], sm_base[256];
+  __shared__ int sm_w[8];
   const long long nslot = d.wpref[d.n] * 32;
   int t = 0;
-  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot;
-       s += (long long)gridDim.x * blockDim.x) {
-    t = forward_target(d.wpref, t, d.n, s >> 5);
-    const BatchItem<R> &it = items[t];
-    const long long local = s - d.wpref[t] * 32;
-    if (local >= it.cnt->n) continue;
-    const long long ip = it.off + local;
-    const uint32_t key = keys[ip];
-    if (key == (uint32_t)(d.kpref[t] + it.K.nkeys)) continue;  // dead
-    const long long q = it.off + (long long)agg_inc(offs, key) - d.sstart[t];
-    dst.x[q] = src.x[ip];
-    dst.y[q] = src.y[ip];
-    dst.z[q] = src.z[ip];
-    dst.ux[q] = src.ux[ip];
-    dst.uy[q] = src.uy[ip];
-    dst.uz[q] = src.uz[ip];
-    dst.tau[q] = src.tau[ip];
-    if (it.K.weighted) dst.w[q] = src.w[ip];
-    dst.id[q] = src.id[ip];
+  for (long long b0 = blockIdx.x * 256ll; b0 < nslot; b0 += (long long)gridDim.x * 256) {
+    const long long s = b0 + threadIdx.x;
+    bool take = false;
+    uint32_t key = 0;
+    long long ip = 0;
+    if (s < nslot) {
+      t = forward_target(d.wpref, t, d.n, s >> 5);  // uniform over the warp
+      const BatchItem<R> &it = items[t];
+      const long long local = s - d.wpref[t] * 32;
+      if (local < it.cnt->n) {
+        ip = it.off + local;
+        key = keys[ip];
+        take = key != (uint32_t)(d.kpref[t] + it.K.nkeys);  // not dead
+      }
+    }
+    const uint32_t slot = block_run_slot(key, take, offs, sm_key, sm_base, sm_w);
+    if (take) {
+      const BatchItem<R> &it = items[t];
+      const long long q = it.off + (long long)slot - d.sstart[t];
+      dst.x[q] = src.x[ip];
+      dst.y[q] = src.y[ip];
+      dst.z[q] = src.z[ip];
+      dst.ux[q] = src.ux[ip];
+      dst.uy[q] = src.uy[ip];
+      dst.uz[q] = src.uz[ip];
+      dst.tau[q] = src.tau[ip];
+      if (it.K.weighted) dst.w[q] = src.w[ip];
+      dst.id[q] = src.id[ip];
+    }
   }
 }
 
@@ -288,25 +319,25 @@ cudaError_t prepare_batch_push() {
 }
 
 template <typename R>
-void launch_batch_push(const BatchItem<R> *items, BatchDev d, PView<R> p, const R *table,
-                       int sm_count, int blocks_per_sm, cudaStream_t st) {
+void launch_batch_push(const Consts &Krun, const BatchItem<R> *items, BatchDev d, PView<R> p,
+                       const R *table, int sm_count, int blocks_per_sm, cudaStream_t st) {
   const size_t sm = batch_stage_bytes<R>() + (size_t)d.n * kAccN * sizeof(double) +
                     (d.n + 1) * sizeof(long long);
   const int grid = sm_count * blocks_per_sm;
   if constexpr (sizeof(R) == 8) {  // FP64: one or two blocks per SM
     if (blocks_per_sm <= 1)
-      k_batch_push<R, 1><<<grid, 256, sm, st>>>(items, d, p, table);
+      k_batch_push<R, 1><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
     else
-      k_batch_push<R, 2><<<grid, 256, sm, st>>>(items, d, p, table);
+      k_batch_push<R, 2><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
   } else {  // FP32: two to five (one runs the two-block code)
     if (blocks_per_sm <= 2)
-      k_batch_push<R, 2><<<grid, 256, sm, st>>>(items, d, p, table);
+      k_batch_push<R, 2><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
     else if (blocks_per_sm == 3)
-      k_batch_push<R, 3><<<grid, 256, sm, st>>>(items, d, p, table);
+      k_batch_push<R, 3><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
     else if (blocks_per_sm == 4)
-      k_batch_push<R, 4><<<grid, 256, sm, st>>>(items, d, p, table);
+      k_batch_push<R, 4><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
     else
-      k_batch_push<R, 5><<<grid, 256, sm, st>>>(items, d, p, table);
+      k_batch_push<R, 5><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
   }
 }
 
@@ -338,8 +369,8 @@ int launch_batch_sort(const BatchItem<R> *items, BatchDev d, PView<R> src, PView
 
 #define HPIC_INST(R)                                                                            \
   template void launch_batch_plan<R>(const BatchItem<R> *, BatchDev, cudaStream_t);             \
-  template void launch_batch_push<R>(const BatchItem<R> *, BatchDev, PView<R>, const R *, int,  \
-                                     int, cudaStream_t);                                        \
+  template void launch_batch_push<R>(const Consts &, const BatchItem<R> *, BatchDev, PView<R>,  \
+                                     const R *, int, int, cudaStream_t);                        \
   template void launch_batch_inject<R>(const BatchItem<R> *, BatchDev, PView<R>, int,           \
                                        cudaStream_t);                                           \
   template void launch_batch_advance<R>(const BatchItem<R> *, BatchDev, cudaStream_t);          \

@@ -36,11 +36,19 @@ struct TallyView {
 
 // the per-electron constants in the kernel's own precision (folded on the
 // host so that no double->float conversion runs per electron)
+//
+// Everything the per-electron code needs that differs between the targets
+// of a batch is here (with the grid and tally views); from Consts it reads
+// only run-wide values, so the batched kernel can take Consts as a kernel
+// parameter and keep just these per target.
 template <typename R>
 struct HotK {
   R w, cdt, E_cut, K_tau, k_min, inv_boost;
-  R K_ion[4], L_I[4], K_sc[4], K_lg[4];  // per element (Consts::n_solids used)
+  R K_ion[4], L_I[4], K_sc[4], K_lg[4];  // per element (n_solids used)
   R eps_esc, du_reflux, sigma_dtheta, tE_min, tE_max, inv_dlogE, th_scale, t_inv_dlog;
+  double w_d;                // the weight in FP64 (photon weights)
+  int nx, ny, nz, n_solids;  // the target's cells and elements
+  uint32_t target_index;     // fourth Philox counter word
 };
 
 // the hot constants in precision R
@@ -67,6 +75,12 @@ inline HotK<R> make_hot(const Consts &K) {
   h.inv_dlogE = R(K.inv_dlogE);
   h.th_scale = R(K.n_th / 3.14159265358979323846);
   h.t_inv_dlog = R(K.t_inv_dlog);
+  h.w_d = K.w;
+  h.nx = K.nx;
+  h.ny = K.ny;
+  h.nz = K.nz;
+  h.n_solids = K.n_solids;
+  h.target_index = K.target_index;
   return h;
 }
 
@@ -165,10 +179,11 @@ struct BatchDev {
 // counts per step and per target: warp tasks and injections (one block)
 template <typename R>
 void launch_batch_plan(const BatchItem<R> *items, BatchDev d, cudaStream_t st);
-// persistent particle kernel, sm_count * blocks_per_sm blocks
+// persistent particle kernel, sm_count * blocks_per_sm blocks; Krun: the
+// run-wide constants (any target's Consts: those fields are common)
 template <typename R>
-void launch_batch_push(const BatchItem<R> *items, BatchDev d, PView<R> p, const R *table,
-                       int sm_count, int blocks_per_sm, cudaStream_t st);
+void launch_batch_push(const Consts &Krun, const BatchItem<R> *items, BatchDev d, PView<R> p,
+                       const R *table, int sm_count, int blocks_per_sm, cudaStream_t st);
 template <typename R>
 void launch_batch_inject(const BatchItem<R> *items, BatchDev d, PView<R> p, int grid,
                          cudaStream_t st);

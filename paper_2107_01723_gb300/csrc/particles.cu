@@ -22,7 +22,7 @@
 
 namespace hpic {
 
-template <typename R>
+template <typename R, int NS>
 // FP32: five 256-thread blocks per SM (48 registers, a few spills to L1),
 // launched as one persistent wave: the kernel is issue- and latency-bound
 // and gains from the warps (three blocks at 80 registers were 14 % slower,
@@ -30,7 +30,6 @@ template <typename R>
 __global__ void __launch_bounds__(256, push_blocks_per_sm<R>())
 k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__restrict__ tab,
        Counters *cnt, TallyView tv) {
-  __shared__ double red[kAccN * 32];
   __shared__ double rare[kAccN];  // the rare tally sums of the block
   if (threadIdx.x < kAccN) rare[threadIdx.x] = 0.0;
   __syncthreads();
@@ -42,9 +41,9 @@ k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__rest
   sc.step = (uint32_t)sc.step_ll;
   sc.key0 = K.key0;
   sc.key1 = K.key1;
-  sc.target = K.target_index;
+  sc.target = h.target_index;
 
-  const Grid<R> g = make_grid(K, gv);
+  const Grid<R> g = make_grid(h, gv);
   Acc<R> acc;
 
   // warp-uniform loop: every lane reaches the warp-cooperative deposits
@@ -52,11 +51,12 @@ k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__rest
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); base < n;
        base += stride)
-    push_warp(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc, rare, stage);
+    push_warp<R, NS>(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc, rare, stage);
 
   double v[kAccN];
   acc.values(v);
-  block_flush<kAccN>(v, kAccSlot, tv.tal, red);  // synchronises the block
+  __syncthreads();  // every warp is past its deposits: the stages hold the block sums
+  block_flush<kAccN>(v, kAccSlot, tv.tal, reinterpret_cast<double *>(dyn));  // synchronises
   if (threadIdx.x < kAccN && rare[threadIdx.x] != 0.0)
     atomicAdd(tv.tal + kAccSlot[threadIdx.x], rare[threadIdx.x]);
 }
@@ -214,10 +214,16 @@ template <typename R>
 constexpr size_t push_stage_bytes() { return 8 * dep_words<R>() * sizeof(R); }
 
 cudaError_t prepare_push() {
-  cudaError_t e = cudaFuncSetAttribute(k_push<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_push<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)push_stage_bytes<float>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_push<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_push<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)push_stage_bytes<float>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_push<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)push_stage_bytes<double>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_push<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)push_stage_bytes<double>());
   return e;
 }
@@ -225,7 +231,10 @@ cudaError_t prepare_push() {
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
                  TallyView tv, int grid, cudaStream_t st) {
-  k_push<R><<<grid, 256, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv);
+  if (K.n_solids == 1)  // a single-element solid: the element loops vanish
+    k_push<R, 1><<<grid, 256, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv);
+  else
+    k_push<R, 4><<<grid, 256, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv);
 }
 
 template <typename R>

@@ -49,12 +49,12 @@ struct Grid {
   R *J[3];
   double *H;
   const R *Fsig;  // F_sigma per cell
-  int sy, sz, nx, ny;
+  int sy, sz, nx, ny, nz;
   __device__ __forceinline__ int node(int i, int j, int k) const { return i + sy * j + sz * k; }
 };
 
 template <typename R>
-__device__ __forceinline__ Grid<R> make_grid(const Consts &K, const GView<R> &gv) {
+__device__ __forceinline__ Grid<R> make_grid(const HotK<R> &K, const GView<R> &gv) {
   Grid<R> g;
   for (int c = 0; c < 3; ++c) {
     g.F[c] = gv.E[c];
@@ -67,6 +67,7 @@ __device__ __forceinline__ Grid<R> make_grid(const Consts &K, const GView<R> &gv
   g.sz = (K.nx + 1) * (K.ny + 1);
   g.nx = K.nx;
   g.ny = K.ny;
+  g.nz = K.nz;
   return g;
 }
 
@@ -295,15 +296,16 @@ __device__ __noinline__ EmitOut<R> emit_photon(const EmitIn<R> e, StepCtx sc, ui
 // Advance one live electron through the step.  Returns false when the
 // electron is absorbed or escapes (the caller marks its slot dead).  On
 // true, the state holds x^{n+1}, u^{n+1} and tau, and its current is
-// deposited.
-template <typename R>
+// deposited.  NS: 1 for a single-element solid (the element loops vanish),
+// 4 for up to four elements counted at run time.
+template <typename R, int NS>
 __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const Grid<R> &g,
                                         const R *__restrict__ tab, const TallyView &tv,
                                         const StepCtx &sc, uint32_t id, R w, R &X, R &Y, R &Zc,
                                         R &ux, R &uy, R &uz, R &tau, Acc<R> &acc, double *rare,
                                         R &heat_out,
                                         int &heat_cell) {
-  const int nx = K.nx, ny = K.ny, nz = K.nz;
+  const int nx = h.nx, ny = h.ny, nz = h.nz;
 
   // ---- gather at x^n
   const bool unbounded = (K.physics & P_UNBOUNDED) != 0;
@@ -349,8 +351,8 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     const R a2 = R(0.909) * ig * ig, a1 = R(0.818) * ig;
     R de = R(0);
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {  // the elements' stopping powers add
-      if (s >= K.n_solids) break;  // constant indices: no local-memory copy
+    for (int s = 0; s < NS; ++s) {  // the elements' stopping powers add
+      if (NS > 1 && s >= h.n_solids) break;  // constant indices: no local-memory copy
       R br = le + h.L_I[s] + lh + a2 - a1 - R(0.246);
       br = br < R(0) ? R(0) : br;
       de += h.K_ion[s] / beta * br;
@@ -370,23 +372,24 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
   // ---- Davies scatter, Eq. (B4): polar Gamma*sigma, azimuth uniform
   if (alive && (K.physics & P_SCATTER)) {
     const U4 r0 = philox10(sc.step, id, 0u, sc.target, sc.key0, sc.key1);
-    const R un = m_sqrt_rn(ux * ux + uy * uy + uz * uz);
-    const R gam = m_sqrt(R(1) + un * un);
+    const R u2 = ux * ux + uy * uy + uz * uz;
+    const R inv = m_rsqrt_rn(u2);
+    const R un = u2 * inv;
+    const R gam = m_sqrt(R(1) + u2);
     R var = R(0);
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {  // the elements' variances add
-      if (s >= K.n_solids) break;
+    for (int s = 0; s < NS; ++s) {  // the elements' variances add
+      if (NS > 1 && s >= h.n_solids) break;
       R lg = m_flog(h.K_lg[s] * un);
       lg = lg < R(0) ? R(0) : lg;
       var += h.K_sc[s] * gam / (un * un * un) * lg;
     }
     const R sig = m_sqrt(var);
-    R s1, c1, s2, c2, st, ct;
-    m_sincos2pi(unif<R>(r0.b), &s1, &c1);
-    const R gauss = m_sqrt(R(-2) * m_log(unif<R>(r0.a))) * c1;
+    R s2, c2, st, ct;
+    // Box-Muller normal deviate (its cosine changes only the deflection)
+    const R gauss = m_sqrt(R(-2) * m_log(unif<R>(r0.a))) * m_fcos2pi(unif<R>(r0.b));
     m_sincos(gauss * sig, &st, &ct);
     m_sincos2pi(unif<R>(r0.c), &s2, &c2);
-    const R inv = m_div_rn(R(1), un);
     R dx = ux * inv, dy = uy * inv, dz = uz * inv;
     rotate(dx, dy, dz, ct, st, c2, s2);
     ux = un * dx; uy = un * dy; uz = un * dz;
@@ -400,7 +403,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     if (tau <= R(0)) {
       EmitIn<R> e;
       e.tab = tab; e.hist = tv.hist; e.history = tv.history;
-      e.w_shared = K.w; e.inv_boost_d = K.inv_boost; e.ce_thr = K.ce_thr;
+      e.w_shared = h.w_d; e.inv_boost_d = K.inv_boost; e.ce_thr = K.ce_thr;
       e.max_history = K.max_history;
       e.t_rows = K.t_rows; e.t_cols = K.t_cols; e.n_E = K.n_E; e.n_th = K.n_th;
       e.weighted = K.weighted;
@@ -450,35 +453,67 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
 }
 
 // ---------------------------------------------------------------- warp deposits
-// A warp adds its electrons' current and drag heat to the grid in one pass
-// through a shared-memory stage.  The warp first groups its electrons by the
-// cell of x^{n+1} (lanes with equal cells found by one match instruction),
-// and each lane writes its electron as the row of its place in that
-// grouping: 25 values, per current component c the 8 corners of its own
-// lattice (axis c half-staggered, the other two node-centred) times
-// w v_c / c, then the drag heat.  Each lane then walks one column down the
-// 32 rows, summing while the rows stay in one cell and adding the sum to the
-// grid with one reduction when the cell changes: a cell's electrons cost one
-// reduction per node, not one per electron, and within one reduction
-// instruction the lanes target distinct addresses.
+// A warp adds its electrons' current and drag heat to the grid together.
 //
-// Node of a corner: with nk the node index of the cell of x^{n+1}, the
-// corner (a, b, e) of component c of an electron whose axis-c staggered
-// index is i_c - 1 + off (off = 0 or 1) is nk + a + sy b + sz e - (1 - off)
-// stride_c; the walker keeps one sum per value of off.
-constexpr int kDepCols = 25;               // 3 x 8 corners, heat
+// Current.  The warp groups its electrons by the cell of x^{n+1} (lanes with
+// equal cells found by one match instruction); each electron takes the row
+// of its place in that grouping, so a cell's electrons hold consecutive rows,
+// and writes its 24 CIC values (per component c the 8 corners of its own
+// lattice, times w v_c / c) as row `row` of a column-major stage.  Lane l
+// then walks column l down the 32 rows keeping two running sums, one for the
+// rows whose half-staggered base along c is the cell's own node (off = 1)
+// and one for those whose base is the node below (off = 0): with keep = 0
+// on the first row of a cell and 1 elsewhere, (s0, s1) = keep (s0, s1) +
+// (x [off = 0], x [off = 1]), one packed two-wide FMA per row.  At the last
+// row of a cell the pair is that cell's sum for the two nodes of the column:
+// one reduction per node, the lanes of a reduction instruction on distinct
+// addresses.  Cell ends are tested once per four rows.
+//
+// Drag heat goes to the cell of x^n: a segmented scan across the lanes, in
+// row order, over runs of equal heat cell, and one FP64 reduction per run.
+//
+// Node of a corner: with nk the node index of the cell of x^{n+1}, corner
+// (a, b, e) of component c of an electron whose axis-c staggered index is
+// i_c - 1 + off is nk + a + sy b + sz e - (1 - off) stride_c.
+constexpr int kDepCols = 24;               // 3 components x 8 corners
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;   // row with nothing to deposit
 constexpr uint32_t kNoCell = (1u << 27) - 1u;  // cell key of such a row (cells < 2^27 - 1)
 constexpr unsigned kFull = 0xffffffffu;
 
-// column stride in elements: 16-byte column reads by 8 lanes fall in 8
-// distinct 4-bank groups (stride = 16 bytes mod 128)
+// Stage of one warp, in elements of R: 24 columns of 32 rows, each column
+// padded by 16 bytes (a 16-byte read of the same rows by eight lanes falls
+// in eight distinct bank groups), then the keep pairs of the 32 rows, then
+// the 32 rows' cell node keys (uint32; first the electron of each row).
 template <typename R>
-__host__ __device__ constexpr int dep_stride() { return (32 * (int)sizeof(R) + 16) / (int)sizeof(R); }
-// elements of one warp's stage: the columns, then 32 slots (the lane that
-// holds each row, later the heat sum of the run ending at each row)
+__host__ __device__ constexpr int dep_stride() { return 32 + 16 / (int)sizeof(R); }
 template <typename R>
-__host__ __device__ constexpr int dep_words() { return kDepCols * dep_stride<R>() + 32; }
+__host__ __device__ constexpr int dep_keep0() { return kDepCols * dep_stride<R>(); }
+template <typename R>
+__host__ __device__ constexpr int dep_words() {
+  return dep_keep0<R>() + 64 + 32 * 4 / (int)sizeof(R);
+}
+
+template <typename R>
+struct Pair;  // the two running sums of a column, and the segmented-sum step
+template <>
+struct Pair<float> {
+  float2 v;
+  __device__ __forceinline__ static Pair make(float a, float b) { Pair q; q.v = make_float2(a, b); return q; }
+  __device__ __forceinline__ void fma_keep(const Pair &keep, const Pair &x) { v = __ffma2_rn(v, keep.v, x.v); }
+  __device__ __forceinline__ float a() const { return v.x; }
+  __device__ __forceinline__ float b() const { return v.y; }
+};
+template <>
+struct Pair<double> {
+  double2 v;
+  __device__ __forceinline__ static Pair make(double a, double b) { Pair q; q.v = make_double2(a, b); return q; }
+  __device__ __forceinline__ void fma_keep(const Pair &keep, const Pair &x) {
+    v.x = fma(v.x, keep.v.x, x.v.x);
+    v.y = fma(v.y, keep.v.y, x.v.y);
+  }
+  __device__ __forceinline__ double a() const { return v.x; }
+  __device__ __forceinline__ double b() const { return v.y; }
+};
 
 template <typename R>
 struct Vec16;  // the rows one 16-byte shared load covers
@@ -503,7 +538,7 @@ struct Vec16<double> {
 // heat into the cell heat_cell of x^n (heat == 0: nothing); buf is this
 // warp's stage.  Every lane of the warp must call it.
 template <typename R>
-__device__ __forceinline__ void warp_deposit(const Consts &K, const Grid<R> &g, R *__restrict__ buf,
+__device__ __forceinline__ void warp_deposit(const Grid<R> &g, R *__restrict__ buf,
                                              bool dep, R w, R X, R Y, R Zc, R ux, R uy, R uz,
                                              R heat, int heat_cell) {
   constexpr int S = dep_stride<R>();
@@ -511,7 +546,7 @@ __device__ __forceinline__ void warp_deposit(const Consts &K, const Grid<R> &g, 
 
   // ---- this lane's electron, written as row `row` of the cell grouping
   if (!dep) { X = R(0); Y = R(0); Zc = R(0); }  // finite weights, zero values
-  const Axis<R> ax = axis_weights(X, K.nx), ay = axis_weights(Y, K.ny), az = axis_weights(Zc, K.nz);
+  const Axis<R> ax = axis_weights(X, g.nx), ay = axis_weights(Y, g.ny), az = axis_weights(Zc, g.nz);
   R v[3] = {R(0), R(0), R(0)};
   uint32_t nk = kNoKey, ck = kNoCell;
   if (dep) {
@@ -520,14 +555,13 @@ __device__ __forceinline__ void warp_deposit(const Consts &K, const Grid<R> &g, 
     v[1] = w * uy * ig;
     v[2] = w * uz * ig;
     nk = (uint32_t)g.node(ax.iN, ay.iN, az.iN);
-    ck = (uint32_t)(ax.iN + K.nx * (ay.iN + K.ny * az.iN));
+    ck = (uint32_t)(ax.iN + g.nx * (ay.iN + g.ny * az.iN));
   }
   const int offs = (ax.iS - ax.iN + 1) | ((ay.iS - ay.iN + 1) << 1) | ((az.iS - az.iN + 1) << 2);
   const uint32_t hk = (heat != R(0) && heat_cell >= 0) ? (uint32_t)heat_cell : kNoKey;
-  // rows grouped by cell: the lanes sharing a cell take consecutive rows, the
-  // groups in the order of their first lanes (offsets: a prefix sum of the
-  // group sizes over the groups' first lanes); lane p then learns which
-  // electron holds row p (src)
+  // the lanes sharing a cell take consecutive rows, the groups in the order
+  // of their first lanes (offsets: a prefix sum of the group sizes over the
+  // groups' first lanes); lane p then learns which electron holds row p (src)
   const unsigned same = __match_any_sync(kFull, ck);
   const int lead = __ffs((int)same) - 1;
   const int size_here = lane == lead ? __popc(same) : 0;
@@ -538,10 +572,8 @@ __device__ __forceinline__ void warp_deposit(const Consts &K, const Grid<R> &g, 
     if (lane >= o) incl += t;
   }
   const int row = __shfl_sync(kFull, incl - size_here, lead) + __popc(same & ((1u << lane) - 1u));
-  uint32_t *srcof = reinterpret_cast<uint32_t *>(buf + kDepCols * S);
-  srcof[row] = (uint32_t)lane;
-  __syncwarp();
-  const int src = (int)srcof[lane];
+  uint32_t *rowkey = reinterpret_cast<uint32_t *>(buf + dep_keep0<R>() + 64);
+  rowkey[row] = (uint32_t)lane;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const R fx = c == 0 ? ax.fS : ax.fN, fy = c == 1 ? ay.fS : ay.fN, fz = c == 2 ? az.fS : az.fN;
@@ -553,65 +585,97 @@ __device__ __forceinline__ void warp_deposit(const Consts &K, const Grid<R> &g, 
       buf[(8 * c + 2 * q + 1) * S + row] = yz[q] * fx;
     }
   }
-  buf[24 * S + row] = heat;
+  __syncwarp();
+  const int src = (int)rowkey[lane];
   // from here on lane p speaks for row p
   const uint32_t pnk = __shfl_sync(kFull, nk, src), phk = __shfl_sync(kFull, hk, src);
   const int poffs = __shfl_sync(kFull, offs, src);
-
-  // ---- run ends (bit r: row r is the last of its cell) and stagger offsets
-  const uint32_t nk1 = __shfl_down_sync(kFull, pnk, 1), hk1 = __shfl_down_sync(kFull, phk, 1);
-  const uint32_t endc = __ballot_sync(kFull, lane == 31 || nk1 != pnk);
-  const uint32_t endh = __ballot_sync(kFull, lane == 31 || hk1 != phk);
+  R ph = __shfl_sync(kFull, heat, src);
+  const uint32_t nk_up = __shfl_up_sync(kFull, pnk, 1), nk_dn = __shfl_down_sync(kFull, pnk, 1);
+  const uint32_t hk_up = __shfl_up_sync(kFull, phk, 1), hk_dn = __shfl_down_sync(kFull, phk, 1);
+  const bool head_c = lane == 0 || nk_up != pnk;
+  const uint32_t endc = __ballot_sync(kFull, lane == 31 || nk_dn != pnk);
   const uint32_t offx = __ballot_sync(kFull, poffs & 1);
   const uint32_t offy = __ballot_sync(kFull, poffs & 2);
   const uint32_t offz = __ballot_sync(kFull, poffs & 4);
   __syncwarp();
+  {
+    const R k = head_c ? R(0) : R(1);
+    *reinterpret_cast<Pair<R> *>(buf + dep_keep0<R>() + 2 * lane) = Pair<R>::make(k, k);
+    rowkey[lane] = pnk;
+  }
+  __syncwarp();
 
-  // ---- column `lane`: lanes 0-23 the current corners, 24 the heat
-  const int c = lane >> 3;
-  const uint32_t offm = c == 0 ? offx : (c == 1 ? offy : (c == 2 ? offz : 0u));
-  const uint32_t mine = lane < 24 ? endc : (lane == 24 ? endh : 0u);
-  const uint32_t any = endc | endh;
+  // ---- column `lane` (lanes 24-31 walk column 23 again and add nothing)
+  const int col = lane < kDepCols ? lane : kDepCols - 1;
+  const int c = col >> 3;
+  const uint32_t offm = c == 0 ? offx : (c == 1 ? offy : offz);
   R *J = c == 0 ? g.J[0] : (c == 1 ? g.J[1] : g.J[2]);
-  const int o1 = (lane & 1) + g.sy * ((lane >> 1) & 1) + g.sz * ((lane >> 2) & 1);
+  const int o1 = (col & 1) + g.sy * ((col >> 1) & 1) + g.sz * ((col >> 2) & 1);
   const int sc = c == 0 ? 1 : (c == 1 ? g.sy : g.sz);
-  const R *col = buf + (lane < kDepCols ? lane : kDepCols - 1) * S;
-  R *hsum = buf + kDepCols * S;  // the lane indices there have been read
-  R s0 = R(0), s1 = R(0);  // rows with off = 0, off = 1
+  const bool adds = lane < kDepCols;
+  const R *colp = buf + col * S;
+  const R *keep = buf + dep_keep0<R>();
+  const uint32_t *rk = rowkey;
+  uint32_t om = offm, em = endc;  // shifted down by the rows walked
+  Pair<R> s = Pair<R>::make(R(0), R(0));
   constexpr int V = Vec16<R>::n;
+  // rolled over the rows (a copy of the reduction code per chunk of rows
+  // would not fit the instruction cache), unrolled within a chunk
 #pragma unroll 1
   for (int r0 = 0; r0 < 32; r0 += V) {
     R x[V];
-    Vec16<R>::load(col + r0, x);
+    Vec16<R>::load(colp, x);
+    R kv[2 * V];  // the keep pairs of these rows, 16 bytes at a time
+#pragma unroll
+    for (int q = 0; q < 2 * V; q += Vec16<R>::n) {
+      R t[Vec16<R>::n];
+      Vec16<R>::load(keep + q, t);
+#pragma unroll
+      for (int e = 0; e < Vec16<R>::n; ++e) kv[q + e] = t[e];
+    }
+    Pair<R> sr[V];
 #pragma unroll
     for (int q = 0; q < V; ++q) {
-      const int r = r0 + q;
-      if (offm & (1u << r)) s1 += x[q]; else s0 += x[q];
-      if (any & (1u << r)) {  // warp-uniform
-        const uint32_t kc = __shfl_sync(kFull, pnk, r);
-        if (mine & (1u << r)) {
-          if (lane < 24) {
-            if (kc != kNoKey) {
-              const long long q1 = (long long)kc + o1;
-              if (s1 != R(0)) atomicAdd(J + q1, s1);
-              if (s0 != R(0)) atomicAdd(J + (q1 - sc), s0);
-            }
-          } else {
-            hsum[r] = s0;  // the heat of the run ending at row r
+      const bool up = (om >> q) & 1u;
+      s.fma_keep(Pair<R>::make(kv[2 * q], kv[2 * q + 1]),
+                 Pair<R>::make(up ? R(0) : x[q], up ? x[q] : R(0)));
+      sr[q] = s;
+    }
+    const uint32_t ends = em & ((1u << V) - 1u);
+    if (ends) {  // warp-uniform: a cell ends in these rows
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        if ((ends >> q) & 1u) {
+          const uint32_t kc = rk[q];
+          if (adds && kc != kNoKey) {
+            const long long q1 = (long long)kc + o1;
+            if (sr[q].b() != R(0)) atomicAdd(J + q1, sr[q].b());
+            if (sr[q].a() != R(0)) atomicAdd(J + (q1 - sc), sr[q].a());
           }
-          s0 = R(0);
-          s1 = R(0);
         }
       }
     }
+    om >>= V;
+    em >>= V;
+    colp += V;
+    keep += 2 * V;
+    rk += V;
   }
-  __syncwarp();
-  // lane p adds the heat run ending at row p (one FP64 conversion per warp,
-  // not one per row in the walk)
-  if ((endh >> lane) & 1u) {
-    const R hv = hsum[lane];
-    if (phk != kNoKey && hv != R(0)) atomicAdd(g.H + phk, (double)hv);
+
+  // ---- drag heat: segmented scan over runs of equal heat cell in row order
+  bool head_h = lane == 0 || hk_up != phk;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const R hu = __shfl_up_sync(kFull, ph, o);
+    const bool fu = __shfl_up_sync(kFull, head_h, o);
+    if (lane >= o && !head_h) {
+      ph += hu;
+      head_h = fu;
+    }
   }
+  if ((lane == 31 || hk_dn != phk) && phk != kNoKey && ph != R(0))
+    atomicAdd(g.H + phk, (double)ph);
   __syncwarp();  // the stage is rewritten by the warp's next electrons
 }
 
@@ -627,7 +691,7 @@ __device__ __forceinline__ void st_stream(R *p, R v) { __stcs(p, v); }
 // current and drag heat together through the warp's shared-memory stage
 // (dep_words<R>() elements, 16-byte aligned).  Every lane of the warp must
 // call it.
-template <typename R>
+template <typename R, int NS>
 __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, const Grid<R> &g,
                                           const R *__restrict__ tab, const TallyView &tv,
                                           const StepCtx &sc, const PView<R> &p, long long ip,
@@ -655,7 +719,8 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
   }
   if (live) {
     ++acc.n_steps;
-    dep = advance(K, h, g, tab, tv, sc, id, w, X, Y, Zc, ux, uy, uz, tau, acc, rare, heat, heat_cell);
+    dep = advance<R, NS>(K, h, g, tab, tv, sc, id, w, X, Y, Zc, ux, uy, uz, tau, acc, rare, heat,
+                         heat_cell);
     if (dep) {
       st_stream(p.x + ip, X); st_stream(p.y + ip, Y); st_stream(p.z + ip, Zc);
       st_stream(p.ux + ip, ux); st_stream(p.uy + ip, uy); st_stream(p.uz + ip, uz);
@@ -665,7 +730,7 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
     }
   }
   if (!(K.physics & P_UNBOUNDED))  // uniform over the warp
-    warp_deposit(K, g, stage, dep, w, X, Y, Zc, ux, uy, uz, heat, heat_cell);
+    warp_deposit(g, stage, dep, w, X, Y, Zc, ux, uy, uz, heat, heat_cell);
 }
 
 // ---------------------------------------------------------------- injection

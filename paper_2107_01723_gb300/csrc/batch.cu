@@ -56,6 +56,7 @@ struct hpic_batch {
   double *t64 = nullptr;
   float *t32 = nullptr;
   bool any_inject = false;
+  bool single = true;  // every target a single-element solid
   long long host_step = 0;
   hpic_batch_tuning tune{};
   cudaGraphExec_t gstep[2] = {nullptr, nullptr}, gsort[2] = {nullptr, nullptr};
@@ -151,7 +152,7 @@ int enqueue_step(hpic_batch *b) {
     BCK(cudaEventRecord(b->ev[b->ev_used], b->stream));
   }
   hpic::launch_batch_push<R>(b->tg[0]->K, items, b->d, P, tab, b->sm_count, b->tune.blocks_per_sm,
-                             b->stream);
+                             b->single, b->stream);
   ++k;
   if (b->prof) {
     BCK(cudaEventRecord(b->ev[b->ev_used + 1], b->stream));
@@ -394,6 +395,7 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
     c->sm_count = b->sm_count;
     hpic::fold(c->tgt, c->run, c->have_laser ? &c->laser : nullptr, c->K);
     if (c->have_laser && c->K.n_macro > 0) b->any_inject = true;
+    if (c->K.n_solids != 1) b->single = false;
     const long long need = (c->have_laser ? c->K.n_macro : 0) + spare_slots;
     c->cap = round_up(need < 32 ? 32 : need, 32);
     c->poff = slots;

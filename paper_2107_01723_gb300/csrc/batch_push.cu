@@ -65,7 +65,7 @@ __device__ __forceinline__ void flush_acc(const Acc<R> &acc, double *dst) {
 template <typename R>
 struct TargetHot {
   HotK<R> h;
-  GView<R> g;
+  Grid<R> grid;  // read in place by the push (not held in registers)
   TallyView tv;
   long long off;  // first particle slot of the target
   long long step, n;  // the target's step and slot count
@@ -74,7 +74,7 @@ struct TargetHot {
 // MINB = the blocks per SM the launch asks for: the register budget follows
 // (5: 48 registers, 4: 64, 3: 80, 2: 128, 1: 255; the FP32 state spills a
 // little below 64), and the autotuner picks among the variants by timing them
-template <typename R, int MINB>
+template <typename R, int MINB, int NS>
 __global__ void __launch_bounds__(256, MINB)
 k_batch_push(const Consts Krun, const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
              const R *__restrict__ tab) {
@@ -111,9 +111,9 @@ k_batch_push(const Consts Krun, const BatchItem<R> *__restrict__ items, BatchDev
         for (int k = lane; k < bytes / 4; k += 32) b[k] = __ldg(a + k);
       };
       copy(&it.h, &src->h, (int)sizeof(HotK<R>));
-      copy(&it.g, &src->g, (int)sizeof(GView<R>));
       copy(&it.tv, &src->tv, (int)sizeof(TallyView));
       if (lane == 0) {
+        it.grid = make_grid(src->h, src->g);
         it.off = src->off;
         it.step = src->cnt->step;
         it.n = src->cnt->n;
@@ -128,7 +128,7 @@ k_batch_push(const Consts Krun, const BatchItem<R> *__restrict__ items, BatchDev
     sc.key1 = Krun.key1;
     sc.target = it.h.target_index;
     const long long local = (w - wpref_s[t]) * 32 + lane;
-    push_warp<R, 4>(Krun, it.h, make_grid(it.h, it.g), tab, it.tv, sc, p, it.off + local,
+    push_warp<R, NS>(Krun, it.h, it.grid, tab, it.tv, sc, p, it.off + local,
                     local < it.n, acc, tal_s + t * kAccN, stage);
   }
   if (t >= 0) flush_acc(acc, tal_s + t * kAccN);
@@ -248,39 +248,27 @@ template <typename R>
 __global__ void __launch_bounds__(256)
 k_batch_sort_scatter(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> src,
                      PView<R> dst, const uint32_t *keys, uint32_t *offs) {
-  __shared__ uint32_t sm_key[256], sm_base[256];
-  __shared__ int sm_w[8];
   const long long nslot = d.wpref[d.n] * 32;
   int t = 0;
-  for (long long b0 = blockIdx.x * 256ll; b0 < nslot; b0 += (long long)gridDim.x * 256) {
-    const long long s = b0 + threadIdx.x;
-    bool take = false;
-    uint32_t key = 0;
-    long long ip = 0;
-    if (s < nslot) {
-      t = forward_target(d.wpref, t, d.n, s >> 5);  // uniform over the warp
-      const BatchItem<R> &it = items[t];
-      const long long local = s - d.wpref[t] * 32;
-      if (local < it.cnt->n) {
-        ip = it.off + local;
-        key = keys[ip];
-        take = key != (uint32_t)(d.kpref[t] + it.K.nkeys);  // not dead
-      }
-    }
-    const uint32_t slot = block_run_slot(key, take, offs, sm_key, sm_base, sm_w);
-    if (take) {
-      const BatchItem<R> &it = items[t];
-      const long long q = it.off + (long long)slot - d.sstart[t];
-      dst.x[q] = src.x[ip];
-      dst.y[q] = src.y[ip];
-      dst.z[q] = src.z[ip];
-      dst.ux[q] = src.ux[ip];
-      dst.uy[q] = src.uy[ip];
-      dst.uz[q] = src.uz[ip];
-      dst.tau[q] = src.tau[ip];
-      if (it.K.weighted) dst.w[q] = src.w[ip];
-      dst.id[q] = src.id[ip];
-    }
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot;
+       s += (long long)gridDim.x * blockDim.x) {
+    t = forward_target(d.wpref, t, d.n, s >> 5);
+    const BatchItem<R> &it = items[t];
+    const long long local = s - d.wpref[t] * 32;
+    if (local >= it.cnt->n) continue;
+    const long long ip = it.off + local;
+    const uint32_t key = keys[ip];
+    if (key == (uint32_t)(d.kpref[t] + it.K.nkeys)) continue;  // dead
+    const long long q = it.off + (long long)agg_inc(offs, key) - d.sstart[t];
+    dst.x[q] = src.x[ip];
+    dst.y[q] = src.y[ip];
+    dst.z[q] = src.z[ip];
+    dst.ux[q] = src.ux[ip];
+    dst.uy[q] = src.uy[ip];
+    dst.uz[q] = src.uz[ip];
+    dst.tau[q] = src.tau[ip];
+    if (it.K.weighted) dst.w[q] = src.w[ip];
+    dst.id[q] = src.id[ip];
   }
 }
 
@@ -309,36 +297,57 @@ constexpr size_t batch_push_smem_max() {
 cudaError_t prepare_batch_push() {
   const int f = (int)batch_push_smem_max<float>(), d = (int)batch_push_smem_max<double>();
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_batch_push<float, 2>, a, f);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_push<float, 3>, a, f);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_push<float, 4>, a, f);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_push<float, 5>, a, f);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_push<double, 1>, a, d);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_push<double, 2>, a, d);
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void *fn, int bytes) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, a, bytes);
+  };
+  set((const void *)k_batch_push<float, 2, 1>, f);
+  set((const void *)k_batch_push<float, 3, 1>, f);
+  set((const void *)k_batch_push<float, 4, 1>, f);
+  set((const void *)k_batch_push<float, 5, 1>, f);
+  set((const void *)k_batch_push<float, 2, 4>, f);
+  set((const void *)k_batch_push<float, 3, 4>, f);
+  set((const void *)k_batch_push<float, 4, 4>, f);
+  set((const void *)k_batch_push<float, 5, 4>, f);
+  set((const void *)k_batch_push<double, 1, 1>, d);
+  set((const void *)k_batch_push<double, 2, 1>, d);
+  set((const void *)k_batch_push<double, 1, 4>, d);
+  set((const void *)k_batch_push<double, 2, 4>, d);
   return e;
 }
 
+template <typename R, int NS>
+void launch_batch_push_ns(const Consts &Krun, const BatchItem<R> *items, BatchDev d, PView<R> p,
+                          const R *table, int grid, int blocks_per_sm, size_t sm, cudaStream_t st) {
+  if constexpr (sizeof(R) == 8) {  // FP64: one or two blocks per SM
+    if (blocks_per_sm <= 1)
+      k_batch_push<R, 1, NS><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
+    else
+      k_batch_push<R, 2, NS><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
+  } else {  // FP32: two to five (one runs the two-block code)
+    if (blocks_per_sm <= 2)
+      k_batch_push<R, 2, NS><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
+    else if (blocks_per_sm == 3)
+      k_batch_push<R, 3, NS><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
+    else if (blocks_per_sm == 4)
+      k_batch_push<R, 4, NS><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
+    else
+      k_batch_push<R, 5, NS><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
+  }
+}
+
+// single: every target is a single-element solid (the element loops vanish)
 template <typename R>
 void launch_batch_push(const Consts &Krun, const BatchItem<R> *items, BatchDev d, PView<R> p,
-                       const R *table, int sm_count, int blocks_per_sm, cudaStream_t st) {
+                       const R *table, int sm_count, int blocks_per_sm, bool single,
+                       cudaStream_t st) {
   const size_t sm = batch_stage_bytes<R>() + (size_t)d.n * kAccN * sizeof(double) +
                     (d.n + 1) * sizeof(long long);
   const int grid = sm_count * blocks_per_sm;
-  if constexpr (sizeof(R) == 8) {  // FP64: one or two blocks per SM
-    if (blocks_per_sm <= 1)
-      k_batch_push<R, 1><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
-    else
-      k_batch_push<R, 2><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
-  } else {  // FP32: two to five (one runs the two-block code)
-    if (blocks_per_sm <= 2)
-      k_batch_push<R, 2><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
-    else if (blocks_per_sm == 3)
-      k_batch_push<R, 3><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
-    else if (blocks_per_sm == 4)
-      k_batch_push<R, 4><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
-    else
-      k_batch_push<R, 5><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
-  }
+  if (single)
+    launch_batch_push_ns<R, 1>(Krun, items, d, p, table, grid, blocks_per_sm, sm, st);
+  else
+    launch_batch_push_ns<R, 4>(Krun, items, d, p, table, grid, blocks_per_sm, sm, st);
 }
 
 template <typename R>
@@ -370,7 +379,7 @@ int launch_batch_sort(const BatchItem<R> *items, BatchDev d, PView<R> src, PView
 #define HPIC_INST(R)                                                                            \
   template void launch_batch_plan<R>(const BatchItem<R> *, BatchDev, cudaStream_t);             \
   template void launch_batch_push<R>(const Consts &, const BatchItem<R> *, BatchDev, PView<R>,  \
-                                     const R *, int, int, cudaStream_t);                        \
+                                     const R *, int, int, bool, cudaStream_t);                  \
   template void launch_batch_inject<R>(const BatchItem<R> *, BatchDev, PView<R>, int,           \
                                        cudaStream_t);                                           \
   template void launch_batch_advance<R>(const BatchItem<R> *, BatchDev, cudaStream_t);          \

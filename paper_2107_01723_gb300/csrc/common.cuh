@@ -221,42 +221,6 @@ __device__ __forceinline__ uint32_t agg_inc(uint32_t *ctr, uint32_t key) {
   return base + rank;
 }
 
-// Destination of each thread's electron in a counting-sort scatter.  The
-// threads of the block hold consecutive source slots, which are nearly in
-// key order (the electrons moved little since the last sort); neighbours
-// with equal keys form a run, and each run takes consecutive destination
-// slots by one atomic add of its length on the key's running offset, so the
-// run is written as one contiguous stretch.  take = false: the thread's
-// electron stays (dead, or past the end).  sm_key and sm_base hold
-// blockDim.x words, sm_w blockDim.x / 32.  Every thread of the block must
-// call it; returns the slot (0 where take is false).
-__device__ __forceinline__ uint32_t block_run_slot(uint32_t key, bool take, uint32_t *offs,
-                                                   uint32_t *sm_key, uint32_t *sm_base, int *sm_w) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t k = take ? key : 0xFFFFFFFFu;
-  sm_key[tid] = k;
-  __syncthreads();
-  const bool head = tid == 0 || sm_key[tid - 1] != k;
-  const bool tail = tid == (int)blockDim.x - 1 || sm_key[tid + 1] != k;
-  // this thread's run starts at the last head at or before it: a running
-  // maximum of (head ? tid : 0), across the warp by shuffles, then the warps
-  int hp = head ? tid : 0;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int u = __shfl_up_sync(0xffffffffu, hp, o);
-    if (lane >= o) hp = max(hp, u);
-  }
-  if (lane == 31) sm_w[warp] = hp;
-  __syncthreads();
-  for (int w = 0; w < warp; ++w) hp = max(hp, sm_w[w]);
-  const int idx = tid - hp;
-  if (take && tail) sm_base[hp] = atomicAdd(offs + key, (uint32_t)(idx + 1));
-  __syncthreads();
-  const uint32_t q = take ? sm_base[hp] + (uint32_t)idx : 0u;
-  __syncthreads();  // the shared words are reused by the next call
-  return q;
-}
-
 // Sum `nq` per-thread values over the block and add them to dst[slot[q]].
 // smem must hold nq * 32 doubles.  All threads of the block must call it.
 template <int NQ>

@@ -197,31 +197,25 @@ __global__ void __launch_bounds__(1024) k_scan_apply(uint32_t *counts, long long
   }
 }
 
-// Each block moves 256 consecutive source slots; runs of equal keys among
-// them are written as contiguous stretches (block_run_slot).
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_sort_scatter(const Consts K, PView<R> src, PView<R> dst, const Counters *cnt,
                const uint32_t *keys, uint32_t *offsets) {
-  __shared__ uint32_t sm_key[256], sm_base[256];
-  __shared__ int sm_w[8];
   const long long n = cnt->n;
-  for (long long b0 = blockIdx.x * 256ll; b0 < n; b0 += (long long)gridDim.x * 256) {
-    const long long ip = b0 + threadIdx.x;
-    const uint32_t key = ip < n ? keys[ip] : (uint32_t)K.nkeys;
-    const bool take = key < (uint32_t)K.nkeys;
-    const uint32_t q = block_run_slot(key, take, offsets, sm_key, sm_base, sm_w);
-    if (take) {
-      dst.x[q] = src.x[ip];
-      dst.y[q] = src.y[ip];
-      dst.z[q] = src.z[ip];
-      dst.ux[q] = src.ux[ip];
-      dst.uy[q] = src.uy[ip];
-      dst.uz[q] = src.uz[ip];
-      dst.tau[q] = src.tau[ip];
-      if (K.weighted) dst.w[q] = src.w[ip];
-      dst.id[q] = src.id[ip];
-    }
+  for (long long ip = blockIdx.x * (long long)blockDim.x + threadIdx.x; ip < n;
+       ip += (long long)gridDim.x * blockDim.x) {
+    const uint32_t key = keys[ip];
+    if (key >= (uint32_t)K.nkeys) continue;
+    const uint32_t q = agg_inc(offsets, key);
+    dst.x[q] = src.x[ip];
+    dst.y[q] = src.y[ip];
+    dst.z[q] = src.z[ip];
+    dst.ux[q] = src.ux[ip];
+    dst.uy[q] = src.uy[ip];
+    dst.uz[q] = src.uz[ip];
+    dst.tau[q] = src.tau[ip];
+    if (K.weighted) dst.w[q] = src.w[ip];
+    dst.id[q] = src.id[ip];
   }
 }
 

@@ -180,10 +180,12 @@ struct BatchDev {
 template <typename R>
 void launch_batch_plan(const BatchItem<R> *items, BatchDev d, cudaStream_t st);
 // persistent particle kernel, sm_count * blocks_per_sm blocks; Krun: the
-// run-wide constants (any target's Consts: those fields are common)
+// run-wide constants (any target's Consts: those fields are common);
+// single: every target is a single-element solid
 template <typename R>
 void launch_batch_push(const Consts &Krun, const BatchItem<R> *items, BatchDev d, PView<R> p,
-                       const R *table, int sm_count, int blocks_per_sm, cudaStream_t st);
+                       const R *table, int sm_count, int blocks_per_sm, bool single,
+                       cudaStream_t st);
 template <typename R>
 void launch_batch_inject(const BatchItem<R> *items, BatchDev d, PView<R> p, int grid,
                          cudaStream_t st);

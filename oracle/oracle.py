@@ -2,7 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the
 benchmark's CPU-baseline leg load this module; the CUDA library never does.
-`build()` compiles the oracle with gcc into oracle/_build/liboracle.so.
+`build()` compiles the oracle with gcc into oracle/_build/liboracle.so;
+`build(threads=True)` compiles the same sources with OpenMP into
+liboracle_omp.so, used only to time the oracle on all host cores (the
+serial library is the one the tests check against).
 """
 from __future__ import annotations
 
@@ -15,6 +18,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
+LIB_OMP_PATH = os.path.join(BUILD_DIR, "liboracle_omp.so")
 SOURCES = ["physics.c", "sim.c", "model.c"]
 
 ORC_DRAG, ORC_SCATTER, ORC_BREM, ORC_FIELDS, ORC_FARADAY, ORC_HEATING = 1, 2, 4, 8, 16, 32
@@ -25,19 +29,21 @@ GRID = {"T": 0, "eta": 1, "Ex": 2, "Ey": 3, "Ez": 4, "Bx": 5, "By": 6, "Bz": 7,
         "jx": 8, "jy": 9, "jz": 10, "heat": 11, "Ti": 12}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle (plain C11, no FMA contraction so x86 and Arm agree)."""
+def build(force: bool = False, threads: bool = False) -> str:
+    """Compile the oracle (plain C11, no FMA contraction so x86 and Arm agree);
+    threads: the OpenMP build for all-core timing."""
+    path = LIB_OMP_PATH if threads else LIB_PATH
     srcs = [os.path.join(HERE, s) for s in SOURCES]
     newest = max(os.path.getmtime(p) for p in srcs + [os.path.join(HERE, "oracle.h")])
-    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
-        return LIB_PATH
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= newest:
+        return path
     os.makedirs(BUILD_DIR, exist_ok=True)
-    tmp = LIB_PATH + f".{os.getpid()}.tmp"
+    tmp = path + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", tmp] + srcs + ["-lm"]
+           *(["-fopenmp"] if threads else []), "-o", tmp] + srcs + ["-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 class Solid(C.Structure):
@@ -101,14 +107,13 @@ class Tallies(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = C.CDLL(build())
-        L = _lib
+def lib(threads: bool = False):
+    if threads not in _libs:
+        L = C.CDLL(build(threads=threads))
+        _libs[threads] = L
         dp = C.POINTER(C.c_double)
         up = C.POINTER(C.c_uint32)
         L.orc_create.restype = C.c_void_p
@@ -172,7 +177,7 @@ def lib():
         L.orc_get_weights.argtypes = [C.c_void_p, dp]
         L.orc_set_weights.argtypes = [C.c_void_p, C.c_int64, dp]
         L.orc_boris.argtypes = [dp, dp, dp, C.c_double]
-    return _lib
+    return _libs[threads]
 
 
 def _dp(a: np.ndarray):
@@ -204,13 +209,13 @@ def weights(sim) -> np.ndarray:
     n = sim.n
     w = np.empty(n)
     if n:
-        lib().orc_get_weights(sim.h, _dp(w))
+        sim._L.orc_get_weights(sim.h, _dp(w))
     return w
 
 
 def set_weights(sim, w) -> None:
     w = np.ascontiguousarray(w, dtype=np.float64)
-    lib().orc_set_weights(sim.h, len(w), _dp(w))
+    sim._L.orc_set_weights(sim.h, len(w), _dp(w))
 
 
 def make_run(d: dict) -> Run:
@@ -220,39 +225,41 @@ def make_run(d: dict) -> Run:
 class OracleSim:
     """One target advanced by the FP64 CPU oracle."""
 
-    def __init__(self, target: dict, laser: dict, run: dict):
+    def __init__(self, target: dict, laser: dict, run: dict, threads: bool = False):
+        """threads: step with the OpenMP build on all host cores (timing only)."""
         self.target, self.laser, self.run = dict(target), dict(laser), dict(run)
+        self._L = lib(threads)
         self._t = make_target(target)
         self._l = make_laser(laser)
         self._r = make_run(run)
-        self.h = lib().orc_create(C.byref(self._t), C.byref(self._l), C.byref(self._r))
+        self.h = self._L.orc_create(C.byref(self._t), C.byref(self._l), C.byref(self._r))
         if not self.h:
             raise ValueError("oracle rejected the configuration")
 
     def __del__(self):
         h = getattr(self, "h", None)
         if h:
-            lib().orc_destroy(h)
+            self._L.orc_destroy(h)
             self.h = None
 
     def step(self, n: int = 1) -> None:
-        lib().orc_step(self.h, int(n))
+        self._L.orc_step(self.h, int(n))
 
     def fields(self) -> None:
-        lib().orc_fields(self.h)
+        self._L.orc_fields(self.h)
 
     def seed(self, n: int, mean_eps: float) -> None:
-        lib().orc_seed(self.h, int(n), float(mean_eps))
+        self._L.orc_seed(self.h, int(n), float(mean_eps))
 
     @property
     def n(self) -> int:
-        return int(lib().orc_n_particles(self.h))
+        return int(self._L.orc_n_particles(self.h))
 
     def particles(self) -> dict:
         n = self.n
         out = {k: np.empty(n) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")}
         out["id"] = np.empty(n, dtype=np.uint32)
-        lib().orc_get_particles(self.h, *[_dp(out[k]) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")],
+        self._L.orc_get_particles(self.h, *[_dp(out[k]) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")],
                                 _up(out["id"]))
         return out
 
@@ -260,58 +267,58 @@ class OracleSim:
         n = len(p["id"])
         arrs = [np.ascontiguousarray(p[k], dtype=np.float64) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")]
         ids = np.ascontiguousarray(p["id"], dtype=np.uint32)
-        lib().orc_set_particles(self.h, n, *[_dp(a) for a in arrs], _up(ids))
+        self._L.orc_set_particles(self.h, n, *[_dp(a) for a in arrs], _up(ids))
 
     def grid(self, which: str) -> np.ndarray:
         w = GRID[which]
-        out = np.empty(lib().orc_grid_len(self.h, w))
-        lib().orc_get_grid(self.h, w, _dp(out))
+        out = np.empty(self._L.orc_grid_len(self.h, w))
+        self._L.orc_get_grid(self.h, w, _dp(out))
         return out
 
     def set_grid(self, which: str, values: np.ndarray) -> None:
         w = GRID[which]
         a = np.ascontiguousarray(values, dtype=np.float64)
-        assert a.size == lib().orc_grid_len(self.h, w)
-        lib().orc_set_grid(self.h, w, _dp(a))
+        assert a.size == self._L.orc_grid_len(self.h, w)
+        self._L.orc_set_grid(self.h, w, _dp(a))
 
     def tallies(self) -> dict:
         t = Tallies()
-        lib().orc_get_tallies(self.h, C.byref(t))
+        self._L.orc_get_tallies(self.h, C.byref(t))
         d = t.as_dict()
-        d["E_live"] = lib().orc_live_energy(self.h)
-        d["E_B_field"] = lib().orc_field_energy(self.h)
+        d["E_live"] = self._L.orc_live_energy(self.h)
+        d["E_B_field"] = self._L.orc_field_energy(self.h)
         return d
 
     def reset_tallies(self) -> None:
-        lib().orc_reset_tallies(self.h)
+        self._L.orc_reset_tallies(self.h)
 
     def hist(self):
         rows = self.run["n_E"] + 2
         hE = np.empty(rows * self.run["n_theta"])
         hN = np.empty_like(hE)
-        lib().orc_get_hist(self.h, _dp(hE), _dp(hN))
+        self._L.orc_get_hist(self.h, _dp(hE), _dp(hN))
         return hE.reshape(rows, -1), hN.reshape(rows, -1)
 
     def history(self) -> np.ndarray:
         out = np.empty(max(self.run["max_history"], 0))
-        lib().orc_get_history(self.h, _dp(out))
+        self._L.orc_get_history(self.h, _dp(out))
         return out
 
     def clock(self):
         a, b = C.c_int64(), C.c_int64()
-        lib().orc_get_clock(self.h, C.byref(a), C.byref(b))
+        self._L.orc_get_clock(self.h, C.byref(a), C.byref(b))
         return a.value, b.value
 
     def set_clock(self, step: int, n_ids: int) -> None:
-        lib().orc_set_clock(self.h, int(step), int(n_ids))
+        self._L.orc_set_clock(self.h, int(step), int(n_ids))
 
     @property
     def weight(self) -> float:
-        return lib().orc_weight(self.h)
+        return self._L.orc_weight(self.h)
 
     @property
     def a0(self) -> float:
-        return lib().orc_a0_of(self.h)
+        return self._L.orc_a0_of(self.h)
 
 
 # ---- single formulas ----

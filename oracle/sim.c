@@ -27,6 +27,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q_E 1.602176634e-19
 #define M_E 9.1093837015e-31
@@ -53,6 +56,7 @@ struct orc_sim {
   orc_tallies tal;
   double *histE, *histN, *history;
   double *table;
+  double *ohm;  /* Ohmic energy of each cell in the current step (heating) */
 };
 
 static double kinetic(const double u[3]) {
@@ -343,6 +347,7 @@ static void field_update(orc_sim *s) {
   if (s->r.physics & ORC_FIELDS) {
     /* Ohm's law with the return current on interior edges; tangential E is
      * zero on the outer faces (conducting walls) */
+#pragma omp parallel for schedule(static)
     for (int k = 0; k <= nz; ++k)
       for (int j = 0; j <= ny; ++j)
         for (int i = 0; i <= nx; ++i) {
@@ -366,6 +371,7 @@ static void field_update(orc_sim *s) {
         }
   }
   if (s->r.physics & ORC_FARADAY) {
+#pragma omp parallel for schedule(static)
     for (int k = 0; k <= nz; ++k)
       for (int j = 0; j <= ny; ++j)
         for (int i = 0; i <= nx; ++i) {
@@ -391,6 +397,10 @@ static void heating(orc_sim *s) {
   double *T = s->g[ORC_T], *eta = s->g[ORC_ETA], *Ti = s->g[ORC_TI];
   const double *heat = s->g[ORC_HEAT];
   const int fields = (s->r.physics & ORC_FIELDS) != 0;
+  double *ohm = s->ohm;
+  /* each cell on its own (in parallel in the OpenMP build); the cells'
+   * Ohmic energies are summed into the tally afterwards in cell order */
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -404,7 +414,7 @@ static void heating(orc_sim *s) {
           double jbz = 0.25 * (jz[vidx(s, i, j, k)] + jz[vidx(s, i + 1, j, k)] +
                                jz[vidx(s, i, j + 1, k)] + jz[vidx(s, i + 1, j + 1, k)]);
           double rho_ohm = eta[c] * (jbx * jbx + jby * jby + jbz * jbz) * dt;
-          s->tal.E_ohmic_grid += rho_ohm * V;
+          ohm[c] = rho_ohm * V;
           rho += rho_ohm;
         }
         if (s->r.physics & ORC_HEATING) T[c] += orc_temperature_rise(&s->t, T[c], rho);
@@ -422,6 +432,8 @@ static void heating(orc_sim *s) {
         }
         if (s->r.physics & (ORC_HEATING | ORC_EI)) eta[c] = orc_resistivity(&s->t, T[c]);
       }
+  if (fields)
+    for (int64_t c = 0; c < s->ncell; ++c) s->tal.E_ohmic_grid += ohm[c];
 }
 
 /* ---------------- injection: Eq. (B1) ---------------- */
@@ -613,6 +625,7 @@ orc_sim *orc_create(const orc_target *t, const orc_laser *l, const orc_run *r) {
   s->nvec = (int64_t)(t->nx + 1) * (t->ny + 1) * (t->nz + 1);
   s->ncell = (int64_t)t->nx * t->ny * t->nz;
   for (int w = 0; w < 13; ++w) s->g[w] = calloc(orc_grid_len(s, w), sizeof(double));
+  s->ohm = calloc(s->ncell, sizeof(double));
   for (int64_t c = 0; c < s->ncell; ++c) {
     s->g[ORC_T][c] = t->T0;
     s->g[ORC_TI][c] = t->T0;
@@ -632,9 +645,59 @@ void orc_destroy(orc_sim *s) {
   free(s->x); free(s->y); free(s->z); free(s->ux); free(s->uy); free(s->uz);
   free(s->tau); free(s->wt); free(s->id); free(s->alive);
   for (int w = 0; w < 13; ++w) free(s->g[w]);
-  free(s->histE); free(s->histN); free(s->history); free(s->table);
+  free(s->histE); free(s->histN); free(s->history); free(s->table); free(s->ohm);
   free(s);
 }
+
+#ifdef _OPENMP
+/* The electrons of a step on nt threads (the OpenMP build, used only to time
+ * the oracle on all host cores): each thread adds into private copies of
+ * what the step accumulates (tallies, photon histograms and history,
+ * current, drag heat), which are then added to the context's in thread
+ * order.  The electrons' own state is written in place (one thread each). */
+static void electrons_threads(orc_sim *s, int nt) {
+  const size_t hl = (size_t)(s->r.n_E + 2) * (size_t)s->r.n_theta;
+  const size_t hy = s->r.max_history > 0 ? (size_t)s->r.max_history : 1;
+  const int acc[4] = {ORC_JX, ORC_JY, ORC_JZ, ORC_HEAT};
+  orc_sim *loc = malloc((size_t)nt * sizeof(orc_sim));
+  for (int t = 0; t < nt; ++t) {
+    loc[t] = *s;
+    memset(&loc[t].tal, 0, sizeof(orc_tallies));
+    loc[t].histE = calloc(hl, sizeof(double));
+    loc[t].histN = calloc(hl, sizeof(double));
+    loc[t].history = calloc(hy, sizeof(double));
+    for (int a = 0; a < 4; ++a) loc[t].g[acc[a]] = calloc(orc_grid_len(s, acc[a]), sizeof(double));
+  }
+#pragma omp parallel num_threads(nt)
+  {
+    orc_sim *me = loc + omp_get_thread_num();
+#pragma omp for schedule(static)
+    for (int64_t ip = 0; ip < s->n; ++ip) particle_update(me, ip);
+  }
+  double *dst = (double *)&s->tal;
+  for (int t = 0; t < nt; ++t) {
+    const double *src = (const double *)&loc[t].tal;
+    for (size_t k = 0; k < sizeof(orc_tallies) / sizeof(double); ++k) dst[k] += src[k];
+  }
+  for (int a = 0; a < 4; ++a) {
+    double *g = s->g[acc[a]];
+    const int64_t len = orc_grid_len(s, acc[a]);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < len; ++q)
+      for (int t = 0; t < nt; ++t) g[q] += loc[t].g[acc[a]][q];
+  }
+  for (int t = 0; t < nt; ++t) {
+    for (size_t q = 0; q < hl; ++q) {
+      s->histE[q] += loc[t].histE[q];
+      s->histN[q] += loc[t].histN[q];
+    }
+    for (size_t q = 0; q < hy; ++q) s->history[q] += loc[t].history[q];
+    free(loc[t].histE); free(loc[t].histN); free(loc[t].history);
+    for (int a = 0; a < 4; ++a) free(loc[t].g[acc[a]]);
+  }
+  free(loc);
+}
+#endif
 
 int orc_step(orc_sim *s, int64_t nsteps) {
   for (int64_t it = 0; it < nsteps; ++it) {
@@ -642,6 +705,10 @@ int orc_step(orc_sim *s, int64_t nsteps) {
     memset(s->g[ORC_JY], 0, s->nvec * sizeof(double));
     memset(s->g[ORC_JZ], 0, s->nvec * sizeof(double));
     memset(s->g[ORC_HEAT], 0, s->ncell * sizeof(double));
+#ifdef _OPENMP
+    if (omp_get_max_threads() > 1 && s->n > 0) electrons_threads(s, omp_get_max_threads());
+    else
+#endif
     for (int64_t ip = 0; ip < s->n; ++ip) particle_update(s, ip);
     int64_t m = 0;
     for (int64_t ip = 0; ip < s->n; ++ip) {

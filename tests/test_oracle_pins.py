@@ -1140,3 +1140,32 @@ def test_compound_mixture_rules():
     assert cold == pytest.approx(rho / (ne * sc.k * 0.3), rel=1e-6)
     hot = O.temperature_rise(ch, 1e12, rho)
     assert hot == pytest.approx(rho / (ne * sc.k * 1.5), rel=1e-3)
+
+
+# ---------------------------------------------------------------- all-core build
+def test_openmp_oracle_equals_serial_up_to_rounding_order():
+    """The oracle's OpenMP build (used only to time the oracle on all host
+    cores) advances the same electrons as the serial oracle: the same
+    survivors, and states and tallies equal up to the order of the
+    floating-point additions (1e-12 relative)."""
+    try:
+        O.build(threads=True)
+    except Exception as e:  # noqa: BLE001
+        pytest.skip(f"no OpenMP build here: {e}")
+    cfg = W.config_small(n=(12, 10, 14), n_macro=6000, I_Wcm2=1e21, steps=40, spot_r=3e-6,
+                         t_inj=20e-15)
+    a = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
+    b = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"], threads=True)
+    a.step(40)
+    b.step(40)
+    pa, pb = a.particles(), b.particles()
+    oa, ob = np.argsort(pa["id"]), np.argsort(pb["id"])
+    assert np.array_equal(pa["id"][oa], pb["id"][ob])
+    for k in ("x", "ux", "tau"):
+        assert np.allclose(pa[k][oa], pb[k][ob], rtol=1e-12, atol=1e-18), k
+    ta, tb = a.tallies(), b.tallies()
+    for k in ta:
+        assert tb[k] == pytest.approx(ta[k], rel=1e-12, abs=1e-30), k
+    for k in ("T", "Bz", "jx"):
+        ga, gb = a.grid(k), b.grid(k)
+        assert np.abs(ga - gb).max() <= 1e-12 * np.abs(ga).max(), k

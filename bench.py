@@ -43,7 +43,12 @@ NCU_DRAM_BYTES_PER_PSTEP = {"fp32": 56.0, "fp64": None}
 # the same for k_batch_push, captured on the first 16 targets of the scan
 # (the full scan holds too much device memory for a multi-pass capture): the traffic is the
 # electron state streamed once, so it scales with the particle-steps
-NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": 65.5, "fp64": None}
+NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": 60.8, "fp64": None}
+# FP64 FLOP per particle-step of the FP64 k_push (2 per DFMA, 1 per DADD and
+# DMUL; ncu thread-level counts on config 1 in FP64, launches at steps 110
+# and 111) and the FP64 rate the GB300 is stated to have (TFLOP/s)
+NCU_FP64_FLOP_PER_PSTEP = 1239.0
+FP64_STATED_TFLOPS = 1.25
 # the accuracy window: the injection (200 steps) and 1 ps beyond
 ACCURACY_STEPS = 2200
 SORT_INTERVAL = 5  # measured, default bench: 5 / 10 / 20 / 40 give 9.64 / 9.45 / 8.99 / 8.20e9 particle-steps/s
@@ -326,6 +331,12 @@ def run_gpu(args, world, rank, local):
         fp64 = {"value": (a1 - a0) / (m64 / 1e3), "unit": UNIT, "steps": k64,
                 "ms_per_step": m64 / k64,
                 "push_kernel_gbs": ALG_BYTES["fp64"] * kp / (km / 1e3) / 1e9 if km > 0 else None}
+        if km > 0:
+            tf = NCU_FP64_FLOP_PER_PSTEP * kp / (km / 1e3) / 1e12
+            fp64["alu"] = {"bound": "fp64", "achieved_tflops": tf, "peak_tflops": FP64_STATED_TFLOPS,
+                           "frac": tf / FP64_STATED_TFLOPS, "peak_source": "stated (GB300 FP64 rate)",
+                           "flop_per_particle_step": NCU_FP64_FLOP_PER_PSTEP,
+                           "flop_source": "ncu DFMA/DADD/DMUL counts on config 1 in FP64"}
         if not args.no_accuracy:
             done64 = 200 + args.warmup + k64
             acc_steps = max(ACCURACY_STEPS, done64)
@@ -509,6 +520,38 @@ def run_thick(args):
            "dE_dOmega_peak_deg": float(np.degrees(0.5 * (edges[:-1] + edges[1:]))[int(np.argmax(dEdO))]),
            "forward_fraction_0_30deg": float(E_th[edges[1:] <= math.radians(30.0) + 1e-12].sum() / E_th.sum())}
     print(json.dumps(out), flush=True)
+
+
+def run_small(args):
+    """Config 1 (32^3 cells of 1 um gold, 1e5 electrons over 100 fs at
+    1e20 W/cm^2) stepped `--full-steps` steps (default 200) in the chosen
+    precision: particle-steps/s and the live count (not the headline line;
+    a small case for counter captures)."""
+    import torch
+
+    from paper_2107_01723_gb300 import build as B
+    from paper_2107_01723_gb300 import hpic
+    from paper_2107_01723_gb300 import workloads as W
+    B.build()
+    cfg = W.config1()
+    steps = args.full_steps if args.full_steps > 0 else cfg["steps"]
+    prec = hpic.HPIC_FP32_MIXED if args.precision == "fp32" else hpic.HPIC_FP64
+    stream = torch.cuda.Stream()
+    sim = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec,
+                   stream=stream.cuda_stream, sort_interval=SORT_INTERVAL)
+    live = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sim.step(1)
+        live.append(sim.n)
+    e1.record(stream)
+    e1.synchronize()
+    t = sim.tallies()
+    sim.close()
+    print(json.dumps({"what": "config 1, " + args.precision, "steps": steps,
+                      "particle_steps_per_s": t["particle_steps"] / (e0.elapsed_time(e1) / 1e3),
+                      "live_after_step": live}), flush=True)
 
 
 def emission_result(n: int, steps: dict, warmup: int) -> dict:
@@ -736,7 +779,7 @@ def run_model(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "emission", "batch", "model", "thick"])
+                    choices=["headline", "emission", "batch", "model", "thick", "small"])
     ap.add_argument("--model-n-I", type=int, default=256, help="loss-channel heatmap: intensities")
     ap.add_argument("--emission-n", type=int, default=2 ** 27)
     ap.add_argument("--batch-targets", type=int, default=64,
@@ -769,6 +812,9 @@ def main():
         return
     if args.workload == "thick":
         run_thick(args)
+        return
+    if args.workload == "small":
+        run_small(args)
         return
     if args.workload == "batch":
         run_batch(args)

@@ -101,6 +101,9 @@ std::vector<InjCell> injection_cells(const hpic_target_desc &t, const hpic_laser
 // is launched as one persistent wave of sm_count times this many blocks
 template <typename R>
 constexpr int push_blocks_per_sm() { return sizeof(R) == 4 ? 5 : 2; }
+// threads per block of the single-target particle kernel (a warp-sized
+// deposit stage per warp)
+constexpr int kPushThreads = 256;
 
 // host transfers of the electron state (the C-ABI's read and load calls):
 // live-slot compaction in storage order and FP64 <-> R conversion on the device

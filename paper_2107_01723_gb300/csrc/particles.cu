@@ -27,7 +27,7 @@ template <typename R, int NS>
 // launched as one persistent wave: the kernel is issue- and latency-bound
 // and gains from the warps (three blocks at 80 registers were 14 % slower,
 // four and six slower too).  FP64 keeps two.
-__global__ void __launch_bounds__(256, push_blocks_per_sm<R>())
+__global__ void __launch_bounds__(kPushThreads, push_blocks_per_sm<R>())
 k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__restrict__ tab,
        Counters *cnt, TallyView tv) {
   __shared__ double rare[kAccN];  // the rare tally sums of the block
@@ -211,7 +211,7 @@ __global__ void k_advance(Counters *cnt, long long cap) {
 // ---------------------------------------------------------------- launchers
 
 template <typename R>
-constexpr size_t push_stage_bytes() { return 8 * dep_words<R>() * sizeof(R); }
+constexpr size_t push_stage_bytes() { return (kPushThreads / 32) * dep_words<R>() * sizeof(R); }
 
 cudaError_t prepare_push() {
   cudaError_t e = cudaFuncSetAttribute(k_push<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -232,9 +232,9 @@ template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
                  TallyView tv, int grid, cudaStream_t st) {
   if (K.n_solids == 1)  // a single-element solid: the element loops vanish
-    k_push<R, 1><<<grid, 256, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv);
+    k_push<R, 1><<<grid, kPushThreads, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv);
   else
-    k_push<R, 4><<<grid, 256, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv);
+    k_push<R, 4><<<grid, kPushThreads, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv);
 }
 
 template <typename R>

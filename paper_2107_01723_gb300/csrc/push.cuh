@@ -345,7 +345,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     alive = false;
   } else if (K.physics & P_DRAG) {
     const R gam = R(1) + eps;
-    const R beta = m_sqrt(eps * (eps + R(2))) / gam;  // scales a tallied loss only
+    const R beta = u_of_eps(eps) / gam;
     const R ig = R(1) / gam;
     const R le = m_flog(eps), lh = R(0.5) * m_flog(gam + R(1));
     const R a2 = R(0.909) * ig * ig, a1 = R(0.818) * ig;
@@ -397,7 +397,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
 
   // ---- bremsstrahlung by optical depth (App. B)
   if (alive && (K.physics & P_BREM) && eps > h.k_min) {
-    R dtau = h.K_tau * m_sqrt(eps * (eps + R(2))) / eps * shape_G(h.k_min / eps);
+    R dtau = h.K_tau * u_of_eps(eps) / eps * shape_G(h.k_min / eps);
     if (K.physics & P_FSIGMA) dtau *= __ldg(g.Fsig + ax.iN + nx * (ay.iN + ny * az.iN));
     tau -= dtau;
     if (tau <= R(0)) {

@@ -51,7 +51,10 @@ NCU_FP64_FLOP_PER_PSTEP = 1239.0
 FP64_STATED_TFLOPS = 1.25
 # the accuracy window: the injection (200 steps) and 1 ps beyond
 ACCURACY_STEPS = 2200
-SORT_INTERVAL = 5  # measured, default bench: 5 / 10 / 20 / 40 give 9.64 / 9.45 / 8.99 / 8.20e9 particle-steps/s
+# cell sort every 5 steps, keyed by the cell reached 3 steps ahead; measured over 600 steps
+# after the injection: intervals 5 / 6 / 7 / 8 give 1.173 / 1.180 / 1.185 / 1.184e10
+# particle-steps/s with k_push at 0.642 / 0.649 / 0.656 / 0.660 ms (5 keeps the push kernel fastest)
+SORT_INTERVAL = 5
 
 
 def peaks() -> dict:

@@ -180,7 +180,11 @@ typedef struct {
   double table_Emax_J;  /* top electron energy of the table */
   int32_t curlB_term;   /* 1: E = eta(curl B/mu0 - j_h) (Eq. A2); 0: E = -eta j_h */
   int32_t physics;      /* HPIC_* bitmask */
-  int32_t sort_interval;/* steps between cell sorts (0 = never) */
+  int32_t sort_interval;/* steps between cell sorts inside hpic_step (0 = never);
+                           such a sort orders the electrons by the cell each
+                           reaches (sort_interval + 1)/2 steps ahead at its
+                           current velocity (clamped to the grid), the middle
+                           of the steps it serves */
   int32_t max_history;  /* length of the per-step X-ray history */
 } hpic_run_params;
 
@@ -233,8 +237,11 @@ int hpic_seed_electrons(hpic_ctx *ctx, int64_t n, double mean_energy_J);
 /* Advance n_steps >= 0 steps (asynchronous).  Errors: HPIC_EINVAL, HPIC_ECUDA. */
 int hpic_step(hpic_ctx *ctx, int64_t n_steps);
 
-/* Counting sort of the electrons by cell; drops absorbed/escaped slots.
- * Also run every sort_interval steps inside hpic_step.  Asynchronous. */
+/* Counting sort of the electrons by the cell they are in (4x4x4 cell tiles,
+ * x-fastest); drops absorbed/escaped slots.  The sort that hpic_step runs
+ * every sort_interval steps keys each electron by the cell it reaches
+ * (sort_interval + 1)/2 steps ahead instead (the order only; no electron
+ * moves).  Asynchronous. */
 int hpic_sort(hpic_ctx *ctx);
 
 /* Tallies accumulated since creation or the last reset (synchronises). */
@@ -368,7 +375,8 @@ const char *hpic_last_error(const hpic_ctx *ctx);
 
 typedef struct {
   int32_t blocks_per_sm;   /* persistent particle-kernel blocks per SM (1..5; FP64 1..2) */
-  int32_t sort_interval;   /* steps between cell sorts (0: never) */
+  int32_t sort_interval;   /* steps between cell sorts (0: never); keyed by the cell
+                              reached (sort_interval + 1)/2 steps ahead */
   int32_t use_graph;       /* replay captured CUDA graphs (1) or launch directly (0) */
   int32_t reserved;
   double ms_per_step;      /* autotuner: measured time of the chosen setting */

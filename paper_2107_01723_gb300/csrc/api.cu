@@ -469,7 +469,7 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
     if (ctx->run.sort_interval > 0 && ctx->host_step % ctx->run.sort_interval == 0) {
       ctx->launches += hpic::launch_sort<R>(ctx->K, P(ctx->cur), P(ctx->cur ^ 1), ctx->cnt,
                                             ctx->keys, ctx->counts, ctx->partials, gp,
-                                            ctx->stream);
+                                            ctx->stream, hpic::sort_lead(ctx->run.sort_interval));
       ctx->cur ^= 1;
     }
     CK(cudaGetLastError());
@@ -481,7 +481,7 @@ template <typename R>
 int sort_impl(hpic_ctx *ctx) {
   ctx->launches += hpic::launch_sort<R>(ctx->K, pview<R>(ctx, ctx->cur), pview<R>(ctx, ctx->cur ^ 1),
                                         ctx->cnt, ctx->keys, ctx->counts, ctx->partials,
-                                        grid_blocks(ctx, ctx->cap), ctx->stream);
+                                        grid_blocks(ctx, ctx->cap), ctx->stream, 0.0);
   ctx->cur ^= 1;
   CK(cudaGetLastError());
   return HPIC_OK;

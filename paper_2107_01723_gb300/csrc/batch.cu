@@ -183,7 +183,7 @@ int enqueue_sort(hpic_batch *b) {
   const int k = hpic::launch_batch_sort<R>(items, b->d, pview_all<R>(b, b->cur),
                                            pview_all<R>(b, b->cur ^ 1), b->keys, b->counts,
                                            b->partials, b->nkeys_total, grid_for(b, b->slots),
-                                           b->stream);
+                                           b->stream, hpic::sort_lead(b->tune.sort_interval));
   BCK(cudaGetLastError());
   return k;
 }

@@ -210,7 +210,7 @@ __global__ void k_batch_advance(const BatchItem<R> *items, BatchDev d) {
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_batch_sort_keys(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
-                  uint32_t *keys, uint32_t *counts) {
+                  uint32_t *keys, uint32_t *counts, R lead) {
   const long long nslot = d.wpref[d.n] * 32;
   int t = 0;
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot;
@@ -222,7 +222,15 @@ k_batch_sort_keys(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p
     const long long ip = it.off + local;
     uint32_t key = (uint32_t)(d.kpref[t] + it.K.nkeys);
     if (p.id[ip] != kDead) {
-      int i = (int)m_floor(p.x[ip]), j = (int)m_floor(p.y[ip]), k = (int)m_floor(p.z[ip]);
+      R X = p.x[ip], Y = p.y[ip], Z = p.z[ip];
+      if (lead != R(0)) {  // the cell reached `lead` steps ahead (cdt: cells per step at c)
+        const R ux = p.ux[ip], uy = p.uy[ip], uz = p.uz[ip];
+        const R a = lead * it.h.cdt / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+        X += a * ux;
+        Y += a * uy;
+        Z += a * uz;
+      }
+      int i = (int)m_floor(X), j = (int)m_floor(Y), k = (int)m_floor(Z);
       i = min(max(i, 0), it.K.nx - 1);
       j = min(max(j, 0), it.K.ny - 1);
       k = min(max(k, 0), it.K.nz - 1);
@@ -365,10 +373,10 @@ void launch_batch_advance(const BatchItem<R> *items, BatchDev d, cudaStream_t st
 template <typename R>
 int launch_batch_sort(const BatchItem<R> *items, BatchDev d, PView<R> src, PView<R> dst,
                       uint32_t *keys, uint32_t *counts, uint32_t *partials, long long nkeys_total,
-                      int grid, cudaStream_t st) {
+                      int grid, cudaStream_t st, double lead) {
   k_batch_plan<R><<<1, 256, 0, st>>>(items, d);  // tasks from the current counts
   cudaMemsetAsync(counts, 0, nkeys_total * sizeof(uint32_t), st);
-  k_batch_sort_keys<R><<<grid, 256, 0, st>>>(items, d, src, keys, counts);
+  k_batch_sort_keys<R><<<grid, 256, 0, st>>>(items, d, src, keys, counts, R(lead));
   int launches = 2 + launch_scan(counts, nkeys_total, partials, st);
   k_batch_sort_starts<R><<<1, 256, 0, st>>>(items, d, counts);
   k_batch_sort_scatter<R><<<grid, 256, 0, st>>>(items, d, src, dst, keys, counts);
@@ -385,7 +393,7 @@ int launch_batch_sort(const BatchItem<R> *items, BatchDev d, PView<R> src, PView
   template void launch_batch_advance<R>(const BatchItem<R> *, BatchDev, cudaStream_t);          \
   template int launch_batch_sort<R>(const BatchItem<R> *, BatchDev, PView<R>, PView<R>,         \
                                     uint32_t *, uint32_t *, uint32_t *, long long, int,         \
-                                    cudaStream_t);
+                                    cudaStream_t, double);
 HPIC_INST(float)
 HPIC_INST(double)
 #undef HPIC_INST

@@ -81,15 +81,26 @@ __global__ void __launch_bounds__(256) k_batch_bheat(const BatchItem<R> *items, 
 }
 
 // ---------------------------------------------------------------- counting sort
+// Key of each slot: the tile key of the cell at x + lead (u/gamma), lead in
+// cells per unit of u/gamma (0: the current cell), clamped to the grid.
 template <typename R>
 __global__ void __launch_bounds__(256)
-k_sort_keys(const Consts K, PView<R> p, const Counters *cnt, uint32_t *keys, uint32_t *counts) {
+k_sort_keys(const Consts K, PView<R> p, const Counters *cnt, uint32_t *keys, uint32_t *counts,
+            R lead) {
   const long long n = cnt->n;
   for (long long ip = blockIdx.x * (long long)blockDim.x + threadIdx.x; ip < n;
        ip += (long long)gridDim.x * blockDim.x) {
     uint32_t key = (uint32_t)K.nkeys;
     if (p.id[ip] != kDead) {
-      int i = (int)m_floor(p.x[ip]), j = (int)m_floor(p.y[ip]), k = (int)m_floor(p.z[ip]);
+      R X = p.x[ip], Y = p.y[ip], Z = p.z[ip];
+      if (lead != R(0)) {  // uniform over the launch
+        const R ux = p.ux[ip], uy = p.uy[ip], uz = p.uz[ip];
+        const R a = lead / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+        X += a * ux;
+        Y += a * uy;
+        Z += a * uz;
+      }
+      int i = (int)m_floor(X), j = (int)m_floor(Y), k = (int)m_floor(Z);
       i = min(max(i, 0), K.nx - 1);
       j = min(max(j, 0), K.ny - 1);
       k = min(max(k, 0), K.nz - 1);
@@ -321,10 +332,10 @@ int launch_scan(uint32_t *counts, long long m, uint32_t *partials, cudaStream_t 
 
 template <typename R>
 int launch_sort(const Consts &K, PView<R> src, PView<R> dst, Counters *cnt, uint32_t *keys,
-                uint32_t *counts, uint32_t *partials, int grid, cudaStream_t st) {
+                uint32_t *counts, uint32_t *partials, int grid, cudaStream_t st, double lead) {
   const long long m = K.nkeys + 1;
   cudaMemsetAsync(counts, 0, m * sizeof(uint32_t), st);
-  k_sort_keys<R><<<grid, 256, 0, st>>>(K, src, cnt, keys, counts);
+  k_sort_keys<R><<<grid, 256, 0, st>>>(K, src, cnt, keys, counts, R(lead * K.cdt_dx));
   launch_scan(counts, m, partials, st);
   k_sort_scatter<R><<<grid, 256, 0, st>>>(K, src, dst, cnt, keys, counts);
   k_sort_finish<<<1, 32, 0, st>>>(cnt, counts, K.nkeys);
@@ -519,7 +530,7 @@ template void launch_compact<uint32_t, uint32_t>(const uint32_t *, const uint32_
   template void launch_efield<R>(const Consts &, GView<R>, int, cudaStream_t);                \
   template void launch_bheat<R>(const Consts &, GView<R>, TallyView, int, cudaStream_t);      \
   template int launch_sort<R>(const Consts &, PView<R>, PView<R>, Counters *, uint32_t *,     \
-                              uint32_t *, uint32_t *, int, cudaStream_t);                     \
+                              uint32_t *, uint32_t *, int, cudaStream_t, double);             \
   template void launch_live_energy<R>(const Consts &, PView<R>, Counters *, double *, int,    \
                                       cudaStream_t);                                          \
   template void launch_field_energy<R>(const Consts &, GView<R>, double *, int, cudaStream_t); \

@@ -141,10 +141,18 @@ void launch_efield(const Consts &K, GView<R> g, int grid, cudaStream_t st);
 template <typename R>
 void launch_bheat(const Consts &K, GView<R> g, TallyView tv, int grid, cudaStream_t st);
 
-// counting sort by cell: keys/counts/offsets are scratch; returns launches made
+// counting sort by cell: keys/counts/offsets are scratch; electrons are keyed
+// by the cell they reach `lead` steps ahead at their current velocity (0: the
+// cell they are in); returns launches made
 template <typename R>
 int launch_sort(const Consts &K, PView<R> src, PView<R> dst, Counters *cnt, uint32_t *keys,
-                uint32_t *counts, uint32_t *partials, int grid, cudaStream_t st);
+                uint32_t *counts, uint32_t *partials, int grid, cudaStream_t st, double lead);
+
+// Lead (steps) of the sort that runs every `interval` steps: the cell each
+// electron reaches halfway through the coming interval, so that the gathers
+// at x^n and the deposits at x^{n+1} of the steps until the next sort find
+// a warp's electrons in as few cells as the drift allows
+inline double sort_lead(int interval) { return interval > 0 ? 0.5 * (interval + 1) : 0.0; }
 
 void launch_table(const Consts &K, double k_min, double E_max, double *t64, float *t32,
                   cudaStream_t st);
@@ -202,7 +210,7 @@ void launch_batch_bheat(const BatchItem<R> *items, BatchDev d, int grid, cudaStr
 template <typename R>
 int launch_batch_sort(const BatchItem<R> *items, BatchDev d, PView<R> src, PView<R> dst,
                       uint32_t *keys, uint32_t *counts, uint32_t *partials, long long nkeys_total,
-                      int grid, cudaStream_t st);
+                      int grid, cudaStream_t st, double lead);
 // counts summed per block of the scan; the partials scratch of a scan of m
 // counts holds scan_partials(m) words
 constexpr long long kScanTile = 4096;

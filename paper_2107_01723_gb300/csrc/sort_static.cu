@@ -176,10 +176,10 @@ extern "C" int hpic_sort_cells_noalloc(int32_t nx, int32_t ny, int32_t nz, int32
   k_noalloc_begin<<<1, 32, 0, st>>>(cnt, n);
   if (precision == HPIC_FP32_MIXED)
     hpic::launch_sort<float>(K, view_of<float>(in), view_of<float>(out_soa), cnt, keys, counts,
-                             partials, grid, st);
+                             partials, grid, st, 0.0);
   else
     hpic::launch_sort<double>(K, view_of<double>(in), view_of<double>(out_soa), cnt, keys,
-                              counts, partials, grid, st);
+                              counts, partials, grid, st, 0.0);
   k_noalloc_end<<<1, 32, 0, st>>>(cnt, reinterpret_cast<long long *>(n_live_dev));
   e = cudaGetLastError();
   if (e != cudaSuccess) return noalloc_fail(HPIC_ECUDA, cudaGetErrorString(e));

@@ -5,7 +5,7 @@ Workload: 128^3 cells of 1 um gold, 1e7 macro-electrons injected over
 100 fs at 1e21 W/cm^2 (T_hot = 13.7 MeV), dt = 0.5 fs, reflux on all faces;
 the 200-step injection runs before timing, then K steps are timed with the
 full population resident in HBM.  One step = push/collide/emit/deposit,
-E and B update, heating, (injection), and the cell sort every 5 steps.
+E and B update, heating, (injection), and a cell sort folded into every third step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
     python bench.py --impl reference ...   # the FP64 CPU oracle, timed alone
@@ -36,6 +36,9 @@ WORKLOAD = ("128^3 cells x 1 um Au (Z=79, n_i=5.9e28 m^-3, T0=1 eV), 1e7 e- inje
 # algorithmic bytes per particle-step of the push kernel: the SoA state is
 # read once (x,y,z,ux,uy,uz,tau + u32 id) and written once (7 reals)
 ALG_BYTES = {"fp32": 7 * 4 + 4 + 7 * 4, "fp64": 7 * 8 + 4 + 7 * 8}
+# a step that also sorts (every SORT_INTERVAL steps) reads each slot's sort key
+# and rank and writes its id to the sorted slot: 12 B more per particle-step
+SORT_STEP_EXTRA_BYTES = 4 + 4 + 4
 # DRAM bytes (read + write) per particle-step of k_push measured by ncu on
 # this workload (dram__bytes_read.sum + dram__bytes_write.sum of one launch
 # over its particle-steps); None where not captured
@@ -51,10 +54,17 @@ NCU_FP64_FLOP_PER_PSTEP = 1239.0
 FP64_STATED_TFLOPS = 1.25
 # the accuracy window: the injection (200 steps) and 1 ps beyond
 ACCURACY_STEPS = 2200
-# cell sort every 5 steps, keyed by the cell reached 3 steps ahead; measured over 600 steps
-# after the injection: intervals 5 / 6 / 7 / 8 give 1.173 / 1.180 / 1.185 / 1.184e10
-# particle-steps/s with k_push at 0.642 / 0.649 / 0.656 / 0.660 ms (5 keeps the push kernel fastest)
-SORT_INTERVAL = 5
+# cell sort every 3 steps, folded into the step and keyed by the cell reached halfway
+# through the interval; measured over 600 steps after the injection: intervals 3 / 4 / 5 /
+# 6 / 8 give steps of 0.796 / 0.794 / 0.792 / 0.795 / 0.801 ms with k_push at 0.639 /
+# 0.646 / 0.650 / 0.657 / 0.668 ms (the step is flat; 3 keeps the push kernel fastest)
+SORT_INTERVAL = 3
+
+
+def push_bytes(precision: str, k_ps: float, k_launches: int, step0: int, steps: int) -> float:
+    """Algorithmic bytes of the push launches of steps [step0, step0 + steps)."""
+    n_sort = sum(1 for s in range(step0, step0 + steps) if (s + 1) % SORT_INTERVAL == 0)
+    return ALG_BYTES[precision] * k_ps + SORT_STEP_EXTRA_BYTES * n_sort * k_ps / max(k_launches, 1)
 
 
 def peaks() -> dict:
@@ -333,7 +343,8 @@ def run_gpu(args, world, rank, local):
         hpic.hpic_profile(s64.h, False)
         fp64 = {"value": (a1 - a0) / (m64 / 1e3), "unit": UNIT, "steps": k64,
                 "ms_per_step": m64 / k64,
-                "push_kernel_gbs": ALG_BYTES["fp64"] * kp / (km / 1e3) / 1e9 if km > 0 else None}
+                "push_kernel_gbs": (push_bytes("fp64", kp, kl, 200 + args.warmup, k64) / (km / 1e3) / 1e9
+                                    if km > 0 else None)}
         if km > 0:
             tf = NCU_FP64_FLOP_PER_PSTEP * kp / (km / 1e3) / 1e12
             fp64["alu"] = {"bound": "fp64", "achieved_tflops": tf, "peak_tflops": FP64_STATED_TFLOPS,
@@ -372,7 +383,8 @@ def run_gpu(args, world, rank, local):
         return
     pk = peaks()
     k_avg_ms = k_ms / max(k_launches, 1)
-    achieved = ALG_BYTES[args.precision] * (k_ps / max(k_launches, 1)) / (k_avg_ms / 1e3) / 1e9
+    k_bytes = push_bytes(args.precision, k_ps, k_launches, int(snap_clock[0]), args.steps)
+    achieved = k_bytes / max(k_launches, 1) / (k_avg_ms / 1e3) / 1e9
     tb = NCU_DRAM_BYTES_PER_PSTEP[args.precision]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"],
@@ -380,7 +392,8 @@ def run_gpu(args, world, rank, local):
                 "traffic_unit": "bytes per launch (ncu dram read+write, scaled by particle-steps)",
                 "kernel": "k_push (push/collide/emit/deposit)",
                 "kernel_ms_avg": k_avg_ms, "kernel_share_of_step": k_ms / ms if ms > 0 else None,
-                "bytes_per_particle_step": ALG_BYTES[args.precision], "peak_source": pk["source"]}
+                "bytes_per_particle_step": k_bytes / k_ps if k_ps > 0 else None,
+                "peak_source": pk["source"]}
     cpu = None
     if not args.no_cpu_baseline:
         keys = ("value", "unit", "cores", "kind", "sample", "cpu_model", "host_cores")

@@ -180,11 +180,12 @@ typedef struct {
   double table_Emax_J;  /* top electron energy of the table */
   int32_t curlB_term;   /* 1: E = eta(curl B/mu0 - j_h) (Eq. A2); 0: E = -eta j_h */
   int32_t physics;      /* HPIC_* bitmask */
-  int32_t sort_interval;/* steps between cell sorts inside hpic_step (0 = never);
-                           such a sort orders the electrons by the cell each
-                           reaches (sort_interval + 1)/2 steps ahead at its
-                           current velocity (clamped to the grid), the middle
-                           of the steps it serves */
+  int32_t sort_interval;/* cell sort inside every sort_interval-th step of
+                           hpic_step (0 = never): the step writes the electrons
+                           in the order of the cell each reaches
+                           (sort_interval + 1)/2 steps after it at its
+                           velocity (clamped to the grid), the middle of the
+                           steps that order serves */
   int32_t max_history;  /* length of the per-step X-ray history */
 } hpic_run_params;
 
@@ -238,10 +239,12 @@ int hpic_seed_electrons(hpic_ctx *ctx, int64_t n, double mean_energy_J);
 int hpic_step(hpic_ctx *ctx, int64_t n_steps);
 
 /* Counting sort of the electrons by the cell they are in (4x4x4 cell tiles,
- * x-fastest); drops absorbed/escaped slots.  The sort that hpic_step runs
- * every sort_interval steps keys each electron by the cell it reaches
- * (sort_interval + 1)/2 steps ahead instead (the order only; no electron
- * moves).  Asynchronous. */
+ * x-fastest); drops absorbed/escaped slots.  The sort inside every
+ * sort_interval-th step of hpic_step is folded into that step: its keys come
+ * from the state at the start of the step, one step further ahead, and the
+ * push writes each electron to its sorted slot (the order only; electrons
+ * absorbed or escaping in that step leave their slots there marked dead
+ * until the next sort).  Asynchronous. */
 int hpic_sort(hpic_ctx *ctx);
 
 /* Tallies accumulated since creation or the last reset (synchronises). */

@@ -101,7 +101,7 @@ int reserve(hpic_ctx *ctx, long long need) {
       return fail(ctx, HPIC_ENOMEM, "particle storage allocation failed");
     }
   }
-  if (cudaMalloc(&nk, cap * sizeof(uint32_t)) != cudaSuccess) {
+  if (cudaMalloc(&nk, 2 * cap * sizeof(uint32_t)) != cudaSuccess) {  // sort keys, then ranks
     cudaGetLastError();
     cudaFree(nb[0]);
     cudaFree(nb[1]);
@@ -429,6 +429,22 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
       CK(cudaMemsetAsync(G.J[0], 0, 3 * ctx->vstride * ctx->rsz, ctx->stream));
       CK(cudaMemsetAsync(ctx->H, 0, ctx->K.ncell * sizeof(double), ctx->stream));
     }
+    // every sort_interval steps the cell sort rides on the step: its keys
+    // come from the start-of-step state one step further ahead, and the push
+    // writes each electron to its sorted slot in the other buffer
+    const int si = ctx->run.sort_interval;
+    const bool sort_now = si > 0 && (ctx->host_step + 1) % si == 0 && ctx->keys;
+    hpic::SortOut<R> so{};
+    if (sort_now) {
+      uint32_t *ranks = ctx->keys + ctx->cap;
+      ctx->launches += hpic::launch_sort_keys<R>(ctx->K, P(ctx->cur), ctx->cnt, ctx->keys, ranks,
+                                                 ctx->counts, ctx->partials, gp, ctx->stream,
+                                                 hpic::sort_lead(si) + 1.0);
+      so.dst = P(ctx->cur ^ 1);
+      so.keys = ctx->keys;
+      so.ranks = ranks;
+      so.offsets = ctx->counts;
+    }
     if (ctx->prof) {
       if (ctx->ev_used + 2 > ctx->ev.size()) {
         for (int q = 0; q < 64; ++q) {
@@ -440,7 +456,7 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
       CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
     }
     hpic::launch_push<R>(ctx->K, P(ctx->cur), G, tab, ctx->cnt, tv,
-                         ctx->sm_count * hpic::push_blocks_per_sm<R>(), ctx->stream);
+                         ctx->sm_count * hpic::push_blocks_per_sm<R>(), ctx->stream, so);
     ctx->launches += 1;
     if (ctx->prof) {
       CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
@@ -455,6 +471,10 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
       hpic::launch_bheat<R>(ctx->K, G, tv, gg, ctx->stream);
       ctx->launches += 1;
     }
+    if (sort_now) {  // the kept electrons now fill the front of the other buffer
+      ctx->launches += hpic::launch_sort_finish(ctx->K, ctx->cnt, ctx->counts, ctx->stream);
+      ctx->cur ^= 1;
+    }
     if (ctx->have_laser && ctx->host_step < ctx->K.n_inj_steps && injection_total(ctx) > 0) {
       const long long S = ctx->K.n_inj_steps, N = ctx->K.n_macro, st = ctx->host_step;
       const long long c = ctx->K.weighted ? ctx->K.per_cell * ctx->K.n_inj_cells
@@ -466,12 +486,6 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
     hpic::launch_advance(ctx->cnt, ctx->cap, ctx->stream);
     ctx->launches += 1;
     ctx->host_step += 1;
-    if (ctx->run.sort_interval > 0 && ctx->host_step % ctx->run.sort_interval == 0) {
-      ctx->launches += hpic::launch_sort<R>(ctx->K, P(ctx->cur), P(ctx->cur ^ 1), ctx->cnt,
-                                            ctx->keys, ctx->counts, ctx->partials, gp,
-                                            ctx->stream, hpic::sort_lead(ctx->run.sort_interval));
-      ctx->cur ^= 1;
-    }
     CK(cudaGetLastError());
   }
   return HPIC_OK;

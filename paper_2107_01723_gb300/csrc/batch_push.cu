@@ -129,7 +129,7 @@ k_batch_push(const Consts Krun, const BatchItem<R> *__restrict__ items, BatchDev
     sc.target = it.h.target_index;
     const long long local = (w - wpref_s[t]) * 32 + lane;
     push_warp<R, NS>(Krun, it.h, it.grid, tab, it.tv, sc, p, it.off + local,
-                    local < it.n, acc, tal_s + t * kAccN, stage);
+                    local < it.n, acc, tal_s + t * kAccN, stage, SortOut<R>{});
   }
   if (t >= 0) flush_acc(acc, tal_s + t * kAccN);
   __syncthreads();

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) k_batch_bheat(const BatchItem<R> *items, 
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_sort_keys(const Consts K, PView<R> p, const Counters *cnt, uint32_t *keys, uint32_t *counts,
-            R lead) {
+            R lead, uint32_t *ranks) {
   const long long n = cnt->n;
   for (long long ip = blockIdx.x * (long long)blockDim.x + threadIdx.x; ip < n;
        ip += (long long)gridDim.x * blockDim.x) {
@@ -107,7 +107,10 @@ k_sort_keys(const Consts K, PView<R> p, const Counters *cnt, uint32_t *keys, uin
       key = tile_key(i, j, k, K.nti, K.ntj);
     }
     keys[ip] = key;
-    agg_inc(counts, key);
+    if (ranks)  // uniform over the launch
+      ranks[ip] = agg_inc(counts, key);
+    else
+      agg_inc(counts, key);
   }
 }
 
@@ -335,11 +338,25 @@ int launch_sort(const Consts &K, PView<R> src, PView<R> dst, Counters *cnt, uint
                 uint32_t *counts, uint32_t *partials, int grid, cudaStream_t st, double lead) {
   const long long m = K.nkeys + 1;
   cudaMemsetAsync(counts, 0, m * sizeof(uint32_t), st);
-  k_sort_keys<R><<<grid, 256, 0, st>>>(K, src, cnt, keys, counts, R(lead * K.cdt_dx));
+  k_sort_keys<R><<<grid, 256, 0, st>>>(K, src, cnt, keys, counts, R(lead * K.cdt_dx), nullptr);
   launch_scan(counts, m, partials, st);
   k_sort_scatter<R><<<grid, 256, 0, st>>>(K, src, dst, cnt, keys, counts);
   k_sort_finish<<<1, 32, 0, st>>>(cnt, counts, K.nkeys);
   return 6;
+}
+
+template <typename R>
+int launch_sort_keys(const Consts &K, PView<R> p, Counters *cnt, uint32_t *keys, uint32_t *ranks,
+                     uint32_t *counts, uint32_t *partials, int grid, cudaStream_t st, double lead) {
+  const long long m = K.nkeys + 1;
+  cudaMemsetAsync(counts, 0, m * sizeof(uint32_t), st);
+  k_sort_keys<R><<<grid, 256, 0, st>>>(K, p, cnt, keys, counts, R(lead * K.cdt_dx), ranks);
+  return 1 + launch_scan(counts, m, partials, st);
+}
+
+int launch_sort_finish(const Consts &K, Counters *cnt, const uint32_t *offsets, cudaStream_t st) {
+  k_sort_finish<<<1, 32, 0, st>>>(cnt, offsets, K.nkeys);
+  return 1;
 }
 
 void launch_table(const Consts &K, double k_min, double E_max, double *t64, float *t32,
@@ -531,6 +548,8 @@ template void launch_compact<uint32_t, uint32_t>(const uint32_t *, const uint32_
   template void launch_bheat<R>(const Consts &, GView<R>, TallyView, int, cudaStream_t);      \
   template int launch_sort<R>(const Consts &, PView<R>, PView<R>, Counters *, uint32_t *,     \
                               uint32_t *, uint32_t *, int, cudaStream_t, double);             \
+  template int launch_sort_keys<R>(const Consts &, PView<R>, Counters *, uint32_t *, uint32_t *, \
+                                   uint32_t *, uint32_t *, int, cudaStream_t, double);        \
   template void launch_live_energy<R>(const Consts &, PView<R>, Counters *, double *, int,    \
                                       cudaStream_t);                                          \
   template void launch_field_energy<R>(const Consts &, GView<R>, double *, int, cudaStream_t); \

@@ -124,9 +124,21 @@ void launch_fill(R *dst, long long n, R v, int grid, cudaStream_t st);
 // default 48 KB for FP64 and the batch); once per device, before any launch
 cudaError_t prepare_push();
 cudaError_t prepare_batch_push();
+// Where a step that also sorts writes its electrons: an electron live at
+// the start of the step goes to slot offsets[key] + rank of dst, where the
+// counting sort's key pass ran on that start-of-step state (key and rank
+// of each slot) and its scan turned the counts into offsets; one that is
+// absorbed or escapes leaves its slot there marked dead.  dst.x == nullptr:
+// the electrons stay in their slots.
+template <typename R>
+struct SortOut {
+  PView<R> dst;
+  const uint32_t *keys, *ranks, *offsets;
+};
+
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
-                 TallyView tv, int grid, cudaStream_t st);
+                 TallyView tv, int grid, cudaStream_t st, const SortOut<R> &so);
 template <typename R>
 void launch_inject(const Consts &K, PView<R> p, Counters *cnt, long long cap, TallyView tv,
                    int grid, cudaStream_t st);
@@ -153,6 +165,16 @@ int launch_sort(const Consts &K, PView<R> src, PView<R> dst, Counters *cnt, uint
 // at x^n and the deposits at x^{n+1} of the steps until the next sort find
 // a warp's electrons in as few cells as the drift allows
 inline double sort_lead(int interval) { return interval > 0 ? 0.5 * (interval + 1) : 0.0; }
+
+// The counting sort folded into a step: keys, ranks (each slot's place among
+// the slots of its key) and the scanned offsets of the electrons in p, keyed
+// `lead` steps ahead; the step's push then writes each electron to its
+// sorted slot (SortOut) and launch_sort_finish sets the slot count to the
+// electrons kept.  Return launches made.
+template <typename R>
+int launch_sort_keys(const Consts &K, PView<R> p, Counters *cnt, uint32_t *keys, uint32_t *ranks,
+                     uint32_t *counts, uint32_t *partials, int grid, cudaStream_t st, double lead);
+int launch_sort_finish(const Consts &K, Counters *cnt, const uint32_t *offsets, cudaStream_t st);
 
 void launch_table(const Consts &K, double k_min, double E_max, double *t64, float *t32,
                   cudaStream_t st);

@@ -29,7 +29,7 @@ template <typename R, int NS>
 // four and six slower too).  FP64 keeps two.
 __global__ void __launch_bounds__(kPushThreads, push_blocks_per_sm<R>())
 k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__restrict__ tab,
-       Counters *cnt, TallyView tv) {
+       Counters *cnt, TallyView tv, const SortOut<R> so) {
   __shared__ double rare[kAccN];  // the rare tally sums of the block
   if (threadIdx.x < kAccN) rare[threadIdx.x] = 0.0;
   __syncthreads();
@@ -51,7 +51,7 @@ k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__rest
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); base < n;
        base += stride)
-    push_warp<R, NS>(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc, rare, stage);
+    push_warp<R, NS>(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc, rare, stage, so);
 
   double v[kAccN];
   acc.values(v);
@@ -230,11 +230,11 @@ cudaError_t prepare_push() {
 
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
-                 TallyView tv, int grid, cudaStream_t st) {
+                 TallyView tv, int grid, cudaStream_t st, const SortOut<R> &so) {
   if (K.n_solids == 1)  // a single-element solid: the element loops vanish
-    k_push<R, 1><<<grid, kPushThreads, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv);
+    k_push<R, 1><<<grid, kPushThreads, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv, so);
   else
-    k_push<R, 4><<<grid, kPushThreads, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv);
+    k_push<R, 4><<<grid, kPushThreads, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv, so);
 }
 
 template <typename R>
@@ -248,9 +248,10 @@ void launch_advance(Counters *cnt, long long cap, cudaStream_t st) {
 }
 
 template void launch_push<float>(const Consts &, PView<float>, GView<float>, const float *,
-                                 Counters *, TallyView, int, cudaStream_t);
+                                 Counters *, TallyView, int, cudaStream_t, const SortOut<float> &);
 template void launch_push<double>(const Consts &, PView<double>, GView<double>, const double *,
-                                  Counters *, TallyView, int, cudaStream_t);
+                                  Counters *, TallyView, int, cudaStream_t,
+                                  const SortOut<double> &);
 template void launch_inject<float>(const Consts &, PView<float>, Counters *, long long, TallyView,
                                    int, cudaStream_t);
 template void launch_inject<double>(const Consts &, PView<double>, Counters *, long long,

@@ -696,7 +696,8 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
                                           const R *__restrict__ tab, const TallyView &tv,
                                           const StepCtx &sc, const PView<R> &p, long long ip,
                                           bool in_range, Acc<R> &acc, double *rare,
-                                          R *__restrict__ stage) {
+                                          R *__restrict__ stage, const SortOut<R> &so) {
+  const bool sorting = so.dst.x != nullptr;  // uniform over the launch
   bool live = false, dep = false;
   uint32_t id = kDead;
   R X = 0, Y = 0, Zc = 0, ux = 0, uy = 0, uz = 0, tau = 0, heat = 0, w = h.w;
@@ -712,7 +713,10 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
           isfinite(uz) && isfinite(tau)) {
         live = true;
       } else {
-        p.id[ip] = kDead;
+        if (sorting)
+          so.dst.id[(long long)so.offsets[so.keys[ip]] + so.ranks[ip]] = kDead;
+        else
+          p.id[ip] = kDead;
         atomicAdd(rare + A_N_NF, 1.0);
       }
     }
@@ -721,7 +725,18 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
     ++acc.n_steps;
     dep = advance<R, NS>(K, h, g, tab, tv, sc, id, w, X, Y, Zc, ux, uy, uz, tau, acc, rare, heat,
                          heat_cell);
-    if (dep) {
+    if (sorting) {  // loaded here so that no register holds them through the step
+      const long long q = (long long)so.offsets[ld_stream(so.keys + ip)] + ld_stream(so.ranks + ip);
+      if (dep) {
+        st_stream(so.dst.x + q, X); st_stream(so.dst.y + q, Y); st_stream(so.dst.z + q, Zc);
+        st_stream(so.dst.ux + q, ux); st_stream(so.dst.uy + q, uy); st_stream(so.dst.uz + q, uz);
+        st_stream(so.dst.tau + q, tau);
+        if (K.weighted) st_stream(so.dst.w + q, w);
+        so.dst.id[q] = id;
+      } else {
+        so.dst.id[q] = kDead;
+      }
+    } else if (dep) {
       st_stream(p.x + ip, X); st_stream(p.y + ip, Y); st_stream(p.z + ip, Zc);
       st_stream(p.ux + ip, ux); st_stream(p.uy + ip, uy); st_stream(p.uz + ip, uz);
       st_stream(p.tau + ip, tau);

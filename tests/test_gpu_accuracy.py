@@ -26,7 +26,7 @@ def built():
 
 def ce_and_closure(prec):
     cfg = W.config2()
-    sim = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec, sort_interval=5)
+    sim = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec, sort_interval=3)
     sim.step(STEPS)
     t = sim.tallies()
     sim.close()

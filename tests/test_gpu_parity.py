@@ -322,7 +322,7 @@ def test_load_checks_before_writing(prec):
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_full_size_headline(prec):
     """128^3 gold, 1e7 electrons at 1e21 W/cm^2 (the headline workload) in the
-    launch configuration the benchmark times (cell sort every 5 steps).
+    launch configuration the benchmark times (cell sort every 3 steps).
 
     (1) The oracle computes the first two steps itself -- 5e4 electrons
     injected at step 0 and pushed at step 1 through the full 128^3 grid, plus
@@ -331,7 +331,7 @@ def test_full_size_headline(prec):
     energy closure, total current, div B, heating, tally consistency."""
     cfg = W.config2()
     prec_id, tol, abs_frac = PREC[prec]
-    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec_id, sort_interval=5)
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec_id, sort_interval=3)
     o = O.OracleSim(cfg["target"], cfg["laser"], cfg["run"])
     g.step(2)
     o.step(2)
@@ -468,13 +468,13 @@ def test_full_size_live_fields(which, prec):
     and heating stencils and the reflux is exercised at 128^3 and at
     500 x 256 x 256 with non-zero values.  The GPU context is cell-sorted
     first and sorts again at the end of the step (the benchmark's launch
-    configuration, a sort every 5 steps); one step, then every electron and
+    configuration, a sort every 3 steps); one step, then every electron and
     grid element against the oracle.  In FP32 the deposit's bound adds the
     rounding of the FP32 cell coordinates (derived below)."""
     cfg, before, after = _live_reference(which)
     prec_id, tol, abs_frac = PREC[prec]
     assert max(np.abs(before["g"][k]).max() for k in ("Ex", "By")) > 0
-    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec_id, sort_interval=5)
+    g = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=prec_id, sort_interval=3)
     g.set_particles(before["p"])
     for k, v in before["g"].items():
         g.set_grid(k, v)

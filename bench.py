@@ -41,8 +41,11 @@ ALG_BYTES = {"fp32": 7 * 4 + 4 + 7 * 4, "fp64": 7 * 8 + 4 + 7 * 8}
 SORT_STEP_EXTRA_BYTES = 4 + 4 + 4
 # DRAM bytes (read + write) per particle-step of k_push measured by ncu on
 # this workload (dram__bytes_read.sum + dram__bytes_write.sum of one launch
-# over its particle-steps); None where not captured
-NCU_DRAM_BYTES_PER_PSTEP = {"fp32": 56.0, "fp64": None}
+# over its particle-steps; launches 204-205 plain, 206 a sort step): a plain
+# step streams the state once (absorbed slots are not rewritten), a sort step
+# adds key and rank and scatters its stores (partial sectors); None where not
+# captured
+NCU_DRAM_BYTES_PER_PSTEP = {"fp32": {"plain": 55.9, "sort": 91.6}, "fp64": None}
 # the same for k_batch_push, captured on the first 16 targets of the scan
 # (the full scan holds too much device memory for a multi-pass capture): the traffic is the
 # electron state streamed once, so it scales with the particle-steps
@@ -61,10 +64,26 @@ ACCURACY_STEPS = 2200
 SORT_INTERVAL = 3
 
 
+def n_sort_steps(step0: int, steps: int) -> int:
+    """Steps of [step0, step0 + steps) that also sort."""
+    return sum(1 for s in range(step0, step0 + steps) if (s + 1) % SORT_INTERVAL == 0)
+
+
 def push_bytes(precision: str, k_ps: float, k_launches: int, step0: int, steps: int) -> float:
     """Algorithmic bytes of the push launches of steps [step0, step0 + steps)."""
-    n_sort = sum(1 for s in range(step0, step0 + steps) if (s + 1) % SORT_INTERVAL == 0)
+    n_sort = n_sort_steps(step0, steps)
     return ALG_BYTES[precision] * k_ps + SORT_STEP_EXTRA_BYTES * n_sort * k_ps / max(k_launches, 1)
+
+
+def push_traffic(precision: str, k_ps: float, k_launches: int, step0: int, steps: int):
+    """ncu DRAM bytes per push launch of those steps, from the per-particle-step
+    figures of a plain and a sort step."""
+    tb = NCU_DRAM_BYTES_PER_PSTEP[precision]
+    if not tb or k_launches <= 0:
+        return None
+    n_sort = n_sort_steps(step0, steps)
+    per_ps = (tb["plain"] * (k_launches - n_sort) + tb["sort"] * n_sort) / k_launches
+    return per_ps * k_ps / k_launches
 
 
 def peaks() -> dict:
@@ -385,10 +404,9 @@ def run_gpu(args, world, rank, local):
     k_avg_ms = k_ms / max(k_launches, 1)
     k_bytes = push_bytes(args.precision, k_ps, k_launches, int(snap_clock[0]), args.steps)
     achieved = k_bytes / max(k_launches, 1) / (k_avg_ms / 1e3) / 1e9
-    tb = NCU_DRAM_BYTES_PER_PSTEP[args.precision]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"],
-                "traffic": tb * k_ps / max(k_launches, 1) if tb else None,
+                "traffic": push_traffic(args.precision, k_ps, k_launches, int(snap_clock[0]), args.steps),
                 "traffic_unit": "bytes per launch (ncu dram read+write, scaled by particle-steps)",
                 "kernel": "k_push (push/collide/emit/deposit)",
                 "kernel_ms_avg": k_avg_ms, "kernel_share_of_step": k_ms / ms if ms > 0 else None,

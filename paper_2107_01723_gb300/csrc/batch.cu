@@ -127,10 +127,14 @@ void drop_graphs(hpic_batch *b) {
 }
 
 // one step of every target; returns the kernels launched, or < 0 on error
+// One step of every target; with sort, the cell sort rides on it (keys from
+// the start-of-step state one step further ahead, the push writing each
+// electron to its sorted slot of the other buffer, injection into that one).
 template <typename R>
-int enqueue_step(hpic_batch *b) {
+int enqueue_step(hpic_batch *b, bool sort) {
   const auto *items = static_cast<const hpic::BatchItem<R> *>(b->items);
   const hpic::PView<R> P = pview_all<R>(b, b->cur);
+  const hpic::PView<R> Pnext = sort ? pview_all<R>(b, b->cur ^ 1) : P;
   const R *tab = b->fp32 ? reinterpret_cast<const R *>(b->t32) : reinterpret_cast<const R *>(b->t64);
   const bool grid_on = !(b->run.physics & HPIC_UNBOUNDED);
   const int gg = grid_for(b, b->nodes_total);
@@ -141,6 +145,17 @@ int enqueue_step(hpic_batch *b) {
   }
   hpic::launch_batch_plan<R>(items, b->d, b->stream);
   ++k;
+  hpic::SortOut<R> so{};
+  if (sort) {
+    uint32_t *ranks = b->keys + b->slots;
+    k += hpic::launch_batch_sort_keys<R>(items, b->d, P, b->keys, ranks, b->counts, b->partials,
+                                         b->nkeys_total, grid_for(b, b->slots), b->stream,
+                                         hpic::sort_lead(b->tune.sort_interval) + 1.0);
+    so.dst = Pnext;
+    so.keys = b->keys;
+    so.ranks = ranks;
+    so.offsets = b->counts;
+  }
   if (b->prof) {
     if (b->ev_used + 2 > b->ev.size()) {
       for (int q = 0; q < 64; ++q) {
@@ -152,7 +167,7 @@ int enqueue_step(hpic_batch *b) {
     BCK(cudaEventRecord(b->ev[b->ev_used], b->stream));
   }
   hpic::launch_batch_push<R>(b->tg[0]->K, items, b->d, P, tab, b->sm_count, b->tune.blocks_per_sm,
-                             b->single, b->stream);
+                             b->single, b->stream, so);
   ++k;
   if (b->prof) {
     BCK(cudaEventRecord(b->ev[b->ev_used + 1], b->stream));
@@ -167,8 +182,9 @@ int enqueue_step(hpic_batch *b) {
     hpic::launch_batch_bheat<R>(items, b->d, gg, b->stream);
     ++k;
   }
+  if (sort) k += hpic::launch_batch_sort_finish<R>(items, b->d, b->stream);
   if (b->any_inject) {
-    hpic::launch_batch_inject<R>(items, b->d, P, b->sm_count * 2, b->stream);
+    hpic::launch_batch_inject<R>(items, b->d, Pnext, b->sm_count * 2, b->stream);
     ++k;
   }
   hpic::launch_batch_advance<R>(items, b->d, b->stream);
@@ -177,23 +193,11 @@ int enqueue_step(hpic_batch *b) {
   return k;
 }
 
-template <typename R>
-int enqueue_sort(hpic_batch *b) {
-  const auto *items = static_cast<const hpic::BatchItem<R> *>(b->items);
-  const int k = hpic::launch_batch_sort<R>(items, b->d, pview_all<R>(b, b->cur),
-                                           pview_all<R>(b, b->cur ^ 1), b->keys, b->counts,
-                                           b->partials, b->nkeys_total, grid_for(b, b->slots),
-                                           b->stream, hpic::sort_lead(b->tune.sort_interval));
-  BCK(cudaGetLastError());
-  return k;
-}
-
 int enqueue(hpic_batch *b, bool sort) {
-  if (sort) return b->fp32 ? enqueue_sort<float>(b) : enqueue_sort<double>(b);
-  return b->fp32 ? enqueue_step<float>(b) : enqueue_step<double>(b);
+  return b->fp32 ? enqueue_step<float>(b, sort) : enqueue_step<double>(b, sort);
 }
 
-// capture the step and the sort for both particle buffers
+// capture the plain step and the step that sorts, for both particle buffers
 int capture_graphs(hpic_batch *b) {
   if (b->gstep[0]) return HPIC_OK;
   const int keep = b->cur;
@@ -237,28 +241,19 @@ int run_steps(hpic_batch *b, long long nsteps) {
     if (rc) return rc;
   }
   for (long long s = 0; s < nsteps; ++s) {
+    const int si = b->tune.sort_interval;
+    const bool sort = si > 0 && (b->host_step + 1) % si == 0;
     if (graphs) {
-      BCK(cudaGraphLaunch(b->gstep[b->cur], b->stream));
-      b->launches += b->kstep;
+      BCK(cudaGraphLaunch((sort ? b->gsort : b->gstep)[b->cur], b->stream));
+      b->launches += sort ? b->ksort : b->kstep;
     } else {
-      const int k = enqueue(b, false);
+      const int k = enqueue(b, sort);
       if (k < 0) return k;
       b->launches += k;
     }
     b->host_step += 1;
     for (hpic_ctx *c : b->tg) c->host_step = b->host_step;
-    const int si = b->tune.sort_interval;
-    if (si > 0 && b->host_step % si == 0) {
-      if (graphs) {
-        BCK(cudaGraphLaunch(b->gsort[b->cur], b->stream));
-        b->launches += b->ksort;
-      } else {
-        const int k = enqueue(b, true);
-        if (k < 0) return k;
-        b->launches += k;
-      }
-      set_cur(b, b->cur ^ 1);
-    }
+    if (sort) set_cur(b, b->cur ^ 1);
   }
   return HPIC_OK;
 }
@@ -448,7 +443,7 @@ int hpic_batch_init(hpic_batch **out, int32_t n_targets, const hpic_target_desc 
   const size_t a_n = take((n_targets + 1) * sizeof(long long));
   const size_t a_k = take((n_targets + 1) * sizeof(long long));
   const size_t a_s0 = take(n_targets * sizeof(long long)), a_s1 = take(n_targets * sizeof(long long));
-  const size_t a_keys = take(slots * sizeof(uint32_t));
+  const size_t a_keys = take(2 * slots * sizeof(uint32_t));  // sort keys, then ranks
   const size_t a_cnts = take(b->nkeys_total * sizeof(uint32_t));
   const size_t a_part = take(hpic::scan_partials(b->nkeys_total) * sizeof(uint32_t));
   const size_t a_t64 = take(tab * sizeof(double)), a_t32 = take(tab * sizeof(float));

@@ -69,15 +69,17 @@ struct TargetHot {
   TallyView tv;
   long long off;  // first particle slot of the target
   long long step, n;  // the target's step and slot count
+  long long sshift;   // a sorting step: the target's first slot minus its first sorted offset
 };
 
-// MINB = the blocks per SM the launch asks for: the register budget follows
+// SORT: the step also sorts (so says where the electrons go; without it the
+// sorting code is compiled out).  MINB = the blocks per SM the launch asks for: the register budget follows
 // (5: 48 registers, 4: 64, 3: 80, 2: 128, 1: 255; the FP32 state spills a
 // little below 64), and the autotuner picks among the variants by timing them
-template <typename R, int MINB, int NS>
+template <typename R, int MINB, int NS, bool SORT>
 __global__ void __launch_bounds__(256, MINB)
 k_batch_push(const Consts Krun, const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
-             const R *__restrict__ tab) {
+             const R *__restrict__ tab, const SortOut<R> so) {
   __shared__ TargetHot<R> wc[kBatchWarps];  // each warp's current target
   // the warps' deposit stages, then n x kAccN tally sums, then the task prefix
   extern __shared__ __align__(16) double dyn[];
@@ -115,6 +117,7 @@ k_batch_push(const Consts Krun, const BatchItem<R> *__restrict__ items, BatchDev
       if (lane == 0) {
         it.grid = make_grid(src->h, src->g);
         it.off = src->off;
+        if constexpr (SORT) it.sshift = src->off - d.sstart[t];
         it.step = src->cnt->step;
         it.n = src->cnt->n;
       }
@@ -128,8 +131,9 @@ k_batch_push(const Consts Krun, const BatchItem<R> *__restrict__ items, BatchDev
     sc.key1 = Krun.key1;
     sc.target = it.h.target_index;
     const long long local = (w - wpref_s[t]) * 32 + lane;
-    push_warp<R, NS>(Krun, it.h, it.grid, tab, it.tv, sc, p, it.off + local,
-                    local < it.n, acc, tal_s + t * kAccN, stage, SortOut<R>{});
+    push_warp<R, NS, SORT>(Krun, it.h, it.grid, tab, it.tv, sc, p, it.off + local,
+                          local < it.n, acc, tal_s + t * kAccN, stage, SORT ? &so : nullptr,
+                          SORT ? &it.sshift : nullptr);
   }
   if (t >= 0) flush_acc(acc, tal_s + t * kAccN);
   __syncthreads();
@@ -210,7 +214,7 @@ __global__ void k_batch_advance(const BatchItem<R> *items, BatchDev d) {
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_batch_sort_keys(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
-                  uint32_t *keys, uint32_t *counts, R lead) {
+                  uint32_t *keys, uint32_t *ranks, uint32_t *counts, R lead) {
   const long long nslot = d.wpref[d.n] * 32;
   int t = 0;
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot;
@@ -237,7 +241,7 @@ k_batch_sort_keys(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p
       key = (uint32_t)d.kpref[t] + tile_key(i, j, k, it.K.nti, it.K.ntj);
     }
     keys[ip] = key;
-    agg_inc(counts, key);
+    ranks[ip] = agg_inc(counts, key);
   }
 }
 
@@ -249,34 +253,6 @@ __global__ void k_batch_sort_starts(const BatchItem<R> *items, BatchDev d, const
     const long long k0 = d.kpref[t];
     d.sstart[t] = offs[k0];
     d.snew[t] = (long long)offs[k0 + items[t].K.nkeys] - (long long)offs[k0];
-  }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(256)
-k_batch_sort_scatter(const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> src,
-                     PView<R> dst, const uint32_t *keys, uint32_t *offs) {
-  const long long nslot = d.wpref[d.n] * 32;
-  int t = 0;
-  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nslot;
-       s += (long long)gridDim.x * blockDim.x) {
-    t = forward_target(d.wpref, t, d.n, s >> 5);
-    const BatchItem<R> &it = items[t];
-    const long long local = s - d.wpref[t] * 32;
-    if (local >= it.cnt->n) continue;
-    const long long ip = it.off + local;
-    const uint32_t key = keys[ip];
-    if (key == (uint32_t)(d.kpref[t] + it.K.nkeys)) continue;  // dead
-    const long long q = it.off + (long long)agg_inc(offs, key) - d.sstart[t];
-    dst.x[q] = src.x[ip];
-    dst.y[q] = src.y[ip];
-    dst.z[q] = src.z[ip];
-    dst.ux[q] = src.ux[ip];
-    dst.uy[q] = src.uy[ip];
-    dst.uz[q] = src.uz[ip];
-    dst.tau[q] = src.tau[ip];
-    if (it.K.weighted) dst.w[q] = src.w[ip];
-    dst.id[q] = src.id[ip];
   }
 }
 
@@ -309,38 +285,51 @@ cudaError_t prepare_batch_push() {
   auto set = [&](const void *fn, int bytes) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, a, bytes);
   };
-  set((const void *)k_batch_push<float, 2, 1>, f);
-  set((const void *)k_batch_push<float, 3, 1>, f);
-  set((const void *)k_batch_push<float, 4, 1>, f);
-  set((const void *)k_batch_push<float, 5, 1>, f);
-  set((const void *)k_batch_push<float, 2, 4>, f);
-  set((const void *)k_batch_push<float, 3, 4>, f);
-  set((const void *)k_batch_push<float, 4, 4>, f);
-  set((const void *)k_batch_push<float, 5, 4>, f);
-  set((const void *)k_batch_push<double, 1, 1>, d);
-  set((const void *)k_batch_push<double, 2, 1>, d);
-  set((const void *)k_batch_push<double, 1, 4>, d);
-  set((const void *)k_batch_push<double, 2, 4>, d);
+  set((const void *)k_batch_push<float, 2, 1, false>, f);
+  set((const void *)k_batch_push<float, 2, 1, true>, f);
+  set((const void *)k_batch_push<float, 3, 1, false>, f);
+  set((const void *)k_batch_push<float, 3, 1, true>, f);
+  set((const void *)k_batch_push<float, 4, 1, false>, f);
+  set((const void *)k_batch_push<float, 4, 1, true>, f);
+  set((const void *)k_batch_push<float, 5, 1, false>, f);
+  set((const void *)k_batch_push<float, 5, 1, true>, f);
+  set((const void *)k_batch_push<float, 2, 4, false>, f);
+  set((const void *)k_batch_push<float, 2, 4, true>, f);
+  set((const void *)k_batch_push<float, 3, 4, false>, f);
+  set((const void *)k_batch_push<float, 3, 4, true>, f);
+  set((const void *)k_batch_push<float, 4, 4, false>, f);
+  set((const void *)k_batch_push<float, 4, 4, true>, f);
+  set((const void *)k_batch_push<float, 5, 4, false>, f);
+  set((const void *)k_batch_push<float, 5, 4, true>, f);
+  set((const void *)k_batch_push<double, 1, 1, false>, d);
+  set((const void *)k_batch_push<double, 1, 1, true>, d);
+  set((const void *)k_batch_push<double, 2, 1, false>, d);
+  set((const void *)k_batch_push<double, 2, 1, true>, d);
+  set((const void *)k_batch_push<double, 1, 4, false>, d);
+  set((const void *)k_batch_push<double, 1, 4, true>, d);
+  set((const void *)k_batch_push<double, 2, 4, false>, d);
+  set((const void *)k_batch_push<double, 2, 4, true>, d);
   return e;
 }
 
-template <typename R, int NS>
+template <typename R, int NS, bool SORT>
 void launch_batch_push_ns(const Consts &Krun, const BatchItem<R> *items, BatchDev d, PView<R> p,
-                          const R *table, int grid, int blocks_per_sm, size_t sm, cudaStream_t st) {
+                          const R *table, int grid, int blocks_per_sm, size_t sm, cudaStream_t st,
+                          const SortOut<R> &so) {
   if constexpr (sizeof(R) == 8) {  // FP64: one or two blocks per SM
     if (blocks_per_sm <= 1)
-      k_batch_push<R, 1, NS><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
+      k_batch_push<R, 1, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
     else
-      k_batch_push<R, 2, NS><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
+      k_batch_push<R, 2, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
   } else {  // FP32: two to five (one runs the two-block code)
     if (blocks_per_sm <= 2)
-      k_batch_push<R, 2, NS><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
+      k_batch_push<R, 2, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
     else if (blocks_per_sm == 3)
-      k_batch_push<R, 3, NS><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
+      k_batch_push<R, 3, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
     else if (blocks_per_sm == 4)
-      k_batch_push<R, 4, NS><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
+      k_batch_push<R, 4, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
     else
-      k_batch_push<R, 5, NS><<<grid, 256, sm, st>>>(Krun, items, d, p, table);
+      k_batch_push<R, 5, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
   }
 }
 
@@ -348,14 +337,19 @@ void launch_batch_push_ns(const Consts &Krun, const BatchItem<R> *items, BatchDe
 template <typename R>
 void launch_batch_push(const Consts &Krun, const BatchItem<R> *items, BatchDev d, PView<R> p,
                        const R *table, int sm_count, int blocks_per_sm, bool single,
-                       cudaStream_t st) {
+                       cudaStream_t st, const SortOut<R> &so) {
   const size_t sm = batch_stage_bytes<R>() + (size_t)d.n * kAccN * sizeof(double) +
                     (d.n + 1) * sizeof(long long);
   const int grid = sm_count * blocks_per_sm;
-  if (single)
-    launch_batch_push_ns<R, 1>(Krun, items, d, p, table, grid, blocks_per_sm, sm, st);
+  const bool sort = so.dst.x != nullptr;
+  if (single && sort)
+    launch_batch_push_ns<R, 1, true>(Krun, items, d, p, table, grid, blocks_per_sm, sm, st, so);
+  else if (single)
+    launch_batch_push_ns<R, 1, false>(Krun, items, d, p, table, grid, blocks_per_sm, sm, st, so);
+  else if (sort)
+    launch_batch_push_ns<R, 4, true>(Krun, items, d, p, table, grid, blocks_per_sm, sm, st, so);
   else
-    launch_batch_push_ns<R, 4>(Krun, items, d, p, table, grid, blocks_per_sm, sm, st);
+    launch_batch_push_ns<R, 4, false>(Krun, items, d, p, table, grid, blocks_per_sm, sm, st, so);
 }
 
 template <typename R>
@@ -371,29 +365,34 @@ void launch_batch_advance(const BatchItem<R> *items, BatchDev d, cudaStream_t st
 }
 
 template <typename R>
-int launch_batch_sort(const BatchItem<R> *items, BatchDev d, PView<R> src, PView<R> dst,
-                      uint32_t *keys, uint32_t *counts, uint32_t *partials, long long nkeys_total,
-                      int grid, cudaStream_t st, double lead) {
-  k_batch_plan<R><<<1, 256, 0, st>>>(items, d);  // tasks from the current counts
+int launch_batch_sort_keys(const BatchItem<R> *items, BatchDev d, PView<R> p, uint32_t *keys,
+                           uint32_t *ranks, uint32_t *counts, uint32_t *partials,
+                           long long nkeys_total, int grid, cudaStream_t st, double lead) {
   cudaMemsetAsync(counts, 0, nkeys_total * sizeof(uint32_t), st);
-  k_batch_sort_keys<R><<<grid, 256, 0, st>>>(items, d, src, keys, counts, R(lead));
-  int launches = 2 + launch_scan(counts, nkeys_total, partials, st);
+  k_batch_sort_keys<R><<<grid, 256, 0, st>>>(items, d, p, keys, ranks, counts, R(lead));
+  const int launches = 1 + launch_scan(counts, nkeys_total, partials, st);
   k_batch_sort_starts<R><<<1, 256, 0, st>>>(items, d, counts);
-  k_batch_sort_scatter<R><<<grid, 256, 0, st>>>(items, d, src, dst, keys, counts);
+  return launches + 1;
+}
+
+template <typename R>
+int launch_batch_sort_finish(const BatchItem<R> *items, BatchDev d, cudaStream_t st) {
   k_batch_sort_finish<R><<<1, 256, 0, st>>>(items, d);
-  return launches + 3;
+  return 1;
 }
 
 #define HPIC_INST(R)                                                                            \
   template void launch_batch_plan<R>(const BatchItem<R> *, BatchDev, cudaStream_t);             \
   template void launch_batch_push<R>(const Consts &, const BatchItem<R> *, BatchDev, PView<R>,  \
-                                     const R *, int, int, bool, cudaStream_t);                  \
+                                     const R *, int, int, bool, cudaStream_t,                   \
+                                     const SortOut<R> &);                                       \
   template void launch_batch_inject<R>(const BatchItem<R> *, BatchDev, PView<R>, int,           \
                                        cudaStream_t);                                           \
   template void launch_batch_advance<R>(const BatchItem<R> *, BatchDev, cudaStream_t);          \
-  template int launch_batch_sort<R>(const BatchItem<R> *, BatchDev, PView<R>, PView<R>,         \
-                                    uint32_t *, uint32_t *, uint32_t *, long long, int,         \
-                                    cudaStream_t, double);
+  template int launch_batch_sort_keys<R>(const BatchItem<R> *, BatchDev, PView<R>, uint32_t *, \
+                                         uint32_t *, uint32_t *, uint32_t *, long long, int,    \
+                                         cudaStream_t, double);                                 \
+  template int launch_batch_sort_finish<R>(const BatchItem<R> *, BatchDev, cudaStream_t);
 HPIC_INST(float)
 HPIC_INST(double)
 #undef HPIC_INST

@@ -125,11 +125,12 @@ void launch_fill(R *dst, long long n, R v, int grid, cudaStream_t st);
 cudaError_t prepare_push();
 cudaError_t prepare_batch_push();
 // Where a step that also sorts writes its electrons: an electron live at
-// the start of the step goes to slot offsets[key] + rank of dst, where the
-// counting sort's key pass ran on that start-of-step state (key and rank
-// of each slot) and its scan turned the counts into offsets; one that is
-// absorbed or escapes leaves its slot there marked dead.  dst.x == nullptr:
-// the electrons stay in their slots.
+// the start of the step goes to slot offsets[key] + rank (+ a shift: 0 for
+// one target; a batch target's first slot minus its first offset) of dst,
+// where the counting sort's key pass ran on that start-of-step state (key
+// and rank of each slot) and its scan turned the counts into offsets; one
+// that is absorbed or escapes leaves its slot there marked dead.
+// dst.x == nullptr: the electrons stay in their slots.
 template <typename R>
 struct SortOut {
   PView<R> dst;
@@ -218,7 +219,7 @@ void launch_batch_plan(const BatchItem<R> *items, BatchDev d, cudaStream_t st);
 template <typename R>
 void launch_batch_push(const Consts &Krun, const BatchItem<R> *items, BatchDev d, PView<R> p,
                        const R *table, int sm_count, int blocks_per_sm, bool single,
-                       cudaStream_t st);
+                       cudaStream_t st, const SortOut<R> &so);
 template <typename R>
 void launch_batch_inject(const BatchItem<R> *items, BatchDev d, PView<R> p, int grid,
                          cudaStream_t st);
@@ -228,11 +229,17 @@ template <typename R>
 void launch_batch_efield(const BatchItem<R> *items, BatchDev d, int grid, cudaStream_t st);
 template <typename R>
 void launch_batch_bheat(const BatchItem<R> *items, BatchDev d, int grid, cudaStream_t st);
-// cell sort of every target inside its own slots; returns launches made
+// the cell sort of every target inside its own slots, folded into a step as
+// for one target: keys, ranks and scan over the targets' concatenated key
+// ranges, each target's first offset and kept slots (the step's plan must
+// have run), then the push writes each electron to its sorted slot and the
+// finish sets each target's slot count; return launches made
 template <typename R>
-int launch_batch_sort(const BatchItem<R> *items, BatchDev d, PView<R> src, PView<R> dst,
-                      uint32_t *keys, uint32_t *counts, uint32_t *partials, long long nkeys_total,
-                      int grid, cudaStream_t st, double lead);
+int launch_batch_sort_keys(const BatchItem<R> *items, BatchDev d, PView<R> p, uint32_t *keys,
+                           uint32_t *ranks, uint32_t *counts, uint32_t *partials,
+                           long long nkeys_total, int grid, cudaStream_t st, double lead);
+template <typename R>
+int launch_batch_sort_finish(const BatchItem<R> *items, BatchDev d, cudaStream_t st);
 // counts summed per block of the scan; the partials scratch of a scan of m
 // counts holds scan_partials(m) words
 constexpr long long kScanTile = 4096;

@@ -22,7 +22,9 @@
 
 namespace hpic {
 
-template <typename R, int NS>
+// SORT: the step also sorts (so says where the electrons go; without it the
+// sorting code is compiled out).
+template <typename R, int NS, bool SORT>
 // FP32: five 256-thread blocks per SM (48 registers, a few spills to L1),
 // launched as one persistent wave: the kernel is issue- and latency-bound
 // and gains from the warps (three blocks at 80 registers were 14 % slower,
@@ -45,13 +47,15 @@ k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__rest
 
   const Grid<R> g = make_grid(h, gv);
   Acc<R> acc;
+  const long long no_shift = 0;  // one target: the sorted slot is offset + rank
 
   // warp-uniform loop: every lane reaches the warp-cooperative deposits
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); base < n;
        base += stride)
-    push_warp<R, NS>(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc, rare, stage, so);
+    push_warp<R, NS, SORT>(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc, rare,
+                           stage, SORT ? &so : nullptr, SORT ? &no_shift : nullptr);
 
   double v[kAccN];
   acc.values(v);
@@ -214,27 +218,36 @@ template <typename R>
 constexpr size_t push_stage_bytes() { return (kPushThreads / 32) * dep_words<R>() * sizeof(R); }
 
 cudaError_t prepare_push() {
-  cudaError_t e = cudaFuncSetAttribute(k_push<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)push_stage_bytes<float>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_push<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)push_stage_bytes<float>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_push<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)push_stage_bytes<double>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_push<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)push_stage_bytes<double>());
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void *fn, size_t bytes) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  set((const void *)k_push<float, 1, false>, push_stage_bytes<float>());
+  set((const void *)k_push<float, 1, true>, push_stage_bytes<float>());
+  set((const void *)k_push<float, 4, false>, push_stage_bytes<float>());
+  set((const void *)k_push<float, 4, true>, push_stage_bytes<float>());
+  set((const void *)k_push<double, 1, false>, push_stage_bytes<double>());
+  set((const void *)k_push<double, 1, true>, push_stage_bytes<double>());
+  set((const void *)k_push<double, 4, false>, push_stage_bytes<double>());
+  set((const void *)k_push<double, 4, true>, push_stage_bytes<double>());
   return e;
 }
 
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
                  TallyView tv, int grid, cudaStream_t st, const SortOut<R> &so) {
-  if (K.n_solids == 1)  // a single-element solid: the element loops vanish
-    k_push<R, 1><<<grid, kPushThreads, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv, so);
+  const HotK<R> h = make_hot<R>(K);
+  const size_t sm = push_stage_bytes<R>();
+  const bool sort = so.dst.x != nullptr;
+  if (K.n_solids == 1 && sort)  // a single-element solid: the element loops vanish
+    k_push<R, 1, true><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so);
+  else if (K.n_solids == 1)
+    k_push<R, 1, false><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so);
+  else if (sort)
+    k_push<R, 4, true><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so);
   else
-    k_push<R, 4><<<grid, kPushThreads, push_stage_bytes<R>(), st>>>(K, make_hot<R>(K), p, g, table, cnt, tv, so);
+    k_push<R, 4, false><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so);
 }
 
 template <typename R>

@@ -690,14 +690,16 @@ __device__ __forceinline__ void st_stream(R *p, R v) { __stcs(p, v); }
 // in_range false: nothing there) through the step, then deposit their
 // current and drag heat together through the warp's shared-memory stage
 // (dep_words<R>() elements, 16-byte aligned).  Every lane of the warp must
-// call it.
-template <typename R, int NS>
+// call it.  SORT: the step also sorts, and *so (with *shift: see SortOut; read
+// only then, so it may stay in shared memory) says where the electrons go;
+// both may be null otherwise.
+template <typename R, int NS, bool SORT>
 __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, const Grid<R> &g,
                                           const R *__restrict__ tab, const TallyView &tv,
                                           const StepCtx &sc, const PView<R> &p, long long ip,
                                           bool in_range, Acc<R> &acc, double *rare,
-                                          R *__restrict__ stage, const SortOut<R> &so) {
-  const bool sorting = so.dst.x != nullptr;  // uniform over the launch
+                                          R *__restrict__ stage, const SortOut<R> *so,
+                                          const long long *shift) {
   bool live = false, dep = false;
   uint32_t id = kDead;
   R X = 0, Y = 0, Zc = 0, ux = 0, uy = 0, uz = 0, tau = 0, heat = 0, w = h.w;
@@ -713,8 +715,8 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
           isfinite(uz) && isfinite(tau)) {
         live = true;
       } else {
-        if (sorting)
-          so.dst.id[(long long)so.offsets[so.keys[ip]] + so.ranks[ip]] = kDead;
+        if constexpr (SORT)
+          so->dst.id[(long long)so->offsets[so->keys[ip]] + so->ranks[ip] + *shift] = kDead;
         else
           p.id[ip] = kDead;
         atomicAdd(rare + A_N_NF, 1.0);
@@ -725,16 +727,18 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
     ++acc.n_steps;
     dep = advance<R, NS>(K, h, g, tab, tv, sc, id, w, X, Y, Zc, ux, uy, uz, tau, acc, rare, heat,
                          heat_cell);
-    if (sorting) {  // loaded here so that no register holds them through the step
-      const long long q = (long long)so.offsets[ld_stream(so.keys + ip)] + ld_stream(so.ranks + ip);
+    if constexpr (SORT) {  // loaded here so that no register holds them through the step
+      const long long q =
+          (long long)so->offsets[ld_stream(so->keys + ip)] + ld_stream(so->ranks + ip) + *shift;
+      const PView<R> &o = so->dst;
       if (dep) {
-        st_stream(so.dst.x + q, X); st_stream(so.dst.y + q, Y); st_stream(so.dst.z + q, Zc);
-        st_stream(so.dst.ux + q, ux); st_stream(so.dst.uy + q, uy); st_stream(so.dst.uz + q, uz);
-        st_stream(so.dst.tau + q, tau);
-        if (K.weighted) st_stream(so.dst.w + q, w);
-        so.dst.id[q] = id;
+        st_stream(o.x + q, X); st_stream(o.y + q, Y); st_stream(o.z + q, Zc);
+        st_stream(o.ux + q, ux); st_stream(o.uy + q, uy); st_stream(o.uz + q, uz);
+        st_stream(o.tau + q, tau);
+        if (K.weighted) st_stream(o.w + q, w);
+        o.id[q] = id;
       } else {
-        so.dst.id[q] = kDead;
+        o.id[q] = kDead;
       }
     } else if (dep) {
       st_stream(p.x + ip, X); st_stream(p.y + ip, Y); st_stream(p.z + ip, Zc);

@@ -49,7 +49,7 @@ NCU_DRAM_BYTES_PER_PSTEP = {"fp32": {"plain": 55.9, "sort": 91.6}, "fp64": None}
 # the same for k_batch_push, captured on the first 16 targets of the scan
 # (the full scan holds too much device memory for a multi-pass capture): the traffic is the
 # electron state streamed once, so it scales with the particle-steps
-NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": 60.8, "fp64": None}
+NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": {"plain": 61.0, "sort": 93.1}, "fp64": None}
 # FP64 FLOP per particle-step of the FP64 k_push (2 per DFMA, 1 per DADD and
 # DMUL; ncu thread-level counts on config 1 in FP64, launches at steps 110
 # and 111) and the FP64 rate the GB300 is stated to have (TFLOP/s)
@@ -64,24 +64,30 @@ ACCURACY_STEPS = 2200
 SORT_INTERVAL = 3
 
 
-def n_sort_steps(step0: int, steps: int) -> int:
+def n_sort_steps(step0: int, steps: int, interval: int = SORT_INTERVAL) -> int:
     """Steps of [step0, step0 + steps) that also sort."""
-    return sum(1 for s in range(step0, step0 + steps) if (s + 1) % SORT_INTERVAL == 0)
+    if interval <= 0:
+        return 0
+    return sum(1 for s in range(step0, step0 + steps) if (s + 1) % interval == 0)
 
 
-def push_bytes(precision: str, k_ps: float, k_launches: int, step0: int, steps: int) -> float:
+def push_bytes(precision: str, k_ps: float, k_launches: int, step0: int, steps: int,
+               interval: int = SORT_INTERVAL) -> float:
     """Algorithmic bytes of the push launches of steps [step0, step0 + steps)."""
-    n_sort = n_sort_steps(step0, steps)
+    n_sort = n_sort_steps(step0, steps, interval)
     return ALG_BYTES[precision] * k_ps + SORT_STEP_EXTRA_BYTES * n_sort * k_ps / max(k_launches, 1)
 
 
-def push_traffic(precision: str, k_ps: float, k_launches: int, step0: int, steps: int):
+def push_traffic(table: dict, precision: str, k_ps: float, k_launches: int, step0: int,
+                 steps: int, interval: int = SORT_INTERVAL):
     """ncu DRAM bytes per push launch of those steps, from the per-particle-step
     figures of a plain and a sort step."""
-    tb = NCU_DRAM_BYTES_PER_PSTEP[precision]
+    tb = table[precision]
     if not tb or k_launches <= 0:
         return None
-    n_sort = n_sort_steps(step0, steps)
+    n_sort = n_sort_steps(step0, steps, interval)
+    if n_sort and tb.get("sort") is None:
+        return None
     per_ps = (tb["plain"] * (k_launches - n_sort) + tb["sort"] * n_sort) / k_launches
     return per_ps * k_ps / k_launches
 
@@ -406,7 +412,8 @@ def run_gpu(args, world, rank, local):
     achieved = k_bytes / max(k_launches, 1) / (k_avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"],
-                "traffic": push_traffic(args.precision, k_ps, k_launches, int(snap_clock[0]), args.steps),
+                "traffic": push_traffic(NCU_DRAM_BYTES_PER_PSTEP, args.precision, k_ps, k_launches,
+                                        int(snap_clock[0]), args.steps),
                 "traffic_unit": "bytes per launch (ncu dram read+write, scaled by particle-steps)",
                 "kernel": "k_push (push/collide/emit/deposit)",
                 "kernel_ms_avg": k_avg_ms, "kernel_share_of_step": k_ms / ms if ms > 0 else None,
@@ -685,12 +692,15 @@ def batch_result(n_targets: int, warm: int, steps: int, precision: str = "fp32",
     ps1 = sum(b.target(t).tallies()["particle_steps"] for t in range(len(b)))
     value, ms_max, _ = replica_rate(world, ms, ps1 - ps0)
     # the particle kernel alone, from direct launches bracketed by events
+    step0 = int(b.target(0).clock()[0])
     hpic.hpic_batch_profile(b.b, True)
     b.step(40)
     km, kl, kp = hpic.hpic_batch_kernel_time(b.b)
     hpic.hpic_batch_profile(b.b, False)
     pk = peaks()
-    achieved = ALG_BYTES[precision] * (kp / kl) / (km / kl / 1e3) / 1e9
+    si = int(tune["sort_interval"])
+    kbytes = push_bytes(precision, kp, kl, step0, 40, si)
+    achieved = kbytes / kl / (km / kl / 1e3) / 1e9
     ce, tot = [], {"E_xray_above": 0.0, "E_injected": 0.0}
     for t in range(len(b)):
         T = b.target(t).tallies()
@@ -712,11 +722,12 @@ def batch_result(n_targets: int, warm: int, steps: int, precision: str = "fp32",
                                     f"{sum(l['n_macro'] for l in cfg['lasers']):.3g} e- in all "
                                     "(1e5..4e6 per target)"),
                        "live_electrons_at_start": live, "tuning": tune,
-                       "graphs": "step and sort replayed from captured CUDA graphs"},
+                       "graphs": "plain and sorting steps replayed from captured CUDA graphs"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / pk["hbm_gbs"],
-                         "traffic": (NCU_BATCH_DRAM_BYTES_PER_PSTEP[precision] * kp / kl
-                                     if NCU_BATCH_DRAM_BYTES_PER_PSTEP[precision] else None),
+                         "traffic": push_traffic(NCU_BATCH_DRAM_BYTES_PER_PSTEP, precision, kp, kl,
+                                                 step0, 40, si),
+                         "bytes_per_particle_step": kbytes / kp if kp > 0 else None,
                          "traffic_unit": "bytes per launch (ncu dram read+write on 16 targets, "
                                          "scaled by particle-steps)",
                          "kernel": "k_batch_push", "kernel_ms_avg": km / kl,

@@ -418,7 +418,7 @@ int hpic_batch_set_tuning(hpic_batch *b, const hpic_batch_tuning *in);
 /* Autotuner: from a snapshot of the whole batch state, time trial_steps
  * steps (>= 1, rounded up to a multiple of 40) for every candidate
  * (blocks_per_sm 2..5 in FP32, 1..2 in FP64, x sort_interval in
- * {5, 10, 20, 40}, graphs on), restore the snapshot after each trial, and
+ * {3, 5, 10, 20}, graphs on), restore the snapshot after each trial, and
  * keep the fastest.  The simulation is left exactly where it was.  Needs
  * device memory for one copy of the batch state; the result is written to
  * *out when out is not NULL. */

@@ -22,7 +22,7 @@ thread_local std::string g_batch_error;
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
-constexpr int kSortChoices[4] = {5, 10, 20, 40};
+constexpr int kSortChoices[4] = {3, 5, 10, 20};
 constexpr int kTrialPeriod = 40;  // every sort interval tried divides it
 
 }  // namespace

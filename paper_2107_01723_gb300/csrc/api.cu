@@ -61,6 +61,14 @@ long long injection_total(const hpic_ctx *c) {
   return c->K.n_macro;
 }
 
+// one resident wave of the field and heating kernels (or fewer blocks)
+int field_blocks(const hpic_ctx *c, long long nodes) {
+  const long long want = (nodes + 255) / 256;
+  const long long cap = (long long)c->sm_count * hpic::kFieldBlocksPerSm;
+  long long g = want < cap ? want : cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
 int grid_blocks(const hpic_ctx *c, long long work) {
   const long long want = (work + 255) / 256;
   const long long cap = (long long)c->sm_count * 8;
@@ -422,7 +430,7 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
   const R *tab = ctx->fp32 ? reinterpret_cast<const R *>(ctx->t32)
                            : reinterpret_cast<const R *>(ctx->t64);
   const int gp = grid_blocks(ctx, ctx->cap);
-  const int gg = grid_blocks(ctx, ctx->K.nvec);
+  const int gg = field_blocks(ctx, ctx->K.nvec);
   const bool grid_on = !(ctx->K.physics & hpic::P_UNBOUNDED);
   for (long long s = 0; s < nsteps; ++s) {
     if (grid_on) {

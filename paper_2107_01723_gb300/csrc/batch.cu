@@ -137,7 +137,8 @@ int enqueue_step(hpic_batch *b, bool sort) {
   const hpic::PView<R> Pnext = sort ? pview_all<R>(b, b->cur ^ 1) : P;
   const R *tab = b->fp32 ? reinterpret_cast<const R *>(b->t32) : reinterpret_cast<const R *>(b->t64);
   const bool grid_on = !(b->run.physics & HPIC_UNBOUNDED);
-  const int gg = grid_for(b, b->nodes_total);
+  const int gg = (int)std::min<long long>((b->nodes_total + 255) / 256,
+                                          (long long)b->sm_count * hpic::kBatchFieldBlocksPerSm);
   int k = 0;
   if (grid_on) {
     BCK(cudaMemsetAsync(b->jall, 0, b->jall_bytes, b->stream));

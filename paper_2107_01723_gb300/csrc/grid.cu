@@ -13,14 +13,14 @@
 namespace hpic {
 
 template <typename R>
-__global__ void __launch_bounds__(256, 6) k_efield(const Consts K, GView<R> g) {
+__global__ void __launch_bounds__(256, kFieldBlocksPerSm) k_efield(const Consts K, GView<R> g) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < K.nvec;
        q += (long long)gridDim.x * blockDim.x)
     efield_node(K, g, q);
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256, 6) k_bheat(const Consts K, GView<R> g, TallyView tv) {
+__global__ void __launch_bounds__(256, kFieldBlocksPerSm) k_bheat(const Consts K, GView<R> g, TallyView tv) {
   __shared__ double smem[32];
   double e_ohm = 0.0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < K.nvec;
@@ -41,7 +41,8 @@ __device__ __forceinline__ int advance_target(const long long *pref, int t, int 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_batch_efield(const BatchItem<R> *items, BatchDev d) {
+__global__ void __launch_bounds__(256, kBatchFieldBlocksPerSm)
+k_batch_efield(const BatchItem<R> *items, BatchDev d) {
   extern __shared__ long long npref_s[];
   for (int t = threadIdx.x; t <= d.n; t += blockDim.x) npref_s[t] = d.npref[t];
   __syncthreads();
@@ -55,7 +56,8 @@ __global__ void __launch_bounds__(256) k_batch_efield(const BatchItem<R> *items,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_batch_bheat(const BatchItem<R> *items, BatchDev d) {
+__global__ void __launch_bounds__(256, kBatchFieldBlocksPerSm)
+k_batch_bheat(const BatchItem<R> *items, BatchDev d) {
   extern __shared__ long long npref_s[];
   double *ohm_s = reinterpret_cast<double *>(npref_s + d.n + 1);
   for (int t = threadIdx.x; t <= d.n; t += blockDim.x) npref_s[t] = d.npref[t];

@@ -104,6 +104,11 @@ constexpr int push_blocks_per_sm() { return sizeof(R) == 4 ? 5 : 2; }
 // threads per block of the single-target particle kernel (a warp-sized
 // deposit stage per warp)
 constexpr int kPushThreads = 256;
+// resident 256-thread blocks per SM of the field and heating kernels (their
+// launch bounds); they are launched as one wave of sm_count times this many
+// blocks (grid-stride over the nodes), so no partial second wave trails
+constexpr int kFieldBlocksPerSm = 6;
+constexpr int kBatchFieldBlocksPerSm = 5;
 
 // host transfers of the electron state (the C-ABI's read and load calls):
 // live-slot compaction in storage order and FP64 <-> R conversion on the device

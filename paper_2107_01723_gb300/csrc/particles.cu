@@ -10,6 +10,8 @@
 //   bremsstrahlung by optical depth + photon tally   App. B
 //   x^{n+1} = x^n + v dt, then escape/reflux         Sec. II.A
 //   current deposit at x^{n+1}                       j_h of Eq. (A2)
+// On a step that also sorts (SORT) the new state goes to the electron's slot
+// of the sorted order in the other buffer instead of its own slot.
 // Random numbers: Philox4x32-10, counter (step, id, block, target), key = seed;
 // block 0 scatter, 1 emission, 2..4 reflux on x/y/z faces, 8-9 injection.
 //

@@ -37,15 +37,18 @@ WORKLOAD = ("128^3 cells x 1 um Au (Z=79, n_i=5.9e28 m^-3, T0=1 eV), 1e7 e- inje
 # read once (x,y,z,ux,uy,uz,tau + u32 id) and written once (7 reals)
 ALG_BYTES = {"fp32": 7 * 4 + 4 + 7 * 4, "fp64": 7 * 8 + 4 + 7 * 8}
 # a step that also sorts (every SORT_INTERVAL steps) reads each slot's sort key
-# and rank and writes its id to the sorted slot: 12 B more per particle-step
+# and rank and writes its id to the sorted slot: 12 B more per particle-step;
+# in the single-target step, the step before it (when it injects nothing)
+# writes each surviving electron's key and rank: 8 B more
 SORT_STEP_EXTRA_BYTES = 4 + 4 + 4
+KEY_STEP_EXTRA_BYTES = 4 + 4
 # DRAM bytes (read + write) per particle-step of k_push measured by ncu on
 # this workload (dram__bytes_read.sum + dram__bytes_write.sum of one launch
-# over its particle-steps; launches 204-205 plain, 206 a sort step): a plain
-# step streams the state once (absorbed slots are not rewritten), a sort step
-# adds key and rank and scatters its stores (partial sectors); None where not
-# captured
-NCU_DRAM_BYTES_PER_PSTEP = {"fp32": {"plain": 55.9, "sort": 91.6}, "fp64": None}
+# over its particle-steps; launch 204 a plain step, 205 a keying step, 206 a
+# sorting step): a plain step streams the state once (absorbed slots are not
+# rewritten), a keying step adds the keys and ranks it writes, a sorting step
+# reads them and scatters its stores (partial sectors); None where not captured
+NCU_DRAM_BYTES_PER_PSTEP = {"fp32": {"plain": 56.1, "key": 64.3, "sort": 80.6}, "fp64": None}
 # the same for k_batch_push, captured on the first 16 targets of the scan
 # (the full scan holds too much device memory for a multi-pass capture): the traffic is the
 # electron state streamed once, so it scales with the particle-steps
@@ -71,24 +74,38 @@ def n_sort_steps(step0: int, steps: int, interval: int = SORT_INTERVAL) -> int:
     return sum(1 for s in range(step0, step0 + steps) if (s + 1) % interval == 0)
 
 
+def n_key_steps(step0: int, steps: int, interval: int = SORT_INTERVAL) -> int:
+    """Steps of [step0, step0 + steps) whose push keys the next sort (single
+    target, past the injection window)."""
+    if interval < 2:
+        return 0
+    return sum(1 for s in range(step0, step0 + steps) if (s + 2) % interval == 0)
+
+
 def push_bytes(precision: str, k_ps: float, k_launches: int, step0: int, steps: int,
-               interval: int = SORT_INTERVAL) -> float:
-    """Algorithmic bytes of the push launches of steps [step0, step0 + steps)."""
+               interval: int = SORT_INTERVAL, keyed: bool = True) -> float:
+    """Algorithmic bytes of the push launches of steps [step0, step0 + steps)
+    (keyed: the pushes of the steps before a sort compute its keys)."""
     n_sort = n_sort_steps(step0, steps, interval)
-    return ALG_BYTES[precision] * k_ps + SORT_STEP_EXTRA_BYTES * n_sort * k_ps / max(k_launches, 1)
+    n_key = n_key_steps(step0, steps, interval) if keyed else 0
+    per_launch = k_ps / max(k_launches, 1)
+    return (ALG_BYTES[precision] * k_ps + SORT_STEP_EXTRA_BYTES * n_sort * per_launch
+            + KEY_STEP_EXTRA_BYTES * n_key * per_launch)
 
 
 def push_traffic(table: dict, precision: str, k_ps: float, k_launches: int, step0: int,
-                 steps: int, interval: int = SORT_INTERVAL):
+                 steps: int, interval: int = SORT_INTERVAL, keyed: bool = True):
     """ncu DRAM bytes per push launch of those steps, from the per-particle-step
-    figures of a plain and a sort step."""
+    figures of a plain, a keying (keyed) and a sorting step."""
     tb = table[precision]
     if not tb or k_launches <= 0:
         return None
     n_sort = n_sort_steps(step0, steps, interval)
-    if n_sort and tb.get("sort") is None:
+    n_key = n_key_steps(step0, steps, interval) if keyed else 0
+    if (n_sort and tb.get("sort") is None) or (n_key and tb.get("key") is None):
         return None
-    per_ps = (tb["plain"] * (k_launches - n_sort) + tb["sort"] * n_sort) / k_launches
+    per_ps = (tb["plain"] * (k_launches - n_sort - n_key) + tb["sort"] * n_sort
+              + (tb["key"] * n_key if n_key else 0.0)) / k_launches
     return per_ps * k_ps / k_launches
 
 
@@ -699,7 +716,7 @@ def batch_result(n_targets: int, warm: int, steps: int, precision: str = "fp32",
     hpic.hpic_batch_profile(b.b, False)
     pk = peaks()
     si = int(tune["sort_interval"])
-    kbytes = push_bytes(precision, kp, kl, step0, 40, si)
+    kbytes = push_bytes(precision, kp, kl, step0, 40, si, keyed=False)
     achieved = kbytes / kl / (km / kl / 1e3) / 1e9
     ce, tot = [], {"E_xray_above": 0.0, "E_injected": 0.0}
     for t in range(len(b)):
@@ -726,7 +743,7 @@ def batch_result(n_targets: int, warm: int, steps: int, precision: str = "fp32",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / pk["hbm_gbs"],
                          "traffic": push_traffic(NCU_BATCH_DRAM_BYTES_PER_PSTEP, precision, kp, kl,
-                                                 step0, 40, si),
+                                                 step0, 40, si, keyed=False),
                          "bytes_per_particle_step": kbytes / kp if kp > 0 else None,
                          "traffic_unit": "bytes per launch (ncu dram read+write on 16 targets, "
                                          "scaled by particle-steps)",

@@ -95,6 +95,7 @@ int write_counters(hpic_ctx *ctx, const hpic::Counters *h) {
 // grow particle storage to hold `need` slots, keeping the first n
 int reserve(hpic_ctx *ctx, long long need) {
   if (need <= ctx->cap) return HPIC_OK;
+  ctx->keys_step = -1;  // the key buffers are reallocated
   if (ctx->owner) return fail(ctx, HPIC_ENOMEM, "more particles than the target's slots in the batch");
   hpic::Counters h;
   int rc = read_counters(ctx, &h);
@@ -439,20 +440,38 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
     }
     // every sort_interval steps the cell sort rides on the step: its keys
     // come from the start-of-step state one step further ahead, and the push
-    // writes each electron to its sorted slot in the other buffer
+    // writes each electron to its sorted slot in the other buffer.  The keys,
+    // ranks and counts are computed by the push of the step before when that
+    // step injects nothing (the new electrons would need keys too), else by a
+    // key pass at the start of the sorting step.
     const int si = ctx->run.sort_interval;
     const bool sort_now = si > 0 && (ctx->host_step + 1) % si == 0 && ctx->keys;
+    const bool inject_now =
+        ctx->have_laser && ctx->host_step < ctx->K.n_inj_steps && injection_total(ctx) > 0;
+    const bool keys_now = si >= 2 && (ctx->host_step + 2) % si == 0 && ctx->keys && !inject_now;
+    uint32_t *ranks = ctx->keys ? ctx->keys + ctx->cap : nullptr;
     hpic::SortOut<R> so{};
+    hpic::KeyOut<R> ko{};
     if (sort_now) {
-      uint32_t *ranks = ctx->keys + ctx->cap;
-      ctx->launches += hpic::launch_sort_keys<R>(ctx->K, P(ctx->cur), ctx->cnt, ctx->keys, ranks,
-                                                 ctx->counts, ctx->partials, gp, ctx->stream,
-                                                 hpic::sort_lead(si) + 1.0);
+      if (ctx->keys_step == ctx->host_step) {
+        ctx->launches += hpic::launch_scan(ctx->counts, ctx->K.nkeys + 1, ctx->partials, ctx->stream);
+      } else {
+        ctx->launches += hpic::launch_sort_keys<R>(ctx->K, P(ctx->cur), ctx->cnt, ctx->keys, ranks,
+                                                   ctx->counts, ctx->partials, gp, ctx->stream,
+                                                   hpic::sort_lead(si) + 1.0);
+      }
       so.dst = P(ctx->cur ^ 1);
       so.keys = ctx->keys;
       so.ranks = ranks;
       so.offsets = ctx->counts;
+    } else if (keys_now) {
+      CK(cudaMemsetAsync(ctx->counts, 0, (ctx->K.nkeys + 1) * sizeof(uint32_t), ctx->stream));
+      ko.keys = ctx->keys;
+      ko.ranks = ranks;
+      ko.counts = ctx->counts;
+      ko.lead = R((hpic::sort_lead(si) + 1.0) * ctx->K.cdt_dx);
     }
+    ctx->keys_step = keys_now ? ctx->host_step + 1 : -1;
     if (ctx->prof) {
       if (ctx->ev_used + 2 > ctx->ev.size()) {
         for (int q = 0; q < 64; ++q) {
@@ -464,7 +483,7 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
       CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
     }
     hpic::launch_push<R>(ctx->K, P(ctx->cur), G, tab, ctx->cnt, tv,
-                         ctx->sm_count * hpic::push_blocks_per_sm<R>(), ctx->stream, so);
+                         ctx->sm_count * hpic::push_blocks_per_sm<R>(), ctx->stream, so, ko);
     ctx->launches += 1;
     if (ctx->prof) {
       CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
@@ -483,7 +502,7 @@ int step_impl(hpic_ctx *ctx, long long nsteps) {
       ctx->launches += hpic::launch_sort_finish(ctx->K, ctx->cnt, ctx->counts, ctx->stream);
       ctx->cur ^= 1;
     }
-    if (ctx->have_laser && ctx->host_step < ctx->K.n_inj_steps && injection_total(ctx) > 0) {
+    if (inject_now) {
       const long long S = ctx->K.n_inj_steps, N = ctx->K.n_macro, st = ctx->host_step;
       const long long c = ctx->K.weighted ? ctx->K.per_cell * ctx->K.n_inj_cells
                                           : (N * (st + 1)) / S - (N * st) / S;
@@ -769,6 +788,7 @@ int hpic_inject_electrons(hpic_ctx *ctx, const hpic_laser_desc *l) {
   if (!ctx || !l) return fail(ctx, HPIC_EINVAL, "NULL argument");
   if (ctx->owner) return refuse_batch_target(ctx);
   if (ctx->have_laser) return fail(ctx, HPIC_ESTATE, "a laser is already scheduled");
+  ctx->keys_step = -1;
   if (const char *why = hpic::check_laser(*l, ctx->tgt)) return fail(ctx, HPIC_EINVAL, why);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   hpic::Counters h;
@@ -805,6 +825,7 @@ int hpic_inject_electrons(hpic_ctx *ctx, const hpic_laser_desc *l) {
 int hpic_seed_electrons(hpic_ctx *ctx, int64_t n, double mean_energy_J) {
   if (!ctx) return HPIC_EINVAL;
   if (ctx->owner) return refuse_batch_target(ctx);
+  ctx->keys_step = -1;
   if (n < 0 || !(mean_energy_J > 0)) return fail(ctx, HPIC_EINVAL, "bad seeding arguments");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   hpic::Counters h;
@@ -837,6 +858,7 @@ int hpic_step(hpic_ctx *ctx, int64_t n) {
 int hpic_sort(hpic_ctx *ctx) {
   if (!ctx) return HPIC_EINVAL;
   if (ctx->owner) return refuse_batch_target(ctx);
+  ctx->keys_step = -1;  // the sort reuses the key buffers
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   return ctx->fp32 ? sort_impl<float>(ctx) : sort_impl<double>(ctx);
 }
@@ -1055,6 +1077,7 @@ int hpic_read_weights(hpic_ctx *ctx, double *w, int64_t cap, int64_t *n_out) {
 
 int hpic_load_weights(hpic_ctx *ctx, int64_t n, const double *w) {
   if (!ctx || n < 0 || (n > 0 && !w)) return fail(ctx, HPIC_EINVAL, "bad weight arguments");
+  ctx->keys_step = -1;
   if (!ctx->K.weighted) return fail(ctx, HPIC_ESTATE, "per-electron weights need the Gaussian envelope");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   hpic::Counters h;
@@ -1080,6 +1103,7 @@ int hpic_load_particles(hpic_ctx *ctx, int64_t n, const double *x, const double 
                         const double *tau, const uint32_t *id) {
   if (!ctx || n < 0 || (n > 0 && (!x || !y || !z || !ux || !uy || !uz || !tau || !id)))
     return fail(ctx, HPIC_EINVAL, "bad particle arguments");
+  ctx->keys_step = -1;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   return ctx->fp32 ? load_particles_impl<float>(ctx, n, x, y, z, ux, uy, uz, tau, id)
                    : load_particles_impl<double>(ctx, n, x, y, z, ux, uy, uz, tau, id);
@@ -1099,6 +1123,7 @@ int hpic_get_clock(hpic_ctx *ctx, int64_t *step, int64_t *next_id) {
 int hpic_set_clock(hpic_ctx *ctx, int64_t step, int64_t next_id) {
   if (!ctx || step < 0 || next_id < 0 || step >= 0xFFFFFFFFll || next_id >= 0xFFFFFFFFll)
     return fail(ctx, HPIC_EINVAL, "clock out of range");
+  ctx->keys_step = -1;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   hpic::Counters h;
   int rc = read_counters(ctx, &h);

@@ -131,9 +131,9 @@ k_batch_push(const Consts Krun, const BatchItem<R> *__restrict__ items, BatchDev
     sc.key1 = Krun.key1;
     sc.target = it.h.target_index;
     const long long local = (w - wpref_s[t]) * 32 + lane;
-    push_warp<R, NS, SORT>(Krun, it.h, it.grid, tab, it.tv, sc, p, it.off + local,
-                          local < it.n, acc, tal_s + t * kAccN, stage, SORT ? &so : nullptr,
-                          SORT ? &it.sshift : nullptr);
+    push_warp<R, NS, SORT ? kPushSort : kPushPlain>(
+        Krun, it.h, it.grid, tab, it.tv, sc, p, it.off + local, local < it.n, acc,
+        tal_s + t * kAccN, stage, SORT ? &so : nullptr, SORT ? &it.sshift : nullptr, nullptr);
   }
   if (t >= 0) flush_acc(acc, tal_s + t * kAccN);
   __syncthreads();

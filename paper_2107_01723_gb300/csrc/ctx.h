@@ -55,6 +55,10 @@ struct hpic_ctx {
   float *t32 = nullptr;
   hpic::Counters *cnt = nullptr;
   long long host_step = 0;
+  // the host step whose start-of-step state the stored sort keys and ranks
+  // (with their counts) describe, computed by the step before it; -1: none.
+  // Every call that changes the electrons between steps clears it.
+  long long keys_step = -1;
   long long launches = 0;
   // profiling of the particle kernel
   bool prof = false;

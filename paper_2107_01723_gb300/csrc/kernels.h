@@ -142,9 +142,25 @@ struct SortOut {
   const uint32_t *keys, *ranks, *offsets;
 };
 
+// The sort key pass folded into the step before a sort: each electron that
+// survives the step gets, from its new state, the key of the cell it reaches
+// `lead` cells per unit of u/gamma ahead (as the key pass computes it from
+// the start of the sorting step) and its rank among its key's electrons
+// (counts must be cleared before).  keys == nullptr: no keys.
+template <typename R>
+struct KeyOut {
+  uint32_t *keys, *ranks, *counts;
+  R lead;
+};
+
+// the push kernel's modes: a plain step, a step that also computes the next
+// sort's keys (KeyOut), a step that also sorts (SortOut)
+enum PushMode { kPushPlain = 0, kPushKeys = 1, kPushSort = 2 };
+
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
-                 TallyView tv, int grid, cudaStream_t st, const SortOut<R> &so);
+                 TallyView tv, int grid, cudaStream_t st, const SortOut<R> &so,
+                 const KeyOut<R> &ko);
 template <typename R>
 void launch_inject(const Consts &K, PView<R> p, Counters *cnt, long long cap, TallyView tv,
                    int grid, cudaStream_t st);

@@ -10,8 +10,10 @@
 //   bremsstrahlung by optical depth + photon tally   App. B
 //   x^{n+1} = x^n + v dt, then escape/reflux         Sec. II.A
 //   current deposit at x^{n+1}                       j_h of Eq. (A2)
-// On a step that also sorts (SORT) the new state goes to the electron's slot
-// of the sorted order in the other buffer instead of its own slot.
+// On a step that also sorts (kPushSort) the new state goes to the electron's
+// slot of the sorted order in the other buffer instead of its own slot; on
+// the step before (kPushKeys) each surviving electron also gets its key and
+// rank for that sort.
 // Random numbers: Philox4x32-10, counter (step, id, block, target), key = seed;
 // block 0 scatter, 1 emission, 2..4 reflux on x/y/z faces, 8-9 injection.
 //
@@ -24,16 +26,17 @@
 
 namespace hpic {
 
-// SORT: the step also sorts (so says where the electrons go; without it the
-// sorting code is compiled out).
-template <typename R, int NS, bool SORT>
+// MODE: a plain step, one that also keys the next sort (ko), or one that
+// also sorts (so says where the electrons go); the other modes' code is
+// compiled out.
+template <typename R, int NS, int MODE>
 // FP32: five 256-thread blocks per SM (48 registers, a few spills to L1),
 // launched as one persistent wave: the kernel is issue- and latency-bound
 // and gains from the warps (three blocks at 80 registers were 14 % slower,
 // four and six slower too).  FP64 keeps two.
 __global__ void __launch_bounds__(kPushThreads, push_blocks_per_sm<R>())
 k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__restrict__ tab,
-       Counters *cnt, TallyView tv, const SortOut<R> so) {
+       Counters *cnt, TallyView tv, const SortOut<R> so, const KeyOut<R> ko) {
   __shared__ double rare[kAccN];  // the rare tally sums of the block
   if (threadIdx.x < kAccN) rare[threadIdx.x] = 0.0;
   __syncthreads();
@@ -56,8 +59,10 @@ k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__rest
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); base < n;
        base += stride)
-    push_warp<R, NS, SORT>(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc, rare,
-                           stage, SORT ? &so : nullptr, SORT ? &no_shift : nullptr);
+    push_warp<R, NS, MODE>(K, h, g, tab, tv, sc, p, base + lane, base + lane < n, acc, rare,
+                           stage, MODE == kPushSort ? &so : nullptr,
+                           MODE == kPushSort ? &no_shift : nullptr,
+                           MODE == kPushKeys ? &ko : nullptr);
 
   double v[kAccN];
   acc.values(v);
@@ -225,31 +230,43 @@ cudaError_t prepare_push() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   };
-  set((const void *)k_push<float, 1, false>, push_stage_bytes<float>());
-  set((const void *)k_push<float, 1, true>, push_stage_bytes<float>());
-  set((const void *)k_push<float, 4, false>, push_stage_bytes<float>());
-  set((const void *)k_push<float, 4, true>, push_stage_bytes<float>());
-  set((const void *)k_push<double, 1, false>, push_stage_bytes<double>());
-  set((const void *)k_push<double, 1, true>, push_stage_bytes<double>());
-  set((const void *)k_push<double, 4, false>, push_stage_bytes<double>());
-  set((const void *)k_push<double, 4, true>, push_stage_bytes<double>());
+  set((const void *)k_push<float, 1, kPushPlain>, push_stage_bytes<float>());
+  set((const void *)k_push<float, 1, kPushKeys>, push_stage_bytes<float>());
+  set((const void *)k_push<float, 1, kPushSort>, push_stage_bytes<float>());
+  set((const void *)k_push<float, 4, kPushPlain>, push_stage_bytes<float>());
+  set((const void *)k_push<float, 4, kPushKeys>, push_stage_bytes<float>());
+  set((const void *)k_push<float, 4, kPushSort>, push_stage_bytes<float>());
+  set((const void *)k_push<double, 1, kPushPlain>, push_stage_bytes<double>());
+  set((const void *)k_push<double, 1, kPushKeys>, push_stage_bytes<double>());
+  set((const void *)k_push<double, 1, kPushSort>, push_stage_bytes<double>());
+  set((const void *)k_push<double, 4, kPushPlain>, push_stage_bytes<double>());
+  set((const void *)k_push<double, 4, kPushKeys>, push_stage_bytes<double>());
+  set((const void *)k_push<double, 4, kPushSort>, push_stage_bytes<double>());
   return e;
+}
+
+template <typename R, int NS>
+void launch_push_ns(const Consts &K, const HotK<R> &h, PView<R> p, GView<R> g, const R *table,
+                    Counters *cnt, TallyView tv, int grid, cudaStream_t st, const SortOut<R> &so,
+                    const KeyOut<R> &ko) {
+  const size_t sm = push_stage_bytes<R>();
+  if (so.dst.x)
+    k_push<R, NS, kPushSort><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so, ko);
+  else if (ko.keys)
+    k_push<R, NS, kPushKeys><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so, ko);
+  else
+    k_push<R, NS, kPushPlain><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so, ko);
 }
 
 template <typename R>
 void launch_push(const Consts &K, PView<R> p, GView<R> g, const R *table, Counters *cnt,
-                 TallyView tv, int grid, cudaStream_t st, const SortOut<R> &so) {
+                 TallyView tv, int grid, cudaStream_t st, const SortOut<R> &so,
+                 const KeyOut<R> &ko) {
   const HotK<R> h = make_hot<R>(K);
-  const size_t sm = push_stage_bytes<R>();
-  const bool sort = so.dst.x != nullptr;
-  if (K.n_solids == 1 && sort)  // a single-element solid: the element loops vanish
-    k_push<R, 1, true><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so);
-  else if (K.n_solids == 1)
-    k_push<R, 1, false><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so);
-  else if (sort)
-    k_push<R, 4, true><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so);
+  if (K.n_solids == 1)  // a single-element solid: the element loops vanish
+    launch_push_ns<R, 1>(K, h, p, g, table, cnt, tv, grid, st, so, ko);
   else
-    k_push<R, 4, false><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so);
+    launch_push_ns<R, 4>(K, h, p, g, table, cnt, tv, grid, st, so, ko);
 }
 
 template <typename R>
@@ -263,10 +280,11 @@ void launch_advance(Counters *cnt, long long cap, cudaStream_t st) {
 }
 
 template void launch_push<float>(const Consts &, PView<float>, GView<float>, const float *,
-                                 Counters *, TallyView, int, cudaStream_t, const SortOut<float> &);
+                                 Counters *, TallyView, int, cudaStream_t, const SortOut<float> &,
+                                 const KeyOut<float> &);
 template void launch_push<double>(const Consts &, PView<double>, GView<double>, const double *,
                                   Counters *, TallyView, int, cudaStream_t,
-                                  const SortOut<double> &);
+                                  const SortOut<double> &, const KeyOut<double> &);
 template void launch_inject<float>(const Consts &, PView<float>, Counters *, long long, TallyView,
                                    int, cudaStream_t);
 template void launch_inject<double>(const Consts &, PView<double>, Counters *, long long,

@@ -690,16 +690,18 @@ __device__ __forceinline__ void st_stream(R *p, R v) { __stcs(p, v); }
 // in_range false: nothing there) through the step, then deposit their
 // current and drag heat together through the warp's shared-memory stage
 // (dep_words<R>() elements, 16-byte aligned).  Every lane of the warp must
-// call it.  SORT: the step also sorts, and *so (with *shift: see SortOut; read
-// only then, so it may stay in shared memory) says where the electrons go;
-// both may be null otherwise.
-template <typename R, int NS, bool SORT>
+// call it.  MODE kPushSort: the step also sorts, and *so (with *shift: see
+// SortOut; read only then, so it may stay in shared memory) says where the
+// electrons go; kPushKeys: the step also keys the next sort (*ko); the
+// pointers may be null otherwise.
+template <typename R, int NS, int MODE>
 __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, const Grid<R> &g,
                                           const R *__restrict__ tab, const TallyView &tv,
                                           const StepCtx &sc, const PView<R> &p, long long ip,
                                           bool in_range, Acc<R> &acc, double *rare,
                                           R *__restrict__ stage, const SortOut<R> *so,
-                                          const long long *shift) {
+                                          const long long *shift, const KeyOut<R> *ko) {
+  constexpr bool SORT = MODE == kPushSort;
   bool live = false, dep = false;
   uint32_t id = kDead;
   R X = 0, Y = 0, Zc = 0, ux = 0, uy = 0, uz = 0, tau = 0, heat = 0, w = h.w;
@@ -744,6 +746,17 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
       st_stream(p.x + ip, X); st_stream(p.y + ip, Y); st_stream(p.z + ip, Zc);
       st_stream(p.ux + ip, ux); st_stream(p.uy + ip, uy); st_stream(p.uz + ip, uz);
       st_stream(p.tau + ip, tau);
+      if constexpr (MODE == kPushKeys) {  // the next sort's key and rank
+        const R a = ko->lead / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+        int i = (int)m_floor(X + a * ux), j = (int)m_floor(Y + a * uy),
+            k = (int)m_floor(Zc + a * uz);
+        i = min(max(i, 0), K.nx - 1);
+        j = min(max(j, 0), K.ny - 1);
+        k = min(max(k, 0), K.nz - 1);
+        const uint32_t key = tile_key(i, j, k, K.nti, K.ntj);
+        ko->keys[ip] = key;
+        ko->ranks[ip] = agg_inc(ko->counts, key);
+      }
     } else {
       p.id[ip] = kDead;
     }

@@ -8,9 +8,11 @@ id -- through the same trajectory as a run that never sorts, with the same
 survivors and the same tallies and grids; the two differ only in the order
 of the floating-point atomic additions (FP64 here, so by rounding).  The
 cases cover sorting steps during the injection (new electrons appended to
-the sorted buffer), electrons absorbed or escaping on a sorting step (their
-sorted slots left dead), a sort on every step, one target and an uneven
-batch.
+the sorted buffer; the keys from a key pass) and after it (the keys from
+the push of the step before), electrons absorbed or escaping on a sorting
+step (their sorted slots left dead), a sort on every step, keys dropped when
+the electrons are reloaded between the keying and the sorting step, one
+target and an uneven batch.
 """
 import numpy as np
 import pytest
@@ -23,7 +25,7 @@ from parity import (assert_field_close, assert_particles_close, assert_tallies_c
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-10  # 30 FP64 steps: rounding-order differences grow slowly through the fields
+TOL = 1e-9  # up to 60 FP64 steps: rounding-order differences grow slowly through the fields
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -53,7 +55,7 @@ def test_sorting_run_equals_unsorted_run(interval):
     for si in (interval, 0):
         s = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=hpic.HPIC_FP64,
                      sort_interval=si)
-        s.step(30)  # injecting throughout; the last step sorts for both intervals
+        s.step(60)  # injecting for 40 steps, then 20 without; the last step sorts
         runs[si] = s
     a, b = runs[interval], runs[0]
     t = b.tallies()
@@ -66,6 +68,26 @@ def test_sorting_run_equals_unsorted_run(interval):
     assert a.n <= t["n_injected"]
     a.close()
     b.close()
+
+
+def test_keys_are_dropped_when_the_electrons_change():
+    """After a keying step (host step 49 keys the sort of step 50) the electrons
+    are read and loaded back, which packs them into new slots: the sorting step
+    must key them afresh, not use the stale keys and ranks of the old slots."""
+    cfg = W.config_small(n=(12, 10, 14), n_macro=6000, I_Wcm2=1e21, steps=40, spot_r=3e-6,
+                         t_inj=20e-15)
+    dx = cfg["target"]["dx"]
+    runs = {}
+    for si in (3, 0):
+        s = hpic.Sim(cfg["target"], cfg["laser"], cfg["run"], precision=hpic.HPIC_FP64,
+                     sort_interval=si)
+        s.step(50)
+        s.set_particles(s.particles())
+        s.step(10)
+        runs[si] = s
+    assert_same_run(runs[3], runs[0], dx)
+    for s in runs.values():
+        s.close()
 
 
 def test_sorting_batch_equals_unsorted_batch():

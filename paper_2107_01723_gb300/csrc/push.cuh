@@ -295,16 +295,16 @@ __device__ __noinline__ EmitOut<R> emit_photon(const EmitIn<R> e, StepCtx sc, ui
 
 // Advance one live electron through the step.  Returns false when the
 // electron is absorbed or escapes (the caller marks its slot dead).  On
-// true, the state holds x^{n+1}, u^{n+1} and tau, and its current is
-// deposited.  NS: 1 for a single-element solid (the element loops vanish),
-// 4 for up to four elements counted at run time.
+// true, the state holds x^{n+1}, u^{n+1} and tau, ig = 1/gamma of u^{n+1}
+// (the deposit's velocity factor), and its current is deposited.  NS: 1 for
+// a single-element solid (the element loops vanish), 4 for up to four
+// elements counted at run time.
 template <typename R, int NS>
 __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const Grid<R> &g,
                                         const R *__restrict__ tab, const TallyView &tv,
                                         const StepCtx &sc, uint32_t id, R w, R &X, R &Y, R &Zc,
                                         R &ux, R &uy, R &uz, R &tau, Acc<R> &acc, double *rare,
-                                        R &heat_out,
-                                        int &heat_cell) {
+                                        R &heat_out, int &heat_cell, R &ig) {
   const int nx = h.nx, ny = h.ny, nz = h.nz;
 
   // ---- gather at x^n
@@ -431,7 +431,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
   }
 
   // ---- move, then escape or reflux at each face crossed (out of line: rare)
-  R ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+  ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
   R pos[3] = {X + ux * ig * h.cdt, Y + uy * ig * h.cdt, Zc + uz * ig * h.cdt};
   if (!unbounded && !(pos[0] >= R(0) && pos[0] <= R(nx) && pos[1] >= R(0) && pos[1] <= R(ny) &&
                       pos[2] >= R(0) && pos[2] <= R(nz))) {
@@ -446,6 +446,7 @@ __device__ __forceinline__ bool advance(const Consts &K, const HotK<R> &h, const
     if (!c.alive) return false;
     pos[0] = c.pos[0]; pos[1] = c.pos[1]; pos[2] = c.pos[2];
     ux = c.u[0]; uy = c.u[1]; uz = c.u[2];
+    ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
   }
   X = pos[0]; Y = pos[1]; Zc = pos[2];
 
@@ -534,13 +535,13 @@ struct Vec16<double> {
   }
 };
 
-// current J += w (u/gamma) S(x^{n+1}) of the lanes with dep set, and drag
-// heat into the cell heat_cell of x^n (heat == 0: nothing); buf is this
-// warp's stage.  Every lane of the warp must call it.
+// current J += w (u/gamma) S(x^{n+1}) of the lanes with dep set (ig =
+// 1/gamma), and drag heat into the cell heat_cell of x^n (heat == 0:
+// nothing); buf is this warp's stage.  Every lane of the warp must call it.
 template <typename R>
 __device__ __forceinline__ void warp_deposit(const Grid<R> &g, R *__restrict__ buf,
                                              bool dep, R w, R X, R Y, R Zc, R ux, R uy, R uz,
-                                             R heat, int heat_cell) {
+                                             R ig, R heat, int heat_cell) {
   constexpr int S = dep_stride<R>();
   const int lane = threadIdx.x & 31;
 
@@ -550,7 +551,6 @@ __device__ __forceinline__ void warp_deposit(const Grid<R> &g, R *__restrict__ b
   R v[3] = {R(0), R(0), R(0)};
   uint32_t nk = kNoKey, ck = kNoCell;
   if (dep) {
-    const R ig = R(1) / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
     v[0] = w * ux * ig;
     v[1] = w * uy * ig;
     v[2] = w * uz * ig;
@@ -704,15 +704,18 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
   constexpr bool SORT = MODE == kPushSort;
   bool live = false, dep = false;
   uint32_t id = kDead;
-  R X = 0, Y = 0, Zc = 0, ux = 0, uy = 0, uz = 0, tau = 0, heat = 0, w = h.w;
+  R X = 0, Y = 0, Zc = 0, ux = 0, uy = 0, uz = 0, tau = 0, heat = 0, w = h.w, ig = 0;
   int heat_cell = -1;
   if (in_range) {
+    // the state is loaded together with the id, not after testing it, so
+    // that a slot costs one memory round trip (a dead slot's values are
+    // read and left unused)
     id = ld_stream(p.id + ip);
+    X = ld_stream(p.x + ip); Y = ld_stream(p.y + ip); Zc = ld_stream(p.z + ip);
+    ux = ld_stream(p.ux + ip); uy = ld_stream(p.uy + ip); uz = ld_stream(p.uz + ip);
+    tau = ld_stream(p.tau + ip);
+    if (K.weighted) w = ld_stream(p.w + ip);  // uniform over the launch
     if (id != kDead) {
-      X = ld_stream(p.x + ip); Y = ld_stream(p.y + ip); Zc = ld_stream(p.z + ip);
-      ux = ld_stream(p.ux + ip); uy = ld_stream(p.uy + ip); uz = ld_stream(p.uz + ip);
-      tau = ld_stream(p.tau + ip);
-      if (K.weighted) w = ld_stream(p.w + ip);  // uniform over the launch
       if (isfinite(X) && isfinite(Y) && isfinite(Zc) && isfinite(ux) && isfinite(uy) &&
           isfinite(uz) && isfinite(tau)) {
         live = true;
@@ -728,7 +731,7 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
   if (live) {
     ++acc.n_steps;
     dep = advance<R, NS>(K, h, g, tab, tv, sc, id, w, X, Y, Zc, ux, uy, uz, tau, acc, rare, heat,
-                         heat_cell);
+                         heat_cell, ig);
     if constexpr (SORT) {  // loaded here so that no register holds them through the step
       const long long q =
           (long long)so->offsets[ld_stream(so->keys + ip)] + ld_stream(so->ranks + ip) + *shift;
@@ -747,7 +750,7 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
       st_stream(p.ux + ip, ux); st_stream(p.uy + ip, uy); st_stream(p.uz + ip, uz);
       st_stream(p.tau + ip, tau);
       if constexpr (MODE == kPushKeys) {  // the next sort's key and rank
-        const R a = ko->lead / m_sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+        const R a = ko->lead * ig;
         int i = (int)m_floor(X + a * ux), j = (int)m_floor(Y + a * uy),
             k = (int)m_floor(Zc + a * uz);
         i = min(max(i, 0), K.nx - 1);
@@ -762,7 +765,7 @@ __device__ __forceinline__ void push_warp(const Consts &K, const HotK<R> &h, con
     }
   }
   if (!(K.physics & P_UNBOUNDED))  // uniform over the warp
-    warp_deposit(g, stage, dep, w, X, Y, Zc, ux, uy, uz, heat, heat_cell);
+    warp_deposit(g, stage, dep, w, X, Y, Zc, ux, uy, uz, ig, heat, heat_cell);
 }
 
 // ---------------------------------------------------------------- injection

@@ -97,13 +97,17 @@ double fsigma_of(const Consts &K, double Ti);
 // the injecting face cells of a Gaussian-envelope laser (empty otherwise)
 std::vector<InjCell> injection_cells(const hpic_target_desc &t, const hpic_laser_desc &l);
 
-// resident 256-thread blocks per SM of the single-target particle kernel; it
-// is launched as one persistent wave of sm_count times this many blocks
+// Launch shape of the single-target particle kernel: resident blocks per SM
+// (it is launched as one persistent wave of sm_count times this many blocks)
+// and threads per block (one deposit stage per warp).  FP32: three blocks of
+// 384 threads, 36 warps at 56 registers with few spills; a block's twelve
+// warps take consecutive slots, so their gathers share L1 lines.  (Five
+// blocks of 256 at 48 registers spilled 84 B and were 3.4 % slower, 288 x 4
+// 2.2 %, 192 x 6 0.5 %; 576 x 2 was level.)  FP64: two blocks of 256.
 template <typename R>
-constexpr int push_blocks_per_sm() { return sizeof(R) == 4 ? 5 : 2; }
-// threads per block of the single-target particle kernel (a warp-sized
-// deposit stage per warp)
-constexpr int kPushThreads = 256;
+constexpr int push_blocks_per_sm() { return sizeof(R) == 4 ? 3 : 2; }
+template <typename R>
+constexpr int push_threads() { return sizeof(R) == 4 ? 384 : 256; }
 // resident 256-thread blocks per SM of the field and heating kernels (their
 // launch bounds); they are launched as one wave of sm_count times this many
 // blocks (grid-stride over the nodes), so no partial second wave trails

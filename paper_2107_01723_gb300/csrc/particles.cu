@@ -30,11 +30,10 @@ namespace hpic {
 // also sorts (so says where the electrons go); the other modes' code is
 // compiled out.
 template <typename R, int NS, int MODE>
-// FP32: five 256-thread blocks per SM (48 registers, a few spills to L1),
-// launched as one persistent wave: the kernel is issue- and latency-bound
-// and gains from the warps (three blocks at 80 registers were 14 % slower,
-// four and six slower too).  FP64 keeps two.
-__global__ void __launch_bounds__(kPushThreads, push_blocks_per_sm<R>())
+// Launched as one persistent wave in the shape push_threads/push_blocks_per_sm
+// give: the kernel is issue- and latency-bound and gains from the warps, up
+// to the register count at which spills begin.
+__global__ void __launch_bounds__(push_threads<R>(), push_blocks_per_sm<R>())
 k_push(const Consts K, const HotK<R> h, PView<R> p, GView<R> gv, const R *__restrict__ tab,
        Counters *cnt, TallyView tv, const SortOut<R> so, const KeyOut<R> ko) {
   __shared__ double rare[kAccN];  // the rare tally sums of the block
@@ -222,7 +221,7 @@ __global__ void k_advance(Counters *cnt, long long cap) {
 // ---------------------------------------------------------------- launchers
 
 template <typename R>
-constexpr size_t push_stage_bytes() { return (kPushThreads / 32) * dep_words<R>() * sizeof(R); }
+constexpr size_t push_stage_bytes() { return (push_threads<R>() / 32) * dep_words<R>() * sizeof(R); }
 
 cudaError_t prepare_push() {
   cudaError_t e = cudaSuccess;
@@ -251,11 +250,11 @@ void launch_push_ns(const Consts &K, const HotK<R> &h, PView<R> p, GView<R> g, c
                     const KeyOut<R> &ko) {
   const size_t sm = push_stage_bytes<R>();
   if (so.dst.x)
-    k_push<R, NS, kPushSort><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so, ko);
+    k_push<R, NS, kPushSort><<<grid, push_threads<R>(), sm, st>>>(K, h, p, g, table, cnt, tv, so, ko);
   else if (ko.keys)
-    k_push<R, NS, kPushKeys><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so, ko);
+    k_push<R, NS, kPushKeys><<<grid, push_threads<R>(), sm, st>>>(K, h, p, g, table, cnt, tv, so, ko);
   else
-    k_push<R, NS, kPushPlain><<<grid, kPushThreads, sm, st>>>(K, h, p, g, table, cnt, tv, so, ko);
+    k_push<R, NS, kPushPlain><<<grid, push_threads<R>(), sm, st>>>(K, h, p, g, table, cnt, tv, so, ko);
 }
 
 template <typename R>

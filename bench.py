@@ -48,15 +48,15 @@ KEY_STEP_EXTRA_BYTES = 4 + 4
 # sorting step): a plain step streams the state once (absorbed slots are not
 # rewritten), a keying step adds the keys and ranks it writes, a sorting step
 # reads them and scatters its stores (partial sectors); None where not captured
-NCU_DRAM_BYTES_PER_PSTEP = {"fp32": {"plain": 56.1, "key": 64.3, "sort": 80.6}, "fp64": None}
+NCU_DRAM_BYTES_PER_PSTEP = {"fp32": {"plain": 55.1, "key": 62.8, "sort": 76.9}, "fp64": None}
 # the same for k_batch_push, captured on the first 16 targets of the scan
 # (the full scan holds too much device memory for a multi-pass capture): the traffic is the
 # electron state streamed once, so it scales with the particle-steps
-NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": {"plain": 61.0, "sort": 93.1}, "fp64": None}
+NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": {"plain": 60.9, "sort": 93.7}, "fp64": None}
 # FP64 FLOP per particle-step of the FP64 k_push (2 per DFMA, 1 per DADD and
 # DMUL; ncu thread-level counts on config 1 in FP64, launches at steps 110
 # and 111) and the FP64 rate the GB300 is stated to have (TFLOP/s)
-NCU_FP64_FLOP_PER_PSTEP = 1239.0
+NCU_FP64_FLOP_PER_PSTEP = 1210.0
 FP64_STATED_TFLOPS = 1.25
 # the accuracy window: the injection (200 steps) and 1 ps beyond
 ACCURACY_STEPS = 2200

@@ -377,7 +377,9 @@ const char *hpic_last_error(const hpic_ctx *ctx);
 #define HPIC_BATCH_MAX_TARGETS 256
 
 typedef struct {
-  int32_t blocks_per_sm;   /* persistent particle-kernel blocks per SM (1..5; FP64 1..2) */
+  int32_t blocks_per_sm;   /* persistent particle-kernel blocks per SM (1..5; FP64 1..2);
+                              FP32 blocks hold 512 threads at 1..2 per SM, 384 at 3,
+                              256 at 4..5; FP64 blocks 256 */
   int32_t sort_interval;   /* steps between cell sorts (0: never); keyed by the cell
                               reached (sort_interval + 1)/2 steps ahead */
   int32_t use_graph;       /* replay captured CUDA graphs (1) or launch directly (0) */

@@ -16,7 +16,21 @@
 
 namespace hpic {
 
-constexpr int kBatchWarps = 8;  // 256-thread blocks
+// Threads per block of the persistent push, by precision and blocks per SM
+// (MINB): FP32 runs 512 at two blocks per SM (64 registers) and 384 at three
+// (56 registers), 256 otherwise; FP64 runs 256.  A block's warps take
+// consecutive tasks, so larger blocks share more of their gathers' L1 lines
+// (the single-target kernel measured three blocks of 384 3.4 % faster than
+// five of 256 at 48 registers).
+template <typename R, int MINB>
+__host__ __device__ constexpr int batch_threads() {
+  return sizeof(R) != 4 ? 256 : (MINB <= 2 ? 512 : (MINB == 3 ? 384 : 256));
+}
+constexpr int kBatchMaxWarps = 16;
+// the same, chosen at run time
+inline int batch_threads_rt(bool fp32, int blocks_per_sm) {
+  return !fp32 ? 256 : (blocks_per_sm <= 2 ? 512 : (blocks_per_sm == 3 ? 384 : 256));
+}
 
 // ---------------------------------------------------------------- plan
 // wpref: warp tasks from the live slot counts; ipref: electrons injected in
@@ -73,13 +87,16 @@ struct TargetHot {
 };
 
 // SORT: the step also sorts (so says where the electrons go; without it the
-// sorting code is compiled out).  MINB = the blocks per SM the launch asks for: the register budget follows
-// (5: 48 registers, 4: 64, 3: 80, 2: 128, 1: 255; the FP32 state spills a
-// little below 64), and the autotuner picks among the variants by timing them
+// sorting code is compiled out).  MINB = the blocks per SM the launch asks
+// for, with batch_threads threads each: the register budget follows (FP32
+// 5: 48 registers, 4: 64, 3: 56 at 384 threads, 2: 64 at 512; FP64 2: 128,
+// 1: 255; the FP32 state spills a little below 64), and the autotuner picks
+// among the variants by timing them
 template <typename R, int MINB, int NS, bool SORT>
-__global__ void __launch_bounds__(256, MINB)
+__global__ void __launch_bounds__(batch_threads<R, MINB>(), MINB)
 k_batch_push(const Consts Krun, const BatchItem<R> *__restrict__ items, BatchDev d, PView<R> p,
              const R *__restrict__ tab, const SortOut<R> so) {
+  constexpr int kBatchWarps = batch_threads<R, MINB>() / 32;
   __shared__ TargetHot<R> wc[kBatchWarps];  // each warp's current target
   // the warps' deposit stages, then n x kAccN tally sums, then the task prefix
   extern __shared__ __align__(16) double dyn[];
@@ -269,12 +286,14 @@ void launch_batch_plan(const BatchItem<R> *items, BatchDev d, cudaStream_t st) {
 }
 
 template <typename R>
-constexpr size_t batch_stage_bytes() { return (size_t)kBatchWarps * dep_words<R>() * sizeof(R); }
+constexpr size_t batch_stage_bytes(int warps) { return (size_t)warps * dep_words<R>() * sizeof(R); }
 
 // dynamic shared memory of the push for up to the maximum number of targets
+// at the largest block
 template <typename R>
 constexpr size_t batch_push_smem_max() {
-  return batch_stage_bytes<R>() + (size_t)HPIC_BATCH_MAX_TARGETS * kAccN * sizeof(double) +
+  return batch_stage_bytes<R>(kBatchMaxWarps) +
+         (size_t)HPIC_BATCH_MAX_TARGETS * kAccN * sizeof(double) +
          (HPIC_BATCH_MAX_TARGETS + 1) * sizeof(long long);
 }
 
@@ -323,9 +342,11 @@ void launch_batch_push_ns(const Consts &Krun, const BatchItem<R> *items, BatchDe
       k_batch_push<R, 2, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
   } else {  // FP32: two to five (one runs the two-block code)
     if (blocks_per_sm <= 2)
-      k_batch_push<R, 2, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
+      k_batch_push<R, 2, NS, SORT><<<grid, batch_threads<R, 2>(), sm, st>>>(Krun, items, d, p,
+                                                                            table, so);
     else if (blocks_per_sm == 3)
-      k_batch_push<R, 3, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
+      k_batch_push<R, 3, NS, SORT><<<grid, batch_threads<R, 3>(), sm, st>>>(Krun, items, d, p,
+                                                                            table, so);
     else if (blocks_per_sm == 4)
       k_batch_push<R, 4, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
     else
@@ -338,7 +359,8 @@ template <typename R>
 void launch_batch_push(const Consts &Krun, const BatchItem<R> *items, BatchDev d, PView<R> p,
                        const R *table, int sm_count, int blocks_per_sm, bool single,
                        cudaStream_t st, const SortOut<R> &so) {
-  const size_t sm = batch_stage_bytes<R>() + (size_t)d.n * kAccN * sizeof(double) +
+  const int warps = batch_threads_rt(sizeof(R) == 4, blocks_per_sm) / 32;
+  const size_t sm = batch_stage_bytes<R>(warps) + (size_t)d.n * kAccN * sizeof(double) +
                     (d.n + 1) * sizeof(long long);
   const int grid = sm_count * blocks_per_sm;
   const bool sort = so.dst.x != nullptr;

@@ -53,6 +53,9 @@ NCU_DRAM_BYTES_PER_PSTEP = {"fp32": {"plain": 55.1, "key": 62.8, "sort": 76.9}, 
 # (the full scan holds too much device memory for a multi-pass capture): the traffic is the
 # electron state streamed once, so it scales with the particle-steps
 NCU_BATCH_DRAM_BYTES_PER_PSTEP = {"fp32": {"plain": 60.9, "sort": 93.7}, "fp64": None}
+# the launch shape those counters were taken at (blocks per SM of 256 threads);
+# another shape runs the same code but reports no traffic of its own
+NCU_BATCH_CAPTURE_BLOCKS = 4
 # FP64 FLOP per particle-step of the FP64 k_push (2 per DFMA, 1 per DADD and
 # DMUL; ncu thread-level counts on config 1 in FP64, launches at steps 110
 # and 111) and the FP64 rate the GB300 is stated to have (TFLOP/s)
@@ -742,11 +745,14 @@ def batch_result(n_targets: int, warm: int, steps: int, precision: str = "fp32",
                        "graphs": "plain and sorting steps replayed from captured CUDA graphs"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / pk["hbm_gbs"],
-                         "traffic": push_traffic(NCU_BATCH_DRAM_BYTES_PER_PSTEP, precision, kp, kl,
-                                                 step0, 40, si, keyed=False),
+                         "traffic": (push_traffic(NCU_BATCH_DRAM_BYTES_PER_PSTEP, precision, kp, kl,
+                                                  step0, 40, si, keyed=False)
+                                     if int(tune["blocks_per_sm"]) == NCU_BATCH_CAPTURE_BLOCKS
+                                     else None),
                          "bytes_per_particle_step": kbytes / kp if kp > 0 else None,
-                         "traffic_unit": "bytes per launch (ncu dram read+write on 16 targets, "
-                                         "scaled by particle-steps)",
+                         "traffic_unit": ("bytes per launch (ncu dram read+write on 16 targets at "
+                                          f"{NCU_BATCH_CAPTURE_BLOCKS} blocks of 256 threads per SM, "
+                                          "scaled by particle-steps; null at another launch shape)"),
                          "kernel": "k_batch_push", "kernel_ms_avg": km / kl,
                          "measured_over": f"{kl} direct launches after the timed window",
                          "peak_source": pk["source"]},

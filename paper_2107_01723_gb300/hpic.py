@@ -300,14 +300,28 @@ def hpic_count_particles(h) -> int:
     return n.value
 
 
-def hpic_read_particles(h) -> dict:
-    n = hpic_count_particles(h)
-    out = {k: np.empty(n) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")}
-    out["id"] = np.empty(n, dtype=np.uint32)
+def hpic_read_particles(h, out: dict | None = None) -> dict:
+    """The live electrons in storage order.  With `out` (float64 arrays x ..
+    tau and a uint32 array id, C-contiguous, all of one length: the capacity,
+    e.g. page-locked buffers allocated once) they are written there and views
+    of the first n entries are returned; otherwise new arrays are made."""
+    keys = ("x", "y", "z", "ux", "uy", "uz", "tau")
+    if out is None:
+        n = hpic_count_particles(h)
+        out = {k: np.empty(n) for k in keys}
+        out["id"] = np.empty(n, dtype=np.uint32)
+    else:
+        n = len(out["id"])
+        for k in keys:
+            if out[k].dtype != np.float64 or not out[k].flags.c_contiguous or len(out[k]) != n:
+                raise ValueError(f"out[{k!r}] must be a C-contiguous float64 array of length {n}")
+        if out["id"].dtype != np.uint32 or not out["id"].flags.c_contiguous:
+            raise ValueError("out['id'] must be a C-contiguous uint32 array")
     got = C.c_int64()
-    _check(lib().hpic_read_particles(h, *[_dp(out[k]) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")],
-                                     _up(out["id"]), n, C.byref(got)), h)
-    return out
+    _check(lib().hpic_read_particles(h, *[_dp(out[k]) for k in keys], _up(out["id"]), n,
+                                     C.byref(got)), h)
+    m = got.value
+    return {k: v[:m] for k, v in out.items()}
 
 
 def hpic_load_particles(h, p: dict) -> None:
@@ -510,8 +524,8 @@ class Target:
     def n(self) -> int:
         return hpic_count_particles(self.h)
 
-    def particles(self) -> dict:
-        return hpic_read_particles(self.h)
+    def particles(self, out: dict | None = None) -> dict:
+        return hpic_read_particles(self.h, out)
 
     def set_particles(self, p: dict) -> None:
         hpic_load_particles(self.h, p)

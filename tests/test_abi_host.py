@@ -206,3 +206,16 @@ def test_noalloc_sort_refuses_overlapping_arrays(lib):
         with pytest.raises(hpic.HpicError) as e:
             hpic.hpic_sort_cells_noalloc(8, 8, 8, prec, n, ins, ok, base - 64)
         assert e.value.code != hpic.HPIC_EINVAL
+
+
+def test_read_into_buffers_checks_them_first():
+    """Reading the electrons into caller-owned buffers (page-locked ones, for
+    instance) checks each buffer's type, layout and length before any library
+    call, so a wrong buffer is an error and never a partial copy."""
+    n = 4
+    good = {k: np.zeros(n) for k in ("x", "y", "z", "ux", "uy", "uz", "tau")}
+    good["id"] = np.zeros(n, dtype=np.uint32)
+    for k, bad in (("ux", np.zeros(n, dtype=np.float32)), ("x", np.zeros(2 * n)[::2]),
+                   ("tau", np.zeros(n + 1)), ("id", np.zeros(n, dtype=np.int64))):
+        with pytest.raises(ValueError):
+            hpic.hpic_read_particles(None, dict(good, **{k: bad}))

@@ -22,15 +22,21 @@ namespace hpic {
 // consecutive tasks, so larger blocks share more of their gathers' L1 lines
 // (the single-target kernel measured three blocks of 384 3.4 % faster than
 // five of 256 at 48 registers).
-template <typename R, int MINB>
-__host__ __device__ constexpr int batch_threads() {
-  return sizeof(R) != 4 ? 256 : (MINB <= 2 ? 512 : (MINB == 3 ? 384 : 256));
-}
-constexpr int kBatchMaxWarps = 16;
-// the same, chosen at run time
-inline int batch_threads_rt(bool fp32, int blocks_per_sm) {
+// One definition serves the kernels' launch bounds, the launches and the
+// dynamic shared memory sized for them (an FP32 request of one block per SM
+// runs the two-block code, as launch_batch_push_ns does).
+__host__ __device__ constexpr int batch_threads_for(bool fp32, int blocks_per_sm) {
   return !fp32 ? 256 : (blocks_per_sm <= 2 ? 512 : (blocks_per_sm == 3 ? 384 : 256));
 }
+template <typename R, int MINB>
+__host__ __device__ constexpr int batch_threads() { return batch_threads_for(sizeof(R) == 4, MINB); }
+constexpr int kBatchMaxWarps = 16;
+static_assert(batch_threads_for(true, 2) / 32 <= kBatchMaxWarps &&
+                  batch_threads_for(true, 3) / 32 <= kBatchMaxWarps &&
+                  batch_threads_for(false, 2) / 32 <= kBatchMaxWarps,
+              "the largest block's stages are what the shared-memory limit is set for");
+static_assert(batch_threads_for(true, 1) == batch_threads_for(true, 2),
+              "one block per SM in FP32 runs the two-block kernel");
 
 // ---------------------------------------------------------------- plan
 // wpref: warp tasks from the live slot counts; ipref: electrons injected in
@@ -337,9 +343,11 @@ void launch_batch_push_ns(const Consts &Krun, const BatchItem<R> *items, BatchDe
                           const SortOut<R> &so) {
   if constexpr (sizeof(R) == 8) {  // FP64: one or two blocks per SM
     if (blocks_per_sm <= 1)
-      k_batch_push<R, 1, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
+      k_batch_push<R, 1, NS, SORT><<<grid, batch_threads<R, 1>(), sm, st>>>(Krun, items, d, p,
+                                                                            table, so);
     else
-      k_batch_push<R, 2, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
+      k_batch_push<R, 2, NS, SORT><<<grid, batch_threads<R, 2>(), sm, st>>>(Krun, items, d, p,
+                                                                            table, so);
   } else {  // FP32: two to five (one runs the two-block code)
     if (blocks_per_sm <= 2)
       k_batch_push<R, 2, NS, SORT><<<grid, batch_threads<R, 2>(), sm, st>>>(Krun, items, d, p,
@@ -348,9 +356,11 @@ void launch_batch_push_ns(const Consts &Krun, const BatchItem<R> *items, BatchDe
       k_batch_push<R, 3, NS, SORT><<<grid, batch_threads<R, 3>(), sm, st>>>(Krun, items, d, p,
                                                                             table, so);
     else if (blocks_per_sm == 4)
-      k_batch_push<R, 4, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
+      k_batch_push<R, 4, NS, SORT><<<grid, batch_threads<R, 4>(), sm, st>>>(Krun, items, d, p,
+                                                                            table, so);
     else
-      k_batch_push<R, 5, NS, SORT><<<grid, 256, sm, st>>>(Krun, items, d, p, table, so);
+      k_batch_push<R, 5, NS, SORT><<<grid, batch_threads<R, 5>(), sm, st>>>(Krun, items, d, p,
+                                                                            table, so);
   }
 }
 
@@ -359,7 +369,7 @@ template <typename R>
 void launch_batch_push(const Consts &Krun, const BatchItem<R> *items, BatchDev d, PView<R> p,
                        const R *table, int sm_count, int blocks_per_sm, bool single,
                        cudaStream_t st, const SortOut<R> &so) {
-  const int warps = batch_threads_rt(sizeof(R) == 4, blocks_per_sm) / 32;
+  const int warps = batch_threads_for(sizeof(R) == 4, blocks_per_sm) / 32;
   const size_t sm = batch_stage_bytes<R>(warps) + (size_t)d.n * kAccN * sizeof(double) +
                     (d.n + 1) * sizeof(long long);
   const int grid = sm_count * blocks_per_sm;

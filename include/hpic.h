@@ -273,7 +273,10 @@ int hpic_count_particles(hpic_ctx *ctx, int64_t *n);
  * to double run on the device in a scratch buffer the context owns (grown
  * to 8 bytes per electron slot, freed by hpic_destroy or
  * hpic_batch_destroy); HPIC_ENOMEM if it cannot be allocated.  This call
- * and hpic_load_particles / hpic_count_particles synchronise the stream. */
+ * and hpic_load_particles / hpic_count_particles synchronise the stream.
+ * The host arrays here and in hpic_load_particles may be page-locked
+ * (cudaHostAlloc) or pageable; page-locked ones, allocated once and reused,
+ * avoid the driver's staging copies and the page faults of fresh memory. */
 int hpic_read_particles(hpic_ctx *ctx, double *x, double *y, double *z,
                         double *ux, double *uy, double *uz, double *tau,
                         uint32_t *id, int64_t cap, int64_t *n);

@@ -159,6 +159,47 @@ def test_gyro_orbit_closed_form():
     assert abs(s.tallies()["W_field"]) < 1e-12 * s.weight * eps
 
 
+def test_boris_electric_kick_is_exact():
+    """With B = 0 the two half kicks add to the whole impulse: u gains
+    q E dt / (m_e c) with q = -e, so the electron is pushed against E."""
+    rng = np.random.default_rng(5)
+    dt = 0.5e-15
+    for _ in range(20):
+        u = rng.normal(size=3) * 3.0
+        E = rng.normal(size=3) * 1e12
+        du = O.boris(u, E, [0.0, 0.0, 0.0], dt) - u
+        expect = -sc.e * E * dt / (sc.m_e * sc.c)
+        # to the CODATA 2018 vs 2022 m_e and the rounding of u + du
+        assert np.max(np.abs(du - expect)) <= 1e-8 * np.max(np.abs(expect)) + 1e-15 * np.max(np.abs(u))
+
+
+def test_boris_e_cross_b_drift():
+    """In crossed uniform fields (E = E_y y, B = B_z z, E_y / B_z = 0.01 c) an
+    electron starting at rest drifts along E x B (+x, whatever the charge's
+    sign) at E_y / B_z, with no mean motion along E; the position is advanced
+    with v = u c / gamma after each push, as the step does."""
+    Bz = 1000.0
+    vd = 0.01 * sc.c
+    Ey = vd * Bz
+    omega = sc.e * Bz / sc.m_e
+    dt = 2.0 * math.pi / omega / 50.0
+    n = 50_000
+    u = np.zeros(3)
+    x = y = 0.0
+    xs, ys = np.empty(n), np.empty(n)
+    for i in range(n):
+        u = O.boris(u, [0.0, Ey, 0.0], [0.0, 0.0, Bz], dt)
+        g = math.sqrt(1.0 + float(u @ u))
+        x += u[0] / g * sc.c * dt
+        y += u[1] / g * sc.c * dt
+        xs[i], ys[i] = x, y
+    t = np.arange(1, n + 1) * dt
+    assert np.polyfit(t, xs, 1)[0] == pytest.approx(vd, rel=1e-4)
+    assert abs(np.polyfit(t, ys, 1)[0]) < 1e-4 * vd
+    # the gyration about the drifting centre stays bounded (|y| <= 2 r_L)
+    assert np.max(np.abs(ys)) < 2.01 * vd / omega
+
+
 def test_gather_is_exact_for_linear_fields():
     tgt = W.target(n=(8, 8, 8))
     s = O.OracleSim(tgt, W.laser(tgt, n_macro=0), quiet_run())

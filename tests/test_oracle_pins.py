@@ -246,6 +246,86 @@ def test_deposit_conserves_total_current():
         assert s.grid(comp).sum() == pytest.approx(expect, rel=1e-10)
 
 
+def test_gather_is_exact_for_fields_linear_in_every_coordinate():
+    """Each component lives on its own Yee lattice (E_x at ((i+1/2), j, k) dx
+    and so on): a field that is linear in x, y and z (with its xy, yz, zx and
+    xyz products), written at the component's own node positions, is
+    interpolated exactly at any interior point.  A component gathered on the
+    wrong staggering along any axis misses by half a cell's slope."""
+    tgt = W.target(n=(8, 8, 8))
+    s = O.OracleSim(tgt, W.laser(tgt, n_macro=0), quiet_run())
+    n1, dx = 9, tgt["dx"]
+    i, j, k = np.meshgrid(np.arange(n1), np.arange(n1), np.arange(n1), indexing="ij")
+    i, j, k = [a.transpose(2, 1, 0).ravel().astype(float) for a in (i, j, k)]  # x fastest
+    rng = np.random.default_rng(11)
+    coef = {c: rng.normal(size=8) * np.array([1e10, 1e9, 1e9, 1e9, 1e8, 1e8, 1e8, 1e7])
+            for c in "xyz"}
+
+    def field(c, X, Y, Z):  # X, Y, Z in cells
+        q = coef[c]
+        return (q[0] + q[1] * X + q[2] * Y + q[3] * Z + q[4] * X * Y + q[5] * Y * Z
+                + q[6] * Z * X + q[7] * X * Y * Z)
+
+    s.set_grid("Ex", field("x", i + 0.5, j, k))
+    s.set_grid("Ey", field("y", i, j + 0.5, k))
+    s.set_grid("Ez", field("z", i, j, k + 0.5))
+    npart = 64
+    pos = rng.uniform(0.6, 7.4, size=(3, npart))
+    u0 = 4.0  # moving, so that the 1 keV tracking cut keeps it; B = 0: the kick alone
+    s.set_particles({"x": pos[0] * dx, "y": pos[1] * dx, "z": pos[2] * dx,
+                     "ux": np.full(npart, u0), "uy": np.zeros(npart), "uz": np.zeros(npart),
+                     "tau": np.full(npart, 50.0), "id": np.arange(npart, dtype=np.uint32)})
+    s.step(1)
+    p = s.particles()
+    assert len(p["id"]) == npart
+    order = np.argsort(p["id"])
+    kick = -sc.e * s.run["dt"] / (sc.m_e * sc.c)
+    for c, key, base in (("x", "ux", u0), ("y", "uy", 0.0), ("z", "uz", 0.0)):
+        got = (p[key][order] - base) / kick
+        want = field(c, *pos)
+        assert np.max(np.abs(got - want)) <= 1e-8 * np.max(np.abs(want)), c
+
+
+def test_deposit_is_the_transpose_of_the_gather():
+    """CIC deposit and gather share their weights: the deposit of one electron
+    at x^{n+1}, read as weights over the nodes of each component's lattice,
+    averages any field G on that lattice to the gather of G at x^{n+1}
+    (sum_n G_n J_n / sum_n J_n = G(x^{n+1})).  With the gather pinned above,
+    this fixes every deposit weight, not only their sum."""
+    tgt = W.target(n=(8, 8, 8))
+    dx = tgt["dx"]
+    rng = np.random.default_rng(12)
+    for _ in range(8):
+        a = O.OracleSim(tgt, W.laser(tgt, n_macro=0), quiet_run())
+        x0 = rng.uniform(1.0, 7.0, size=3) * dx
+        u0 = rng.normal(size=3) * 2.0
+        a.set_particles({"x": [x0[0]], "y": [x0[1]], "z": [x0[2]], "ux": [u0[0]], "uy": [u0[1]],
+                         "uz": [u0[2]], "tau": [50.0], "id": np.array([7], np.uint32)})
+        a.step(1)
+        p1 = a.particles()
+        J = {c: a.grid("j" + c) for c in "xyz"}
+        # fields of ~1e10 V/m, so that the kick stands well above the rounding of u = 4
+        G = {c: rng.normal(size=J[c].shape) * 1e10 for c in "xyz"}
+        # the oracle's gather of G at x^{n+1}: the kick of an electron placed
+        # there (moving, so that the 1 keV tracking cut keeps it; B = 0)
+        b = O.OracleSim(tgt, W.laser(tgt, n_macro=0), quiet_run())
+        for c in "xyz":
+            b.set_grid("E" + c, G[c])
+        b.set_particles({"x": p1["x"], "y": p1["y"], "z": p1["z"], "ux": [4.0], "uy": [0.0],
+                         "uz": [0.0], "tau": [50.0], "id": np.array([7], np.uint32)})
+        b.step(1)
+        p2 = b.particles()
+        assert len(p2["id"]) == 1
+        kick = -sc.e * b.run["dt"] / (sc.m_e * sc.c)
+        du = {"x": p2["ux"][0] - 4.0, "y": p2["uy"][0], "z": p2["uz"][0]}
+        for c in "xyz":
+            if abs(J[c].sum()) < 1e-12 * max(abs(J[k].sum()) for k in "xyz"):
+                continue
+            want = du[c] / kick
+            # to the CODATA 2018 vs 2022 m_e in the kick
+            assert np.sum(G[c] * J[c]) / np.sum(J[c]) == pytest.approx(want, rel=1e-8), c
+
+
 # ---------------------------------------------------------------- fields
 def test_ohm_law_in_uniform_medium():
     """Uniform eta, B = 0, uniform j_h: E = -eta j_h on every interior edge, zero

@@ -286,6 +286,57 @@ def test_gather_is_exact_for_fields_linear_in_every_coordinate():
         assert np.max(np.abs(got - want)) <= 1e-8 * np.max(np.abs(want)), c
 
 
+def test_magnetic_gather_is_exact_for_fields_linear_in_every_coordinate():
+    """B lives on the faces (B_x at (i, j+1/2, k+1/2) dx and so on).  A B field
+    linear in every coordinate, written at each component's own positions, is
+    recovered from the rotation of the push: the Boris rotation obeys
+    u+ - u- = (u+ + u-) x t with t = q B dt / (2 m_e gamma), so electrons
+    moving along x, y and z through one point give the three components."""
+    tgt = W.target(n=(8, 8, 8))
+    n1, dx = 9, tgt["dx"]
+    i, j, k = np.meshgrid(np.arange(n1), np.arange(n1), np.arange(n1), indexing="ij")
+    i, j, k = [a.transpose(2, 1, 0).ravel().astype(float) for a in (i, j, k)]  # x fastest
+    rng = np.random.default_rng(13)
+    coef = {c: rng.normal(size=8) * np.array([100.0, 10, 10, 10, 1, 1, 1, 0.1]) for c in "xyz"}
+
+    def field(c, X, Y, Z):  # X, Y, Z in cells
+        q = coef[c]
+        return (q[0] + q[1] * X + q[2] * Y + q[3] * Z + q[4] * X * Y + q[5] * Y * Z
+                + q[6] * Z * X + q[7] * X * Y * Z)
+
+    s = O.OracleSim(tgt, W.laser(tgt, n_macro=0), quiet_run())
+    s.set_grid("Bx", field("x", i, j + 0.5, k + 0.5))
+    s.set_grid("By", field("y", i + 0.5, j, k + 0.5))
+    s.set_grid("Bz", field("z", i + 0.5, j + 0.5, k))
+    npos, u0 = 16, 4.0
+    pos = np.repeat(rng.uniform(0.6, 7.4, size=(3, npos)), 3, axis=1)  # three electrons a point
+    u = np.tile(np.eye(3), npos) * u0
+    s.set_particles({"x": pos[0] * dx, "y": pos[1] * dx, "z": pos[2] * dx, "ux": u[0],
+                     "uy": u[1], "uz": u[2], "tau": np.full(3 * npos, 50.0),
+                     "id": np.arange(3 * npos, dtype=np.uint32)})
+    s.step(1)
+    p = s.particles()
+    assert len(p["id"]) == 3 * npos
+    order = np.argsort(p["id"])
+    up = np.stack([p["ux"][order], p["uy"][order], p["uz"][order]])
+    d, m = up - u, up + u
+    gam = math.sqrt(1.0 + u0 * u0)
+    to_B = 2.0 * sc.m_e * gam / (-sc.e * s.run["dt"])
+
+    def cross_matrix(v):  # M t = v x t
+        return np.array([[0.0, -v[2], v[1]], [v[2], 0.0, -v[0]], [-v[1], v[0], 0.0]])
+
+    for q in range(npos):
+        e3 = range(3 * q, 3 * q + 3)  # the electrons moving along x, y, z
+        M = np.vstack([cross_matrix(m[:, e]) for e in e3])
+        rhs = np.concatenate([d[:, e] for e in e3])
+        t, res, rank, _ = np.linalg.lstsq(M, rhs, rcond=None)
+        assert rank == 3 and np.max(np.abs(M @ t - rhs)) <= 1e-12 * np.max(np.abs(rhs))
+        want = np.array([field(c, *pos[:, 3 * q]) for c in "xyz"])
+        # to the CODATA 2018 vs 2022 m_e
+        assert np.max(np.abs(to_B * t - want)) <= 1e-7 * np.max(np.abs(want)), q
+
+
 def test_deposit_is_the_transpose_of_the_gather():
     """CIC deposit and gather share their weights: the deposit of one electron
     at x^{n+1}, read as weights over the nodes of each component's lattice,

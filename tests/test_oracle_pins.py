@@ -407,6 +407,40 @@ def test_ohm_law_in_uniform_medium():
     assert np.max(np.abs(By[1:nz - 1, 1:ny, 1:nx - 1])) < 1e-14 * scale
 
 
+def test_ohmic_heating_uses_the_cell_centred_current():
+    """Eq. (A4)'s Ohmic term takes the current at the cell centre, the mean of
+    the four edges of each component around it: a current linear across its
+    own direction (j_x = a + b y + c z on the x edges, and so on) gives
+    eta |j(centre)|^2 dt per unit volume in every cell, which the Ohmic tally
+    sums and each cell's temperature rise follows."""
+    nx, ny, nz = 5, 6, 7
+    tgt = W.target(n=(nx, ny, nz))
+    run = W.run(physics=O.ORC_FIELDS | O.ORC_HEATING)
+    s = O.OracleSim(tgt, W.laser(tgt, n_macro=0), run)
+    eta = s.grid("eta")[0]
+    assert np.all(s.grid("eta") == eta)
+    i, j, k = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    i, j, k = [a.transpose(2, 1, 0).ravel().astype(float) for a in (i, j, k)]  # x fastest
+    q = {"x": (1.0e15, 3.0e14, -2.0e14), "y": (-2.0e15, 1.0e14, 4.0e14), "z": (5.0e14, -3.0e14, 2.0e14)}
+    s.set_grid("jx", q["x"][0] + q["x"][1] * j + q["x"][2] * k)
+    s.set_grid("jy", q["y"][0] + q["y"][1] * i + q["y"][2] * k)
+    s.set_grid("jz", q["z"][0] + q["z"][1] * i + q["z"][2] * j)
+    T0 = s.grid("T").copy()
+    s.fields()
+    ci, cj, ck = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5, np.arange(nz) + 0.5, indexing="ij")
+    ci, cj, ck = [a.transpose(2, 1, 0).ravel() for a in (ci, cj, ck)]
+    jc2 = ((q["x"][0] + q["x"][1] * cj + q["x"][2] * ck) ** 2
+           + (q["y"][0] + q["y"][1] * ci + q["y"][2] * ck) ** 2
+           + (q["z"][0] + q["z"][1] * ci + q["z"][2] * cj) ** 2)
+    rho = eta * jc2 * run["dt"]
+    V = tgt["dx"] ** 3
+    assert s.tallies()["E_ohmic_grid"] == pytest.approx(np.sum(rho) * V, rel=1e-12)
+    dT = s.grid("T") - T0
+    assert np.all(dT > 0)
+    r = dT / rho  # 1/(Z n_i C k_B) at T0, the same in every cell (dT << T0)
+    assert np.max(np.abs(r / r.mean() - 1.0)) < 1e-6
+
+
 def test_magnetic_diffusion_eigenmode():
     """With j_h = 0 and uniform eta, a Neumann cosine mode of Bz(x) decays per step
     by exactly 1 - (eta dt/mu0)(4/dx^2) sin^2(m pi / 2 nx) (the discrete Laplacian

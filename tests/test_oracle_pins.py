@@ -407,6 +407,38 @@ def test_ohm_law_in_uniform_medium():
     assert np.max(np.abs(By[1:nz - 1, 1:ny, 1:nx - 1])) < 1e-14 * scale
 
 
+def test_edge_resistivity_is_the_mean_of_the_four_cells_around_the_edge():
+    """E on an edge takes eta at the edge, the mean of the four cells that
+    share it (reading of the Yee layout): with eta linear in the cell indices
+    and a uniform j_h (B = 0), E_x on the edge (i + 1/2, j, k) is
+    -eta(i + 1/2, j, k) j_x with eta evaluated at the edge's own position, and
+    likewise for E_y and E_z."""
+    nx, ny, nz = 5, 6, 7
+    tgt = W.target(n=(nx, ny, nz))
+    s = O.OracleSim(tgt, W.laser(tgt, n_macro=0), W.run(physics=O.ORC_FIELDS))
+    a0, bi, bj, bk = 1.0e-6, 2.0e-8, -3.0e-8, 5.0e-8
+
+    def eta(X, Y, Z):  # X, Y, Z: cell-centre coordinates in cells
+        return a0 + bi * X + bj * Y + bk * Z
+
+    ci, cj, ck = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5, np.arange(nz) + 0.5, indexing="ij")
+    ci, cj, ck = [a.transpose(2, 1, 0).ravel() for a in (ci, cj, ck)]  # x fastest
+    s.set_grid("eta", eta(ci, cj, ck))
+    jv = (1.3e16, -2.1e16, 0.7e16)
+    for comp, val in zip(("jx", "jy", "jz"), jv):
+        s.set_grid(comp, np.full(s.grid(comp).size, val))
+    s.fields()
+    shp = (nz + 1, ny + 1, nx + 1)
+    K, J, I = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    Ex, Ey, Ez = (s.grid(c).reshape(shp) for c in ("Ex", "Ey", "Ez"))
+    want_x = -eta(I + 0.5, J, K) * jv[0]
+    want_y = -eta(I, J + 0.5, K) * jv[1]
+    want_z = -eta(I, J, K + 0.5) * jv[2]
+    assert np.allclose(Ex[1:nz, 1:ny, :nx], want_x[1:nz, 1:ny, :nx], rtol=1e-13, atol=0)
+    assert np.allclose(Ey[1:nz, :ny, 1:nx], want_y[1:nz, :ny, 1:nx], rtol=1e-13, atol=0)
+    assert np.allclose(Ez[:nz, 1:ny, 1:nx], want_z[:nz, 1:ny, 1:nx], rtol=1e-13, atol=0)
+
+
 def test_ohmic_heating_uses_the_cell_centred_current():
     """Eq. (A4)'s Ohmic term takes the current at the cell centre, the mean of
     the four edges of each component around it: a current linear across its

@@ -101,9 +101,10 @@ std::vector<InjCell> injection_cells(const hpic_target_desc &t, const hpic_laser
 // (it is launched as one persistent wave of sm_count times this many blocks)
 // and threads per block (one deposit stage per warp).  FP32: three blocks of
 // 384 threads, 36 warps at 56 registers with few spills; a block's twelve
-// warps take consecutive slots, so their gathers share L1 lines.  (Five
-// blocks of 256 at 48 registers spilled 84 B and were 3.4 % slower, 288 x 4
-// 2.2 %, 192 x 6 0.5 %; 576 x 2 was level.)  FP64: two blocks of 256.
+// warps take consecutive slots, so their gathers share L1 lines.  (Against
+// it: five blocks of 256 at 48 registers, 84 B of spills, 3.5 % slower; six
+// of 192 at 56 registers 3.2 %; four of 288 1.2 %; two of 576 level.)  FP64:
+// two blocks of 256.
 template <typename R>
 constexpr int push_blocks_per_sm() { return sizeof(R) == 4 ? 3 : 2; }
 template <typename R>
